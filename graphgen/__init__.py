@@ -1,0 +1,134 @@
+"""Seeded synthetic community-labelled graphs.
+
+The one input module shared by the CPU oracle and the GPU path.  It draws
+graphs shaped like the paper's social-network workloads (Sec. VI, the small and
+large dataset tables): a planted-partition SBM and a degree-corrected SBM with
+power-law community sizes and degrees.  It contains none of the scoring
+arithmetic.  The C source is ``rsgen.c``; it is compiled on first use with gcc.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rsgen.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "librsgen.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile rsgen.c into graphgen/_build/librsgen.so (idempotent)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P, I64, I32, U64, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
+        lib.rsgen_new.restype = P
+        lib.rsgen_free.argtypes = [P]
+        lib.rsgen_n.restype = I64; lib.rsgen_n.argtypes = [P]
+        lib.rsgen_nnz.restype = I64; lib.rsgen_nnz.argtypes = [P]
+        lib.rsgen_k.restype = I32; lib.rsgen_k.argtypes = [P]
+        lib.rsgen_err.restype = ctypes.c_char_p; lib.rsgen_err.argtypes = [P]
+        lib.rsgen_copy.argtypes = [P, P, P, P]
+        lib.rsgen_sbm.restype = ctypes.c_int
+        lib.rsgen_sbm.argtypes = [P, I32, I32, D, D, U64]
+        lib.rsgen_dcsbm.restype = ctypes.c_int
+        lib.rsgen_dcsbm.argtypes = [P, I64, I32, D, D, I32, I32, D, U64]
+        _lib = lib
+    return _lib
+
+
+@dataclass
+class Graph:
+    """Undirected graph as symmetric CSR with community labels."""
+    n: int
+    k: int
+    offsets: np.ndarray  # int64[n+1]
+    cols: np.ndarray     # int32[nnz], each row sorted ascending
+    labels: np.ndarray   # int32[n], values in [0, k)
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.cols.shape[0])
+
+    @property
+    def m(self) -> int:
+        """Undirected edge count."""
+        return self.nnz // 2
+
+    def degrees(self) -> np.ndarray:
+        return np.diff(self.offsets)
+
+
+def _run(fn, *args, name=""):
+    lib = _load()
+    h = lib.rsgen_new()
+    try:
+        if fn(h, *args) != 0:
+            raise ValueError(lib.rsgen_err(h).decode())
+        n, nnz, k = lib.rsgen_n(h), lib.rsgen_nnz(h), lib.rsgen_k(h)
+        off = np.empty(n + 1, np.int64)
+        cols = np.empty(max(nnz, 1), np.int32)
+        lab = np.empty(n, np.int32)
+        lib.rsgen_copy(h, off.ctypes.data, cols.ctypes.data, lab.ctypes.data)
+        return Graph(n=n, k=k, offsets=off, cols=cols[:nnz].copy(), labels=lab, name=name)
+    finally:
+        lib.rsgen_free(h)
+
+
+def sbm(nblocks: int, block_size: int, p_in: float, p_out: float, seed: int, name: str = "") -> Graph:
+    """Planted-partition SBM: equal blocks, independent Bernoulli edges over all pairs."""
+    return _run(_load().rsgen_sbm, nblocks, block_size, p_in, p_out, seed, name=name or "sbm")
+
+
+def dcsbm(n: int, k: int, size_min: float, gamma: float, dmin: int, dmax: int, mu: float,
+          seed: int, name: str = "") -> Graph:
+    """Degree-corrected SBM (configuration model) with rank-size community sizes."""
+    return _run(_load().rsgen_dcsbm, n, k, size_min, gamma, dmin, dmax, mu, seed,
+                name=name or "dcsbm")
+
+
+# ---- named workloads -------------------------------------------------------
+
+def sbm_2000(seed: int = 1) -> Graph:
+    """2,000 nodes in 20 planted blocks of 100; mean intra degree 8, mean inter degree 1."""
+    return sbm(20, 100, 8.0 / 99.0, 1.0 / 1900.0, seed, name="sbm-2k-20x100")
+
+
+def dcsbm_1m(seed: int = 2) -> Graph:
+    """1M nodes, 1,000 power-law communities (exponent 2, min 50), degrees power law 2.5 on
+    [8, 5000], mu 0.2: about 10.3M undirected edges (min degree 8 rather than 2 gives ~10M)."""
+    return dcsbm(1_000_000, 1000, 50.0, 2.5, 8, 5000, 0.2, seed, name="dcsbm-1m-k1000")
+
+
+def dcsbm_1m_dmin2(seed: int = 2) -> Graph:
+    """As dcsbm_1m with the literal minimum degree 2 (about 2.3M edges)."""
+    return dcsbm(1_000_000, 1000, 50.0, 2.5, 2, 5000, 0.2, seed, name="dcsbm-1m-k1000-dmin2")
+
+
+def dcsbm_8m(seed: int = 3) -> Graph:
+    """8M nodes, 50,000 communities (sizes ~1/r), degrees power law 2.1 on [4, 100000], mu 0.1."""
+    return dcsbm(8_000_000, 50_000, 1.0, 2.1, 4, 100_000, 0.1, seed, name="dcsbm-8m-k50000")
+
+
+def dcsbm_small(n: int, seed: int, dmax: int = 1000, mu: float = 0.2, gamma: float = 2.5,
+                dmin: int = 7) -> Graph:
+    """Scaled DC-SBM with the 1M workload's shape: k = n / 100 communities (min size 50)."""
+    k = max(2, n // 100)
+    return dcsbm(n, k, 50.0 if n >= 100 * 50 else 1.0, gamma, dmin, dmax, mu, seed,
+                 name="dcsbm-%d" % n)
