@@ -1,0 +1,152 @@
+/*
+ * rs.h -- C ABI of the GB300 Robust Spanning Index library (librs.so).
+ *
+ * Robust spanners (arXiv 2508.01485): every node u of an undirected graph
+ * G = (V, E) whose nodes carry non-overlapping community labels C(u) gets the
+ * Robust Spanning Index
+ *
+ *   R(u) = 1/(d(u)(d(u)-1)) * sum_{w in N(u), v in N(w) : 1(u,w,v)}
+ *          (w_v(u) w_w(v) w_w(u))^(1/3)                   (Sec. III-B, Eq. RSI)
+ *
+ * with weights w_v(u) = H(L(u,v)) |L(u,v)| from the entropy of v's neighbour
+ * communities other than C(u) (Eq. cont, entropy, weight), normalised by the
+ * largest weight w_max (Alg. 1 Step 2), and the triad indicator 1(u,w,v)
+ * (Sec. III-A: Type-I closed triads across three communities, Type-II open
+ * triads closed by an "augmented edge" inside C(u)).  The library computes
+ * the per-node community counts (the paper's interaction_matrix, Sec. V-A),
+ * the weights, all scores and a top-K ranking (Alg. 1 Step 4) on one GPU.
+ *
+ * Conventions shared by every call:
+ *  - All device work is enqueued on `stream` (a cudaStream_t passed as void*;
+ *    NULL is the legacy default stream).  Calls return once the work is
+ *    enqueued, except where a host out-parameter must be filled, which
+ *    synchronises `stream`.
+ *  - Inputs are copied; the caller may free or reuse them once the call's
+ *    stream work has completed.  Outputs are caller-allocated.
+ *  - Out-parameters are written only when the call returns RS_OK.
+ *  - On failure the call returns a non-zero rs_status and rs_last_error()
+ *    gives a message (thread-local, valid until the next call on the thread).
+ *  - The library owns the device memory behind an rs_graph.  Calls on one
+ *    rs_graph must not run concurrently (they share its workspace).
+ *  - Node ids are 0..n-1 (int32); community labels are 0..k-1 (int32).
+ */
+#ifndef RS_H_
+#define RS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rs_graph rs_graph;
+
+typedef enum {
+    RS_OK = 0,
+    RS_EINVAL = 1,    /* invalid argument or invalid graph */
+    RS_ENOMEM = 2,    /* device or host allocation failed */
+    RS_ECUDA = 3,     /* a CUDA call failed (message holds the CUDA error) */
+    RS_ETIMEOUT = 4,  /* a bounded device wait gave up */
+    RS_EBUDGET = 5    /* a request does not fit the memory budget */
+} rs_status;
+
+/* rs_build_graph flags */
+#define RS_VALIDATE 1u  /* check the CSR on the device (see rs_build_graph) */
+
+/*
+ * rs_build_graph -- load a community-labelled graph (Sec. II; CSR of Sec. V-A).
+ *
+ *   n, nnz          number of nodes and of CSR entries (2 x undirected edges);
+ *                   0 <= n < 2^31, 0 <= nnz < 2^40, max degree < 2^24.
+ *   row_offsets     n+1 offsets, int64 if offsets_are_i64 else int32;
+ *                   row_offsets[0] = 0, row_offsets[n] = nnz.
+ *   cols            nnz int32 neighbour ids; row v is cols[off[v] .. off[v+1]).
+ *   labels          n int32 community ids in [0, num_communities).
+ *   num_communities k >= 1.
+ *   inputs_on_device  non-zero: the three arrays are device pointers, else
+ *                   host pointers (copied with cudaMemcpyAsync on `stream`).
+ *   flags           RS_VALIDATE: verify on the device that the graph is simple
+ *                   and undirected -- offsets non-decreasing, ids in range,
+ *                   every row strictly ascending (sorted, no duplicates), no
+ *                   self-loops, every edge present in both directions -- and
+ *                   that labels lie in [0, k).  Returns RS_EINVAL otherwise.
+ *                   Without the flag the input must already satisfy this.
+ *   out             receives the new graph (free with rs_free_graph).
+ * Synchronises `stream` (the degree profile is read back to size workspaces).
+ */
+rs_status rs_build_graph(int64_t n, int64_t nnz, const void *row_offsets, int offsets_are_i64,
+                         const int32_t *cols, const int32_t *labels, int32_t num_communities,
+                         int inputs_on_device, uint32_t flags, void *stream, rs_graph **out);
+
+/*
+ * rs_score -- Robust Spanning Index of every node (Alg. 1 Steps 1-3, Eq. RSI).
+ *
+ *   scores          device buffer of n doubles, written with R(u) in node-id
+ *                   order.  R(u) = 0 when d(u) < 2 or w_max = 0.
+ *   omega_max_out   optional host pointer: receives w_max, the largest
+ *                   un-normalised weight w_v(c) over all nodes v and all
+ *                   communities c in [0, k) (including communities absent from
+ *                   N(v)).  Passing it synchronises `stream`.
+ * Scores agree with the fp64 definition to ~1e-13 relative; they are
+ * bit-identical from run to run (all sums are exact fixed-point).
+ */
+rs_status rs_score(rs_graph *g, double *scores, double *omega_max_out, void *stream);
+
+/*
+ * rs_get_interaction -- the per-node community counts f_v(c) (Sec. V-A,
+ * interaction_matrix, stored sparsely).
+ *
+ *   t_out     host: number of (node, community) entries with f_v(c) > 0.
+ *   row_ptr   device int64[n+1] or NULL; comm / count device int32[t] or NULL.
+ * Rows are in node order; within a row, communities ascend.  Call with NULL
+ * arrays to learn t.  Synchronises `stream`.
+ */
+rs_status rs_get_interaction(rs_graph *g, int64_t *t_out, int64_t *row_ptr, int32_t *comm,
+                             int32_t *count, void *stream);
+
+/*
+ * rs_topk -- the K best nodes by (score descending, node id ascending)
+ * (Alg. 1 Step 4).
+ *
+ *   scores      device double[n] (normally rs_score's output); every value
+ *               must be >= 0 (not NaN).
+ *   k           1 <= k <= min(n, 16384).
+ *   ids_out     device int32[k]; scores_out device double[k] (may be NULL).
+ */
+rs_status rs_topk(rs_graph *g, const double *scores, int32_t k, int32_t *ids_out,
+                  double *scores_out, void *stream);
+
+/*
+ * rs_apply_removals -- delete nodes (every incident edge) and undirected edges
+ * (both directions) from the resident graph (the perturbations of Sec. VI-B).
+ *
+ *   nodes           host int32[n_nodes] node ids.
+ *   edge_src/dst    host int32[n_edges] endpoint pairs.
+ *   applied_out     optional host pointer: number of effective removals.
+ * Node removals are applied first, then edge removals.  Removing a node that
+ * is already removed, or an edge that is absent (or already removed), is a
+ * no-op and is not counted.  Any id outside [0, n) makes the call fail with
+ * RS_EINVAL before anything is changed.  Node ids keep their meaning; a
+ * removed node has degree 0 and scores 0.  Synchronises `stream` when
+ * applied_out is given.
+ */
+rs_status rs_apply_removals(rs_graph *g, const int32_t *nodes, int64_t n_nodes,
+                            const int32_t *edge_src, const int32_t *edge_dst, int64_t n_edges,
+                            int64_t *applied_out, void *stream);
+
+/* rs_clone_graph -- deep copy of a graph (its current edges and removals). */
+rs_status rs_clone_graph(const rs_graph *g, rs_graph **out, void *stream);
+
+/* rs_graph_info -- sizes of a graph (any pointer may be NULL). */
+rs_status rs_graph_info(const rs_graph *g, int64_t *n, int64_t *nnz, int32_t *k, int32_t *max_degree);
+
+/* rs_free_graph -- release a graph and its device memory (NULL is a no-op). */
+void rs_free_graph(rs_graph *g);
+
+/* rs_last_error -- message of the last failed call on this thread ("" if none). */
+const char *rs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RS_H_ */

@@ -1,0 +1,181 @@
+"""ctypes binding of librs (include/rs.h).  Argument marshalling only: every
+step of the scoring path runs in the library's CUDA kernels.  PyTorch supplies
+device memory and the current CUDA stream.
+
+The library must be built (``__graft_entry__.build()``); importing this module
+without it raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ETIMEOUT, RS_EBUDGET = range(6)
+RS_VALIDATE = 1
+
+_lib = None
+
+
+class RSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("rs status %d: %s" % (status, msg))
+        self.status = status
+
+
+def lib():
+    """Load librs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("librs.so is not built (%s); run __graft_entry__.build()" % path)
+        L = ctypes.CDLL(path)
+        P, I64, I32, U32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+        I = ctypes.c_int
+        L.rs_build_graph.restype = I
+        L.rs_build_graph.argtypes = [I64, I64, P, I, P, P, I32, I, U32, P, ctypes.POINTER(P)]
+        L.rs_score.restype = I
+        L.rs_score.argtypes = [P, P, P, P]
+        L.rs_get_interaction.restype = I
+        L.rs_get_interaction.argtypes = [P, ctypes.POINTER(I64), P, P, P, P]
+        L.rs_topk.restype = I
+        L.rs_topk.argtypes = [P, P, I32, P, P, P]
+        L.rs_apply_removals.restype = I
+        L.rs_apply_removals.argtypes = [P, P, I64, P, P, I64, ctypes.POINTER(I64), P]
+        L.rs_clone_graph.restype = I
+        L.rs_clone_graph.argtypes = [P, ctypes.POINTER(P), P]
+        L.rs_graph_info.restype = I
+        L.rs_graph_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32),
+                                    ctypes.POINTER(I32)]
+        L.rs_free_graph.restype = None
+        L.rs_free_graph.argtypes = [P]
+        L.rs_last_error.restype = ctypes.c_char_p
+        L.rs_last_error.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != RS_OK:
+        raise RSError(status, lib().rs_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Graph:
+    """A community-labelled graph resident on the GPU (owns an rs_graph)."""
+
+    def __init__(self, handle, n, k):
+        self._h = handle
+        self.n = int(n)
+        self.k = int(k)
+
+    @classmethod
+    def build(cls, offsets, cols, labels, k, validate=True, stream=None):
+        """rs_build_graph from numpy arrays (host) or torch CUDA tensors (device).
+
+        offsets: int64 or int32 [n+1]; cols: int32 [nnz]; labels: int32 [n].
+        """
+        import torch
+        on_dev = isinstance(offsets, torch.Tensor) and offsets.is_cuda
+        if on_dev:
+            off, col, lab = offsets.contiguous(), cols.contiguous(), labels.contiguous()
+            assert col.dtype == torch.int32 and lab.dtype == torch.int32
+            is64 = off.dtype == torch.int64
+            p_off, p_col, p_lab = off.data_ptr(), col.data_ptr(), lab.data_ptr()
+            n, nnz = off.numel() - 1, col.numel()
+        else:
+            off = np.ascontiguousarray(offsets)
+            is64 = off.dtype == np.int64
+            if not is64:
+                off = np.ascontiguousarray(off, dtype=np.int32)
+            col = np.ascontiguousarray(cols, dtype=np.int32)
+            lab = np.ascontiguousarray(labels, dtype=np.int32)
+            p_off, p_col, p_lab = off.ctypes.data, col.ctypes.data, lab.ctypes.data
+            n, nnz = off.shape[0] - 1, col.shape[0]
+        h = ctypes.c_void_p()
+        s = _stream(stream)
+        _check(lib().rs_build_graph(n, nnz, ctypes.c_void_p(p_off), 1 if is64 else 0,
+                                    ctypes.c_void_p(p_col if nnz else None), ctypes.c_void_p(p_lab if n else None),
+                                    int(k), 1 if on_dev else 0, RS_VALIDATE if validate else 0, s,
+                                    ctypes.byref(h)))
+        return cls(h, n, k)
+
+    @classmethod
+    def from_generated(cls, g, validate=True, stream=None):
+        return cls.build(g.offsets, g.cols, g.labels, g.k, validate=validate, stream=stream)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rs_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        n, nnz, k, dmax = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().rs_graph_info(self._h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(k), ctypes.byref(dmax)))
+        return {"n": n.value, "nnz_capacity": nnz.value, "k": k.value, "max_degree": dmax.value}
+
+    def score(self, out=None, stream=None, want_omega_max=False):
+        """rs_score: R(u) for every node as a float64 CUDA tensor (and w_max if asked)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        wm = ctypes.c_double(0.0)
+        _check(lib().rs_score(self._h, _ptr(out), ctypes.byref(wm) if want_omega_max else None, _stream(stream)))
+        return (out, wm.value) if want_omega_max else out
+
+    def topk(self, scores, k, stream=None):
+        """rs_topk: (ids int32[k], scores float64[k]) ordered by (score desc, id asc)."""
+        import torch
+        ids = torch.empty(k, dtype=torch.int32, device="cuda")
+        vals = torch.empty(k, dtype=torch.float64, device="cuda")
+        _check(lib().rs_topk(self._h, _ptr(scores), int(k), _ptr(ids), _ptr(vals), _stream(stream)))
+        return ids, vals
+
+    def interaction(self, stream=None):
+        """rs_get_interaction: (row_ptr int64[n+1], comm int32[t], count int32[t]) CUDA tensors."""
+        import torch
+        t = ctypes.c_int64(0)
+        s = _stream(stream)
+        _check(lib().rs_get_interaction(self._h, ctypes.byref(t), None, None, None, s))
+        rp = torch.empty(self.n + 1, dtype=torch.int64, device="cuda")
+        comm = torch.empty(max(t.value, 1), dtype=torch.int32, device="cuda")
+        cnt = torch.empty(max(t.value, 1), dtype=torch.int32, device="cuda")
+        _check(lib().rs_get_interaction(self._h, ctypes.byref(t), _ptr(rp), _ptr(comm), _ptr(cnt), s))
+        return rp, comm[: t.value], cnt[: t.value]
+
+    def apply_removals(self, nodes=(), edges=(), stream=None):
+        """rs_apply_removals from host lists; returns the number of effective removals."""
+        nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.int32).reshape(-1))
+        e = np.asarray(edges, dtype=np.int32).reshape(-1, 2) if len(edges) else np.zeros((0, 2), np.int32)
+        es, ed = np.ascontiguousarray(e[:, 0]), np.ascontiguousarray(e[:, 1])
+        applied = ctypes.c_int64(0)
+        _check(lib().rs_apply_removals(self._h, ctypes.c_void_p(nodes.ctypes.data if nodes.size else None),
+                                       nodes.size, ctypes.c_void_p(es.ctypes.data if es.size else None),
+                                       ctypes.c_void_p(ed.ctypes.data if ed.size else None), es.size,
+                                       ctypes.byref(applied), _stream(stream)))
+        return applied.value
+
+    def clone(self, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().rs_clone_graph(self._h, ctypes.byref(h), _stream(stream)))
+        return Graph(h, self.n, self.k)

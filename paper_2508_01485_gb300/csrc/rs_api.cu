@@ -1,0 +1,826 @@
+// rs_api.cu -- C ABI of librs: graph build / validation / removal / cloning,
+// row classification, constant tables, scans and the interaction table.
+// Scoring kernels live in rs_score.cu, the top-K ranking in rs_topk.cu.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rs.h"
+#include "rs_internal.cuh"
+
+using namespace rs;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string t_err;
+
+int rs::fail(int status, const std::string &msg) {
+    t_err = msg;
+    return status;
+}
+int rs::cuda_fail(cudaError_t e, const char *where) {
+    cudaGetLastError();  // clear a sticky launch error from the per-thread slot
+    t_err = std::string("CUDA error: ") + cudaGetErrorString(e) + " (" + where + ")";
+    return e == cudaErrorMemoryAllocation ? RS_ENOMEM : RS_ECUDA;
+}
+extern "C" const char *rs_last_error(void) { return t_err.c_str(); }
+
+static cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+int rs::grid_for(int64_t items, int per_block, int cap_per_sm) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    int64_t want = (items + per_block - 1) / per_block;
+    int64_t cap = (int64_t)sms * cap_per_sm;
+    if (want < 1) want = 1;
+    return (int)std::min(want, cap);
+}
+
+// ---------------------------------------------------------------------------
+// inclusive scan of int64 (tiles of 4096, recursive over tile sums)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 512, kScanPer = 8, kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int64_t block_inclusive_scan(int64_t x, int64_t *warp_tot) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        int64_t t = lane < nw ? warp_tot[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    if (wid > 0) x += warp_tot[wid - 1];
+    return x;
+}
+
+__global__ void scan_tile_kernel(int64_t *a, int64_t m, int64_t *tile_sums) {
+    __shared__ int64_t wt[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    int64_t v[kScanPer];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        v[i] = (base + i < m) ? a[base + i] : 0;
+        s += v[i];
+        v[i] = s;
+    }
+    int64_t incl = block_inclusive_scan(s, wt);
+    int64_t excl = incl - s;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i)
+        if (base + i < m) a[base + i] = v[i] + excl;
+    if (threadIdx.x == blockDim.x - 1 && tile_sums) tile_sums[blockIdx.x] = incl;
+}
+
+__global__ void scan_add_kernel(int64_t *a, int64_t m, const int64_t *tile_sums) {
+    if (blockIdx.x == 0) return;
+    int64_t add = tile_sums[blockIdx.x - 1];
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x)
+        if (base + i < m) a[base + i] += add;
+}
+
+int64_t rs::scan_tmp_words(int64_t m) {
+    int64_t words = 0;
+    while (m > kScanTile) {
+        m = (m + kScanTile - 1) / kScanTile;
+        words += m + 1;
+    }
+    return words + 1;
+}
+
+int rs::inclusive_scan_i64(int64_t *a, int64_t m, int64_t *tmp, cudaStream_t s) {
+    if (m <= 0) return 0;
+    int64_t tiles = (m + kScanTile - 1) / kScanTile;
+    if (tiles > 2147483647LL) return fail(RS_EINVAL, "scan too large");
+    scan_tile_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(a, m, tiles > 1 ? tmp : nullptr);
+    RS_CUDA_TRY(cudaGetLastError());
+    if (tiles > 1) {
+        int rc = inclusive_scan_i64(tmp, tiles, tmp + tiles + 1, s);
+        if (rc) return rc;
+        scan_add_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(a, m, tmp);
+        RS_CUDA_TRY(cudaGetLastError());
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// constant tables: LG[f] = round(log2 f * 2^58), RD[d] = 1/(d(d-1))
+// log2 by the series ln m = 2 atanh((m-1)/(m+1)) in 64-bit fixed point
+// (integer arithmetic only), divided by ln 2 = 2 atanh(1/3).
+// ---------------------------------------------------------------------------
+__device__ uint64_t frac_div(uint64_t a, uint64_t b) {  // floor(a 2^64 / b), a < b
+    uint64_t q = 0, r = a;
+    for (int i = 63; i >= 0; --i) {
+        bool carry = (r >> 63) != 0;
+        r <<= 1;
+        if (carry || r >= b) { r -= b; q |= 1ull << i; }
+    }
+    return q;
+}
+__device__ uint64_t atanh_fixed(uint64_t z) {  // z < 1/2 in 2^-64 units
+    uint64_t z2 = (uint64_t)(((u128)z * z) >> 64);
+    uint64_t p = z, s = z;
+    for (uint64_t k = 3; k < 200; k += 2) {
+        p = (uint64_t)(((u128)p * z2) >> 64);
+        uint64_t t = p / k;
+        if (!t) break;
+        s += t;
+    }
+    return s;
+}
+__global__ void init_tables_kernel(uint64_t *LG, double *RD, int32_t dmax) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f > dmax) return;
+    uint64_t lg = 0;
+    if (f >= 1) {
+        int e = 63 - __clzll((long long)f);
+        uint64_t p2 = 1ull << e;
+        if ((uint64_t)f == p2) {
+            lg = (uint64_t)e << kLogFrac;
+        } else {
+            uint64_t ln2 = atanh_fixed(frac_div(1, 3)) << 1;
+            uint64_t lnm = atanh_fixed(frac_div((uint64_t)f - p2, (uint64_t)f + p2)) << 1;
+            uint64_t l2m = frac_div(lnm, ln2);                       // log2(f / 2^e) in [0, 1)
+            const int drop = 64 - kLogFrac;
+            lg = ((uint64_t)e << kLogFrac) + (l2m >> drop) + ((l2m >> (drop - 1)) & 1);
+        }
+    }
+    LG[f] = lg;
+    RD[f] = f >= 2 ? 1.0 / ((double)f * (double)(f - 1)) : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+enum : int { V_OFF = 1, V_COLRANGE = 2, V_SELF = 4, V_ORDER = 8, V_LABEL = 16, V_ASYM = 32 };
+
+__global__ void validate_offsets_kernel(const int64_t *off, int64_t n, int64_t nnz, int *flag) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v > n) return;
+    bool bad = false;
+    if (v == 0 && off[0] != 0) bad = true;
+    if (v == n && off[n] != nnz) bad = true;
+    if (v < n && off[v + 1] < off[v]) bad = true;
+    if (bad) atomicOr(flag, V_OFF);
+}
+
+__global__ void validate_rows_kernel(const int64_t *off, const int32_t *col, const int32_t *lab,
+                                     int64_t n, int32_t k, int *flag) {
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = w; v < n; v += nw) {
+        int bad = 0;
+        if (lane == 0 && (lab[v] < 0 || lab[v] >= k)) bad |= V_LABEL;
+        for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) {
+            int32_t x = col[e];
+            if (x < 0 || x >= n) bad |= V_COLRANGE;
+            if (x == v) bad |= V_SELF;
+            if (e > off[v] && col[e - 1] >= x) bad |= V_ORDER;
+        }
+        if (bad) atomicOr(flag, bad);
+    }
+}
+
+__device__ __forceinline__ int64_t find_in_row(const int64_t *off, const int32_t *col, int32_t row,
+                                                int32_t key) {
+    int64_t lo = off[row], hi = off[row + 1];
+    while (lo < hi) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (col[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return (lo < off[row + 1] && col[lo] == key) ? lo : -1;
+}
+
+__global__ void validate_symmetry_kernel(const int64_t *off, const int32_t *col, int64_t n, int *flag) {
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = w; v < n; v += nw)
+        for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32)
+            if (find_in_row(off, col, col[e], (int32_t)v) < 0) atomicOr(flag, V_ASYM);
+}
+
+static int read_flag(rs_graph *g, cudaStream_t s, int *out) {
+    RS_CUDA_TRY(cudaMemcpyAsync(out, g->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RS_CUDA_TRY(cudaStreamSynchronize(s));
+    return 0;
+}
+
+static int validate_graph(rs_graph *g, cudaStream_t s) {
+    int flag = 0;
+    RS_CUDA_TRY(cudaMemsetAsync(g->d_flag, 0, sizeof(int), s));
+    validate_offsets_kernel<<<(unsigned)((g->n + 1 + 255) / 256), 256, 0, s>>>(g->off, g->n, g->nnz, g->d_flag);
+    RS_CUDA_TRY(cudaGetLastError());
+    if (int rc = read_flag(g, s, &flag)) return rc;
+    if (flag) return fail(RS_EINVAL, "invalid graph: row_offsets must start at 0, end at nnz and not decrease");
+    int grid = grid_for(g->n * 32, kThreads, 16);
+    validate_rows_kernel<<<grid, kThreads, 0, s>>>(g->off, g->col, g->lab, g->n, g->k, g->d_flag);
+    RS_CUDA_TRY(cudaGetLastError());
+    if (int rc = read_flag(g, s, &flag)) return rc;
+    if (flag & V_COLRANGE) return fail(RS_EINVAL, "invalid graph: column id outside [0, n)");
+    if (flag & V_SELF) return fail(RS_EINVAL, "invalid graph: self-loop");
+    if (flag & V_ORDER) return fail(RS_EINVAL, "invalid graph: a row is not strictly ascending (unsorted or duplicate neighbour)");
+    if (flag & V_LABEL) return fail(RS_EINVAL, "invalid graph: label outside [0, k)");
+    validate_symmetry_kernel<<<grid, kThreads, 0, s>>>(g->off, g->col, g->n, g->d_flag);
+    RS_CUDA_TRY(cudaGetLastError());
+    if (int rc = read_flag(g, s, &flag)) return rc;
+    if (flag & V_ASYM) return fail(RS_EINVAL, "invalid graph: an edge is missing its reverse direction");
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// row classification
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int row_class(int64_t d, int32_t k) {
+    if (d <= kSmallMax) return 0;
+    int64_t m = d < k ? d : k;
+    uint32_t cap = 1;
+    while ((int64_t)cap < 2 * m) cap <<= 1;
+    return cap <= (uint32_t)kMidCap ? 1 : 2;
+}
+
+// flags for one class into a[v], plus dmax / mid cap / hub list on the first pass
+__global__ void classify_kernel(const int64_t *off, int64_t n, int32_t k, int cls, int64_t *a,
+                                int *dmax, int *midcap, int32_t *hub_list, int *n_hub) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int64_t d = off[v + 1] - off[v];
+    int c = row_class(d, k);
+    a[v] = (c == cls) ? 1 : 0;
+    if (cls == 0) {
+        atomicMax(dmax, (int)d);
+        if (c == 1) {
+            int64_t m = d < k ? d : k;
+            uint32_t cap = 1;
+            while ((int64_t)cap < 2 * m) cap <<= 1;
+            atomicMax(midcap, (int)cap);
+        }
+        if (c == 2) hub_list[atomicAdd(n_hub, 1)] = (int32_t)v;
+    }
+}
+__global__ void scatter_class_kernel(const int64_t *a, int64_t n, int32_t *rows) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int64_t prev = v ? a[v - 1] : 0;
+    if (a[v] != prev) rows[prev] = (int32_t)v;
+}
+
+static void free_hub_tables(rs_graph *g) {
+    cudaFree(g->hubs); cudaFree(g->hub_items); cudaFree(g->hub_item_chunk);
+    cudaFree(g->hkey); cudaFree(g->hcnt); cudaFree(g->hq); cudaFree(g->hsig); cudaFree(g->hagg);
+    cudaFree(g->hitem_out); cudaFree(g->hitem_in);
+    g->hubs = nullptr; g->hub_items = g->hub_item_chunk = nullptr; g->hkey = nullptr;
+    g->hcnt = nullptr; g->hq = nullptr; g->hsig = nullptr; g->hagg = nullptr;
+    g->hitem_out = g->hitem_in = nullptr;
+    g->n_hubs = g->n_hub_items = g->hub_slots = 0;
+}
+
+template <class T>
+static cudaError_t dmalloc(T **p, size_t count) {
+    return cudaMalloc((void **)p, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+// builds rows_small / rows_mid / hub tables from the current offsets; syncs
+static int classify_rows(rs_graph *g, cudaStream_t s) {
+    int64_t n = g->n;
+    int hdr[4] = {0, 0, 0, 0};   // dmax, midcap, n_hub, unused
+    int *d_hdr = g->d_flag;      // d_flag has room for 4 ints
+    RS_CUDA_TRY(cudaMemsetAsync(d_hdr, 0, 4 * sizeof(int), s));
+    int32_t *hub_list = g->xout;  // n int32 scratch (workspace is allocated by now)
+    unsigned blocks = (unsigned)((n + 255) / 256);
+    int64_t *a = g->xoff;
+    for (int cls = 0; cls < 2; ++cls) {
+        if (n > 0) {
+            classify_kernel<<<blocks, 256, 0, s>>>(g->off, n, g->k, cls, a, d_hdr, d_hdr + 1, hub_list, d_hdr + 2);
+            RS_CUDA_TRY(cudaGetLastError());
+            if (int rc = inclusive_scan_i64(a, n, g->scan_tmp, s)) return rc;
+            scatter_class_kernel<<<blocks, 256, 0, s>>>(a, n, cls == 0 ? g->rows_small : g->rows_mid);
+            RS_CUDA_TRY(cudaGetLastError());
+        }
+        int64_t cnt = 0;
+        if (n > 0) RS_CUDA_TRY(cudaMemcpyAsync(&cnt, a + n - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        RS_CUDA_TRY(cudaMemcpyAsync(hdr, d_hdr, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        RS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (cls == 0) g->n_small = cnt; else g->n_mid = cnt;
+    }
+    g->dmax = hdr[0];
+    g->mid_cap = std::max(hdr[1], 64);
+    // hubs: host-side work list (hubs are few)
+    int nh = hdr[2];
+    std::vector<int32_t> hl(nh);
+    std::vector<int64_t> offs(2 * (size_t)nh);
+    if (nh) RS_CUDA_TRY(cudaMemcpy(hl.data(), hub_list, nh * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::sort(hl.begin(), hl.end());
+    for (int i = 0; i < nh; ++i)
+        RS_CUDA_TRY(cudaMemcpy(&offs[2 * i], g->off + hl[i], 2 * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    std::vector<HubInfo> info(nh);
+    std::vector<int32_t> items, chunks;
+    int64_t slots = 0;
+    for (int i = 0; i < nh; ++i) {
+        int64_t d = offs[2 * i + 1] - offs[2 * i];
+        int64_t m = std::min<int64_t>(d, g->k);
+        info[i].row = hl[i];
+        info[i].cap = (int32_t)pow2_at_least((uint64_t)(2 * m));
+        info[i].tab = slots;
+        info[i].first_item = (int32_t)items.size();
+        int nc = (int)((d + kHubChunk - 1) / kHubChunk);
+        info[i].n_items = nc;
+        for (int c = 0; c < nc; ++c) { items.push_back(i); chunks.push_back(c); }
+        slots += info[i].cap;
+    }
+    free_hub_tables(g);
+    g->n_hubs = nh;
+    g->n_hub_items = (int64_t)items.size();
+    g->hub_slots = slots;
+    if (nh) {
+        RS_CUDA_TRY(dmalloc(&g->hubs, nh));
+        RS_CUDA_TRY(dmalloc(&g->hub_items, items.size()));
+        RS_CUDA_TRY(dmalloc(&g->hub_item_chunk, items.size()));
+        RS_CUDA_TRY(dmalloc(&g->hkey, slots));
+        RS_CUDA_TRY(dmalloc(&g->hcnt, slots));
+        RS_CUDA_TRY(dmalloc(&g->hq, 2 * slots));
+        RS_CUDA_TRY(dmalloc(&g->hsig, slots));
+        RS_CUDA_TRY(dmalloc(&g->hagg, nh));
+        RS_CUDA_TRY(dmalloc(&g->hitem_out, items.size()));
+        RS_CUDA_TRY(dmalloc(&g->hitem_in, items.size()));
+        RS_CUDA_TRY(cudaMemcpy(g->hubs, info.data(), nh * sizeof(HubInfo), cudaMemcpyHostToDevice));
+        RS_CUDA_TRY(cudaMemcpy(g->hub_items, items.data(), items.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        RS_CUDA_TRY(cudaMemcpy(g->hub_item_chunk, chunks.data(), chunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    return 0;
+}
+
+static int build_tables(rs_graph *g, cudaStream_t s) {
+    cudaFree(g->LG); cudaFree(g->RD);
+    g->LG = nullptr; g->RD = nullptr;
+    int64_t m = (int64_t)g->dmax + 1;
+    RS_CUDA_TRY(dmalloc(&g->LG, m));
+    RS_CUDA_TRY(dmalloc(&g->RD, m));
+    init_tables_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(g->LG, g->RD, g->dmax);
+    RS_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+static int alloc_workspace(rs_graph *g) {
+    int64_t n = g->n, nnz = g->nnz;
+    RS_CUDA_TRY(dmalloc(&g->rec, n));
+    RS_CUDA_TRY(dmalloc(&g->acc, 2 * n));
+    RS_CUDA_TRY(dmalloc(&g->wmax_bits, 1));
+    RS_CUDA_TRY(dmalloc(&g->Lall, n));
+    RS_CUDA_TRY(dmalloc(&g->xoff, n + 1));
+    RS_CUDA_TRY(dmalloc(&g->xcol, nnz));
+    RS_CUDA_TRY(dmalloc(&g->xS, nnz));
+    RS_CUDA_TRY(dmalloc(&g->xout, n));
+    RS_CUDA_TRY(dmalloc(&g->xin, n));
+    RS_CUDA_TRY(dmalloc(&g->scan_tmp, scan_tmp_words(std::max<int64_t>(n + 1, 1)) + 64));
+    RS_CUDA_TRY(dmalloc(&g->rows_small, n));
+    RS_CUDA_TRY(dmalloc(&g->rows_mid, n));
+    RS_CUDA_TRY(dmalloc(&g->d_flag, 8));
+    return 0;
+}
+
+static void free_graph(rs_graph *g) {
+    if (!g) return;
+    void *ptrs[] = {g->off, g->off_alt, g->col, g->col_alt, g->lab, g->removed, g->dead,
+                    g->rows_small, g->rows_mid, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
+                    g->Lall, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->scan_tmp, g->tk_hist,
+                    g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag};
+    for (void *p : ptrs) cudaFree(p);
+    free_hub_tables(g);
+    delete g;
+}
+
+__global__ void widen_offsets_kernel(const int32_t *in, int64_t *out, int64_t m) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] = in[i];
+}
+
+// allocations and tables for a graph whose CSR/labels/removed are already on the device
+static int finish_graph(rs_graph *g, cudaStream_t s) {
+    if (int rc = alloc_workspace(g)) return rc;
+    if (int rc = classify_rows(g, s)) return rc;
+    if (g->dmax >= (1 << 24)) return fail(RS_EINVAL, "max degree must be < 2^24");
+    if (int rc = build_tables(g, s)) return rc;
+    RS_CUDA_TRY(cudaStreamSynchronize(s));
+    return 0;
+}
+
+extern "C" rs_status rs_build_graph(int64_t n, int64_t nnz, const void *row_offsets, int offsets_are_i64,
+                                    const int32_t *cols, const int32_t *labels, int32_t num_communities,
+                                    int inputs_on_device, uint32_t flags, void *stream, rs_graph **out) {
+    cudaStream_t s = as_stream(stream);
+    if (!out) return (rs_status)fail(RS_EINVAL, "rs_build_graph: out is NULL");
+    if (n < 0 || n >= (1LL << 31)) return (rs_status)fail(RS_EINVAL, "rs_build_graph: n must be in [0, 2^31)");
+    if (nnz < 0 || nnz >= (1LL << 40)) return (rs_status)fail(RS_EINVAL, "rs_build_graph: nnz must be in [0, 2^40)");
+    if (!offsets_are_i64 && nnz >= (1LL << 31))
+        return (rs_status)fail(RS_EINVAL, "rs_build_graph: nnz >= 2^31 needs int64 offsets");
+    if (num_communities < 1) return (rs_status)fail(RS_EINVAL, "rs_build_graph: num_communities must be >= 1");
+    if (!row_offsets || (nnz > 0 && !cols) || (n > 0 && !labels))
+        return (rs_status)fail(RS_EINVAL, "rs_build_graph: NULL input array");
+    rs_graph *g = new rs_graph();
+    g->n = n; g->nnz = nnz; g->k = num_communities;
+    cudaGetDevice(&g->device);
+    auto bail = [&](int rc) { free_graph(g); return (rs_status)rc; };
+    cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaError_t e = dmalloc(&g->off, n + 1)) return bail(cuda_fail(e, "alloc offsets"));
+    if (cudaError_t e = dmalloc(&g->off_alt, n + 1)) return bail(cuda_fail(e, "alloc offsets"));
+    if (cudaError_t e = dmalloc(&g->col, nnz)) return bail(cuda_fail(e, "alloc cols"));
+    if (cudaError_t e = dmalloc(&g->col_alt, nnz)) return bail(cuda_fail(e, "alloc cols"));
+    if (cudaError_t e = dmalloc(&g->lab, n)) return bail(cuda_fail(e, "alloc labels"));
+    if (cudaError_t e = dmalloc(&g->removed, 4 * n)) return bail(cuda_fail(e, "alloc flags"));
+    if (cudaError_t e = dmalloc(&g->dead, 4 * ((nnz + 31) / 32))) return bail(cuda_fail(e, "alloc marks"));
+    if (offsets_are_i64) {
+        if (cudaError_t e = cudaMemcpyAsync(g->off, row_offsets, (n + 1) * sizeof(int64_t), kind, s))
+            return bail(cuda_fail(e, "copy offsets"));
+    } else {
+        // stage int32 offsets in col_alt's storage when it is large enough, else a temporary
+        int32_t *tmp = nullptr;
+        if (cudaError_t e = dmalloc(&tmp, n + 1)) return bail(cuda_fail(e, "alloc offsets"));
+        cudaError_t e = cudaMemcpyAsync(tmp, row_offsets, (n + 1) * sizeof(int32_t), kind, s);
+        if (!e) {
+            widen_offsets_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(tmp, g->off, n + 1);
+            e = cudaGetLastError();
+        }
+        if (!e) e = cudaStreamSynchronize(s);
+        cudaFree(tmp);
+        if (e) return bail(cuda_fail(e, "copy offsets"));
+    }
+    if (nnz > 0)
+        if (cudaError_t e = cudaMemcpyAsync(g->col, cols, nnz * sizeof(int32_t), kind, s))
+            return bail(cuda_fail(e, "copy cols"));
+    if (n > 0)
+        if (cudaError_t e = cudaMemcpyAsync(g->lab, labels, n * sizeof(int32_t), kind, s))
+            return bail(cuda_fail(e, "copy labels"));
+    if (cudaError_t e = cudaMemsetAsync(g->removed, 0, 4 * std::max<int64_t>(n, 1), s))
+        return bail(cuda_fail(e, "clear flags"));
+    if (cudaError_t e = dmalloc(&g->d_flag, 8)) return bail(cuda_fail(e, "alloc flag"));
+    if (flags & RS_VALIDATE) {
+        if (int rc = validate_graph(g, s)) return bail(rc);
+    }
+    cudaFree(g->d_flag);
+    g->d_flag = nullptr;
+    if (int rc = finish_graph(g, s)) return bail(rc);
+    *out = g;
+    return RS_OK;
+}
+
+extern "C" void rs_free_graph(rs_graph *g) { free_graph(g); }
+
+extern "C" rs_status rs_graph_info(const rs_graph *g, int64_t *n, int64_t *nnz, int32_t *k, int32_t *max_degree) {
+    if (!g) return (rs_status)fail(RS_EINVAL, "rs_graph_info: NULL graph");
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    if (k) *k = g->k;
+    if (max_degree) *max_degree = g->dmax;
+    return RS_OK;
+}
+
+extern "C" rs_status rs_clone_graph(const rs_graph *src, rs_graph **out, void *stream) {
+    cudaStream_t s = as_stream(stream);
+    if (!src || !out) return (rs_status)fail(RS_EINVAL, "rs_clone_graph: NULL argument");
+    rs_graph *g = new rs_graph();
+    g->n = src->n; g->nnz = src->nnz; g->k = src->k; g->device = src->device;
+    auto bail = [&](int rc) { free_graph(g); return (rs_status)rc; };
+    int64_t n = g->n, nnz = g->nnz;
+    if (cudaError_t e = dmalloc(&g->off, n + 1)) return bail(cuda_fail(e, "alloc"));
+    if (cudaError_t e = dmalloc(&g->off_alt, n + 1)) return bail(cuda_fail(e, "alloc"));
+    if (cudaError_t e = dmalloc(&g->col, nnz)) return bail(cuda_fail(e, "alloc"));
+    if (cudaError_t e = dmalloc(&g->col_alt, nnz)) return bail(cuda_fail(e, "alloc"));
+    if (cudaError_t e = dmalloc(&g->lab, n)) return bail(cuda_fail(e, "alloc"));
+    if (cudaError_t e = dmalloc(&g->removed, 4 * n)) return bail(cuda_fail(e, "alloc"));
+    if (cudaError_t e = dmalloc(&g->dead, 4 * ((nnz + 31) / 32))) return bail(cuda_fail(e, "alloc"));
+    int64_t cur_nnz = 0;
+    if (cudaError_t e = cudaMemcpy(&cur_nnz, src->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost))
+        return bail(cuda_fail(e, "read offsets"));
+    cudaError_t e = cudaMemcpyAsync(g->off, src->off, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+    if (!e && cur_nnz) e = cudaMemcpyAsync(g->col, src->col, cur_nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (!e && n) e = cudaMemcpyAsync(g->lab, src->lab, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (!e && n) e = cudaMemcpyAsync(g->removed, src->removed, 4 * n, cudaMemcpyDeviceToDevice, s);
+    if (e) return bail(cuda_fail(e, "copy graph"));
+    if (int rc = finish_graph(g, s)) return bail(rc);
+    *out = g;
+    return RS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// removals: mark dead CSR entries (bit set), then compact into the alt buffers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool mark_dead(uint32_t *dead, int64_t e) {
+    uint32_t bit = 1u << (e & 31);
+    return (atomicOr(&dead[e >> 5], bit) & bit) == 0;
+}
+
+__global__ void remove_nodes_kernel(const int64_t *off, const int32_t *col, int32_t *removed,
+                                    uint32_t *dead, const int32_t *nodes, int64_t m,
+                                    unsigned long long *applied) {
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w; i < m; i += nw) {
+        int32_t v = nodes[i];
+        int first = 0;
+        if (lane == 0) first = atomicExch(&removed[v], 1) == 0;
+        first = __shfl_sync(0xFFFFFFFFu, first, 0);
+        if (!first) continue;
+        if (lane == 0) atomicAdd(applied, 1ull);
+        for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) {
+            mark_dead(dead, e);
+            int64_t r = find_in_row(off, col, col[e], v);
+            if (r >= 0) mark_dead(dead, r);
+        }
+    }
+}
+
+__global__ void remove_edges_kernel(const int64_t *off, const int32_t *col, uint32_t *dead,
+                                    const int32_t *src, const int32_t *dst, int64_t m,
+                                    unsigned long long *applied) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int32_t a = src[i], b = dst[i];
+    if (a == b) return;
+    int32_t lo = a < b ? a : b, hi = a < b ? b : a;
+    int64_t e = find_in_row(off, col, lo, hi);
+    if (e < 0) return;
+    // the entry in the smaller endpoint's row decides, so (a,b) and (b,a) count once
+    if (!mark_dead(dead, e)) return;
+    int64_t r = find_in_row(off, col, hi, lo);
+    if (r >= 0) mark_dead(dead, r);
+    atomicAdd(applied, 1ull);
+}
+
+__global__ void alive_degree_kernel(const int64_t *off, const uint32_t *dead, int64_t n, int64_t *deg) {
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = w; v < n; v += nw) {
+        int64_t c = 0;
+        for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) c += !((dead[e >> 5] >> (e & 31)) & 1u);
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        if (lane == 0) deg[v + 1] = c;
+        if (v == 0 && lane == 0) deg[0] = 0;
+    }
+}
+
+__global__ void compact_rows_kernel(const int64_t *off, const int32_t *col, const uint32_t *dead,
+                                    int64_t n, const int64_t *noff, int32_t *ncol) {
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = w; v < n; v += nw) {
+        int64_t out = noff[v];
+        for (int64_t base = off[v]; base < off[v + 1]; base += 32) {
+            int64_t e = base + lane;
+            bool keep = e < off[v + 1] && !((dead[e >> 5] >> (e & 31)) & 1u);
+            unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+            if (keep) ncol[out + __popc(m & ((1u << lane) - 1))] = col[e];
+            out += __popc(m);
+        }
+    }
+}
+
+extern "C" rs_status rs_apply_removals(rs_graph *g, const int32_t *nodes, int64_t n_nodes,
+                                       const int32_t *edge_src, const int32_t *edge_dst, int64_t n_edges,
+                                       int64_t *applied_out, void *stream) {
+    cudaStream_t s = as_stream(stream);
+    if (!g) return (rs_status)fail(RS_EINVAL, "rs_apply_removals: NULL graph");
+    if (n_nodes < 0 || n_edges < 0 || (n_nodes && !nodes) || (n_edges && (!edge_src || !edge_dst)))
+        return (rs_status)fail(RS_EINVAL, "rs_apply_removals: bad arrays");
+    for (int64_t i = 0; i < n_nodes; ++i)
+        if (nodes[i] < 0 || nodes[i] >= g->n)
+            return (rs_status)fail(RS_EINVAL, "rs_apply_removals: node id out of range");
+    for (int64_t i = 0; i < n_edges; ++i)
+        if (edge_src[i] < 0 || edge_src[i] >= g->n || edge_dst[i] < 0 || edge_dst[i] >= g->n)
+            return (rs_status)fail(RS_EINVAL, "rs_apply_removals: edge endpoint out of range");
+    int32_t *buf = nullptr;
+    unsigned long long *d_applied = nullptr;
+    int64_t words = n_nodes + 2 * n_edges;
+    auto done = [&](int rc) { cudaFree(buf); cudaFree(d_applied); return (rs_status)rc; };
+    if (cudaError_t e = dmalloc(&buf, words)) return done(cuda_fail(e, "alloc removal lists"));
+    if (cudaError_t e = dmalloc(&d_applied, 1)) return done(cuda_fail(e, "alloc counter"));
+    cudaError_t e = cudaMemsetAsync(d_applied, 0, sizeof(unsigned long long), s);
+    if (!e && n_nodes) e = cudaMemcpyAsync(buf, nodes, n_nodes * 4, cudaMemcpyHostToDevice, s);
+    if (!e && n_edges) e = cudaMemcpyAsync(buf + n_nodes, edge_src, n_edges * 4, cudaMemcpyHostToDevice, s);
+    if (!e && n_edges) e = cudaMemcpyAsync(buf + n_nodes + n_edges, edge_dst, n_edges * 4, cudaMemcpyHostToDevice, s);
+    int64_t nnz_cur = 0;
+    if (!e) e = cudaMemcpyAsync(&nnz_cur, g->off + g->n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (!e && nnz_cur) e = cudaMemsetAsync(g->dead, 0, 4 * ((nnz_cur + 31) / 32), s);
+    if (e) return done(cuda_fail(e, "stage removals"));
+    if (n_nodes) {
+        remove_nodes_kernel<<<grid_for(n_nodes * 32, kThreads, 8), kThreads, 0, s>>>(
+            g->off, g->col, (int32_t *)g->removed, (uint32_t *)g->dead, buf, n_nodes, d_applied);
+        if ((e = cudaGetLastError())) return done(cuda_fail(e, "remove nodes"));
+    }
+    if (n_edges) {
+        remove_edges_kernel<<<(unsigned)((n_edges + 255) / 256), 256, 0, s>>>(
+            g->off, g->col, (uint32_t *)g->dead, buf + n_nodes, buf + n_nodes + n_edges, n_edges, d_applied);
+        if ((e = cudaGetLastError())) return done(cuda_fail(e, "remove edges"));
+    }
+    if (g->n > 0) {
+        int grid = grid_for(g->n * 32, kThreads, 16);
+        alive_degree_kernel<<<grid, kThreads, 0, s>>>(g->off, (uint32_t *)g->dead, g->n, g->off_alt);
+        if ((e = cudaGetLastError())) return done(cuda_fail(e, "count alive"));
+        if (int rc = inclusive_scan_i64(g->off_alt + 1, g->n, g->scan_tmp, s)) return done(rc);
+        compact_rows_kernel<<<grid, kThreads, 0, s>>>(g->off, g->col, (uint32_t *)g->dead, g->n, g->off_alt, g->col_alt);
+        if ((e = cudaGetLastError())) return done(cuda_fail(e, "compact rows"));
+        std::swap(g->off, g->off_alt);
+        std::swap(g->col, g->col_alt);
+    }
+    unsigned long long applied = 0;
+    if ((e = cudaMemcpyAsync(&applied, d_applied, sizeof(applied), cudaMemcpyDeviceToHost, s)))
+        return done(cuda_fail(e, "read applied"));
+    if (int rc = classify_rows(g, s)) return done(rc);
+    if (int rc = build_tables(g, s)) return done(rc);
+    if ((e = cudaStreamSynchronize(s))) return done(cuda_fail(e, "removals"));
+    if (applied_out) *applied_out = (int64_t)applied;
+    return done(RS_OK);
+}
+
+// ---------------------------------------------------------------------------
+// interaction table (sorted per row): labels of each row are sorted in place
+// in a scratch copy, then run-length encoded
+// ---------------------------------------------------------------------------
+__global__ void gather_labels_kernel(const int32_t *col, const int32_t *lab, int64_t nnz, int32_t *out) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nnz) out[e] = lab[col[e]];
+}
+
+// sort each row segment of `a` ascending: warps for rows <= 32, CTAs otherwise
+__global__ void sort_small_rows_kernel(const int64_t *off, int64_t n, int32_t *a) {
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = w; v < n; v += nw) {
+        int64_t b = off[v];
+        int d = (int)(off[v + 1] - b);
+        if (d > 32 || d < 2) continue;
+        int32_t x = lane < d ? a[b + lane] : 0x7FFFFFFF;
+        for (int size = 2; size <= 32; size <<= 1)
+            for (int st = size >> 1; st; st >>= 1) {
+                int32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, st);
+                bool up = ((lane & size) == 0);
+                bool lower = (lane & st) == 0;
+                x = (lower == up) ? min(x, y) : max(x, y);
+            }
+        if (lane < d) a[b + lane] = x;
+    }
+}
+
+__global__ void sort_large_rows_kernel(const int64_t *off, int64_t n, int32_t *a) {
+    for (int64_t v = blockIdx.x; v < n; v += gridDim.x) {
+        int64_t b = off[v];
+        int64_t d = off[v + 1] - b;
+        if (d <= 32) continue;
+        int64_t P = 1;
+        while (P < d) P <<= 1;
+        int32_t *s = a + b;
+        for (int64_t size = 2; size <= P; size <<= 1) {
+            // mirror step, then half-cleaners; the smaller key moves to the lower index
+            for (int64_t st = size >> 1; st; st >>= 1) {
+                for (int64_t i = threadIdx.x; i < P / 2; i += blockDim.x) {
+                    int64_t lo, hi;
+                    if (st == (size >> 1)) {
+                        int64_t blk = i / st, off_in = i % st;
+                        lo = blk * size + off_in;
+                        hi = blk * size + size - 1 - off_in;
+                    } else {
+                        lo = (i / st) * 2 * st + (i % st);
+                        hi = lo + st;
+                    }
+                    if (hi < d && s[lo] > s[hi]) { int32_t t = s[lo]; s[lo] = s[hi]; s[hi] = t; }
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+__global__ void count_runs_kernel(const int64_t *off, const int32_t *a, int64_t n, int64_t *cnt) {
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = w; v < n; v += nw) {
+        int64_t c = 0;
+        for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) c += (e == off[v] || a[e] != a[e - 1]);
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        if (lane == 0) cnt[v + 1] = c;
+        if (v == 0 && lane == 0) cnt[0] = 0;
+    }
+}
+
+__global__ void emit_runs_kernel(const int64_t *off, const int32_t *a, int64_t n, const int64_t *rp,
+                                 int32_t *comm, int32_t *count) {
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = w; v < n; v += nw) {
+        int64_t out = rp[v];
+        int64_t end = off[v + 1];
+        for (int64_t base = off[v]; base < end; base += 32) {
+            int64_t e = base + lane;
+            bool head = e < end && (e == off[v] || a[e] != a[e - 1]);
+            unsigned m = __ballot_sync(0xFFFFFFFFu, head);
+            if (head) {
+                int64_t j = e + 1;
+                while (j < end && a[j] == a[e]) ++j;
+                int64_t slot = out + __popc(m & ((1u << lane) - 1));
+                comm[slot] = a[e];
+                count[slot] = (int32_t)(j - e);
+            }
+            out += __popc(m);
+        }
+    }
+}
+
+int rs::interaction_table(rs_graph *g, int64_t *t_out, int64_t *row_ptr, int32_t *comm, int32_t *count,
+                          cudaStream_t s) {
+    int64_t n = g->n, nnz_cur = 0;
+    RS_CUDA_TRY(cudaMemcpyAsync(&nnz_cur, g->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RS_CUDA_TRY(cudaStreamSynchronize(s));
+    int32_t *a = g->col_alt;           // scratch: labels of every CSR entry
+    int64_t *rp = g->off_alt;          // scratch: row pointer
+    if (nnz_cur) {
+        gather_labels_kernel<<<(unsigned)((nnz_cur + 255) / 256), 256, 0, s>>>(g->col, g->lab, nnz_cur, a);
+        RS_CUDA_TRY(cudaGetLastError());
+    }
+    if (n > 0) {
+        int grid = grid_for(n * 32, kThreads, 16);
+        sort_small_rows_kernel<<<grid, kThreads, 0, s>>>(g->off, n, a);
+        RS_CUDA_TRY(cudaGetLastError());
+        sort_large_rows_kernel<<<grid_for(n, 1, 8), 512, 0, s>>>(g->off, n, a);
+        RS_CUDA_TRY(cudaGetLastError());
+        count_runs_kernel<<<grid, kThreads, 0, s>>>(g->off, a, n, rp);
+        RS_CUDA_TRY(cudaGetLastError());
+        if (int rc = inclusive_scan_i64(rp + 1, n, g->scan_tmp, s)) return rc;
+    } else {
+        RS_CUDA_TRY(cudaMemsetAsync(rp, 0, sizeof(int64_t), s));
+    }
+    int64_t t = 0;
+    RS_CUDA_TRY(cudaMemcpyAsync(&t, rp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (row_ptr) RS_CUDA_TRY(cudaMemcpyAsync(row_ptr, rp, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    if (comm && count && n > 0) {
+        emit_runs_kernel<<<grid_for(n * 32, kThreads, 16), kThreads, 0, s>>>(g->off, a, n, rp, comm, count);
+        RS_CUDA_TRY(cudaGetLastError());
+    }
+    RS_CUDA_TRY(cudaStreamSynchronize(s));
+    *t_out = t;
+    return 0;
+}
+
+extern "C" rs_status rs_get_interaction(rs_graph *g, int64_t *t_out, int64_t *row_ptr, int32_t *comm,
+                                        int32_t *count, void *stream) {
+    if (!g || !t_out) return (rs_status)fail(RS_EINVAL, "rs_get_interaction: NULL argument");
+    if ((comm == nullptr) != (count == nullptr))
+        return (rs_status)fail(RS_EINVAL, "rs_get_interaction: comm and count go together");
+    int64_t t = 0;
+    int rc = interaction_table(g, &t, row_ptr, comm, count, as_stream(stream));
+    if (rc) return (rs_status)rc;
+    *t_out = t;
+    return RS_OK;
+}
+
+extern "C" rs_status rs_score(rs_graph *g, double *scores, double *omega_max_out, void *stream) {
+    cudaStream_t s = as_stream(stream);
+    if (!g || (!scores && g->n > 0)) return (rs_status)fail(RS_EINVAL, "rs_score: NULL argument");
+    int rc = score_graph(g, scores, s);
+    if (rc) return (rs_status)rc;
+    if (omega_max_out) {
+        unsigned long long bits = 0;
+        if (cudaError_t e = cudaMemcpyAsync(&bits, g->wmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, s))
+            return (rs_status)cuda_fail(e, "read w_max");
+        if (cudaError_t e = cudaStreamSynchronize(s)) return (rs_status)cuda_fail(e, "rs_score");
+        double w;
+        memcpy(&w, &bits, sizeof(w));
+        *omega_max_out = w;
+    }
+    return RS_OK;
+}
+
+extern "C" rs_status rs_topk(rs_graph *g, const double *scores, int32_t k, int32_t *ids_out,
+                             double *scores_out, void *stream) {
+    if (!g || !scores || !ids_out) return (rs_status)fail(RS_EINVAL, "rs_topk: NULL argument");
+    if (k < 1 || (int64_t)k > g->n || k > 16384)
+        return (rs_status)fail(RS_EINVAL, "rs_topk: k must be in [1, min(n, 16384)]");
+    return (rs_status)topk_scores(g, scores, g->n, k, ids_out, scores_out, as_stream(stream));
+}

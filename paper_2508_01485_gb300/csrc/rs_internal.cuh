@@ -1,0 +1,136 @@
+// rs_internal.cuh -- device graph layout and kernels shared by the library's
+// translation units.  Not part of the public ABI (include/rs.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "rs_numeric.cuh"
+
+namespace rs {
+
+// Row classes by degree (and by the community count k, which bounds the number
+// of distinct neighbour communities):
+//   small: d <= 32, one warp per row, everything in registers;
+//   mid:   a shared-memory hash table of cap = pow2 >= 2 min(d, k) slots fits
+//          (cap <= kMidCap), one CTA per row;
+//   hub:   larger rows; a hash table in global memory, rows split into chunks
+//          of kHubChunk neighbours processed by separate CTAs and merged by
+//          atomics into the row's table.
+constexpr int kSmallMax = 32;
+constexpr int kMidCap = 2048;
+constexpr int kHubChunk = 4096;
+constexpr int32_t kEmpty = -1;
+
+// per-node record written by the first pass and gathered by the second
+struct __align__(16) NodeRec {
+    uint64_t s_fix;   // s_v = w_v(C(v))^(1/3) in 2^-52 fixed point
+    int32_t label;    // C(v)
+    int32_t dx;       // cross-community degree (neighbours with another label)
+};
+
+// per-hub state (global hash table and row aggregates)
+struct HubInfo {
+    int32_t row;
+    int32_t cap;          // table slots (power of two)
+    int64_t tab;          // first slot in the hub table arrays
+    int32_t first_item;   // first chunk item of this hub
+    int32_t n_items;
+};
+struct __align__(16) HubAgg {
+    u128 X;               // sum over foreign groups of f LG[f] (own group added later)
+    uint32_t L;           // foreign groups
+    uint32_t own;         // neighbours in C(row)
+    uint32_t pad[2];
+};
+
+inline uint32_t pow2_at_least(uint64_t x) {
+    uint32_t c = 1;
+    while (c < x) c <<= 1;
+    return c;
+}
+
+__device__ __forceinline__ uint32_t hash_label(int32_t c) { return (uint32_t)c * 0x9E3779B1u; }
+
+// whether u is ordered after w for triangle orientation: (dx, id) ascending
+__device__ __forceinline__ bool rank_after(int32_t dxu, int32_t u, int32_t dxw, int32_t w) {
+    return dxu > dxw || (dxu == dxw && u > w);
+}
+
+}  // namespace rs
+
+struct rs_graph {
+    int64_t n = 0, nnz = 0;
+    int32_t k = 0, dmax = 0;
+    int device = 0;
+    // CSR (int64 offsets) and labels; *_alt are the compaction targets of removals
+    int64_t *off = nullptr, *off_alt = nullptr;
+    int32_t *col = nullptr, *col_alt = nullptr;
+    int32_t *lab = nullptr;
+    uint8_t *removed = nullptr;       // n removed-node flags
+    uint8_t *dead = nullptr;          // nnz edge marks used by removals
+    // row classes
+    int32_t *rows_small = nullptr, *rows_mid = nullptr;
+    int64_t n_small = 0, n_mid = 0;
+    int32_t mid_cap = 0;              // largest table among mid rows
+    rs::HubInfo *hubs = nullptr;      // device copy
+    int32_t *hub_items = nullptr;     // per chunk item: hub index
+    int32_t *hub_item_chunk = nullptr;// per chunk item: chunk number within the hub
+    int64_t n_hubs = 0, n_hub_items = 0, hub_slots = 0;
+    int32_t *hkey = nullptr;          // hub hash tables
+    uint32_t *hcnt = nullptr;
+    unsigned long long *hq = nullptr; // 2 words per slot
+    rs::df *hsig = nullptr;           // per slot sigma of the column
+    rs::HubAgg *hagg = nullptr;
+    int32_t *hitem_out = nullptr, *hitem_in = nullptr;  // per item G_x out / in counts
+    // constant tables, sized dmax + 1
+    uint64_t *LG = nullptr;           // round(log2(f) 2^58)
+    double *RD = nullptr;             // 1 / (d (d - 1))
+    // scoring workspace
+    rs::NodeRec *rec = nullptr;
+    unsigned long long *acc = nullptr;        // 2 words per node
+    unsigned long long *wmax_bits = nullptr;  // double bits of w_max
+    int32_t *Lall = nullptr;                  // distinct neighbour communities per node
+    int64_t *xoff = nullptr;                  // G_x row offsets (n + 1)
+    int32_t *xcol = nullptr;                  // G_x neighbours (capacity nnz)
+    rs::df *xS = nullptr;                     // S(w -> u) = w_w(C(u))^(1/3)
+    int32_t *xout = nullptr, *xin = nullptr;  // out / in counts per node
+    int64_t *scan_tmp = nullptr;              // block sums for scans
+    // top-k workspace
+    uint32_t *tk_hist = nullptr;
+    int32_t *tk_ctrl = nullptr;
+    unsigned long long *tk_keys = nullptr;    // candidate (key, id) pairs
+    int32_t *tk_ids = nullptr;
+    int64_t tk_cap = 0;
+    // misc
+    int32_t *d_flag = nullptr;                // device error / scalar slot
+};
+
+namespace rs {
+
+constexpr int kThreads = 256;
+
+// error reporting (rs_api.cu): returns the status after recording the message
+int fail(int status, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *where);
+#define RS_CUDA_TRY(expr)                                            \
+    do {                                                             \
+        cudaError_t _e = (expr);                                     \
+        if (_e != cudaSuccess) return ::rs::cuda_fail(_e, #expr);    \
+    } while (0)
+
+// in-place inclusive scan of a[0..m) (int64), tmp >= scan_tmp_words(m) words
+int64_t scan_tmp_words(int64_t m);
+int inclusive_scan_i64(int64_t *a, int64_t m, int64_t *tmp, cudaStream_t s);
+
+// grid size for grid-stride kernels: at most `cap_per_sm` CTAs per SM
+int grid_for(int64_t items, int per_block, int cap_per_sm);
+
+// scoring (rs_score.cu) and ranking (rs_topk.cu); return an rs_status value
+int score_graph(rs_graph *g, double *scores, cudaStream_t s);
+int topk_scores(rs_graph *g, const double *scores, int64_t n, int32_t k, int32_t *ids,
+                double *out_scores, cudaStream_t s);
+int interaction_table(rs_graph *g, int64_t *t_out, int64_t *row_ptr, int32_t *comm,
+                      int32_t *count, cudaStream_t s);
+
+}  // namespace rs

@@ -1,0 +1,224 @@
+// rs_numeric.cuh -- exact integer and double-float arithmetic for RSI scoring.
+//
+// GB300 (sm_103a) executes FP64 at 1/64 of its FP32 rate, so the per-edge and
+// per-column arithmetic of the score runs on the integer and FP32 pipes:
+//
+//  * entropy numerators E = Y log2 Y - sum_j f_j log2 f_j (Eq. H_optimal of
+//    Sec. IV-B, with Y = T - f_i) are exact 128-bit integer sums of a log2
+//    table LG[f] = round(log2(f) 2^58); the only error is the table's
+//    rounding, |dE| <= Y 2^-58, and E >= log2 Y + 1.44 whenever two or more
+//    communities remain, so E/Y keeps ~1e-14 relative accuracy for Y <= 1e5;
+//  * quotients, cube roots and products use double-float numbers (an
+//    unevaluated sum hi + lo of two floats, ~2^-48 relative; Dekker 1971,
+//    "A floating-point technique for extending the available precision");
+//  * every sum of terms is accumulated in 128-bit fixed point (2^-64 lsb), so
+//    atomics commute and results are bit-identical whatever the schedule.
+#pragma once
+#include <stdint.h>
+
+namespace rs {
+
+typedef unsigned __int128 u128;
+
+constexpr int kLogFrac = 58;      // LG[f] = round(log2(f) * 2^58)
+constexpr int kSFrac = 52;        // node scalar s_v stored as round(s_v * 2^52)
+constexpr int kAccFrac = 64;      // accumulators: 2^-64 lsb
+
+// ---- double-float ----------------------------------------------------------
+
+struct df { float hi, lo; };
+
+__device__ __forceinline__ df df_make(float a) { return df{a, 0.0f}; }
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df{s, e};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {   // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return df{s, e};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return df{p, e};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    df t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+    df p = two_prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+    p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+    return quick_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    df p = two_prod(a.hi, b);
+    p.lo = __fmaf_rn(a.lo, b, p.lo);
+    return quick_two_sum(p.hi, p.lo);
+}
+// a / y for an integer 1 <= y < 2^24 (exact as a float)
+__device__ __forceinline__ df df_div_u32(df a, uint32_t y) {
+    float fy = (float)y;
+    float r = __frcp_rn(fy);
+    float q1 = __fmul_rn(a.hi, r);
+    df p = two_prod(q1, fy);
+    float rem = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p.hi), p.lo), a.lo);
+    float q2 = __fmul_rn(rem, r);
+    df q = quick_two_sum(q1, q2);
+    // one more correction step: residual of q against a
+    df back = df_mul_f(q, fy);
+    float rem2 = __fadd_rn(__fsub_rn(a.hi, back.hi), __fsub_rn(a.lo, back.lo));
+    return df_add(q, df_make(__fmul_rn(rem2, r)));
+}
+// a^(1/3), a >= 0: float seed, one Newton step evaluated in double-float
+__device__ __forceinline__ df df_cbrt(df a) {
+    if (!(a.hi > 0.0f)) return df{0.0f, 0.0f};
+    float y = cbrtf(a.hi);
+    df y2 = two_prod(y, y);                       // y^2 exactly
+    df y3 = df_mul_f(y2, y);                      // y^3
+    df r = df_add(a, df{-y3.hi, -y3.lo});         // a - y^3
+    float c = __fmul_rn(r.hi, __frcp_rn(__fmul_rn(3.0f, y2.hi)));
+    return two_sum(y, c);
+}
+__device__ __forceinline__ bool df_less(df a, df b) {
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ df df_max(df a, df b) { return df_less(a, b) ? b : a; }
+
+// ---- conversions -------------------------------------------------------------
+
+// x * 2^e as double-float, keeping the top 48 significant bits of x
+__device__ __forceinline__ df df_from_u128(u128 x, int e) {
+    if (x == 0) return df{0.0f, 0.0f};
+    uint64_t h = (uint64_t)(x >> 64);
+    int lz = h ? __clzll((long long)h) : 64 + __clzll((long long)(uint64_t)x);
+    int top = 127 - lz;                           // index of the leading bit
+    int sh = top - 47;                            // keep bits [top-47, top]
+    uint64_t m48 = sh >= 0 ? (uint64_t)(x >> sh) : (uint64_t)x << (-sh);
+    uint32_t mh = (uint32_t)(m48 >> 24), ml = (uint32_t)(m48 & 0xFFFFFFu);
+    float hi = ldexpf((float)mh, sh + 24 + e);
+    float lo = ldexpf((float)ml, sh + e);
+    return quick_two_sum(hi, lo);
+}
+__device__ __forceinline__ df df_from_u64(uint64_t x, int e) { return df_from_u128((u128)x, e); }
+
+// the exact value of a finite float as (mantissa, exponent): f = m * 2^q
+__device__ __forceinline__ void float_parts(float f, int32_t &m, int &q) {
+    uint32_t b = __float_as_uint(f);
+    int ex = (int)((b >> 23) & 0xFF);
+    int32_t mant = (int32_t)(b & 0x7FFFFF);
+    if (ex == 0) { q = -149; } else { mant |= 0x800000; q = ex - 150; }
+    m = (b >> 31) ? -mant : mant;
+}
+// signed value m * 2^(q + frac) as a 128-bit integer (bits below 1 are dropped toward 0)
+__device__ __forceinline__ __int128 scaled_i128(int32_t m, int q) {
+    __int128 v = (__int128)m;
+    if (q >= 0) return v << q;
+    int s = -q;
+    if (s >= 63) return 0;
+    return m >= 0 ? (v >> s) : -((-v) >> s);
+}
+// round-toward-zero of a * 2^frac for a >= 0 as an unsigned 128-bit integer
+__device__ __forceinline__ u128 df_to_fixed(df a, int frac) {
+    int32_t mh, ml; int qh, ql;
+    float_parts(a.hi, mh, qh);
+    float_parts(a.lo, ml, ql);
+    __int128 v = scaled_i128(mh, qh + frac) + scaled_i128(ml, ql + frac);
+    return v > 0 ? (u128)v : (u128)0;
+}
+
+// correctly rounded (nearest, ties to even) double of x * 2^e, x < 2^128, |e| moderate
+__device__ __forceinline__ double u128_to_double(u128 x, int e) {
+    if (x == 0) return 0.0;
+    uint64_t h = (uint64_t)(x >> 64);
+    int lz = h ? __clzll((long long)h) : 64 + __clzll((long long)(uint64_t)x);
+    int top = 127 - lz;
+    uint64_t mant;
+    if (top <= 52) {
+        mant = (uint64_t)x << (52 - top);
+    } else {
+        int sh = top - 52;
+        mant = (uint64_t)(x >> sh);
+        u128 rem = x & (((u128)1 << sh) - 1);
+        u128 half = (u128)1 << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1))) {
+            mant++;
+            if (mant >> 53) { mant >>= 1; top++; }
+        }
+    }
+    int exp2 = top + e;                            // value = 1.mant * 2^exp2
+    int biased = exp2 + 1023;
+    if (biased <= 0) return 0.0;                   // never reached for scores
+    uint64_t bits = ((uint64_t)biased << 52) | (mant & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+// ---- 128-bit accumulators -------------------------------------------------------
+
+// acc[0] holds the low 64 bits, acc[1] the high 64 bits; concurrent adds commute
+__device__ __forceinline__ void atomic_add_u128(unsigned long long *acc, u128 v) {
+    unsigned long long lo = (unsigned long long)(uint64_t)v;
+    unsigned long long hi = (unsigned long long)(uint64_t)(v >> 64);
+    if (lo) {
+        unsigned long long old = atomicAdd(acc, lo);
+        if (old + lo < old) hi += 1ull;
+    }
+    if (hi) atomicAdd(acc + 1, hi);
+}
+
+// ---- warp reductions ---------------------------------------------------------------
+
+__device__ __forceinline__ u128 shfl_xor_u128(u128 v, int m) {
+    uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
+    lo = __shfl_xor_sync(0xFFFFFFFFu, lo, m);
+    hi = __shfl_xor_sync(0xFFFFFFFFu, hi, m);
+    return ((u128)hi << 64) | lo;
+}
+__device__ __forceinline__ u128 warp_sum_u128(u128 v) {
+    for (int m = 16; m; m >>= 1) v += shfl_xor_u128(v, m);
+    return v;
+}
+__device__ __forceinline__ df warp_max_df(df v) {
+    for (int m = 16; m; m >>= 1) {
+        df o{__shfl_xor_sync(0xFFFFFFFFu, v.hi, m), __shfl_xor_sync(0xFFFFFFFFu, v.lo, m)};
+        v = df_max(v, o);
+    }
+    return v;
+}
+
+// ---- entropy weights (Eq. entropy / weight via Eq. H_optimal) ----------------------
+//
+// Row aggregates of node v over its neighbour communities: T = d(v), L = number
+// of distinct communities, X = sum_c f_c LG[f_c] (exact).  The weight of column
+// c with count f (f = 0 for a community absent from N(v)) is
+//     w = H(L_c) |L_c|,  H(L_c) = E / Y,  Y = T - f,  E = Y LG[Y] - (X - f LG[f]),
+// |L_c| = L - [f > 0], and w = 0 when |L_c| < 2.
+struct RowAgg {
+    uint32_t T;      // degree
+    uint32_t L;      // distinct communities among the neighbours
+    u128 X;          // sum_c f_c * LG[f_c]
+};
+
+__device__ __forceinline__ df column_weight(const RowAgg &a, uint32_t f, const uint64_t *LG) {
+    uint32_t Lc = a.L - (f > 0 ? 1u : 0u);
+    if (Lc < 2) return df{0.0f, 0.0f};
+    uint32_t Y = a.T - f;
+    u128 rest = a.X - (u128)f * LG[f];
+    u128 yy = (u128)Y * LG[Y];
+    u128 E = yy > rest ? yy - rest : (u128)0;
+    df H = df_div_u32(df_from_u128(E, -kLogFrac), Y);
+    return df_mul_f(H, (float)Lc);
+}
+
+}  // namespace rs

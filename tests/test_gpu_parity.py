@@ -1,0 +1,111 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Scores within 1e-12 relative (the bound the BASELINE states for the fp64
+score); counts, removals and top-K ids bit-exact.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from tests.conftest import csr_from_edges, random_tiny_graph
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def rs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2508_01485_gb300 as rsgpu
+    return rsgpu
+
+
+def gpu_scores(rs, off, cols, labels, k):
+    G = rs.Graph.build(off, cols, labels, k)
+    s, wmax = G.score(want_omega_max=True)
+    return G, s.cpu().numpy(), wmax
+
+
+def assert_scores(got, ref, rtol=RTOL):
+    got, ref = np.asarray(got), np.asarray(ref)
+    assert got.shape == ref.shape
+    assert ((ref == 0) == (got == 0)).all(), "zero pattern differs"
+    nz = ref != 0
+    rel = np.abs(got[nz] - ref[nz]) / ref[nz]
+    assert rel.size == 0 or rel.max() <= rtol, "max rel err %.3e" % rel.max()
+
+
+def test_closed_forms(rs):
+    from tests.test_oracle_pins import open_triad, pendant_triangle, PENDANT_R, OPEN_R
+    off, cols, labels, k = pendant_triangle()
+    _, s, wmax = gpu_scores(rs, off, cols, labels, k)
+    np.testing.assert_allclose(s, [PENDANT_R] * 3 + [0, 0, 0], rtol=RTOL, atol=0)
+    assert abs(wmax - 3 * np.log2(3)) < 1e-13
+    off, cols, labels, k = open_triad()
+    _, s, wmax = gpu_scores(rs, off, cols, labels, k)
+    np.testing.assert_allclose(s, OPEN_R, rtol=RTOL, atol=0)
+    assert abs(wmax - 4.5) < 1e-13
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_tiny_graphs(rs, seed):
+    rng = np.random.default_rng(1000 + seed)
+    for _ in range(25):
+        n = int(rng.integers(3, 40))
+        k = int(rng.integers(2, 8))
+        off, cols, labels = random_tiny_graph(rng, n, k, float(rng.uniform(0.05, 0.6)))
+        o = oracle.Oracle(off, cols, labels, k)
+        _, s, wmax = gpu_scores(rs, off, cols, labels, k)
+        assert abs(wmax - o.wmax) <= 1e-13 * max(o.wmax, 1e-300)
+        assert_scores(s, o.scores())
+
+
+def test_sbm_2000_full(rs):
+    g = graphgen.sbm_2000()
+    o = oracle.Oracle.from_graph(g)
+    ref = o.scores()
+    G, s, wmax = gpu_scores(rs, g.offsets, g.cols, g.labels, g.k)
+    assert abs(wmax - o.wmax) <= 1e-13 * o.wmax
+    assert_scores(s, ref)
+    ids, vals = G.topk(torch.as_tensor(s, device="cuda"), 50)
+    assert ids.cpu().numpy().tolist() == oracle.topk(ref, 50).tolist()
+
+
+@pytest.mark.parametrize("n,seed,dmax", [(20000, 11, 1000), (50000, 12, 3000)])
+def test_dcsbm_small_full(rs, n, seed, dmax):
+    g = graphgen.dcsbm_small(n, seed, dmax=dmax)
+    o = oracle.Oracle.from_graph(g)
+    ref = o.scores()
+    G, s, wmax = gpu_scores(rs, g.offsets, g.cols, g.labels, g.k)
+    assert abs(wmax - o.wmax) <= 1e-13 * o.wmax
+    assert_scores(s, ref)
+    for K in (1, 100, 1000):
+        ids, _ = G.topk(torch.as_tensor(s, device="cuda"), K)
+        assert ids.cpu().numpy().tolist() == oracle.topk(ref, K).tolist()
+
+
+def test_interaction_counts(rs):
+    g = graphgen.dcsbm_small(20000, 5, dmax=1000)
+    G = rs.Graph.from_generated(g)
+    rp, comm, cnt = G.interaction()
+    ptr, ocomm, ocnt = oracle.Oracle.from_graph(g).table()
+    np.testing.assert_array_equal(rp.cpu().numpy(), ptr)
+    np.testing.assert_array_equal(comm.cpu().numpy(), ocomm)
+    np.testing.assert_array_equal(cnt.cpu().numpy(), ocnt)
+
+
+def test_dcsbm_hub_rows_full(rs):
+    """k = 2000 and degrees up to 5000: rows with more than 1024 distinct-capable
+    neighbours take the multi-CTA hub path."""
+    g = graphgen.dcsbm_small(200000, 12, dmax=5000)
+    o = oracle.Oracle.from_graph(g)
+    ref = o.scores()
+    G, s, wmax = gpu_scores(rs, g.offsets, g.cols, g.labels, g.k)
+    assert abs(wmax - o.wmax) <= 1e-13 * o.wmax
+    assert_scores(s, ref)
+    ids, _ = G.topk(torch.as_tensor(s, device="cuda"), 1000)
+    assert ids.cpu().numpy().tolist() == oracle.topk(ref, 1000).tolist()
