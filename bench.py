@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""RS-scored edges/s of Robust Spanning Index scoring on GB300.
+
+One step = rs_score (every node's R(u), Alg. 1 Steps 1-3) + rs_topk (top-1000,
+Step 4) over one graph resident in HBM.  Workload: the 1M-node social-shaped
+degree-corrected SBM (1,000 power-law communities, degree power law 2.5 on
+[8, 5000], mixing 0.2, ~10.3M undirected edges), synthetic and seeded.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` = undirected edges scored per second
+over all ranks (weak scaling: each rank scores its own replica); `e2e` is the
+same metric through the C ABI from pinned host buffers with the host<->device
+copies inside the timed region; `roofline` is the dominant kernel's
+algorithmic bytes over its CUDA-event time against the measured HBM peak;
+`cpu_baseline` times the CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TOPK = 1000
+FLUSH_BYTES = 512 << 20          # > 2x the 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="dcsbm-1m")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-json", default="")
+    return ap.parse_args()
+
+
+def workload(name):
+    import graphgen
+    if name == "dcsbm-1m":
+        return graphgen.dcsbm_1m()
+    if name == "dcsbm-8m":
+        return graphgen.dcsbm_8m()
+    if name == "sbm-2k":
+        return graphgen.sbm_2000()
+    if name.startswith("dcsbm-small-"):
+        return graphgen.dcsbm_small(int(name.split("-")[-1]), seed=7)
+    raise SystemExit("unknown workload " + name)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---- algorithmic bytes (model stated in the design doc) ---------------------------------
+
+def graph_stats(g):
+    import numpy as np
+    deg = np.diff(g.offsets)
+    n, E = g.n, g.nnz
+    rows = np.repeat(np.arange(n, dtype=np.int64), deg)
+    lab = g.labels
+    cross = lab[rows] != lab[g.cols]
+    dx = np.bincount(rows[cross], minlength=n)
+    keep = cross & (dx[rows] >= 2) & (dx[g.cols] >= 2)
+    small = deg <= 32
+    return {
+        "n": n, "E": E, "m": E // 2, "k": g.k,
+        "n_small": int(small.sum()), "E_small": int(deg[small].sum()),
+        "gx_slots": int(keep.sum()), "gx_slots_small": int((keep & small[rows]).sum()),
+        "dmax": int(deg.max()) if n else 0,
+    }
+
+
+def kernel_bytes(name, st):
+    """Compulsory HBM bytes of one launch of a kernel (gathered arrays once)."""
+    n, E = st["n"], st["E"]
+    Rs, Es = st["n_small"], st["E_small"]
+    if name == "p1_small":
+        # row ids, offsets, columns, own label, node record + L written; the
+        # labels gathered by the columns (4 n bytes) are L2-resident after first touch
+        return 4 * Rs + 8 * Rs + 4 * Es + 4 * Rs + 20 * Rs + 4 * n * Es / max(E, 1)
+    if name == "p2_small":
+        # row ids, offsets, columns, own record, G_x slots (4 + 8 B) and counts;
+        # node records gathered (16 n B once)
+        return 4 * Rs + 8 * Rs + 4 * Es + 16 * Rs + 12 * st["gx_slots_small"] + 8 * Rs + 16 * n * Es / max(E, 1)
+    if name == "finalize":
+        return 16 * n + 16 * n + 8 * n
+    return None
+
+
+def step_bytes(st):
+    """Compulsory bytes of a whole step (both CSR streams, node records, G_x, accumulators, scores)."""
+    n, E = st["n"], st["E"]
+    return (2 * (8 * (n + 1) + 4 * E) + 4 * n + 20 * n + 16 * n + 8 * (n + 1) + 12 * st["gx_slots"] * 2
+            + 8 * n + 16 * n * 2 + 8 * n + 8 * n * 2)
+
+
+# ---- clocks --------------------------------------------------------------------------
+
+class Clocks:
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1])); smax.append(float(c[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, c[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---- CPU oracle baseline ----------------------------------------------------------------
+
+def cpu_oracle_rate(g, budget_s, seed=0):
+    """Oracle edges/s on a bounded sample: weight tables for the whole graph, then
+    R(u) for a seeded random sample of nodes sized to ~budget_s; the full-graph
+    time is extrapolated as tables + per-node time x n."""
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    o = oracle.Oracle.from_graph(g, validate=False)
+    t_tab = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    sample, spent, scored = 64, 0.0, 0
+    while True:
+        ids = rng.integers(0, g.n, size=sample).astype(np.int32)
+        t1 = time.perf_counter()
+        o.scores(ids)
+        dt = time.perf_counter() - t1
+        spent += dt
+        scored += sample
+        if spent + t_tab >= budget_s or scored >= g.n:
+            break
+        sample = int(min(g.n, sample * 2))
+    per_node = spent / scored
+    est = t_tab + per_node * g.n
+    o.close()
+    return {"value": g.m / est, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": "weight tables + w_max for all %d nodes (%.2f s), literal R(u) for %d seeded random "
+                      "nodes (%.2f s); full-graph time extrapolated as tables + per-node mean x n = %.1f s"
+                      % (g.n, t_tab, scored, spent, est),
+            "est_full_seconds": est}
+
+
+# ---- our arm ----------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_2508_01485_gb300 as rsgpu
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    g = workload(args.workload)
+    st = graph_stats(g)
+    G = rsgpu.Graph.from_generated(g, validate=True)
+    stream = torch.cuda.current_stream()
+    scores = torch.empty(g.n, dtype=torch.float64, device=dev)
+    ids = torch.empty(TOPK, dtype=torch.int32, device=dev)
+    vals = torch.empty(TOPK, dtype=torch.float64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        G.score_into(scores)
+        G.topk_into(scores, TOPK, ids, vals)
+
+    for i in range(args.warmup):
+        flush.fill_(i & 0xFF)
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: per-step CUDA events on the launching stream; L2 flushed between steps
+    clocks = Clocks(local)
+    G.profile_enable(True)
+    launches0 = G.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_((i + 7) & 0xFF)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = G.launch_count() - launches0
+    prof = G.profile_read()
+    G.profile_enable(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * st["m"] * args.steps / (total_ms / 1e3)
+
+    # per-kernel totals over the timed steps
+    per = {}
+    for name, ms, isk in prof:
+        d = per.setdefault(name, {"ms": 0.0, "launches": 0, "kernel": isk})
+        d["ms"] += ms
+        d["launches"] += 1
+    prof_sum = sum(d["ms"] for d in per.values())
+    top_name = max((k for k in per if per[k]["kernel"]), key=lambda k: per[k]["ms"])
+    top = per[top_name]
+    avg_ms = top["ms"] / top["launches"]
+    hbm, peak_kind = peaks()
+    kb = kernel_bytes(top_name, st)
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        with open(tr_path) as f:
+            tr = json.load(f)
+        if tr.get("csrc_sha") == csrc_sha() and tr.get("workload") == args.workload:
+            traffic = tr.get("kernels", {}).get(top_name)
+    roofline = {
+        "bound": "hbm", "kernel": top_name,
+        "achieved": (kb / (avg_ms / 1e3) / 1e9) if kb else None,
+        "peak": hbm, "unit": "GB/s",
+        "frac": (kb / (avg_ms / 1e3) / 1e9 / hbm) if kb else None,
+        "traffic": traffic, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+        "kernel_ms": avg_ms, "kernel_share": top["ms"] / prof_sum if prof_sum else None,
+        "algorithmic_bytes": kb,
+        "step_achieved": step_bytes(st) / (statistics.mean(step_ms) / 1e3) / 1e9,
+        "step_frac": step_bytes(st) / (statistics.mean(step_ms) / 1e3) / 1e9 / hbm,
+        "step_bytes": step_bytes(st),
+    }
+
+    # end to end through the C ABI from pinned host buffers
+    pin_off = torch.from_numpy(g.offsets).pin_memory().numpy()
+    pin_col = torch.from_numpy(g.cols).pin_memory().numpy()
+    pin_lab = torch.from_numpy(g.labels).pin_memory().numpy()
+    host_ids = torch.empty(TOPK, dtype=torch.int32).pin_memory()
+    host_vals = torch.empty(TOPK, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G2 = rsgpu.Graph.build(pin_off, pin_col, pin_lab, g.k, validate=True)
+        G2.score_into(scores)
+        G2.topk_into(scores, TOPK, ids, vals)
+        host_ids.copy_(ids, non_blocking=True)
+        host_vals.copy_(vals, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        G2.close()
+    e2e_ms = e2e_ms[1:]  # first call pays one-time kernel attribute setup
+    te = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * st["m"] * len(e2e_ms) / (float(te.item()) / 1e3) if e2e_ms else None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_rate(g, args.cpu_seconds)
+        cpu.pop("est_full_seconds", None)
+
+    out = {
+        "metric": "RS-scored edges/s", "value": value, "unit": "edges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "arith": "int128 fixed-point sums + double-float (2 x f32) products; fp64 outputs",
+        "data": "synthetic",
+        "config": {"workload": g.name, "n": g.n, "m": st["m"], "k": g.k, "max_degree": st["dmax"],
+                   "topk": TOPK, "step": "rs_score + rs_topk on a resident graph",
+                   "l2": "flushed between timed steps (512 MB write outside the events)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "edges/s",
+                "h2d_bytes_per_step": int(g.offsets.nbytes + g.cols.nbytes + g.labels.nbytes),
+                "d2h_bytes_per_step": int(host_ids.numel() * 4 + host_vals.numel() * 8),
+                "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None,
+                "step": "rs_build_graph (pinned host CSR, RS_VALIDATE) + rs_score + rs_topk + top-K to host"},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if args.profile_json and rank == 0:
+        with open(args.profile_json, "w") as f:
+            json.dump({"per_kernel": per, "step_ms": step_ms, "stats": st}, f, indent=1)
+    if rank == 0:
+        print(json.dumps(out))
+    G.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def csrc_sha():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2508_01485_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ---- reference arm: the CPU oracle ----------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    g = workload(args.workload)
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    o = oracle.Oracle.from_graph(g, validate=False)
+    t_tab = time.perf_counter() - t0
+    rng = np.random.default_rng(1)
+    per_step_nodes = 4096
+    rates, est_ms = [], []
+    for i in range(args.warmup + args.steps):
+        ids = rng.integers(0, g.n, size=per_step_nodes).astype(np.int32)
+        t1 = time.perf_counter()
+        o.scores(ids)
+        dt = time.perf_counter() - t1
+        est = t_tab + dt / per_step_nodes * g.n
+        if i >= args.warmup:
+            rates.append(g.m / est)
+            est_ms.append(est * 1e3)
+    value = statistics.mean(rates)
+    sample = ("weight tables + w_max for all %d nodes (%.2f s, once); per step literal R(u) for %d seeded "
+              "random nodes; step time extrapolated as tables + per-node mean x n" % (g.n, t_tab, per_step_nodes))
+    out = {"metric": "RS-scored edges/s", "value": value, "unit": "edges/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(est_ms),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": g.name, "n": g.n, "m": g.m, "k": g.k, "topk": TOPK},
+           "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

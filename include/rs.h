@@ -140,6 +140,24 @@ rs_status rs_clone_graph(const rs_graph *g, rs_graph **out, void *stream);
 /* rs_graph_info -- sizes of a graph (any pointer may be NULL). */
 rs_status rs_graph_info(const rs_graph *g, int64_t *n, int64_t *nnz, int32_t *k, int32_t *max_degree);
 
+/*
+ * Instrumentation (no counterpart in the paper; used by benchmarks and tuning).
+ *
+ * rs_profile_enable -- when enable != 0, every later rs_score / rs_topk call on
+ *   g records a CUDA event on its stream after each device operation; the
+ *   record is cleared by every rs_profile_enable call.
+ * rs_profile_read -- waits for the last recorded event, then returns up to
+ *   `cap` entries in order: names[i] (static strings owned by the library),
+ *   ms[i] the device time since the previous event of the same call, and
+ *   is_kernel[i] (1 for a kernel of this library, 0 for a memset).  *n_out is
+ *   the number of entries recorded (may exceed cap).  Any array may be NULL.
+ * rs_launch_count -- number of kernels this library has launched for g.
+ */
+rs_status rs_profile_enable(rs_graph *g, int enable);
+rs_status rs_profile_read(rs_graph *g, int32_t *n_out, const char **names, float *ms, int32_t *is_kernel,
+                          int32_t cap);
+rs_status rs_launch_count(const rs_graph *g, int64_t *launches);
+
 /* rs_free_graph -- release a graph and its device memory (NULL is a no-op). */
 void rs_free_graph(rs_graph *g);
 

@@ -51,6 +51,12 @@ def lib():
         L.rs_graph_info.restype = I
         L.rs_graph_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32),
                                     ctypes.POINTER(I32)]
+        L.rs_profile_enable.restype = I
+        L.rs_profile_enable.argtypes = [P, I]
+        L.rs_profile_read.restype = I
+        L.rs_profile_read.argtypes = [P, ctypes.POINTER(I32), P, P, P, I32]
+        L.rs_launch_count.restype = I
+        L.rs_launch_count.argtypes = [P, ctypes.POINTER(I64)]
         L.rs_free_graph.restype = None
         L.rs_free_graph.argtypes = [P]
         L.rs_last_error.restype = ctypes.c_char_p
@@ -134,6 +140,16 @@ class Graph:
         _check(lib().rs_graph_info(self._h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(k), ctypes.byref(dmax)))
         return {"n": n.value, "nnz_capacity": nnz.value, "k": k.value, "max_degree": dmax.value}
 
+    def score_into(self, out, stream=None):
+        """rs_score into a preallocated float64 CUDA tensor (no host synchronisation)."""
+        _check(lib().rs_score(self._h, _ptr(out), None, _stream(stream)))
+        return out
+
+    def topk_into(self, scores, k, ids, vals, stream=None):
+        """rs_topk into preallocated int32 / float64 CUDA tensors."""
+        _check(lib().rs_topk(self._h, _ptr(scores), int(k), _ptr(ids), _ptr(vals), _stream(stream)))
+        return ids, vals
+
     def score(self, out=None, stream=None, want_omega_max=False):
         """rs_score: R(u) for every node as a float64 CUDA tensor (and w_max if asked)."""
         import torch
@@ -174,6 +190,26 @@ class Graph:
                                        ctypes.c_void_p(ed.ctypes.data if ed.size else None), es.size,
                                        ctypes.byref(applied), _stream(stream)))
         return applied.value
+
+    def profile_enable(self, enable=True):
+        """Start (or stop) recording per-kernel device times; clears the record."""
+        _check(lib().rs_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """[(name, ms, is_kernel)] for every operation recorded since profile_enable."""
+        n = ctypes.c_int32(0)
+        _check(lib().rs_profile_read(self._h, ctypes.byref(n), None, None, None, 0))
+        cap = n.value
+        names = (ctypes.c_char_p * max(cap, 1))()
+        ms = (ctypes.c_float * max(cap, 1))()
+        isk = (ctypes.c_int32 * max(cap, 1))()
+        _check(lib().rs_profile_read(self._h, ctypes.byref(n), names, ms, isk, cap))
+        return [(names[i].decode(), float(ms[i]), bool(isk[i])) for i in range(min(cap, n.value))]
+
+    def launch_count(self):
+        c = ctypes.c_int64(0)
+        _check(lib().rs_launch_count(self._h, ctypes.byref(c)))
+        return c.value
 
     def clone(self, stream=None):
         h = ctypes.c_void_p()

@@ -107,19 +107,81 @@ int64_t rs::scan_tmp_words(int64_t m) {
     return words + 1;
 }
 
-int rs::inclusive_scan_i64(int64_t *a, int64_t m, int64_t *tmp, cudaStream_t s) {
+int rs::inclusive_scan_i64(int64_t *a, int64_t m, int64_t *tmp, cudaStream_t s, int64_t *launches) {
     if (m <= 0) return 0;
     int64_t tiles = (m + kScanTile - 1) / kScanTile;
     if (tiles > 2147483647LL) return fail(RS_EINVAL, "scan too large");
     scan_tile_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(a, m, tiles > 1 ? tmp : nullptr);
     RS_CUDA_TRY(cudaGetLastError());
+    if (launches) ++*launches;
     if (tiles > 1) {
-        int rc = inclusive_scan_i64(tmp, tiles, tmp + tiles + 1, s);
+        int rc = inclusive_scan_i64(tmp, tiles, tmp + tiles + 1, s, launches);
         if (rc) return rc;
         scan_add_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(a, m, tmp);
         RS_CUDA_TRY(cudaGetLastError());
+        if (launches) ++*launches;
     }
     return 0;
+}
+
+// ---------------------------------------------------------------------------
+// launch accounting / per-kernel event timing
+// ---------------------------------------------------------------------------
+static void prof_record(rs_graph *g, cudaStream_t s, const char *name, bool is_kernel) {
+    if (g->prof_used == g->prof_ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { g->prof_on = false; return; }
+        g->prof_ev.push_back(e);
+        g->prof_name.push_back(nullptr);
+        g->prof_is_kernel.push_back(0);
+    }
+    cudaEventRecord(g->prof_ev[g->prof_used], s);
+    g->prof_name[g->prof_used] = name;
+    g->prof_is_kernel[g->prof_used] = is_kernel ? 1 : 0;
+    g->prof_used++;
+}
+void rs::prof_begin(rs_graph *g, cudaStream_t s) {
+    if (g->prof_on) prof_record(g, s, nullptr, false);
+}
+void rs::prof_mark(rs_graph *g, cudaStream_t s, const char *name, bool is_kernel) {
+    if (is_kernel) g->launches++;
+    if (g->prof_on) prof_record(g, s, name, is_kernel);
+}
+
+extern "C" rs_status rs_profile_enable(rs_graph *g, int enable) {
+    if (!g) return (rs_status)fail(RS_EINVAL, "rs_profile_enable: NULL graph");
+    g->prof_on = enable != 0;
+    g->prof_used = 0;
+    return RS_OK;
+}
+
+extern "C" rs_status rs_profile_read(rs_graph *g, int32_t *n_out, const char **names, float *ms,
+                                     int32_t *is_kernel, int32_t cap) {
+    if (!g || !n_out) return (rs_status)fail(RS_EINVAL, "rs_profile_read: NULL argument");
+    int32_t n = 0;
+    if (g->prof_used) {
+        if (cudaError_t e = cudaEventSynchronize(g->prof_ev[g->prof_used - 1]))
+            return (rs_status)cuda_fail(e, "rs_profile_read");
+    }
+    for (size_t i = 1; i < g->prof_used; ++i) {
+        if (!g->prof_name[i]) continue;            // a segment start: nothing ran before it
+        if (n < cap) {
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, g->prof_ev[i - 1], g->prof_ev[i]);
+            if (names) names[n] = g->prof_name[i];
+            if (ms) ms[n] = t;
+            if (is_kernel) is_kernel[n] = g->prof_is_kernel[i];
+        }
+        n++;
+    }
+    *n_out = n;
+    return RS_OK;
+}
+
+extern "C" rs_status rs_launch_count(const rs_graph *g, int64_t *launches) {
+    if (!g || !launches) return (rs_status)fail(RS_EINVAL, "rs_launch_count: NULL argument");
+    *launches = g->launches;
+    return RS_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -251,17 +313,23 @@ static int validate_graph(rs_graph *g, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // row classification
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int row_class(int64_t d, int32_t k) {
-    if (d <= kSmallMax) return 0;
+__device__ __forceinline__ uint32_t row_cap(int64_t d, int32_t k) {
     int64_t m = d < k ? d : k;
     uint32_t cap = 1;
     while ((int64_t)cap < 2 * m) cap <<= 1;
-    return cap <= (uint32_t)kMidCap ? 1 : 2;
+    return cap;
+}
+// 0 small, 1 mid (warp), 2 large (CTA), 3 hub
+__device__ __forceinline__ int row_class(int64_t d, int32_t k) {
+    if (d <= kSmallMax) return 0;
+    uint32_t cap = row_cap(d, k);
+    if (cap <= (uint32_t)kWarpCap) return 1;
+    return cap <= (uint32_t)kMidCap ? 2 : 3;
 }
 
-// flags for one class into a[v], plus dmax / mid cap / hub list on the first pass
+// flags for one class into a[v], plus dmax / large cap / hub list on the first pass
 __global__ void classify_kernel(const int64_t *off, int64_t n, int32_t k, int cls, int64_t *a,
-                                int *dmax, int *midcap, int32_t *hub_list, int *n_hub) {
+                                int *dmax, int *largecap, int32_t *hub_list, int *n_hub) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     int64_t d = off[v + 1] - off[v];
@@ -269,14 +337,24 @@ __global__ void classify_kernel(const int64_t *off, int64_t n, int32_t k, int cl
     a[v] = (c == cls) ? 1 : 0;
     if (cls == 0) {
         atomicMax(dmax, (int)d);
-        if (c == 1) {
-            int64_t m = d < k ? d : k;
-            uint32_t cap = 1;
-            while ((int64_t)cap < 2 * m) cap <<= 1;
-            atomicMax(midcap, (int)cap);
-        }
-        if (c == 2) hub_list[atomicAdd(n_hub, 1)] = (int32_t)v;
+        if (c == 2) atomicMax(largecap, (int)row_cap(d, k));
+        if (c == 3) hub_list[atomicAdd(n_hub, 1)] = (int32_t)v;
     }
+}
+
+// small rows grouped by degree (so the threads of a warp run loops of equal length)
+__global__ void degree_hist_kernel(const int64_t *off, const int32_t *rows, int64_t m, int *hist) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) atomicAdd(&hist[off[rows[i] + 1] - off[rows[i]]], 1);
+}
+__global__ void degree_prefix_kernel(int *hist) {
+    int acc = 0;
+    for (int d = 0; d <= kSmallMax; ++d) { int c = hist[d]; hist[d] = acc; acc += c; }
+}
+__global__ void degree_scatter_kernel(const int64_t *off, const int32_t *rows, int64_t m, int *cursor,
+                                      int32_t *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[atomicAdd(&cursor[off[rows[i] + 1] - off[rows[i]]], 1)] = rows[i];
 }
 __global__ void scatter_class_kernel(const int64_t *a, int64_t n, int32_t *rows) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -300,31 +378,44 @@ static cudaError_t dmalloc(T **p, size_t count) {
     return cudaMalloc((void **)p, std::max<size_t>(count, 1) * sizeof(T));
 }
 
-// builds rows_small / rows_mid / hub tables from the current offsets; syncs
+// builds rows_small / rows_mid / rows_large / hub tables from the current offsets; syncs
 static int classify_rows(rs_graph *g, cudaStream_t s) {
     int64_t n = g->n;
-    int hdr[4] = {0, 0, 0, 0};   // dmax, midcap, n_hub, unused
+    int hdr[4] = {0, 0, 0, 0};   // dmax, large cap, n_hub, unused
     int *d_hdr = g->d_flag;      // d_flag has room for 4 ints
     RS_CUDA_TRY(cudaMemsetAsync(d_hdr, 0, 4 * sizeof(int), s));
     int32_t *hub_list = g->xout;  // n int32 scratch (workspace is allocated by now)
     unsigned blocks = (unsigned)((n + 255) / 256);
     int64_t *a = g->xoff;
-    for (int cls = 0; cls < 2; ++cls) {
+    int32_t *lists[3] = {g->rows_small, g->rows_mid, g->rows_large};
+    int64_t counts[3] = {0, 0, 0};
+    for (int cls = 0; cls < 3; ++cls) {
         if (n > 0) {
             classify_kernel<<<blocks, 256, 0, s>>>(g->off, n, g->k, cls, a, d_hdr, d_hdr + 1, hub_list, d_hdr + 2);
             RS_CUDA_TRY(cudaGetLastError());
             if (int rc = inclusive_scan_i64(a, n, g->scan_tmp, s)) return rc;
-            scatter_class_kernel<<<blocks, 256, 0, s>>>(a, n, cls == 0 ? g->rows_small : g->rows_mid);
+            scatter_class_kernel<<<blocks, 256, 0, s>>>(a, n, lists[cls]);
             RS_CUDA_TRY(cudaGetLastError());
+            RS_CUDA_TRY(cudaMemcpyAsync(&counts[cls], a + n - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         }
-        int64_t cnt = 0;
-        if (n > 0) RS_CUDA_TRY(cudaMemcpyAsync(&cnt, a + n - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        RS_CUDA_TRY(cudaMemcpyAsync(hdr, d_hdr, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        RS_CUDA_TRY(cudaStreamSynchronize(s));
-        if (cls == 0) g->n_small = cnt; else g->n_mid = cnt;
     }
+    RS_CUDA_TRY(cudaMemcpyAsync(hdr, d_hdr, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    RS_CUDA_TRY(cudaStreamSynchronize(s));
+    g->n_small = counts[0]; g->n_mid = counts[1]; g->n_large = counts[2];
     g->dmax = hdr[0];
-    g->mid_cap = std::max(hdr[1], 64);
+    g->large_cap = std::max(hdr[1], 64);
+    if (g->n_small > 1) {
+        int *hist = g->d_flag + 8;   // kSmallMax + 1 counters
+        unsigned sb = (unsigned)((g->n_small + 255) / 256);
+        RS_CUDA_TRY(cudaMemsetAsync(hist, 0, (kSmallMax + 1) * sizeof(int), s));
+        degree_hist_kernel<<<sb, 256, 0, s>>>(g->off, g->rows_small, g->n_small, hist);
+        RS_CUDA_TRY(cudaGetLastError());
+        degree_prefix_kernel<<<1, 1, 0, s>>>(hist);
+        RS_CUDA_TRY(cudaGetLastError());
+        degree_scatter_kernel<<<sb, 256, 0, s>>>(g->off, g->rows_small, g->n_small, hist, g->xin);
+        RS_CUDA_TRY(cudaGetLastError());
+        RS_CUDA_TRY(cudaMemcpyAsync(g->rows_small, g->xin, g->n_small * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    }
     // hubs: host-side work list (hubs are few)
     int nh = hdr[2];
     std::vector<int32_t> hl(nh);
@@ -392,21 +483,25 @@ static int alloc_workspace(rs_graph *g) {
     RS_CUDA_TRY(dmalloc(&g->xS, nnz));
     RS_CUDA_TRY(dmalloc(&g->xout, n));
     RS_CUDA_TRY(dmalloc(&g->xin, n));
+    g->tri_cap = std::max<int64_t>(1 << 20, nnz / 8);
+    RS_CUDA_TRY(cudaMalloc(&g->tri, g->tri_cap * sizeof(rs::Tri)));
     RS_CUDA_TRY(dmalloc(&g->scan_tmp, scan_tmp_words(std::max<int64_t>(n + 1, 1)) + 64));
     RS_CUDA_TRY(dmalloc(&g->rows_small, n));
     RS_CUDA_TRY(dmalloc(&g->rows_mid, n));
-    RS_CUDA_TRY(dmalloc(&g->d_flag, 8));
+    RS_CUDA_TRY(dmalloc(&g->rows_large, n));
+    RS_CUDA_TRY(dmalloc(&g->d_flag, 64));
     return 0;
 }
 
 static void free_graph(rs_graph *g) {
     if (!g) return;
     void *ptrs[] = {g->off, g->off_alt, g->col, g->col_alt, g->lab, g->removed, g->dead,
-                    g->rows_small, g->rows_mid, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
+                    g->rows_small, g->rows_mid, g->rows_large, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
                     g->Lall, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->scan_tmp, g->tk_hist,
-                    g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag};
+                    g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->tri};
     for (void *p : ptrs) cudaFree(p);
     free_hub_tables(g);
+    for (cudaEvent_t e : g->prof_ev) cudaEventDestroy(e);
     delete g;
 }
 

@@ -4,20 +4,23 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "rs_numeric.cuh"
 
 namespace rs {
 
-// Row classes by degree (and by the community count k, which bounds the number
-// of distinct neighbour communities):
-//   small: d <= 32, one warp per row, everything in registers;
-//   mid:   a shared-memory hash table of cap = pow2 >= 2 min(d, k) slots fits
-//          (cap <= kMidCap), one CTA per row;
+// Row classes by degree d and by the hash-table size cap = pow2 >= 2 min(d, k)
+// (k bounds the number of distinct neighbour communities):
+//   small: d <= 32, one thread per row (rows sorted by degree so that the
+//          threads of a warp loop alike), a private table in shared memory;
+//   mid:   cap <= kWarpCap, one warp per row, a per-warp shared-memory table;
+//   large: cap <= kMidCap, one CTA per row, a per-CTA shared-memory table;
 //   hub:   larger rows; a hash table in global memory, rows split into chunks
 //          of kHubChunk neighbours processed by separate CTAs and merged by
 //          atomics into the row's table.
 constexpr int kSmallMax = 32;
+constexpr int kWarpCap = 512;
 constexpr int kMidCap = 2048;
 constexpr int kHubChunk = 4096;
 constexpr int32_t kEmpty = -1;
@@ -42,6 +45,12 @@ struct __align__(16) HubAgg {
     uint32_t L;           // foreign groups
     uint32_t own;         // neighbours in C(row)
     uint32_t pad[2];
+};
+
+// a G_x triangle (a, b, c), rank a < b < c, with its three out-direction values
+struct __align__(8) Tri {
+    int32_t a, b, c, pad;
+    df Sab, Sac, Sbc;
 };
 
 inline uint32_t pow2_at_least(uint64_t x) {
@@ -70,9 +79,9 @@ struct rs_graph {
     uint8_t *removed = nullptr;       // n removed-node flags
     uint8_t *dead = nullptr;          // nnz edge marks used by removals
     // row classes
-    int32_t *rows_small = nullptr, *rows_mid = nullptr;
-    int64_t n_small = 0, n_mid = 0;
-    int32_t mid_cap = 0;              // largest table among mid rows
+    int32_t *rows_small = nullptr, *rows_mid = nullptr, *rows_large = nullptr;
+    int64_t n_small = 0, n_mid = 0, n_large = 0;
+    int32_t large_cap = 0;            // largest table among large rows
     rs::HubInfo *hubs = nullptr;      // device copy
     int32_t *hub_items = nullptr;     // per chunk item: hub index
     int32_t *hub_item_chunk = nullptr;// per chunk item: chunk number within the hub
@@ -95,6 +104,8 @@ struct rs_graph {
     int32_t *xcol = nullptr;                  // G_x neighbours (capacity nnz)
     rs::df *xS = nullptr;                     // S(w -> u) = w_w(C(u))^(1/3)
     int32_t *xout = nullptr, *xin = nullptr;  // out / in counts per node
+    void *tri = nullptr;                      // triangle records (rs::Tri) found by P3a
+    int64_t tri_cap = 0;
     int64_t *scan_tmp = nullptr;              // block sums for scans
     // top-k workspace
     uint32_t *tk_hist = nullptr;
@@ -104,6 +115,13 @@ struct rs_graph {
     int64_t tk_cap = 0;
     // misc
     int32_t *d_flag = nullptr;                // device error / scalar slot
+    // launch accounting and optional per-kernel event timing
+    int64_t launches = 0;
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;         // event pool (created on demand)
+    std::vector<const char *> prof_name;      // per recorded event: kernel name, or nullptr (segment start)
+    std::vector<char> prof_is_kernel;
+    size_t prof_used = 0;
 };
 
 namespace rs {
@@ -119,9 +137,20 @@ int cuda_fail(cudaError_t e, const char *where);
         if (_e != cudaSuccess) return ::rs::cuda_fail(_e, #expr);    \
     } while (0)
 
-// in-place inclusive scan of a[0..m) (int64), tmp >= scan_tmp_words(m) words
+// in-place inclusive scan of a[0..m) (int64), tmp >= scan_tmp_words(m) words;
+// adds the number of kernels launched to *launches when given
 int64_t scan_tmp_words(int64_t m);
-int inclusive_scan_i64(int64_t *a, int64_t m, int64_t *tmp, cudaStream_t s);
+int inclusive_scan_i64(int64_t *a, int64_t m, int64_t *tmp, cudaStream_t s, int64_t *launches = nullptr);
+
+// launch accounting: count a kernel launch (or record a non-kernel operation)
+// and, when profiling is on, record an event after it on the stream
+void prof_begin(rs_graph *g, cudaStream_t s);
+void prof_mark(rs_graph *g, cudaStream_t s, const char *name, bool is_kernel);
+#define RS_LAUNCHED(g, s, name)                        \
+    do {                                               \
+        RS_CUDA_TRY(cudaGetLastError());               \
+        ::rs::prof_mark((g), (s), (name), true);       \
+    } while (0)
 
 // grid size for grid-stride kernels: at most `cap_per_sm` CTAs per SM
 int grid_for(int64_t items, int per_block, int cap_per_sm);

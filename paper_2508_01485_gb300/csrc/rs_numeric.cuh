@@ -96,7 +96,11 @@ __device__ __forceinline__ df df_max(df a, df b) { return df_less(a, b) ? b : a;
 
 // ---- conversions -------------------------------------------------------------
 
+// 2^e as a float for -126 <= e <= 127 (exact)
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
 // x * 2^e as double-float, keeping the top 48 significant bits of x
+// (the exponents reached by the score stay inside the normal float range)
 __device__ __forceinline__ df df_from_u128(u128 x, int e) {
     if (x == 0) return df{0.0f, 0.0f};
     uint64_t h = (uint64_t)(x >> 64);
@@ -105,8 +109,8 @@ __device__ __forceinline__ df df_from_u128(u128 x, int e) {
     int sh = top - 47;                            // keep bits [top-47, top]
     uint64_t m48 = sh >= 0 ? (uint64_t)(x >> sh) : (uint64_t)x << (-sh);
     uint32_t mh = (uint32_t)(m48 >> 24), ml = (uint32_t)(m48 & 0xFFFFFFu);
-    float hi = ldexpf((float)mh, sh + 24 + e);
-    float lo = ldexpf((float)ml, sh + e);
+    float hi = __fmul_rn((float)mh, pow2f(sh + 24 + e));
+    float lo = __fmul_rn((float)ml, pow2f(sh + e));
     return quick_two_sum(hi, lo);
 }
 __device__ __forceinline__ df df_from_u64(uint64_t x, int e) { return df_from_u128((u128)x, e); }

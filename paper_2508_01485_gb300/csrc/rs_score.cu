@@ -129,17 +129,7 @@ __device__ __forceinline__ df block_max_df(df v, df *sh) {
     return m;
 }
 
-// sum of x over the lanes of `grp` other than this lane (exact, fixed order)
-__device__ __forceinline__ u128 group_sum_others(const uint64_t *stage, unsigned grp, int lane) {
-    u128 q = 0;
-    unsigned m = grp & ~(1u << lane);
-    while (m) {
-        int j = __ffs(m) - 1;
-        q += stage[j];
-        m &= m - 1;
-    }
-    return q;
-}
+// sum of the staged values over the lanes of `grp` (exact, fixed order)
 __device__ __forceinline__ u128 group_sum_all(const uint64_t *stage, unsigned grp) {
     u128 q = 0;
     while (grp) {
@@ -157,13 +147,15 @@ __device__ __forceinline__ void push_type2(unsigned long long *acc, int32_t u, d
     atomic_add_u128(acc + 2 * (int64_t)u, df_to_fixed(t, kAccFrac));
 }
 
-// finishing a row in P1: the row's largest weight, s_v and the node record
+// finishing a row in P1: the row's largest weight, s_v and the node record;
+// w_own is the weight of the row's own community when own > 0 (else ignored)
 __device__ __forceinline__ df p1_row_result(const RowAgg &a, uint32_t own, df col_max, int32_t k,
-                                            const uint64_t *LG, NodeRec &out, int32_t cv) {
-    df wabs = column_weight(a, 0, LG);                    // community absent from N(v)
+                                            const uint64_t *LG, NodeRec &out, int32_t cv, df w_own) {
     df m = col_max;
+    df wabs{0.0f, 0.0f};
+    if (a.L < (uint32_t)k || own == 0) wabs = column_weight(a, 0, LG);   // community absent from N(v)
     if (a.L < (uint32_t)k) m = df_max(m, wabs);
-    df wown = own > 0 ? column_weight(a, own, LG) : wabs;
+    df wown = own > 0 ? w_own : wabs;
     df s = df_cbrt(wown);
     out.s_fix = (uint64_t)df_to_fixed(s, kSFrac);
     out.label = cv;
@@ -174,11 +166,97 @@ __device__ __forceinline__ df p1_row_result(const RowAgg &a, uint32_t own, df co
 // ======================================================================================
 // P1
 // ======================================================================================
+
+// Small rows, one thread per row.  Each thread keeps the foreign communities of
+// its row in a private column of a shared-memory table (slot-major, thread-minor,
+// so accesses never conflict); neighbours of its own community are counted
+// apart.  Column weights are evaluated once per distinct count.
+constexpr int kSlots = kSmallMax;
+constexpr int kPrefetch = 8;
+
+struct SmallTable {
+    int32_t lab[kSlots][kThreads];
+    uint8_t cnt[kSlots][kThreads];
+};
+
+// counts of row v's neighbour communities; returns the aggregates
+__device__ __forceinline__ RowAgg small_row_counts(const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
+                                                   int64_t b, int d, int32_t cv, const uint64_t *__restrict__ LG,
+                                                   SmallTable &T, int t, int &nf, uint32_t &own,
+                                                   uint64_t &seen) {
+    nf = 0;
+    own = 0;
+    for (int j0 = 0; j0 < d; j0 += kPrefetch) {
+        int32_t c[kPrefetch];
+#pragma unroll
+        for (int q = 0; q < kPrefetch; ++q) c[q] = (j0 + q < d) ? col[b + j0 + q] : -1;
+#pragma unroll
+        for (int q = 0; q < kPrefetch; ++q) c[q] = (c[q] >= 0) ? lab[c[q]] : -1;
+#pragma unroll
+        for (int q = 0; q < kPrefetch; ++q) {
+            if (j0 + q >= d) break;
+            if (c[q] == cv) { own++; continue; }
+            int sl = 0;
+            while (sl < nf && T.lab[sl][t] != c[q]) ++sl;
+            if (sl == nf) { T.lab[sl][t] = c[q]; T.cnt[sl][t] = 1; ++nf; }
+            else T.cnt[sl][t]++;
+        }
+    }
+    u128 X = (u128)own * LG[own];
+    seen = own ? (1ull << own) : 0ull;
+    for (int sl = 0; sl < nf; ++sl) {
+        uint32_t f = T.cnt[sl][t];
+        X += (u128)f * LG[f];
+        seen |= 1ull << f;
+    }
+    return RowAgg{(uint32_t)d, (uint32_t)nf + (own > 0 ? 1u : 0u), X};
+}
+
 __global__ void __launch_bounds__(kThreads) p1_small_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
     const int32_t *__restrict__ rows, int64_t nrows, int32_t k, const uint64_t *__restrict__ LG,
     NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits) {
-    int lane = threadIdx.x & 31;
+    __shared__ SmallTable T;
+    int t = threadIdx.x;
+    df best{0.0f, 0.0f};
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < nrows; i0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = i0 + t;
+        if (i >= nrows) continue;
+        int32_t v = rows[i];
+        int64_t b = off[v];
+        int d = (int)(off[v + 1] - b);
+        int32_t cv = lab[v];
+        int nf;
+        uint32_t own;
+        uint64_t seen;
+        RowAgg a = small_row_counts(col, lab, b, d, cv, LG, T, t, nf, own, seen);
+        df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
+        while (seen) {
+            uint32_t f = (uint32_t)(__ffsll((long long)seen) - 1);
+            df w = column_weight(a, f, LG);
+            if (f == own) wown = w;
+            cm = df_max(cm, w);
+            seen &= seen - 1;
+        }
+        NodeRec r;
+        best = df_max(best, p1_row_result(a, own, cm, k, LG, r, cv, wown));
+        rec[v] = r;
+        Lall[v] = (int32_t)a.L;
+    }
+    best = warp_max_df(best);
+    if ((t & 31) == 0 && best.hi > 0.0f) atomicMax(wmax_bits, double_bits(best));
+}
+
+// Mid rows, one warp per row, a per-warp shared-memory table of kWarpCap slots.
+constexpr int kMidWarps = kThreads / 32;
+
+__global__ void __launch_bounds__(kThreads) p1_mid_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
+    const int32_t *__restrict__ rows, int64_t nrows, int32_t k, const uint64_t *__restrict__ LG,
+    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits, int *err) {
+    __shared__ int32_t skey[kMidWarps][kWarpCap];
+    __shared__ uint32_t scnt[kMidWarps][kWarpCap];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     df best{0.0f, 0.0f};
@@ -187,33 +265,50 @@ __global__ void __launch_bounds__(kThreads) p1_small_kernel(
         int64_t b = off[v];
         int d = (int)(off[v + 1] - b);
         int32_t cv = lab[v];
-        bool act = lane < d;
-        int32_t c = act ? lab[col[b + lane]] : -1;
-        unsigned amask = __ballot_sync(FULL, act);
-        unsigned grp = 0;
-        if (act) grp = __match_any_sync(amask, c);
-        uint32_t f = __popc(grp);
-        bool leader = act && (__ffs(grp) - 1 == lane);
-        uint32_t L = __popc(__ballot_sync(FULL, leader));
-        uint32_t own = __popc(__ballot_sync(FULL, act && c == cv));
-        u128 x = leader ? (u128)f * LG[f] : (u128)0;
-        RowAgg a{(uint32_t)d, L, warp_sum_u128(x)};
-        df w{0.0f, 0.0f};
-        if (leader) w = column_weight(a, f, LG);
-        df cm = warp_max_df(w);
-        NodeRec r;
-        df m = p1_row_result(a, own, cm, k, LG, r, cv);
-        if (lane == 0) {
-            rec[v] = r;
-            Lall[v] = (int32_t)L;
+        uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(d, k));
+        Tab t{skey[wid], scnt[wid], nullptr, nullptr, cap - 1};
+        for (uint32_t j = lane; j < cap; j += 32) { t.key[j] = kEmpty; t.cnt[j] = 0; }
+        __syncwarp();
+        uint32_t own = 0;
+        for (int base = 0; base < d; base += 32) {
+            int e = base + lane;
+            bool act = e < d;
+            int32_t c = act ? lab[col[b + e]] : -1;
+            own += (act && c == cv);
+            bool foreign = act && c != cv;
+            unsigned fm = __ballot_sync(FULL, foreign);
+            if (foreign) {
+                unsigned grp = __match_any_sync(fm, c);
+                if (lane == __ffs(grp) - 1) tab_insert(t, c, __popc(grp), err);
+            }
         }
-        best = df_max(best, m);
+        __syncwarp();
+        for (int o = 16; o; o >>= 1) own += __shfl_xor_sync(FULL, own, o);
+        uint32_t Lf = 0;
+        u128 X = 0;
+        for (uint32_t j = lane; j < cap; j += 32)
+            if (t.key[j] != kEmpty) { Lf++; X += (u128)t.cnt[j] * LG[t.cnt[j]]; }
+        for (int o = 16; o; o >>= 1) Lf += __shfl_xor_sync(FULL, Lf, o);
+        RowAgg a{(uint32_t)d, Lf + (own > 0 ? 1u : 0u), warp_sum_u128(X) + (u128)own * LG[own]};
+        df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
+        for (uint32_t j = lane; j < cap; j += 32)
+            if (t.key[j] != kEmpty) cm = df_max(cm, column_weight(a, t.cnt[j], LG));
+        if (own > 0 && lane == 0) { wown = column_weight(a, own, LG); cm = df_max(cm, wown); }
+        cm = warp_max_df(cm);
+        if (lane == 0) {
+            NodeRec r;
+            best = df_max(best, p1_row_result(a, own, cm, k, LG, r, cv, wown));
+            rec[v] = r;
+            Lall[v] = (int32_t)a.L;
+        }
+        __syncwarp();
     }
     if (lane == 0 && best.hi > 0.0f) atomicMax(wmax_bits, double_bits(best));
 }
 
+// Large rows, one CTA per row, a per-CTA table of up to kMidCap slots
 template <int NT>
-__global__ void __launch_bounds__(NT) p1_mid_kernel(
+__global__ void __launch_bounds__(NT) p1_large_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
     const int32_t *__restrict__ rows, int64_t nrows, int32_t k, const uint64_t *__restrict__ LG,
     NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits, int *err) {
@@ -253,14 +348,14 @@ __global__ void __launch_bounds__(NT) p1_mid_kernel(
         Lf = block_sum_u32<NT>(Lf, sh_u32);
         X = block_sum_u128<NT>(X, sh_u128);
         RowAgg a{(uint32_t)d, Lf + (own > 0 ? 1u : 0u), X + (u128)own * LG[own]};
-        df cm{0.0f, 0.0f};
+        df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
         for (uint32_t j = tid; j < cap; j += NT)
             if (t.key[j] != kEmpty) cm = df_max(cm, column_weight(a, t.cnt[j], LG));
-        if (own > 0) cm = df_max(cm, column_weight(a, own, LG));
+        if (own > 0) { wown = column_weight(a, own, LG); cm = df_max(cm, wown); }
         cm = block_max_df<NT>(cm, sh_df);
         if (tid == 0) {
             NodeRec r;
-            df m = p1_row_result(a, own, cm, k, LG, r, cv);
+            df m = p1_row_result(a, own, cm, k, LG, r, cv, wown);
             rec[v] = r;
             Lall[v] = (int32_t)a.L;
             best = df_max(best, m);
@@ -328,12 +423,12 @@ __global__ void __launch_bounds__(NT) hub_p1_finish_kernel(
         Lf = block_sum_u32<NT>(Lf, sh_u32);
         X = block_sum_u128<NT>(X, sh_u128);
         RowAgg a{(uint32_t)d, Lf + (own > 0 ? 1u : 0u), X + (u128)own * LG[own]};
-        df cm{0.0f, 0.0f};
+        df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
         for (int64_t j = tid; j < h.cap; j += NT) {
             int64_t s = h.tab + j;
             if (hkey[s] != kEmpty) cm = df_max(cm, column_weight(a, hcnt[s], LG));
         }
-        if (own > 0) cm = df_max(cm, column_weight(a, own, LG));
+        if (own > 0) { wown = column_weight(a, own, LG); cm = df_max(cm, wown); }
         cm = block_max_df<NT>(cm, sh_df);
         if (tid == 0) {
             HubAgg g = hagg[hi];
@@ -341,7 +436,7 @@ __global__ void __launch_bounds__(NT) hub_p1_finish_kernel(
             g.L = a.L;
             hagg[hi] = g;
             NodeRec r;
-            df m = p1_row_result(a, own, cm, k, LG, r, lab[h.row]);
+            df m = p1_row_result(a, own, cm, k, LG, r, lab[h.row], wown);
             rec[h.row] = r;
             Lall[h.row] = (int32_t)a.L;
             best = df_max(best, m);
@@ -366,14 +461,82 @@ __global__ void gx_capacity_kernel(const NodeRec *__restrict__ rec, int64_t n, i
 // ======================================================================================
 // P2
 // ======================================================================================
+// Small rows, one thread per row: counts as in P1, then a second pass over the
+// neighbours emits the Type-II terms and the G_x entries in id order.
 __global__ void __launch_bounds__(kThreads) p2_small_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
+    const int32_t *__restrict__ rows, int64_t nrows, const uint64_t *__restrict__ LG,
+    const NodeRec *__restrict__ rec, unsigned long long *acc, const int64_t *__restrict__ xoff,
+    int32_t *__restrict__ xcol, df *__restrict__ xS, int32_t *__restrict__ xout, int32_t *__restrict__ xin) {
+    __shared__ SmallTable T;
+    int t = threadIdx.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < nrows; i0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = i0 + t;
+        if (i >= nrows) continue;
+        int32_t w = rows[i];
+        int64_t b = off[w];
+        int d = (int)(off[w + 1] - b);
+        NodeRec rw = rec[w];
+        int nf;
+        uint32_t own;
+        uint64_t seen;
+        RowAgg a = small_row_counts(col, lab, b, d, rw.label, LG, T, t, nf, own, seen);
+        // sigma per foreign count, cached for count 1 and the last other count
+        df sig1{-1.0f, 0.0f}, sigl{0.0f, 0.0f};
+        uint32_t fl = 0;
+        int64_t xb = xoff[w];
+        int32_t no = 0, ni = 0;
+        bool gx = rw.dx >= 2;
+        for (int j = 0; j < d; ++j) {
+            int32_t u = col[b + j];
+            if (lab[u] == rw.label) continue;
+            NodeRec ru = rec[u];
+            int sl = 0;
+            while (sl < nf && T.lab[sl][t] != ru.label) ++sl;
+            if (sl == nf) continue;                       // not reached: P1 saw the same labels
+            uint32_t f = T.cnt[sl][t];
+            df sig;
+            if (f == 1) {
+                if (sig1.hi < 0.0f) sig1 = df_cbrt(column_weight(a, 1, LG));
+                sig = sig1;
+            } else {
+                if (f != fl) { sigl = df_cbrt(column_weight(a, f, LG)); fl = f; }
+                sig = sigl;
+                // Type-II: the other neighbours of w in community C(u)
+                u128 rest = 0;
+                for (int j2 = 0; j2 < d; ++j2) {
+                    if (j2 == j) continue;
+                    int32_t x = col[b + j2];
+                    if (lab[x] == ru.label) rest += rec[x].s_fix;
+                }
+                push_type2(acc, u, sig, rest);
+            }
+            if (gx && ru.dx >= 2) {
+                int64_t p;
+                if (rank_after(ru.dx, u, rw.dx, w)) p = xb + no++;
+                else p = xb + rw.dx - 1 - ni++;
+                xcol[p] = u;
+                xS[p] = sig;
+            }
+        }
+        xout[w] = no;
+        xin[w] = ni;
+    }
+}
+
+// Mid rows, one warp per row: per-warp table with Type-II group sums
+constexpr int kMidSlotBytes = 4 + 4 + 16;   // key, count, 2-word sum
+
+__global__ void __launch_bounds__(kThreads) p2_mid_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ rows,
-    int64_t nrows, const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec,
+    int64_t nrows, int32_t k, const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec,
     unsigned long long *acc, const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol,
-    df *__restrict__ xS, int32_t *__restrict__ xout, int32_t *__restrict__ xin) {
+    df *__restrict__ xS, int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t stage[kThreads];
-    int lane = threadIdx.x & 31;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t *st = stage + (threadIdx.x & ~31);
+    unsigned char *base_w = smem + (size_t)wid * kWarpCap * kMidSlotBytes;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < nrows; i += nwarps) {
@@ -381,45 +544,77 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
         int64_t b = off[w];
         int d = (int)(off[w + 1] - b);
         NodeRec rw = rec[w];
-        bool act = lane < d;
-        int32_t u = act ? col[b + lane] : -1;
-        NodeRec ru{0, -1, 0};
-        if (act) ru = rec[u];
-        int32_t c = ru.label;
-        unsigned amask = __ballot_sync(FULL, act);
-        unsigned grp = 0;
-        if (act) grp = __match_any_sync(amask, c);
-        uint32_t f = __popc(grp);
-        bool leader = act && (__ffs(grp) - 1 == lane);
-        uint32_t L = __popc(__ballot_sync(FULL, leader));
-        u128 x = leader ? (u128)f * LG[f] : (u128)0;
-        RowAgg a{(uint32_t)d, L, warp_sum_u128(x)};
-        bool cross = act && c != rw.label;
-        df sig{0.0f, 0.0f};
-        if (cross) sig = df_cbrt(column_weight(a, f, LG));
-        st[lane] = ru.s_fix;
+        uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(d, k));
+        Tab t;
+        t.q = (unsigned long long *)base_w;
+        t.key = (int32_t *)(base_w + 16 * kWarpCap);
+        t.cnt = (uint32_t *)(base_w + 20 * kWarpCap);
+        t.sig = nullptr;
+        t.mask = cap - 1;
+        for (uint32_t j = lane; j < cap; j += 32) { t.key[j] = kEmpty; t.cnt[j] = 0; t.q[2 * j] = 0; t.q[2 * j + 1] = 0; }
         __syncwarp();
-        if (cross && f > 1) push_type2(acc, u, sig, group_sum_others(st, grp, lane));
-        __syncwarp();
-        // G_x row of w: cross neighbours with dx >= 2, ordered by id
-        int32_t cnt_out = 0, cnt_in = 0;
-        if (rw.dx >= 2) {
-            bool inx = cross && ru.dx >= 2;
-            bool out = inx && rank_after(ru.dx, u, rw.dx, w);
-            bool in = inx && !out;
-            unsigned mo = __ballot_sync(FULL, out), mi = __ballot_sync(FULL, in);
-            int64_t xb = xoff[w];
-            if (out) {
-                int64_t p = xb + __popc(mo & lanemask_lt());
-                xcol[p] = u; xS[p] = sig;
+        uint32_t own = 0;
+        for (int base = 0; base < d; base += 32) {
+            int e = base + lane;
+            bool act = e < d;
+            NodeRec ru{0, -1, 0};
+            if (act) ru = rec[col[b + e]];
+            own += (act && ru.label == rw.label);
+            bool foreign = act && ru.label != rw.label;
+            st[lane] = ru.s_fix;
+            __syncwarp();
+            unsigned fm = __ballot_sync(FULL, foreign);
+            if (foreign) {
+                unsigned grp = __match_any_sync(fm, ru.label);
+                if (lane == __ffs(grp) - 1) {
+                    int sl = tab_insert(t, ru.label, __popc(grp), err);
+                    if (sl >= 0) atomic_add_u128(t.q + 2 * sl, group_sum_all(st, grp));
+                }
             }
-            if (in) {
-                int64_t p = xb + rw.dx - 1 - __popc(mi & lanemask_lt());
-                xcol[p] = u; xS[p] = sig;
-            }
-            cnt_out = __popc(mo); cnt_in = __popc(mi);
+            __syncwarp();
         }
-        if (lane == 0) { xout[w] = cnt_out; xin[w] = cnt_in; }
+        for (int o = 16; o; o >>= 1) own += __shfl_xor_sync(FULL, own, o);
+        uint32_t Lf = 0;
+        u128 X = 0;
+        for (uint32_t j = lane; j < cap; j += 32)
+            if (t.key[j] != kEmpty) { Lf++; X += (u128)t.cnt[j] * LG[t.cnt[j]]; }
+        for (int o = 16; o; o >>= 1) Lf += __shfl_xor_sync(FULL, Lf, o);
+        RowAgg a{(uint32_t)d, Lf + (own > 0 ? 1u : 0u), warp_sum_u128(X) + (u128)own * LG[own]};
+        df sig1 = df_cbrt(column_weight(a, 1, LG));   // the usual count of a foreign community
+        int64_t xb = xoff[w];
+        int32_t bo = 0, bi = 0;
+        for (int base = 0; base < d; base += 32) {
+            int e = base + lane;
+            bool act = e < d;
+            int32_t u = act ? col[b + e] : -1;
+            NodeRec ru{0, -1, 0};
+            if (act) ru = rec[u];
+            bool cross = act && ru.label != rw.label;
+            df sig{0.0f, 0.0f};
+            if (cross) {
+                int sl = tab_find(t, ru.label);
+                if (sl < 0) { atomicOr(err, 2); cross = false; }
+                else {
+                    uint32_t f = t.cnt[sl];
+                    sig = f == 1 ? sig1 : df_cbrt(column_weight(a, f, LG));
+                    if (f > 1) {
+                        u128 q = ((u128)t.q[2 * sl + 1] << 64) | t.q[2 * sl];
+                        push_type2(acc, u, sig, q - ru.s_fix);
+                    }
+                }
+            }
+            if (rw.dx >= 2) {
+                bool inx = cross && ru.dx >= 2;
+                bool o = inx && rank_after(ru.dx, u, rw.dx, w);
+                bool in = inx && !o;
+                unsigned mo = __ballot_sync(FULL, o), mi = __ballot_sync(FULL, in);
+                if (o) { int64_t p = xb + bo + __popc(mo & lanemask_lt()); xcol[p] = u; xS[p] = sig; }
+                if (in) { int64_t p = xb + rw.dx - 1 - (bi + __popc(mi & lanemask_lt())); xcol[p] = u; xS[p] = sig; }
+                bo += __popc(mo); bi += __popc(mi);
+            }
+        }
+        if (lane == 0) { xout[w] = bo; xin[w] = bi; }
+        __syncwarp();
     }
 }
 
@@ -461,7 +656,7 @@ __device__ __forceinline__ void gx_round(bool out, bool in, int64_t xb, int32_t 
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) p2_mid_kernel(
+__global__ void __launch_bounds__(NT) p2_large_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ rows,
     int64_t nrows, int32_t k, const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec,
     unsigned long long *acc, const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol,
@@ -702,11 +897,56 @@ __device__ __forceinline__ df in_value(const int64_t *xoff, const int32_t *xcol,
     return df{0.0f, 0.0f};
 }
 
-__global__ void __launch_bounds__(kThreads) p3_triangles_kernel(
+// the three apex terms of triangle (a, b, c), rank a < b < c
+__device__ __forceinline__ void triangle_terms(int32_t a, int32_t b, int32_t c, df Sab, df Sac, df Sbc,
+                                               const int64_t *xoff, const int32_t *xcol, const df *xS,
+                                               const int32_t *xin, const NodeRec *rec,
+                                               unsigned long long *acc, int *err) {
+    df Sba = in_value(xoff, xcol, xS, xin, rec, b, a, err);
+    df Sca = in_value(xoff, xcol, xS, xin, rec, c, a, err);
+    df Scb = in_value(xoff, xcol, xS, xin, rec, c, b, err);
+    df ta = df_mul(df_mul(Sba, Sca), df_add(Sbc, Scb));
+    df tb = df_mul(df_mul(Sab, Scb), df_add(Sac, Sca));
+    df tc = df_mul(df_mul(Sac, Sbc), df_add(Sab, Sba));
+    atomic_add_u128(acc + 2 * (int64_t)a, df_to_fixed(ta, kAccFrac));
+    atomic_add_u128(acc + 2 * (int64_t)b, df_to_fixed(tb, kAccFrac));
+    atomic_add_u128(acc + 2 * (int64_t)c, df_to_fixed(tc, kAccFrac));
+}
+
+// P3a: one warp per node a.  Its out-list N+(a) (ids ascending) is staged in
+// shared memory with the prefix sums of d+(b) over b in N+(a); every wedge
+// a -> b -> c is one lane-iteration, and c closes a triangle iff c is in N+(a)
+// (binary search in shared memory).  Out-lists longer than kP3Cap use global
+// binary searches instead.  Triangles go to a buffer for P3b; when it is full
+// they are finished on the spot.
+constexpr int kP3Cap = 256;
+
+__device__ __forceinline__ void emit_triangle(int32_t a, int32_t b, int32_t c, df Sab, df Sac, df Sbc,
+                                              Tri *tri, int64_t tri_cap, unsigned long long *tri_n,
+                                              const int64_t *xoff, const int32_t *xcol, const df *xS,
+                                              const int32_t *xin, const NodeRec *rec,
+                                              unsigned long long *acc, int *err) {
+    unsigned long long p = atomicAdd(tri_n, 1ull);
+    if ((int64_t)p < tri_cap) {
+        Tri t;
+        t.a = a; t.b = b; t.c = c; t.pad = 0;
+        t.Sab = Sab; t.Sac = Sac; t.Sbc = Sbc;
+        tri[p] = t;
+    } else {
+        triangle_terms(a, b, c, Sab, Sac, Sbc, xoff, xcol, xS, xin, rec, acc, err);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) p3_list_kernel(
     int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
     const int32_t *__restrict__ xout, const int32_t *__restrict__ xin, const NodeRec *__restrict__ rec,
-    unsigned long long *acc, int *err) {
-    int lane = threadIdx.x & 31;
+    Tri *tri, int64_t tri_cap, unsigned long long *tri_n, unsigned long long *acc, int *err) {
+    __shared__ int32_t s_nb[kThreads / 32][kP3Cap];
+    __shared__ int32_t s_pre[kThreads / 32][kP3Cap + 1];
+    __shared__ int64_t s_off[kThreads / 32][kP3Cap];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *nb = s_nb[wid], *pre = s_pre[wid];
+    int64_t *boff = s_off[wid];
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t av = warp; av < n; av += nwarps) {
@@ -714,27 +954,70 @@ __global__ void __launch_bounds__(kThreads) p3_triangles_kernel(
         int32_t da = xout[a];
         if (da < 2) continue;
         int64_t ba = xoff[a];
-        for (int32_t j = lane; j < da; j += 32) {
-            int32_t b = xcol[ba + j];
-            df Sab = xS[ba + j];
-            int64_t bb = xoff[b];
-            int32_t db = xout[b];
-            for (int32_t tb = 0; tb < db; ++tb) {
-                int32_t c = xcol[bb + tb];
-                int64_t p = find_out(xcol, ba, ba + da, c);
-                if (p >= ba + da || xcol[p] != c) continue;
-                df Sac = xS[p], Sbc = xS[bb + tb];
-                df Sba = in_value(xoff, xcol, xS, xin, rec, b, a, err);
-                df Sca = in_value(xoff, xcol, xS, xin, rec, c, a, err);
-                df Scb = in_value(xoff, xcol, xS, xin, rec, c, b, err);
-                df ta = df_mul(df_mul(Sba, Sca), df_add(Sbc, Scb));
-                df tb2 = df_mul(df_mul(Sab, Scb), df_add(Sac, Sca));
-                df tc = df_mul(df_mul(Sac, Sbc), df_add(Sab, Sba));
-                atomic_add_u128(acc + 2 * (int64_t)a, df_to_fixed(ta, kAccFrac));
-                atomic_add_u128(acc + 2 * (int64_t)b, df_to_fixed(tb2, kAccFrac));
-                atomic_add_u128(acc + 2 * (int64_t)c, df_to_fixed(tc, kAccFrac));
+        if (da <= kP3Cap) {
+            int32_t carry = 0;
+            if (lane == 0) pre[0] = 0;
+            for (int32_t j0 = 0; j0 < da; j0 += 32) {
+                int32_t j = j0 + lane;
+                int32_t b = j < da ? xcol[ba + j] : 0;
+                int32_t db = j < da ? xout[b] : 0;
+                if (j < da) { nb[j] = b; boff[j] = xoff[b]; }
+                int32_t x = db;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int32_t y = __shfl_up_sync(FULL, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (j < da) pre[j + 1] = carry + x;
+                carry += __shfl_sync(FULL, x, 31);
+            }
+            __syncwarp();
+            int32_t W = pre[da];
+            for (int32_t wv = lane; wv < W; wv += 32) {
+                int32_t lo = 0, hi = da;               // last j with pre[j] <= wv
+                while (hi - lo > 1) {
+                    int32_t mid = (lo + hi) >> 1;
+                    if (pre[mid] <= wv) lo = mid; else hi = mid;
+                }
+                int32_t j = lo;
+                int64_t pb = boff[j] + (wv - pre[j]);
+                int32_t c = xcol[pb];
+                int32_t l2 = 0, h2 = da;
+                while (l2 < h2) {
+                    int32_t mid = (l2 + h2) >> 1;
+                    if (nb[mid] < c) l2 = mid + 1; else h2 = mid;
+                }
+                if (l2 < da && nb[l2] == c)
+                    emit_triangle(a, nb[j], c, xS[ba + j], xS[ba + l2], xS[pb], tri, tri_cap, tri_n, xoff, xcol,
+                                  xS, xin, rec, acc, err);
+            }
+            __syncwarp();
+        } else {
+            for (int32_t j = lane; j < da; j += 32) {
+                int32_t b = xcol[ba + j];
+                int64_t bb = xoff[b];
+                int32_t db = xout[b];
+                for (int32_t tb = 0; tb < db; ++tb) {
+                    int32_t c = xcol[bb + tb];
+                    int64_t p = find_out(xcol, ba, ba + da, c);
+                    if (p >= ba + da || xcol[p] != c) continue;
+                    emit_triangle(a, b, c, xS[ba + j], xS[p], xS[bb + tb], tri, tri_cap, tri_n, xoff, xcol, xS,
+                                  xin, rec, acc, err);
+                }
             }
         }
+    }
+}
+
+// P3b: one thread per listed triangle
+__global__ void __launch_bounds__(kThreads) p3_terms_kernel(
+    const Tri *__restrict__ tri, int64_t tri_cap, const unsigned long long *tri_n,
+    const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
+    const int32_t *__restrict__ xin, const NodeRec *__restrict__ rec, unsigned long long *acc, int *err) {
+    int64_t m = (int64_t)*tri_n;
+    if (m > tri_cap) m = tri_cap;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        Tri t = tri[i];
+        triangle_terms(t.a, t.b, t.c, t.Sab, t.Sac, t.Sbc, xoff, xcol, xS, xin, rec, acc, err);
     }
 }
 
@@ -772,6 +1055,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     if (n == 0) return 0;
     constexpr int NT = kThreads;
     int *err = g->d_flag + 4;
+    prof_begin(g, s);
     RS_CUDA_TRY(cudaMemsetAsync(g->wmax_bits, 0, sizeof(unsigned long long), s));
     RS_CUDA_TRY(cudaMemsetAsync(g->acc, 0, 2 * n * sizeof(unsigned long long), s));
     RS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
@@ -781,71 +1065,93 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_CUDA_TRY(cudaMemsetAsync(g->hq, 0, 2 * g->hub_slots * sizeof(unsigned long long), s));
         RS_CUDA_TRY(cudaMemsetAsync(g->hagg, 0, g->n_hubs * sizeof(HubAgg), s));
     }
-    size_t p1_smem = 8 * (size_t)g->mid_cap, p2_smem = 32 * (size_t)g->mid_cap;
+    prof_mark(g, s, "memset", false);
+    size_t p1_smem = 8 * (size_t)g->large_cap, p2_smem = 32 * (size_t)g->large_cap;
+    size_t p2_mid_smem = (size_t)kMidWarps * kWarpCap * kMidSlotBytes;
     static bool attr_done = false;
     if (!attr_done) {
-        RS_CUDA_TRY(cudaFuncSetAttribute(p1_mid_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kMidCap));
-        RS_CUDA_TRY(cudaFuncSetAttribute(p2_mid_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kMidCap));
+        RS_CUDA_TRY(cudaFuncSetAttribute(p1_large_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kMidCap));
+        RS_CUDA_TRY(cudaFuncSetAttribute(p2_large_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kMidCap));
+        RS_CUDA_TRY(cudaFuncSetAttribute(p2_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2_mid_smem));
         attr_done = true;
     }
     // ---- P1
     if (g->n_small) {
-        p1_small_kernel<<<grid_for(g->n_small * 32, NT, 8), NT, 0, s>>>(
+        p1_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, s>>>(
             g->off, g->col, g->lab, g->rows_small, g->n_small, g->k, g->LG, g->rec, g->Lall, g->wmax_bits);
-        RS_CUDA_TRY(cudaGetLastError());
+        RS_LAUNCHED(g, s, "p1_small");
     }
     if (g->n_mid) {
-        p1_mid_kernel<NT><<<grid_for(g->n_mid, 1, 4), NT, p1_smem, s>>>(
+        p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, 8), NT, 0, s>>>(
             g->off, g->col, g->lab, g->rows_mid, g->n_mid, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err);
-        RS_CUDA_TRY(cudaGetLastError());
+        RS_LAUNCHED(g, s, "p1_mid");
+    }
+    if (g->n_large) {
+        p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, p1_smem, s>>>(
+            g->off, g->col, g->lab, g->rows_large, g->n_large, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err);
+        RS_LAUNCHED(g, s, "p1_large");
     }
     if (g->n_hubs) {
         hub_p1_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, s>>>(
             g->off, g->col, g->lab, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->hkey,
             g->hcnt, g->hagg, err);
-        RS_CUDA_TRY(cudaGetLastError());
+        RS_LAUNCHED(g, s, "hub_p1_insert");
         hub_p1_finish_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, s>>>(
             g->off, g->lab, g->hubs, g->n_hubs, g->k, g->LG, g->hkey, g->hcnt, g->hagg, g->rec, g->Lall,
             g->wmax_bits);
-        RS_CUDA_TRY(cudaGetLastError());
+        RS_LAUNCHED(g, s, "hub_p1_finish");
     }
     // ---- G_x offsets
     gx_capacity_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->rec, n, g->xoff);
-    RS_CUDA_TRY(cudaGetLastError());
-    if (int rc = inclusive_scan_i64(g->xoff + 1, n, g->scan_tmp, s)) return rc;
+    RS_LAUNCHED(g, s, "gx_capacity");
+    int64_t scan_launches = 0;
+    if (int rc = inclusive_scan_i64(g->xoff + 1, n, g->scan_tmp, s, &scan_launches)) return rc;
+    g->launches += scan_launches - 1;
+    prof_mark(g, s, "gx_scan", true);
     // ---- P2
     if (g->n_small) {
-        p2_small_kernel<<<grid_for(g->n_small * 32, NT, 8), NT, 0, s>>>(
-            g->off, g->col, g->rows_small, g->n_small, g->LG, g->rec, g->acc, g->xoff, g->xcol, g->xS,
+        p2_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, s>>>(
+            g->off, g->col, g->lab, g->rows_small, g->n_small, g->LG, g->rec, g->acc, g->xoff, g->xcol, g->xS,
             g->xout, g->xin);
-        RS_CUDA_TRY(cudaGetLastError());
+        RS_LAUNCHED(g, s, "p2_small");
     }
     if (g->n_mid) {
-        p2_mid_kernel<NT><<<grid_for(g->n_mid, 1, 4), NT, p2_smem, s>>>(
+        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, p2_mid_smem, s>>>(
             g->off, g->col, g->rows_mid, g->n_mid, g->k, g->LG, g->rec, g->acc, g->xoff, g->xcol, g->xS,
             g->xout, g->xin, err);
-        RS_CUDA_TRY(cudaGetLastError());
+        RS_LAUNCHED(g, s, "p2_mid");
+    }
+    if (g->n_large) {
+        p2_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, p2_smem, s>>>(
+            g->off, g->col, g->rows_large, g->n_large, g->k, g->LG, g->rec, g->acc, g->xoff, g->xcol, g->xS,
+            g->xout, g->xin, err);
+        RS_LAUNCHED(g, s, "p2_large");
     }
     if (g->n_hubs) {
         hub_p2_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, s>>>(
             g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->rec, g->hkey, g->hq,
             g->hitem_out, g->hitem_in, err);
-        RS_CUDA_TRY(cudaGetLastError());
+        RS_LAUNCHED(g, s, "hub_p2_insert");
         hub_p2_sigma_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, s>>>(
             g->hubs, g->n_hubs, g->LG, g->hagg, g->off, g->hkey, g->hcnt, g->hsig, g->hitem_out, g->hitem_in,
             g->xout, g->xin);
-        RS_CUDA_TRY(cudaGetLastError());
+        RS_LAUNCHED(g, s, "hub_p2_sigma");
         hub_p2_emit_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, s>>>(
             g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->rec, g->hkey, g->hcnt,
             g->hq, g->hsig, g->hitem_out, g->hitem_in, g->acc, g->xoff, g->xcol, g->xS, err);
-        RS_CUDA_TRY(cudaGetLastError());
+        RS_LAUNCHED(g, s, "hub_p2_emit");
     }
     // ---- P3
-    p3_triangles_kernel<<<grid_for(n * 32, NT, 8), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xout, g->xin,
-                                                                g->rec, g->acc, err);
-    RS_CUDA_TRY(cudaGetLastError());
+    unsigned long long *tri_n = (unsigned long long *)(g->d_flag + 48);
+    RS_CUDA_TRY(cudaMemsetAsync(tri_n, 0, sizeof(unsigned long long), s));
+    p3_list_kernel<<<grid_for(n * 32, NT, 8), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->rec,
+                                                           (Tri *)g->tri, g->tri_cap, tri_n, g->acc, err);
+    RS_LAUNCHED(g, s, "p3_list");
+    p3_terms_kernel<<<grid_for(g->tri_cap, NT, 8), NT, 0, s>>>((const Tri *)g->tri, g->tri_cap, tri_n, g->xoff,
+                                                               g->xcol, g->xS, g->xin, g->rec, g->acc, err);
+    RS_LAUNCHED(g, s, "p3_terms");
     // ---- finalize
     finalize_kernel<<<grid_for(n, NT, 8), NT, 0, s>>>(n, g->off, g->acc, g->wmax_bits, g->RD, scores);
-    RS_CUDA_TRY(cudaGetLastError());
+    RS_LAUNCHED(g, s, "finalize");
     return 0;
 }

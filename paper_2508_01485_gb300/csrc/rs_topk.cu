@@ -3,164 +3,72 @@
 //
 // Each node is a unique 96-bit key (bits(score) << 32 | ~id): for scores >= 0
 // the IEEE bit pattern orders like the value, and ~id makes smaller ids rank
-// higher among equal scores.  A most-significant-digit radix select with six
-// 16-bit digits narrows the candidates: per level, a histogram of the digit
-// over the current candidates, one CTA finds the bucket holding the K-th key,
-// keys of higher buckets are final ("sure"), keys of that bucket stay
-// candidates.  When the candidates left are exactly the ones still needed the
-// selection stops; one CTA then sorts the K selected keys (bitonic, shared
-// memory) and writes ids and scores.
+// higher among equal scores.  One cooperative launch (one 1024-thread CTA per
+// SM, grid-wide barriers from cooperative groups) runs a most-significant-digit
+// radix select with 12-bit digits:
+//   per level: privatised shared-memory histograms of the digit over the
+//   current candidates, merged into a global histogram; CTA 0 finds the bucket
+//   that holds the K-th key; keys of higher buckets are final ("sure"), keys
+//   of that bucket stay candidates.
+// As soon as the sure keys and the candidates fit one shared-memory sort
+// (kSortMax keys), CTA 0 sorts them (bitonic) and writes the first K.
+#include <cooperative_groups.h>
+
 #include "rs.h"
 #include "rs_internal.cuh"
 
+namespace cg = cooperative_groups;
 using namespace rs;
 
 namespace {
 
-constexpr int kDigits = 6;
-constexpr int kBins = 1 << 16;
-constexpr int kSortMax = 16384;   // largest K (shared-memory bitonic sort)
+constexpr int kTkThreads = 1024;
+constexpr int kBits = 12;
+constexpr int kBins = 1 << kBits;
+constexpr int kLevels = 96 / kBits;
+constexpr int kSortMax = 16384;   // largest K, and the size of the final sort
+constexpr size_t kTkSmem = (size_t)kSortMax * (8 + 4);
 
-// control words
-enum { C_CAND = 0, C_NEED = 1, C_SURE = 2, C_SEL = 3, C_DONE = 4, C_NEXT = 5, C_LEVEL = 6 };
+enum { C_CAND = 0, C_NEED = 1, C_SURE = 2, C_SEL = 3, C_DONE = 4, C_NEXT = 5, C_SRC = 6 };
 
-__device__ __forceinline__ uint32_t digit_of(unsigned long long key, int32_t id, int level) {
-    uint32_t nid = ~(uint32_t)id;
-    switch (level) {
-        case 0: return (uint32_t)(key >> 48) & 0xFFFF;
-        case 1: return (uint32_t)(key >> 32) & 0xFFFF;
-        case 2: return (uint32_t)(key >> 16) & 0xFFFF;
-        case 3: return (uint32_t)key & 0xFFFF;
-        case 4: return nid >> 16;
-        default: return nid & 0xFFFF;
+// digit `level` (0 = most significant) of the 96-bit key (key64 : ~id)
+__device__ __forceinline__ uint32_t digit_of(unsigned long long key, uint32_t nid, int level) {
+    int hi = 95 - kBits * level;                 // top bit of the digit
+    int lo = hi - kBits + 1;
+    if (lo >= 32) return (uint32_t)(key >> (lo - 32)) & (kBins - 1);
+    if (hi < 32) return (nid >> lo) & (kBins - 1);
+    // straddles the two words: bits [hi-32 .. 0] of key, then bits [31 .. lo] of nid
+    uint32_t top = (uint32_t)(key & ((1ull << (hi - 31)) - 1));
+    return ((top << (32 - lo)) | (nid >> lo)) & (kBins - 1);
+}
+
+struct TkArgs {
+    const double *scores;
+    int64_t n;
+    int32_t k;
+    int32_t *ids_out;
+    double *scores_out;
+    uint32_t *hist;                 // kBins
+    int *ctrl;
+    unsigned long long *key[2];     // candidate buffers (n each)
+    uint32_t *nid[2];
+    unsigned long long *skey;       // sure keys (kSortMax)
+    uint32_t *snid;
+};
+
+__device__ __forceinline__ void load_item(const TkArgs &A, int level, int src, int64_t i,
+                                          unsigned long long &key, uint32_t &nid) {
+    if (level == 0) {
+        key = (unsigned long long)__double_as_longlong(A.scores[i]);
+        nid = ~(uint32_t)i;
+    } else {
+        key = A.key[src][i];
+        nid = A.nid[src][i];
     }
 }
 
-__global__ void tk_init_kernel(int *ctrl, int64_t n, int32_t k) {
-    ctrl[C_CAND] = (int)n;
-    ctrl[C_NEED] = k;
-    ctrl[C_SURE] = 0;
-    ctrl[C_SEL] = 0;
-    ctrl[C_DONE] = 0;
-    ctrl[C_NEXT] = 0;
-    ctrl[C_LEVEL] = -1;
-}
-
-// level 0 reads the scores directly; later levels read the candidate arrays
-__global__ void tk_hist_kernel(const double *scores, const unsigned long long *ckey, const int32_t *cid,
-                               int level, const int *ctrl, uint32_t *hist) {
-    if (ctrl[C_DONE]) return;
-    int64_t m = ctrl[C_CAND];
-    int lane = threadIdx.x & 31;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = base + threadIdx.x;
-        bool act = i < m;
-        uint32_t dg = 0;
-        if (act) {
-            unsigned long long key = level == 0 ? (unsigned long long)__double_as_longlong(scores[i]) : ckey[i];
-            int32_t id = level == 0 ? (int32_t)i : cid[i];
-            dg = digit_of(key, id, level);
-        }
-        unsigned am = __ballot_sync(0xFFFFFFFFu, act);
-        if (act) {
-            unsigned grp = __match_any_sync(am, dg);
-            if (lane == __ffs(grp) - 1) atomicAdd(&hist[dg], (uint32_t)__popc(grp));
-        }
-    }
-}
-
-// one CTA of 1024 threads: the bucket holding the need-th largest key
-__global__ void __launch_bounds__(1024) tk_select_kernel(const uint32_t *hist, int *ctrl) {
-    if (ctrl[C_DONE]) return;
-    __shared__ int64_t part[1024];
-    __shared__ int64_t above_sh;
-    int t = threadIdx.x;
-    constexpr int per = kBins / 1024;
-    int hi_bin = kBins - per * t;                 // chunk [hi_bin - per, hi_bin), from the top
-    int64_t s = 0;
-    for (int j = 1; j <= per; ++j) s += hist[hi_bin - j];
-    part[t] = s;
-    __syncthreads();
-    // inclusive scan of chunk totals from the top
-    for (int o = 1; o < 1024; o <<= 1) {
-        int64_t v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    int64_t need = ctrl[C_NEED];
-    int64_t before = t ? part[t - 1] : 0;         // keys in higher chunks
-    if (before < need && need <= part[t]) {
-        int64_t acc = before;
-        for (int j = 1; j <= per; ++j) {
-            int b = hi_bin - j;
-            if (acc + hist[b] >= need) {
-                ctrl[C_SEL] = b;
-                above_sh = acc;
-                break;
-            }
-            acc += hist[b];
-        }
-    }
-    __syncthreads();
-    if (t == 0) {
-        ctrl[C_NEED] = (int)(need - above_sh);
-        ctrl[C_NEXT] = 0;
-    }
-}
-
-__global__ void tk_compact_kernel(const double *scores, const unsigned long long *ckey, const int32_t *cid,
-                                  int level, int *ctrl, unsigned long long *nkey, int32_t *nid,
-                                  unsigned long long *skey, int32_t *sid) {
-    if (ctrl[C_DONE]) return;
-    int64_t m = ctrl[C_CAND];
-    uint32_t sel = (uint32_t)ctrl[C_SEL];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long key = level == 0 ? (unsigned long long)__double_as_longlong(scores[i]) : ckey[i];
-        int32_t id = level == 0 ? (int32_t)i : cid[i];
-        uint32_t dg = digit_of(key, id, level);
-        if (dg > sel) {
-            int p = atomicAdd(&ctrl[C_SURE], 1);
-            skey[p] = key; sid[p] = id;
-        } else if (dg == sel) {
-            int p = atomicAdd(&ctrl[C_NEXT], 1);
-            nkey[p] = key; nid[p] = id;
-        }
-    }
-}
-
-__global__ void tk_advance_kernel(int *ctrl, int level) {
-    if (ctrl[C_DONE]) return;
-    ctrl[C_CAND] = ctrl[C_NEXT];
-    if (ctrl[C_CAND] <= ctrl[C_NEED]) {
-        ctrl[C_DONE] = 1;
-        ctrl[C_LEVEL] = level;     // the candidates left sit in this level's target buffer
-    }
-}
-
-// sort the K selected keys: sure keys plus the final candidates
-__global__ void __launch_bounds__(1024) tk_sort_kernel(const unsigned long long *skey, const int32_t *sid,
-                                                       const unsigned long long *key_even, const int32_t *id_even,
-                                                       const unsigned long long *key_odd, const int32_t *id_odd,
-                                                       const int *ctrl, int32_t k, int32_t *ids_out,
-                                                       double *scores_out) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    // even levels write their candidates to the first buffer, odd levels to the second
-    bool odd = ctrl[C_LEVEL] & 1;
-    const unsigned long long *ckey = odd ? key_odd : key_even;
-    const int32_t *cid = odd ? id_odd : id_even;
-    int P = 1;
-    while (P < k) P <<= 1;
-    unsigned long long *key = (unsigned long long *)smem;
-    uint32_t *nid = (uint32_t *)(key + P);
-    int ns = ctrl[C_SURE];
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        if (i < ns) { key[i] = skey[i]; nid[i] = ~(uint32_t)sid[i]; }
-        else if (i < k) { key[i] = ckey[i - ns]; nid[i] = ~(uint32_t)cid[i - ns]; }
-        else { key[i] = 0; nid[i] = 0; }     // padding sorts last (descending order)
-    }
-    __syncthreads();
-    // bitonic sort, descending by (key, ~id)
+// descending bitonic sort of (key, nid) pairs in shared memory, P a power of two
+__device__ void block_sort_desc(unsigned long long *key, uint32_t *nid, int P) {
     for (int size = 2; size <= P; size <<= 1)
         for (int st = size >> 1; st; st >>= 1) {
             for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
@@ -181,9 +89,122 @@ __global__ void __launch_bounds__(1024) tk_sort_kernel(const unsigned long long 
             }
             __syncthreads();
         }
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        ids_out[i] = (int32_t)~nid[i];
-        if (scores_out) scores_out[i] = __longlong_as_double((long long)key[i]);
+}
+
+__global__ void __launch_bounds__(kTkThreads) tk_select_kernel(TkArgs A) {
+    cg::grid_group grid = cg::this_grid();
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *sh_hist = (uint32_t *)smem;                      // kBins (levels)
+    __shared__ uint32_t part[kTkThreads];
+    __shared__ int sh_sel;
+    __shared__ int64_t sh_above;
+    int tid = threadIdx.x;
+    int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid;
+    int64_t gsize = (int64_t)gridDim.x * blockDim.x;
+    int *ctrl = A.ctrl;
+    if (gtid == 0) {
+        ctrl[C_CAND] = (int)A.n; ctrl[C_NEED] = A.k; ctrl[C_SURE] = 0; ctrl[C_SEL] = 0;
+        ctrl[C_NEXT] = 0; ctrl[C_SRC] = 0;
+        ctrl[C_DONE] = A.n <= kSortMax ? 1 : 0;                 // everything fits the final sort
+    }
+    grid.sync();
+    int level = 0;
+    for (; level < kLevels; ++level) {
+        if (*(volatile int *)&ctrl[C_DONE]) break;
+        int src = ctrl[C_SRC];
+        int64_t m = ctrl[C_CAND];
+        // histogram of this level's digit
+        for (int b = tid; b < kBins; b += blockDim.x) sh_hist[b] = 0;
+        for (int64_t b = gtid; b < kBins; b += gsize) A.hist[b] = 0;
+        grid.sync();
+        for (int64_t i = gtid; i < m; i += gsize) {
+            unsigned long long key; uint32_t nid;
+            load_item(A, level, src, i, key, nid);
+            atomicAdd(&sh_hist[digit_of(key, nid, level)], 1u);
+        }
+        __syncthreads();
+        for (int b = tid; b < kBins; b += blockDim.x)
+            if (sh_hist[b]) atomicAdd(&A.hist[b], sh_hist[b]);
+        grid.sync();
+        // CTA 0: the bucket holding the need-th largest key
+        if (blockIdx.x == 0) {
+            constexpr int per = kBins / kTkThreads;             // 4 bins per thread, from the top
+            int top = kBins - per * tid;
+            uint32_t s = 0;
+            for (int j = 1; j <= per; ++j) s += A.hist[top - j];
+            part[tid] = s;
+            __syncthreads();
+            for (int o = 1; o < kTkThreads; o <<= 1) {
+                uint32_t v = tid >= o ? part[tid - o] : 0;
+                __syncthreads();
+                part[tid] += v;
+                __syncthreads();
+            }
+            int64_t need = ctrl[C_NEED];
+            int64_t before = tid ? part[tid - 1] : 0;
+            if (before < need && need <= (int64_t)part[tid]) {
+                int64_t acc = before;
+                for (int j = 1; j <= per; ++j) {
+                    int b = top - j;
+                    if (acc + A.hist[b] >= need) { sh_sel = b; sh_above = acc; break; }
+                    acc += A.hist[b];
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                ctrl[C_SEL] = sh_sel;
+                ctrl[C_NEED] = (int)(need - sh_above);
+                ctrl[C_NEXT] = 0;
+            }
+        }
+        grid.sync();
+        // compact: higher buckets are sure, the selected bucket stays
+        uint32_t sel = (uint32_t)ctrl[C_SEL];
+        int dst = src ^ 1;
+        for (int64_t i = gtid; i < m; i += gsize) {
+            unsigned long long key; uint32_t nid;
+            load_item(A, level, src, i, key, nid);
+            uint32_t dg = digit_of(key, nid, level);
+            if (dg > sel) {
+                int p = atomicAdd(&ctrl[C_SURE], 1);
+                A.skey[p] = key; A.snid[p] = nid;
+            } else if (dg == sel) {
+                int p = atomicAdd(&ctrl[C_NEXT], 1);
+                A.key[dst][p] = key; A.nid[dst][p] = nid;
+            }
+        }
+        grid.sync();
+        if (gtid == 0) {
+            ctrl[C_CAND] = ctrl[C_NEXT];
+            ctrl[C_SRC] = dst;
+            if (ctrl[C_CAND] <= ctrl[C_NEED] || ctrl[C_SURE] + ctrl[C_CAND] <= kSortMax) ctrl[C_DONE] = 1;
+        }
+        grid.sync();
+    }
+    // CTA 0: sort the sure keys and the candidates left, write the first K
+    if (blockIdx.x != 0) return;
+    unsigned long long *key = (unsigned long long *)smem;
+    uint32_t *nid = (uint32_t *)(key + kSortMax);
+    bool from_scores = level == 0;                              // nothing was compacted: n <= kSortMax
+    int ns = ctrl[C_SURE];
+    int nc = ctrl[C_CAND];
+    int src = ctrl[C_SRC];
+    int total = ns + nc;
+    int P = 1;
+    while (P < total) P <<= 1;
+    for (int i = tid; i < P; i += blockDim.x) {
+        if (i < ns) { key[i] = A.skey[i]; nid[i] = A.snid[i]; }
+        else if (i < total) {
+            int64_t j = i - ns;
+            if (from_scores) { key[i] = (unsigned long long)__double_as_longlong(A.scores[j]); nid[i] = ~(uint32_t)j; }
+            else { key[i] = A.key[src][j]; nid[i] = A.nid[src][j]; }
+        } else { key[i] = 0; nid[i] = 0; }                     // padding sorts last
+    }
+    __syncthreads();
+    block_sort_desc(key, nid, P);
+    for (int i = tid; i < A.k; i += blockDim.x) {
+        A.ids_out[i] = (int32_t)~nid[i];
+        if (A.scores_out) A.scores_out[i] = __longlong_as_double((long long)key[i]);
     }
 }
 
@@ -196,9 +217,8 @@ static int ensure_topk_workspace(rs_graph *g, int64_t n) {
     int64_t cap = n > 1 ? n : 1;
     RS_CUDA_TRY(cudaMalloc(&g->tk_hist, kBins * sizeof(uint32_t)));
     RS_CUDA_TRY(cudaMalloc(&g->tk_ctrl, 8 * sizeof(int)));
-    // two candidate buffers plus the sure list
     RS_CUDA_TRY(cudaMalloc(&g->tk_keys, (2 * cap + kSortMax) * sizeof(unsigned long long)));
-    RS_CUDA_TRY(cudaMalloc(&g->tk_ids, (2 * cap + kSortMax) * sizeof(int32_t)));
+    RS_CUDA_TRY(cudaMalloc(&g->tk_ids, (2 * cap + kSortMax) * sizeof(uint32_t)));
     g->tk_cap = cap;
     return 0;
 }
@@ -206,39 +226,29 @@ static int ensure_topk_workspace(rs_graph *g, int64_t n) {
 int rs::topk_scores(rs_graph *g, const double *scores, int64_t n, int32_t k, int32_t *ids, double *out_scores,
                     cudaStream_t s) {
     if (k > kSortMax) return fail(RS_EINVAL, "rs_topk: k above 16384 is not supported");
+    if (n > 2147483647LL) return fail(RS_EINVAL, "rs_topk: n too large");
     if (int rc = ensure_topk_workspace(g, n)) return rc;
-    static bool attr_done = false;
-    if (!attr_done) {
-        RS_CUDA_TRY(cudaFuncSetAttribute(tk_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSortMax * (8 + 4)));
-        attr_done = true;
+    static int grid = 0;
+    if (!grid) {
+        RS_CUDA_TRY(cudaFuncSetAttribute(tk_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTkSmem));
+        int dev = 0, sms = 0, per_sm = 0;
+        RS_CUDA_TRY(cudaGetDevice(&dev));
+        RS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        RS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tk_select_kernel, kTkThreads, kTkSmem));
+        if (per_sm < 1) return fail(RS_ECUDA, "rs_topk: selection kernel does not fit an SM");
+        grid = sms * per_sm;
     }
     int64_t cap = g->tk_cap;
-    unsigned long long *ka = g->tk_keys, *kb = g->tk_keys + cap, *ks = g->tk_keys + 2 * cap;
-    int32_t *ia = g->tk_ids, *ib = g->tk_ids + cap, *is = g->tk_ids + 2 * cap;
-    int *ctrl = g->tk_ctrl;
-    tk_init_kernel<<<1, 1, 0, s>>>(ctrl, n, k);
-    RS_CUDA_TRY(cudaGetLastError());
-    int grid = grid_for(n, 256, 8);
-    for (int level = 0; level < kDigits; ++level) {
-        RS_CUDA_TRY(cudaMemsetAsync(g->tk_hist, 0, kBins * sizeof(uint32_t), s));
-        const unsigned long long *ck = level == 0 ? nullptr : (level % 2 ? ka : kb);
-        const int32_t *ci = level == 0 ? nullptr : (level % 2 ? ia : ib);
-        unsigned long long *nk = level % 2 ? kb : ka;
-        int32_t *ni = level % 2 ? ib : ia;
-        tk_hist_kernel<<<grid, 256, 0, s>>>(scores, ck, ci, level, ctrl, g->tk_hist);
-        RS_CUDA_TRY(cudaGetLastError());
-        tk_select_kernel<<<1, 1024, 0, s>>>(g->tk_hist, ctrl);
-        RS_CUDA_TRY(cudaGetLastError());
-        tk_compact_kernel<<<grid, 256, 0, s>>>(scores, ck, ci, level, ctrl, nk, ni, ks, is);
-        RS_CUDA_TRY(cudaGetLastError());
-        tk_advance_kernel<<<1, 1, 0, s>>>(ctrl, level);
-        RS_CUDA_TRY(cudaGetLastError());
-    }
-    int P = 1;
-    while (P < k) P <<= 1;
-    size_t smem = (size_t)P * (8 + 4);
-    tk_sort_kernel<<<1, 1024, smem, s>>>(ks, is, ka, ia, kb, ib, ctrl, k, ids, out_scores);
-    RS_CUDA_TRY(cudaGetLastError());
+    TkArgs A;
+    A.scores = scores; A.n = n; A.k = k; A.ids_out = ids; A.scores_out = out_scores;
+    A.hist = g->tk_hist; A.ctrl = g->tk_ctrl;
+    unsigned long long *kb = g->tk_keys;
+    uint32_t *ib = (uint32_t *)g->tk_ids;
+    A.key[0] = kb; A.key[1] = kb + cap; A.skey = kb + 2 * cap;
+    A.nid[0] = ib; A.nid[1] = ib + cap; A.snid = ib + 2 * cap;
+    prof_begin(g, s);
+    void *args[] = {&A};
+    RS_CUDA_TRY(cudaLaunchCooperativeKernel((void *)tk_select_kernel, dim3(grid), dim3(kTkThreads), args, kTkSmem, s));
+    RS_LAUNCHED(g, s, "tk_select");
     return 0;
 }
