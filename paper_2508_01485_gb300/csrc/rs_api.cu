@@ -478,6 +478,9 @@ static int alloc_workspace(rs_graph *g) {
     RS_CUDA_TRY(dmalloc(&g->acc, 2 * n));
     RS_CUDA_TRY(dmalloc(&g->wmax_bits, 1));
     RS_CUDA_TRY(dmalloc(&g->Lall, n));
+    RS_CUDA_TRY(dmalloc(&g->rsum, n));
+    RS_CUDA_TRY(dmalloc(&g->cl_col, nnz));
+    RS_CUDA_TRY(dmalloc(&g->cl_lab, nnz));
     RS_CUDA_TRY(dmalloc(&g->xoff, n + 1));
     RS_CUDA_TRY(dmalloc(&g->xcol, nnz));
     RS_CUDA_TRY(dmalloc(&g->xS, nnz));
@@ -498,7 +501,7 @@ static void free_graph(rs_graph *g) {
     void *ptrs[] = {g->off, g->off_alt, g->col, g->col_alt, g->lab, g->removed, g->dead,
                     g->rows_small, g->rows_mid, g->rows_large, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
                     g->Lall, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->scan_tmp, g->tk_hist,
-                    g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->tri};
+                    g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->tri, g->rsum, g->cl_col, g->cl_lab};
     for (void *p : ptrs) cudaFree(p);
     free_hub_tables(g);
     for (cudaEvent_t e : g->prof_ev) cudaEventDestroy(e);

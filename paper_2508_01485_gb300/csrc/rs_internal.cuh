@@ -47,6 +47,13 @@ struct __align__(16) HubAgg {
     uint32_t pad[2];
 };
 
+// row aggregates kept from P1 for P2: X = sum_c f_c LG[f_c] (exact) and the
+// number of distinct neighbour communities L
+struct __align__(8) RowSum {
+    uint64_t xlo, xhi;
+    uint32_t L, pad;
+};
+
 // a G_x triangle (a, b, c), rank a < b < c, with its three out-direction values
 struct __align__(8) Tri {
     int32_t a, b, c, pad;
@@ -100,6 +107,9 @@ struct rs_graph {
     unsigned long long *acc = nullptr;        // 2 words per node
     unsigned long long *wmax_bits = nullptr;  // double bits of w_max
     int32_t *Lall = nullptr;                  // distinct neighbour communities per node
+    rs::RowSum *rsum = nullptr;               // per-node aggregates from P1
+    int32_t *cl_col = nullptr;                // cross lists: row v's cross neighbours at
+    int32_t *cl_lab = nullptr;                //   [off[v], off[v] + dx(v)) (ids, labels)
     int64_t *xoff = nullptr;                  // G_x row offsets (n + 1)
     int32_t *xcol = nullptr;                  // G_x neighbours (capacity nnz)
     rs::df *xS = nullptr;                     // S(w -> u) = w_w(C(u))^(1/3)

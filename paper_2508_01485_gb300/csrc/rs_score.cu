@@ -179,23 +179,29 @@ struct SmallTable {
     uint8_t cnt[kSlots][kThreads];
 };
 
-// counts of row v's neighbour communities; returns the aggregates
+// counts of row v's neighbour communities, and its cross list (neighbours of
+// another community, in id order) written to cl_col / cl_lab at b; returns the aggregates
 __device__ __forceinline__ RowAgg small_row_counts(const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
                                                    int64_t b, int d, int32_t cv, const uint64_t *__restrict__ LG,
                                                    SmallTable &T, int t, int &nf, uint32_t &own,
-                                                   uint64_t &seen) {
+                                                   uint64_t &seen, int32_t *__restrict__ cl_col,
+                                                   int32_t *__restrict__ cl_lab) {
     nf = 0;
     own = 0;
+    int nx = 0;
     for (int j0 = 0; j0 < d; j0 += kPrefetch) {
-        int32_t c[kPrefetch];
+        int32_t x[kPrefetch], c[kPrefetch];
 #pragma unroll
-        for (int q = 0; q < kPrefetch; ++q) c[q] = (j0 + q < d) ? col[b + j0 + q] : -1;
+        for (int q = 0; q < kPrefetch; ++q) x[q] = (j0 + q < d) ? col[b + j0 + q] : -1;
 #pragma unroll
-        for (int q = 0; q < kPrefetch; ++q) c[q] = (c[q] >= 0) ? lab[c[q]] : -1;
+        for (int q = 0; q < kPrefetch; ++q) c[q] = (x[q] >= 0) ? lab[x[q]] : -1;
 #pragma unroll
         for (int q = 0; q < kPrefetch; ++q) {
             if (j0 + q >= d) break;
             if (c[q] == cv) { own++; continue; }
+            cl_col[b + nx] = x[q];
+            cl_lab[b + nx] = c[q];
+            ++nx;
             int sl = 0;
             while (sl < nf && T.lab[sl][t] != c[q]) ++sl;
             if (sl == nf) { T.lab[sl][t] = c[q]; T.cnt[sl][t] = 1; ++nf; }
@@ -212,10 +218,20 @@ __device__ __forceinline__ RowAgg small_row_counts(const int32_t *__restrict__ c
     return RowAgg{(uint32_t)d, (uint32_t)nf + (own > 0 ? 1u : 0u), X};
 }
 
+__device__ __forceinline__ void store_rowsum(RowSum *rsum, int32_t v, const RowAgg &a) {
+    RowSum r;
+    r.xlo = (uint64_t)a.X;
+    r.xhi = (uint64_t)(a.X >> 64);
+    r.L = a.L;
+    r.pad = 0;
+    rsum[v] = r;
+}
+
 __global__ void __launch_bounds__(kThreads) p1_small_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
     const int32_t *__restrict__ rows, int64_t nrows, int32_t k, const uint64_t *__restrict__ LG,
-    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits) {
+    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits,
+    RowSum *__restrict__ rsum, int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab) {
     __shared__ SmallTable T;
     int t = threadIdx.x;
     df best{0.0f, 0.0f};
@@ -229,7 +245,8 @@ __global__ void __launch_bounds__(kThreads) p1_small_kernel(
         int nf;
         uint32_t own;
         uint64_t seen;
-        RowAgg a = small_row_counts(col, lab, b, d, cv, LG, T, t, nf, own, seen);
+        RowAgg a = small_row_counts(col, lab, b, d, cv, LG, T, t, nf, own, seen, cl_col, cl_lab);
+        store_rowsum(rsum, v, a);
         df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
         while (seen) {
             uint32_t f = (uint32_t)(__ffsll((long long)seen) - 1);
@@ -253,7 +270,8 @@ constexpr int kMidWarps = kThreads / 32;
 __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
     const int32_t *__restrict__ rows, int64_t nrows, int32_t k, const uint64_t *__restrict__ LG,
-    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits, int *err) {
+    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits, int *err,
+    RowSum *__restrict__ rsum, int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab) {
     __shared__ int32_t skey[kMidWarps][kWarpCap];
     __shared__ uint32_t scnt[kMidWarps][kWarpCap];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -270,17 +288,23 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
         for (uint32_t j = lane; j < cap; j += 32) { t.key[j] = kEmpty; t.cnt[j] = 0; }
         __syncwarp();
         uint32_t own = 0;
+        int32_t nx = 0;
         for (int base = 0; base < d; base += 32) {
             int e = base + lane;
             bool act = e < d;
-            int32_t c = act ? lab[col[b + e]] : -1;
+            int32_t x = act ? col[b + e] : -1;
+            int32_t c = act ? lab[x] : -1;
             own += (act && c == cv);
             bool foreign = act && c != cv;
             unsigned fm = __ballot_sync(FULL, foreign);
             if (foreign) {
+                int64_t p = b + nx + __popc(fm & lanemask_lt());
+                cl_col[p] = x;
+                cl_lab[p] = c;
                 unsigned grp = __match_any_sync(fm, c);
                 if (lane == __ffs(grp) - 1) tab_insert(t, c, __popc(grp), err);
             }
+            nx += __popc(fm);
         }
         __syncwarp();
         for (int o = 16; o; o >>= 1) own += __shfl_xor_sync(FULL, own, o);
@@ -300,6 +324,7 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
             best = df_max(best, p1_row_result(a, own, cm, k, LG, r, cv, wown));
             rec[v] = r;
             Lall[v] = (int32_t)a.L;
+            store_rowsum(rsum, v, a);
         }
         __syncwarp();
     }
@@ -461,62 +486,60 @@ __global__ void gx_capacity_kernel(const NodeRec *__restrict__ rec, int64_t n, i
 // ======================================================================================
 // P2
 // ======================================================================================
-// Small rows, one thread per row: counts as in P1, then a second pass over the
-// neighbours emits the Type-II terms and the G_x entries in id order.
+// P2 for small and mid rows walks the cross list P1 wrote (the neighbours of
+// another community, in id order) and the row aggregates; own-community
+// neighbours are never touched again.
+
+// Small rows, one thread per row.  The count f of a cross neighbour's
+// community is found by scanning the (short) cross list.
 __global__ void __launch_bounds__(kThreads) p2_small_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
-    const int32_t *__restrict__ rows, int64_t nrows, const uint64_t *__restrict__ LG,
-    const NodeRec *__restrict__ rec, unsigned long long *acc, const int64_t *__restrict__ xoff,
-    int32_t *__restrict__ xcol, df *__restrict__ xS, int32_t *__restrict__ xout, int32_t *__restrict__ xin) {
-    __shared__ SmallTable T;
-    int t = threadIdx.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < nrows; i0 += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = i0 + t;
-        if (i >= nrows) continue;
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows,
+    const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
+    const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
+    const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
+    int32_t *__restrict__ xout, int32_t *__restrict__ xin) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x) {
         int32_t w = rows[i];
         int64_t b = off[w];
         int d = (int)(off[w + 1] - b);
         NodeRec rw = rec[w];
-        int nf;
-        uint32_t own;
-        uint64_t seen;
-        RowAgg a = small_row_counts(col, lab, b, d, rw.label, LG, T, t, nf, own, seen);
-        // sigma per foreign count, cached for count 1 and the last other count
-        df sig1{-1.0f, 0.0f}, sigl{0.0f, 0.0f};
-        uint32_t fl = 0;
-        int64_t xb = xoff[w];
+        int dx = rw.dx;
         int32_t no = 0, ni = 0;
-        bool gx = rw.dx >= 2;
-        for (int j = 0; j < d; ++j) {
-            int32_t u = col[b + j];
-            if (lab[u] == rw.label) continue;
-            NodeRec ru = rec[u];
-            int sl = 0;
-            while (sl < nf && T.lab[sl][t] != ru.label) ++sl;
-            if (sl == nf) continue;                       // not reached: P1 saw the same labels
-            uint32_t f = T.cnt[sl][t];
-            df sig;
-            if (f == 1) {
-                if (sig1.hi < 0.0f) sig1 = df_cbrt(column_weight(a, 1, LG));
-                sig = sig1;
-            } else {
-                if (f != fl) { sigl = df_cbrt(column_weight(a, f, LG)); fl = f; }
-                sig = sigl;
-                // Type-II: the other neighbours of w in community C(u)
-                u128 rest = 0;
-                for (int j2 = 0; j2 < d; ++j2) {
-                    if (j2 == j) continue;
-                    int32_t x = col[b + j2];
-                    if (lab[x] == ru.label) rest += rec[x].s_fix;
+        if (dx > 0) {
+            RowSum rs = rsum[w];
+            RowAgg a{(uint32_t)d, rs.L, ((u128)rs.xhi << 64) | rs.xlo};
+            df sig1{-1.0f, 0.0f}, sigl{0.0f, 0.0f};
+            uint32_t fl = 0;
+            int64_t xb = xoff[w];
+            bool gx = dx >= 2;
+            for (int j = 0; j < dx; ++j) {
+                int32_t u = cl_col[b + j];
+                int32_t c = cl_lab[b + j];
+                uint32_t f = 0;
+                for (int j2 = 0; j2 < dx; ++j2) f += (cl_lab[b + j2] == c);
+                df sig;
+                if (f == 1) {
+                    if (sig1.hi < 0.0f) sig1 = df_cbrt(column_weight(a, 1, LG));
+                    sig = sig1;
+                } else {
+                    if (f != fl) { sigl = df_cbrt(column_weight(a, f, LG)); fl = f; }
+                    sig = sigl;
+                    // Type-II: the other cross neighbours of w in community c
+                    u128 rest = 0;
+                    for (int j2 = 0; j2 < dx; ++j2)
+                        if (j2 != j && cl_lab[b + j2] == c) rest += rec[cl_col[b + j2]].s_fix;
+                    push_type2(acc, u, sig, rest);
                 }
-                push_type2(acc, u, sig, rest);
-            }
-            if (gx && ru.dx >= 2) {
-                int64_t p;
-                if (rank_after(ru.dx, u, rw.dx, w)) p = xb + no++;
-                else p = xb + rw.dx - 1 - ni++;
-                xcol[p] = u;
-                xS[p] = sig;
+                if (gx) {
+                    int32_t dxu = rec[u].dx;
+                    if (dxu >= 2) {
+                        int64_t p;
+                        if (rank_after(dxu, u, dx, w)) p = xb + no++;
+                        else p = xb + dx - 1 - ni++;
+                        xcol[p] = u;
+                        xS[p] = sig;
+                    }
+                }
             }
         }
         xout[w] = no;
@@ -524,14 +547,16 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
     }
 }
 
-// Mid rows, one warp per row: per-warp table with Type-II group sums
+// Mid rows, one warp per row: a per-warp table (community -> count, Type-II
+// sum) over the cross list, then the terms and the G_x entries in id order.
 constexpr int kMidSlotBytes = 4 + 4 + 16;   // key, count, 2-word sum
 
 __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ rows,
-    int64_t nrows, int32_t k, const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec,
-    unsigned long long *acc, const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol,
-    df *__restrict__ xS, int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err) {
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, int32_t k,
+    const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
+    const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
+    const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
+    int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t stage[kThreads];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -544,73 +569,68 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
         int64_t b = off[w];
         int d = (int)(off[w + 1] - b);
         NodeRec rw = rec[w];
-        uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(d, k));
-        Tab t;
-        t.q = (unsigned long long *)base_w;
-        t.key = (int32_t *)(base_w + 16 * kWarpCap);
-        t.cnt = (uint32_t *)(base_w + 20 * kWarpCap);
-        t.sig = nullptr;
-        t.mask = cap - 1;
-        for (uint32_t j = lane; j < cap; j += 32) { t.key[j] = kEmpty; t.cnt[j] = 0; t.q[2 * j] = 0; t.q[2 * j + 1] = 0; }
-        __syncwarp();
-        uint32_t own = 0;
-        for (int base = 0; base < d; base += 32) {
-            int e = base + lane;
-            bool act = e < d;
-            NodeRec ru{0, -1, 0};
-            if (act) ru = rec[col[b + e]];
-            own += (act && ru.label == rw.label);
-            bool foreign = act && ru.label != rw.label;
-            st[lane] = ru.s_fix;
-            __syncwarp();
-            unsigned fm = __ballot_sync(FULL, foreign);
-            if (foreign) {
-                unsigned grp = __match_any_sync(fm, ru.label);
-                if (lane == __ffs(grp) - 1) {
-                    int sl = tab_insert(t, ru.label, __popc(grp), err);
-                    if (sl >= 0) atomic_add_u128(t.q + 2 * sl, group_sum_all(st, grp));
-                }
-            }
-            __syncwarp();
-        }
-        for (int o = 16; o; o >>= 1) own += __shfl_xor_sync(FULL, own, o);
-        uint32_t Lf = 0;
-        u128 X = 0;
-        for (uint32_t j = lane; j < cap; j += 32)
-            if (t.key[j] != kEmpty) { Lf++; X += (u128)t.cnt[j] * LG[t.cnt[j]]; }
-        for (int o = 16; o; o >>= 1) Lf += __shfl_xor_sync(FULL, Lf, o);
-        RowAgg a{(uint32_t)d, Lf + (own > 0 ? 1u : 0u), warp_sum_u128(X) + (u128)own * LG[own]};
-        df sig1 = df_cbrt(column_weight(a, 1, LG));   // the usual count of a foreign community
-        int64_t xb = xoff[w];
+        int dx = rw.dx;
         int32_t bo = 0, bi = 0;
-        for (int base = 0; base < d; base += 32) {
-            int e = base + lane;
-            bool act = e < d;
-            int32_t u = act ? col[b + e] : -1;
-            NodeRec ru{0, -1, 0};
-            if (act) ru = rec[u];
-            bool cross = act && ru.label != rw.label;
-            df sig{0.0f, 0.0f};
-            if (cross) {
-                int sl = tab_find(t, ru.label);
-                if (sl < 0) { atomicOr(err, 2); cross = false; }
-                else {
-                    uint32_t f = t.cnt[sl];
-                    sig = f == 1 ? sig1 : df_cbrt(column_weight(a, f, LG));
-                    if (f > 1) {
-                        u128 q = ((u128)t.q[2 * sl + 1] << 64) | t.q[2 * sl];
-                        push_type2(acc, u, sig, q - ru.s_fix);
+        if (dx > 0) {
+            uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(dx, k));
+            Tab t;
+            t.q = (unsigned long long *)base_w;
+            t.key = (int32_t *)(base_w + 16 * kWarpCap);
+            t.cnt = (uint32_t *)(base_w + 20 * kWarpCap);
+            t.sig = nullptr;
+            t.mask = cap - 1;
+            for (uint32_t j = lane; j < cap; j += 32) { t.key[j] = kEmpty; t.cnt[j] = 0; t.q[2 * j] = 0; t.q[2 * j + 1] = 0; }
+            __syncwarp();
+            for (int base = 0; base < dx; base += 32) {
+                int e = base + lane;
+                bool act = e < dx;
+                int32_t c = act ? cl_lab[b + e] : -1;
+                st[lane] = act ? rec[cl_col[b + e]].s_fix : 0;
+                __syncwarp();
+                unsigned am = __ballot_sync(FULL, act);
+                if (act) {
+                    unsigned grp = __match_any_sync(am, c);
+                    if (lane == __ffs(grp) - 1) {
+                        int sl = tab_insert(t, c, __popc(grp), err);
+                        if (sl >= 0) atomic_add_u128(t.q + 2 * sl, group_sum_all(st, grp));
                     }
                 }
+                __syncwarp();
             }
-            if (rw.dx >= 2) {
-                bool inx = cross && ru.dx >= 2;
-                bool o = inx && rank_after(ru.dx, u, rw.dx, w);
-                bool in = inx && !o;
-                unsigned mo = __ballot_sync(FULL, o), mi = __ballot_sync(FULL, in);
-                if (o) { int64_t p = xb + bo + __popc(mo & lanemask_lt()); xcol[p] = u; xS[p] = sig; }
-                if (in) { int64_t p = xb + rw.dx - 1 - (bi + __popc(mi & lanemask_lt())); xcol[p] = u; xS[p] = sig; }
-                bo += __popc(mo); bi += __popc(mi);
+            RowSum rs = rsum[w];
+            RowAgg a{(uint32_t)d, rs.L, ((u128)rs.xhi << 64) | rs.xlo};
+            df sig1 = df_cbrt(column_weight(a, 1, LG));   // the usual count of a foreign community
+            int64_t xb = xoff[w];
+            for (int base = 0; base < dx; base += 32) {
+                int e = base + lane;
+                bool act = e < dx;
+                int32_t u = act ? cl_col[b + e] : -1;
+                int32_t c = act ? cl_lab[b + e] : -1;
+                NodeRec ru{0, -1, 0};
+                if (act) ru = rec[u];
+                df sig{0.0f, 0.0f};
+                bool ok = act;
+                if (act) {
+                    int sl = tab_find(t, c);
+                    if (sl < 0) { atomicOr(err, 2); ok = false; }
+                    else {
+                        uint32_t f = t.cnt[sl];
+                        sig = f == 1 ? sig1 : df_cbrt(column_weight(a, f, LG));
+                        if (f > 1) {
+                            u128 q = ((u128)t.q[2 * sl + 1] << 64) | t.q[2 * sl];
+                            push_type2(acc, u, sig, q - ru.s_fix);
+                        }
+                    }
+                }
+                if (dx >= 2) {
+                    bool inx = ok && ru.dx >= 2;
+                    bool o = inx && rank_after(ru.dx, u, dx, w);
+                    bool in = inx && !o;
+                    unsigned mo = __ballot_sync(FULL, o), mi = __ballot_sync(FULL, in);
+                    if (o) { int64_t p = xb + bo + __popc(mo & lanemask_lt()); xcol[p] = u; xS[p] = sig; }
+                    if (in) { int64_t p = xb + dx - 1 - (bi + __popc(mi & lanemask_lt())); xcol[p] = u; xS[p] = sig; }
+                    bo += __popc(mo); bi += __popc(mi);
+                }
             }
         }
         if (lane == 0) { xout[w] = bo; xin[w] = bi; }
@@ -1078,12 +1098,14 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     // ---- P1
     if (g->n_small) {
         p1_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, s>>>(
-            g->off, g->col, g->lab, g->rows_small, g->n_small, g->k, g->LG, g->rec, g->Lall, g->wmax_bits);
+            g->off, g->col, g->lab, g->rows_small, g->n_small, g->k, g->LG, g->rec, g->Lall, g->wmax_bits,
+            g->rsum, g->cl_col, g->cl_lab);
         RS_LAUNCHED(g, s, "p1_small");
     }
     if (g->n_mid) {
         p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, 8), NT, 0, s>>>(
-            g->off, g->col, g->lab, g->rows_mid, g->n_mid, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err);
+            g->off, g->col, g->lab, g->rows_mid, g->n_mid, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err,
+            g->rsum, g->cl_col, g->cl_lab);
         RS_LAUNCHED(g, s, "p1_mid");
     }
     if (g->n_large) {
@@ -1111,14 +1133,14 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     // ---- P2
     if (g->n_small) {
         p2_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, s>>>(
-            g->off, g->col, g->lab, g->rows_small, g->n_small, g->LG, g->rec, g->acc, g->xoff, g->xcol, g->xS,
-            g->xout, g->xin);
+            g->off, g->rows_small, g->n_small, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
+            g->xcol, g->xS, g->xout, g->xin);
         RS_LAUNCHED(g, s, "p2_small");
     }
     if (g->n_mid) {
         p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, p2_mid_smem, s>>>(
-            g->off, g->col, g->rows_mid, g->n_mid, g->k, g->LG, g->rec, g->acc, g->xoff, g->xcol, g->xS,
-            g->xout, g->xin, err);
+            g->off, g->rows_mid, g->n_mid, g->k, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
+            g->xcol, g->xS, g->xout, g->xin, err);
         RS_LAUNCHED(g, s, "p2_mid");
     }
     if (g->n_large) {
