@@ -141,6 +141,29 @@ rs_status rs_clone_graph(const rs_graph *g, rs_graph **out, void *stream);
 rs_status rs_graph_info(const rs_graph *g, int64_t *n, int64_t *nnz, int32_t *k, int32_t *max_degree);
 
 /*
+ * rs_topk_noalloc -- the same ranking as rs_topk over a device array of n
+ * scores, for callers that cannot allocate device memory: code whose device
+ * memory is owned by another allocator (a framework's caching allocator, a
+ * fixed memory budget), and latency-critical loops that cannot afford
+ * cudaMalloc's implicit device synchronisation or its failure mid-request.
+ * The paper has no counterpart; this is a deployment variant of Step 4.
+ *
+ *   scores      device double[n], every value >= 0 (not NaN); 1 <= n < 2^31.
+ *   k           1 <= k <= min(n, 16384); larger k returns RS_EINVAL.
+ *   ids_out     device int32[k]; scores_out device double[k] (may be NULL).
+ * Allocates nothing: its scratch is one static device array of about 213 KB
+ * (histogram, control words, 16384 keys) that every GPU loading the library
+ * holds until the process exits.  The first call on a device looks up that
+ * array's address and sets the kernel up (per device, once); make that first
+ * call before any stream capture.  Every call shares the array and the kernel
+ * re-initialises it, so calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and must not overlap.  Stream-ordered; no host
+ * synchronisation.
+ */
+rs_status rs_topk_noalloc(const double *scores, int64_t n, int32_t k, int32_t *ids_out, double *scores_out,
+                          void *stream);
+
+/*
  * Instrumentation (no counterpart in the paper; used by benchmarks and tuning).
  *
  * rs_profile_enable -- when enable != 0, every later rs_score / rs_topk call on
