@@ -115,6 +115,20 @@ def step_bytes(st):
             + 8 * n + 16 * n * 2 + 8 * n + 8 * n * 2)
 
 
+# ---- aggregation over ranks -----------------------------------------------------------
+
+def aggregate(local_ms, units_per_rank, world, device=None):
+    """Whole-job throughput over ranks: every rank processed units_per_rank units in
+    local_ms; the job took the slowest rank's time.  Returns (value per second, max ms)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return world * units_per_rank / (ms / 1e3), ms
+
+
 # ---- clocks --------------------------------------------------------------------------
 
 class Clocks:
@@ -247,12 +261,7 @@ def run_ours(args):
     prof = G.profile_read()
     G.profile_enable(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * st["m"] * args.steps / (total_ms / 1e3)
+    value, total_ms = aggregate(sum(step_ms), st["m"] * args.steps, world, dev)
 
     # per-kernel totals over the timed steps
     per = {}
@@ -306,10 +315,7 @@ def run_ours(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         G2.close()
     e2e_ms = e2e_ms[1:]  # first call pays one-time kernel attribute setup
-    te = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * st["m"] * len(e2e_ms) / (float(te.item()) / 1e3) if e2e_ms else None
+    e2e_value = aggregate(sum(e2e_ms), st["m"] * len(e2e_ms), world, dev)[0] if e2e_ms else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

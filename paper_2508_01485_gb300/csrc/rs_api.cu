@@ -545,7 +545,7 @@ extern "C" rs_status rs_build_graph(int64_t n, int64_t nnz, const void *row_offs
     if (cudaError_t e = dmalloc(&g->col, nnz)) return bail(cuda_fail(e, "alloc cols"));
     if (cudaError_t e = dmalloc(&g->col_alt, nnz)) return bail(cuda_fail(e, "alloc cols"));
     if (cudaError_t e = dmalloc(&g->lab, n)) return bail(cuda_fail(e, "alloc labels"));
-    if (cudaError_t e = dmalloc(&g->removed, 4 * n)) return bail(cuda_fail(e, "alloc flags"));
+    if (cudaError_t e = dmalloc(&g->removed, 4 * std::max<int64_t>(n, 1))) return bail(cuda_fail(e, "alloc flags"));
     if (cudaError_t e = dmalloc(&g->dead, 4 * ((nnz + 31) / 32))) return bail(cuda_fail(e, "alloc marks"));
     if (offsets_are_i64) {
         if (cudaError_t e = cudaMemcpyAsync(g->off, row_offsets, (n + 1) * sizeof(int64_t), kind, s))
@@ -605,7 +605,7 @@ extern "C" rs_status rs_clone_graph(const rs_graph *src, rs_graph **out, void *s
     if (cudaError_t e = dmalloc(&g->col, nnz)) return bail(cuda_fail(e, "alloc"));
     if (cudaError_t e = dmalloc(&g->col_alt, nnz)) return bail(cuda_fail(e, "alloc"));
     if (cudaError_t e = dmalloc(&g->lab, n)) return bail(cuda_fail(e, "alloc"));
-    if (cudaError_t e = dmalloc(&g->removed, 4 * n)) return bail(cuda_fail(e, "alloc"));
+    if (cudaError_t e = dmalloc(&g->removed, 4 * std::max<int64_t>(n, 1))) return bail(cuda_fail(e, "alloc"));
     if (cudaError_t e = dmalloc(&g->dead, 4 * ((nnz + 31) / 32))) return bail(cuda_fail(e, "alloc"));
     int64_t cur_nnz = 0;
     if (cudaError_t e = cudaMemcpy(&cur_nnz, src->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost))

@@ -147,14 +147,30 @@ __device__ __forceinline__ void push_type2(unsigned long long *acc, int32_t u, d
     atomic_add_u128(acc + 2 * (int64_t)u, df_to_fixed(t, kAccFrac));
 }
 
+// Every weight of a row with L distinct neighbour communities is at most
+// L log2 L (an entropy over at most L categories is at most log2 L); a row
+// whose bound cannot exceed the w_max found so far needs no column maximum.
+__device__ __forceinline__ bool row_may_raise_max(uint32_t L, float wcur) {
+    if (L < 2) return false;
+    float fl = (float)L;
+    return fl * __log2f(fl) * 1.001f + 1e-6f > wcur;
+}
+// w_max found so far, rounded down to a float (read once per warp)
+__device__ __forceinline__ float current_wmax(const unsigned long long *wmax_bits) {
+    unsigned long long b = *(volatile const unsigned long long *)wmax_bits;
+    return __double2float_rd(__longlong_as_double((long long)b));
+}
+
 // finishing a row in P1: the row's largest weight, s_v and the node record;
 // w_own is the weight of the row's own community when own > 0 (else ignored)
 __device__ __forceinline__ df p1_row_result(const RowAgg &a, uint32_t own, df col_max, int32_t k,
-                                            const uint64_t *LG, NodeRec &out, int32_t cv, df w_own) {
+                                            const uint64_t *LG, NodeRec &out, int32_t cv, df w_own,
+                                            bool want_max) {
     df m = col_max;
     df wabs{0.0f, 0.0f};
-    if (a.L < (uint32_t)k || own == 0) wabs = column_weight(a, 0, LG);   // community absent from N(v)
-    if (a.L < (uint32_t)k) m = df_max(m, wabs);
+    bool absent_col = want_max && a.L < (uint32_t)k;
+    if (absent_col || own == 0) wabs = column_weight(a, 0, LG);   // community absent from N(v)
+    if (absent_col) m = df_max(m, wabs);
     df wown = own > 0 ? w_own : wabs;
     df s = df_cbrt(wown);
     out.s_fix = (uint64_t)df_to_fixed(s, kSFrac);
@@ -236,6 +252,9 @@ __global__ void __launch_bounds__(kThreads) p1_small_kernel(
     int t = threadIdx.x;
     df best{0.0f, 0.0f};
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < nrows; i0 += (int64_t)gridDim.x * blockDim.x) {
+        float wcur = 0.0f;
+        if ((t & 31) == 0) wcur = current_wmax(wmax_bits);
+        wcur = __shfl_sync(FULL, wcur, 0);
         int64_t i = i0 + t;
         if (i >= nrows) continue;
         int32_t v = rows[i];
@@ -247,16 +266,21 @@ __global__ void __launch_bounds__(kThreads) p1_small_kernel(
         uint64_t seen;
         RowAgg a = small_row_counts(col, lab, b, d, cv, LG, T, t, nf, own, seen, cl_col, cl_lab);
         store_rowsum(rsum, v, a);
+        bool want_max = row_may_raise_max(a.L, fmaxf(wcur, best.hi));
         df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
-        while (seen) {
-            uint32_t f = (uint32_t)(__ffsll((long long)seen) - 1);
-            df w = column_weight(a, f, LG);
-            if (f == own) wown = w;
-            cm = df_max(cm, w);
-            seen &= seen - 1;
+        if (want_max) {
+            while (seen) {
+                uint32_t f = (uint32_t)(__ffsll((long long)seen) - 1);
+                df w = column_weight(a, f, LG);
+                if (f == own) wown = w;
+                cm = df_max(cm, w);
+                seen &= seen - 1;
+            }
+        } else if (own > 0) {
+            wown = column_weight(a, own, LG);
         }
         NodeRec r;
-        best = df_max(best, p1_row_result(a, own, cm, k, LG, r, cv, wown));
+        best = df_max(best, p1_row_result(a, own, cm, k, LG, r, cv, wown, want_max));
         rec[v] = r;
         Lall[v] = (int32_t)a.L;
     }
@@ -314,14 +338,18 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
             if (t.key[j] != kEmpty) { Lf++; X += (u128)t.cnt[j] * LG[t.cnt[j]]; }
         for (int o = 16; o; o >>= 1) Lf += __shfl_xor_sync(FULL, Lf, o);
         RowAgg a{(uint32_t)d, Lf + (own > 0 ? 1u : 0u), warp_sum_u128(X) + (u128)own * LG[own]};
+        float wcur = 0.0f;
+        if (lane == 0) wcur = fmaxf(current_wmax(wmax_bits), best.hi);
+        bool want_max = __shfl_sync(FULL, (int)row_may_raise_max(a.L, wcur), 0);
         df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
-        for (uint32_t j = lane; j < cap; j += 32)
-            if (t.key[j] != kEmpty) cm = df_max(cm, column_weight(a, t.cnt[j], LG));
+        if (want_max)
+            for (uint32_t j = lane; j < cap; j += 32)
+                if (t.key[j] != kEmpty) cm = df_max(cm, column_weight(a, t.cnt[j], LG));
         if (own > 0 && lane == 0) { wown = column_weight(a, own, LG); cm = df_max(cm, wown); }
         cm = warp_max_df(cm);
         if (lane == 0) {
             NodeRec r;
-            best = df_max(best, p1_row_result(a, own, cm, k, LG, r, cv, wown));
+            best = df_max(best, p1_row_result(a, own, cm, k, LG, r, cv, wown, want_max));
             rec[v] = r;
             Lall[v] = (int32_t)a.L;
             store_rowsum(rsum, v, a);
@@ -332,15 +360,35 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
 }
 
 // Large rows, one CTA per row, a per-CTA table of up to kMidCap slots
+// CTA-ordered position of the flagged threads of one round; every thread calls
+template <int NT>
+__device__ __forceinline__ int32_t cta_rank(bool flag, int32_t &base, int32_t *sh_cnt) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned m = __ballot_sync(FULL, flag);
+    if (lane == 0) sh_cnt[wid] = __popc(m);
+    __syncthreads();
+    int32_t p = base, tot = 0;
+    for (int j = 0; j < NT / 32; ++j) {
+        if (j < wid) p += sh_cnt[j];
+        tot += sh_cnt[j];
+    }
+    p += __popc(m & lanemask_lt());
+    base += tot;
+    __syncthreads();
+    return p;
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) p1_large_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
     const int32_t *__restrict__ rows, int64_t nrows, int32_t k, const uint64_t *__restrict__ LG,
-    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits, int *err) {
+    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits, int *err,
+    RowSum *__restrict__ rsum, int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t sh_u32[NT / 32];
     __shared__ u128 sh_u128[NT / 32];
     __shared__ df sh_df[NT / 32];
+    __shared__ int32_t sh_cnt[NT / 32];
     int tid = threadIdx.x, lane = tid & 31;
     df best{0.0f, 0.0f};
     for (int64_t i = blockIdx.x; i < nrows; i += gridDim.x) {
@@ -353,10 +401,12 @@ __global__ void __launch_bounds__(NT) p1_large_kernel(
         for (uint32_t j = tid; j < cap; j += NT) { t.key[j] = kEmpty; t.cnt[j] = 0; }
         __syncthreads();
         uint32_t own = 0;
+        int32_t nx = 0;
         for (int base = 0; base < d; base += NT) {
             int e = base + tid;
             bool act = e < d;
-            int32_t c = act ? lab[col[b + e]] : -1;
+            int32_t x = act ? col[b + e] : -1;
+            int32_t c = act ? lab[x] : -1;
             own += (act && c == cv);
             bool foreign = act && c != cv;
             unsigned fm = __ballot_sync(FULL, foreign);
@@ -364,6 +414,8 @@ __global__ void __launch_bounds__(NT) p1_large_kernel(
                 unsigned grp = __match_any_sync(fm, c);
                 if (lane == __ffs(grp) - 1) tab_insert(t, c, __popc(grp), err);
             }
+            int32_t p = cta_rank<NT>(foreign, nx, sh_cnt);
+            if (foreign) { cl_col[b + p] = x; cl_lab[b + p] = c; }
         }
         own = block_sum_u32<NT>(own, sh_u32);      // syncs: the table is complete
         uint32_t Lf = 0;
@@ -373,16 +425,20 @@ __global__ void __launch_bounds__(NT) p1_large_kernel(
         Lf = block_sum_u32<NT>(Lf, sh_u32);
         X = block_sum_u128<NT>(X, sh_u128);
         RowAgg a{(uint32_t)d, Lf + (own > 0 ? 1u : 0u), X + (u128)own * LG[own]};
+        bool want_max = row_may_raise_max(a.L, fmaxf(current_wmax(wmax_bits), 0.0f));
+        want_max = __syncthreads_or(want_max);
         df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
-        for (uint32_t j = tid; j < cap; j += NT)
-            if (t.key[j] != kEmpty) cm = df_max(cm, column_weight(a, t.cnt[j], LG));
+        if (want_max)
+            for (uint32_t j = tid; j < cap; j += NT)
+                if (t.key[j] != kEmpty) cm = df_max(cm, column_weight(a, t.cnt[j], LG));
         if (own > 0) { wown = column_weight(a, own, LG); cm = df_max(cm, wown); }
         cm = block_max_df<NT>(cm, sh_df);
         if (tid == 0) {
             NodeRec r;
-            df m = p1_row_result(a, own, cm, k, LG, r, cv, wown);
+            df m = p1_row_result(a, own, cm, k, LG, r, cv, wown, want_max);
             rec[v] = r;
             Lall[v] = (int32_t)a.L;
+            store_rowsum(rsum, v, a);
             best = df_max(best, m);
         }
         __syncthreads();                              // table reuse
@@ -449,6 +505,7 @@ __global__ void __launch_bounds__(NT) hub_p1_finish_kernel(
         X = block_sum_u128<NT>(X, sh_u128);
         RowAgg a{(uint32_t)d, Lf + (own > 0 ? 1u : 0u), X + (u128)own * LG[own]};
         df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
+        bool want_max = true;
         for (int64_t j = tid; j < h.cap; j += NT) {
             int64_t s = h.tab + j;
             if (hkey[s] != kEmpty) cm = df_max(cm, column_weight(a, hcnt[s], LG));
@@ -461,7 +518,7 @@ __global__ void __launch_bounds__(NT) hub_p1_finish_kernel(
             g.L = a.L;
             hagg[hi] = g;
             NodeRec r;
-            df m = p1_row_result(a, own, cm, k, LG, r, lab[h.row], wown);
+            df m = p1_row_result(a, own, cm, k, LG, r, lab[h.row], wown, want_max);
             rec[h.row] = r;
             Lall[h.row] = (int32_t)a.L;
             best = df_max(best, m);
@@ -677,13 +734,12 @@ __device__ __forceinline__ void gx_round(bool out, bool in, int64_t xb, int32_t 
 
 template <int NT>
 __global__ void __launch_bounds__(NT) p2_large_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ rows,
-    int64_t nrows, int32_t k, const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec,
-    unsigned long long *acc, const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol,
-    df *__restrict__ xS, int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err) {
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, int32_t k,
+    const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
+    const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
+    const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
+    int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ uint32_t sh_u32[NT / 32];
-    __shared__ u128 sh_u128[NT / 32];
     __shared__ int32_t sh_cnt[2 * NT / 32];
     __shared__ uint64_t stage[NT];
     int tid = threadIdx.x, lane = tid & 31;
@@ -693,68 +749,64 @@ __global__ void __launch_bounds__(NT) p2_large_kernel(
         int64_t b = off[w];
         int d = (int)(off[w + 1] - b);
         NodeRec rw = rec[w];
-        uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(d, k));
+        int dx = rw.dx;
+        if (dx == 0) {
+            if (tid == 0) { xout[w] = 0; xin[w] = 0; }
+            continue;
+        }
+        uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(dx, k));
         Tab t = p2_table(smem, cap);
         for (uint32_t j = tid; j < cap; j += NT) {
             t.key[j] = kEmpty; t.cnt[j] = 0; t.q[2 * j] = 0; t.q[2 * j + 1] = 0;
         }
         __syncthreads();
-        uint32_t own = 0;
-        for (int base = 0; base < d; base += NT) {
+        for (int base = 0; base < dx; base += NT) {
             int e = base + tid;
-            bool act = e < d;
-            NodeRec ru{0, -1, 0};
-            if (act) ru = rec[col[b + e]];
-            own += (act && ru.label == rw.label);
-            bool foreign = act && ru.label != rw.label;
-            st[lane] = ru.s_fix;
+            bool act = e < dx;
+            int32_t c = act ? cl_lab[b + e] : -1;
+            st[lane] = act ? rec[cl_col[b + e]].s_fix : 0;
             __syncwarp();
-            unsigned fm = __ballot_sync(FULL, foreign);
-            if (foreign) {
-                unsigned grp = __match_any_sync(fm, ru.label);
+            unsigned am = __ballot_sync(FULL, act);
+            if (act) {
+                unsigned grp = __match_any_sync(am, c);
                 if (lane == __ffs(grp) - 1) {
-                    int s = tab_insert(t, ru.label, __popc(grp), err);
-                    if (s >= 0) atomic_add_u128(t.q + 2 * s, group_sum_all(st, grp));
+                    int sl = tab_insert(t, c, __popc(grp), err);
+                    if (sl >= 0) atomic_add_u128(t.q + 2 * sl, group_sum_all(st, grp));
                 }
             }
             __syncwarp();
         }
-        own = block_sum_u32<NT>(own, sh_u32);
-        uint32_t Lf = 0;
-        u128 X = 0;
-        for (uint32_t j = tid; j < cap; j += NT)
-            if (t.key[j] != kEmpty) { Lf++; X += (u128)t.cnt[j] * LG[t.cnt[j]]; }
-        Lf = block_sum_u32<NT>(Lf, sh_u32);
-        X = block_sum_u128<NT>(X, sh_u128);
-        RowAgg a{(uint32_t)d, Lf + (own > 0 ? 1u : 0u), X + (u128)own * LG[own]};
+        __syncthreads();
+        RowSum rs = rsum[w];
+        RowAgg a{(uint32_t)d, rs.L, ((u128)rs.xhi << 64) | rs.xlo};
         for (uint32_t j = tid; j < cap; j += NT)
             if (t.key[j] != kEmpty) t.sig[j] = df_cbrt(column_weight(a, t.cnt[j], LG));
         __syncthreads();
         int64_t xb = xoff[w];
         int32_t bo = 0, bi = 0;
-        for (int base = 0; base < d; base += NT) {
+        for (int base = 0; base < dx; base += NT) {
             int e = base + tid;
-            bool act = e < d;
-            int32_t u = act ? col[b + e] : -1;
+            bool act = e < dx;
+            int32_t u = act ? cl_col[b + e] : -1;
             NodeRec ru{0, -1, 0};
             if (act) ru = rec[u];
-            bool cross = act && ru.label != rw.label;
+            bool ok = act;
             df sig{0.0f, 0.0f};
-            if (cross) {
-                int s = tab_find(t, ru.label);
-                if (s < 0) { atomicOr(err, 2); cross = false; }
+            if (act) {
+                int sl = tab_find(t, cl_lab[b + e]);
+                if (sl < 0) { atomicOr(err, 2); ok = false; }
                 else {
-                    sig = t.sig[s];
-                    if (t.cnt[s] > 1) {
-                        u128 q = ((u128)t.q[2 * s + 1] << 64) | t.q[2 * s];
+                    sig = t.sig[sl];
+                    if (t.cnt[sl] > 1) {
+                        u128 q = ((u128)t.q[2 * sl + 1] << 64) | t.q[2 * sl];
                         push_type2(acc, u, sig, q - ru.s_fix);
                     }
                 }
             }
-            if (rw.dx >= 2) {
-                bool inx = cross && ru.dx >= 2;
-                bool o = inx && rank_after(ru.dx, u, rw.dx, w);
-                gx_round<NT>(o, inx && !o, xb, rw.dx, u, sig, bo, bi, xcol, xS, sh_cnt);
+            if (dx >= 2) {
+                bool inx = ok && ru.dx >= 2;
+                bool o = inx && rank_after(ru.dx, u, dx, w);
+                gx_round<NT>(o, inx && !o, xb, dx, u, sig, bo, bi, xcol, xS, sh_cnt);
             }
         }
         if (tid == 0) { xout[w] = bo; xin[w] = bi; }
@@ -933,20 +985,34 @@ __device__ __forceinline__ void triangle_terms(int32_t a, int32_t b, int32_t c, 
     atomic_add_u128(acc + 2 * (int64_t)c, df_to_fixed(tc, kAccFrac));
 }
 
-// P3a: one warp per node a.  Its out-list N+(a) (ids ascending) is staged in
-// shared memory with the prefix sums of d+(b) over b in N+(a); every wedge
-// a -> b -> c is one lane-iteration, and c closes a triangle iff c is in N+(a)
-// (binary search in shared memory).  Out-lists longer than kP3Cap use global
-// binary searches instead.  Triangles go to a buffer for P3b; when it is full
-// they are finished on the spot.
+// P3a lists the triangles of G_x once each, from their lowest-ranked node a
+// (out-lists are sorted by id).  A warp takes 32 consecutive nodes and stages
+// their out-lists in shared memory, with, per entry b, the prefix sums of
+// d+(b).  All wedges a -> b -> c of the group then form one flat index space
+// that the lanes share evenly; c closes a triangle iff it is in N+(a)
+// (binary search in shared memory).  Nodes with an out-list longer than
+// kGroupDa, or groups with more than kGroupCap out-entries, take a per-node
+// warp path (staged N+(a), or global binary searches beyond kP3Cap).
+// Triangles go to a buffer for P3b, slots reserved once per warp iteration;
+// when the buffer is full they are finished on the spot.
 constexpr int kP3Cap = 256;
+constexpr int kGroupDa = 64;
+constexpr int kGroupCap = 256;
+constexpr int kP3Warps = kThreads / 32;
 
-__device__ __forceinline__ void emit_triangle(int32_t a, int32_t b, int32_t c, df Sab, df Sac, df Sbc,
-                                              Tri *tri, int64_t tri_cap, unsigned long long *tri_n,
-                                              const int64_t *xoff, const int32_t *xcol, const df *xS,
-                                              const int32_t *xin, const NodeRec *rec,
-                                              unsigned long long *acc, int *err) {
-    unsigned long long p = atomicAdd(tri_n, 1ull);
+struct P3Stage {
+    int32_t nb[kGroupCap];          // out-entries b of the group, node after node
+    int64_t boff[kGroupCap];        // xoff[b]
+    int32_t wpre[kGroupCap + 1];    // prefix sums of d+(b) over the entries
+    uint8_t owner[kGroupCap];       // lane (node) of the entry
+    int32_t seg[33];                // first entry of each node
+    int64_t aoff[32];               // xoff[a]
+};
+
+__device__ __forceinline__ void put_triangle(unsigned long long p, int32_t a, int32_t b, int32_t c, df Sab, df Sac,
+                                             df Sbc, Tri *tri, int64_t tri_cap, const int64_t *xoff,
+                                             const int32_t *xcol, const df *xS, const int32_t *xin,
+                                             const NodeRec *rec, unsigned long long *acc, int *err) {
     if ((int64_t)p < tri_cap) {
         Tri t;
         t.a = a; t.b = b; t.c = c; t.pad = 0;
@@ -957,73 +1023,173 @@ __device__ __forceinline__ void emit_triangle(int32_t a, int32_t b, int32_t c, d
     }
 }
 
+// reserve slots for this iteration's hits, one atomic per warp
+__device__ __forceinline__ unsigned long long reserve(bool hit, unsigned long long *tri_n, int lane) {
+    unsigned hm = __ballot_sync(FULL, hit);
+    unsigned long long hb = 0;
+    if (hm && lane == 0) hb = atomicAdd(tri_n, (unsigned long long)__popc(hm));
+    hb = __shfl_sync(FULL, hb, 0);
+    return hb + __popc(hm & lanemask_lt());
+}
+
+// the whole warp on one node a (out-list longer than kGroupDa)
+__device__ void p3_node_warp(int32_t a, int32_t dA, const int64_t *xoff, const int32_t *xcol, const df *xS,
+                             const int32_t *xout, const int32_t *xin, const NodeRec *rec, Tri *tri,
+                             int64_t tri_cap, unsigned long long *tri_n, unsigned long long *acc, int *err,
+                             P3Stage &S, int lane) {
+    int64_t bA = xoff[a];
+    if (dA <= kP3Cap && dA <= kGroupCap) {
+        int32_t carry = 0;
+        if (lane == 0) S.wpre[0] = 0;
+        for (int32_t j0 = 0; j0 < dA; j0 += 32) {
+            int32_t j = j0 + lane;
+            int32_t b = j < dA ? xcol[bA + j] : 0;
+            int32_t db = j < dA ? xout[b] : 0;
+            if (j < dA) { S.nb[j] = b; S.boff[j] = xoff[b]; }
+            int32_t x = db;
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t y = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += y;
+            }
+            if (j < dA) S.wpre[j + 1] = carry + x;
+            carry += __shfl_sync(FULL, x, 31);
+        }
+        __syncwarp();
+        int32_t W = S.wpre[dA];
+        for (int32_t w0 = 0; w0 < W; w0 += 32) {
+            int32_t wv = w0 + lane;
+            bool hit = false;
+            int32_t j = 0, l2 = 0, c = 0;
+            int64_t pb = 0;
+            if (wv < W) {
+                int32_t lo = 0, hi = dA;
+                while (hi - lo > 1) {
+                    int32_t mid = (lo + hi) >> 1;
+                    if (S.wpre[mid] <= wv) lo = mid; else hi = mid;
+                }
+                j = lo;
+                pb = S.boff[j] + (wv - S.wpre[j]);
+                c = xcol[pb];
+                int32_t h2 = dA;
+                while (l2 < h2) {
+                    int32_t mid = (l2 + h2) >> 1;
+                    if (S.nb[mid] < c) l2 = mid + 1; else h2 = mid;
+                }
+                hit = l2 < dA && S.nb[l2] == c;
+            }
+            unsigned long long p = reserve(hit, tri_n, lane);
+            if (hit)
+                put_triangle(p, a, S.nb[j], c, xS[bA + j], xS[bA + l2], xS[pb], tri, tri_cap, xoff, xcol, xS, xin,
+                             rec, acc, err);
+        }
+        __syncwarp();
+    } else {
+        for (int32_t j = lane; j < dA; j += 32) {
+            int32_t b = xcol[bA + j];
+            int64_t bb = xoff[b];
+            int32_t db = xout[b];
+            for (int32_t tb = 0; tb < db; ++tb) {
+                int32_t c = xcol[bb + tb];
+                int64_t p = find_out(xcol, bA, bA + dA, c);
+                if (p >= bA + dA || xcol[p] != c) continue;
+                put_triangle(atomicAdd(tri_n, 1ull), a, b, c, xS[bA + j], xS[p], xS[bb + tb], tri, tri_cap, xoff,
+                             xcol, xS, xin, rec, acc, err);
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) p3_list_kernel(
     int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
     const int32_t *__restrict__ xout, const int32_t *__restrict__ xin, const NodeRec *__restrict__ rec,
     Tri *tri, int64_t tri_cap, unsigned long long *tri_n, unsigned long long *acc, int *err) {
-    __shared__ int32_t s_nb[kThreads / 32][kP3Cap];
-    __shared__ int32_t s_pre[kThreads / 32][kP3Cap + 1];
-    __shared__ int64_t s_off[kThreads / 32][kP3Cap];
+    __shared__ P3Stage stage[kP3Warps];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int32_t *nb = s_nb[wid], *pre = s_pre[wid];
-    int64_t *boff = s_off[wid];
+    P3Stage &S = stage[wid];
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t av = warp; av < n; av += nwarps) {
-        int32_t a = (int32_t)av;
-        int32_t da = xout[a];
-        if (da < 2) continue;
-        int64_t ba = xoff[a];
-        if (da <= kP3Cap) {
+    for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+        int64_t av = base + lane;
+        int32_t da = av < n ? xout[av] : 0;
+        bool grp = da >= 2 && da <= kGroupDa;
+        int32_t mine = grp ? da : 0;
+        int32_t incl = mine;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int32_t E = __shfl_sync(FULL, incl, 31);
+        bool fits = E <= kGroupCap;
+        unsigned solo = __ballot_sync(FULL, da > kGroupDa || (!fits && da >= 2));
+        if (fits && E > 0) {
+            int32_t e0 = incl - mine;
+            S.seg[lane] = e0;
+            if (lane == 31) S.seg[32] = E;
+            int64_t ba = grp ? xoff[av] : 0;
+            S.aoff[lane] = ba;
+            for (int32_t j = 0; j < mine; ++j) {
+                int32_t b = xcol[ba + j];
+                S.nb[e0 + j] = b;
+                S.boff[e0 + j] = xoff[b];
+                S.wpre[e0 + j + 1] = xout[b];          // counts; turned into prefix sums below
+                S.owner[e0 + j] = (uint8_t)lane;
+            }
+            __syncwarp();
             int32_t carry = 0;
-            if (lane == 0) pre[0] = 0;
-            for (int32_t j0 = 0; j0 < da; j0 += 32) {
+            if (lane == 0) S.wpre[0] = 0;
+            for (int32_t j0 = 0; j0 < E; j0 += 32) {
                 int32_t j = j0 + lane;
-                int32_t b = j < da ? xcol[ba + j] : 0;
-                int32_t db = j < da ? xout[b] : 0;
-                if (j < da) { nb[j] = b; boff[j] = xoff[b]; }
-                int32_t x = db;
+                int32_t x = j < E ? S.wpre[j + 1] : 0;
                 for (int o = 1; o < 32; o <<= 1) {
                     int32_t y = __shfl_up_sync(FULL, x, o);
                     if (lane >= o) x += y;
                 }
-                if (j < da) pre[j + 1] = carry + x;
+                __syncwarp();
+                if (j < E) S.wpre[j + 1] = carry + x;
                 carry += __shfl_sync(FULL, x, 31);
+                __syncwarp();
+            }
+            int32_t W = S.wpre[E];
+            for (int32_t w0 = 0; w0 < W; w0 += 32) {
+                int32_t wv = w0 + lane;
+                bool hit = false;
+                int32_t e = 0, l2 = 0, c = 0, ow = 0;
+                int64_t pb = 0;
+                if (wv < W) {
+                    int32_t lo = 0, hi = E;                 // last entry with wpre[e] <= wv
+                    while (hi - lo > 1) {
+                        int32_t mid = (lo + hi) >> 1;
+                        if (S.wpre[mid] <= wv) lo = mid; else hi = mid;
+                    }
+                    e = lo;
+                    pb = S.boff[e] + (wv - S.wpre[e]);
+                    c = xcol[pb];
+                    ow = S.owner[e];
+                    int32_t s0 = S.seg[ow], s1 = S.seg[ow + 1];
+                    l2 = s0;
+                    int32_t h2 = s1;
+                    while (l2 < h2) {
+                        int32_t mid = (l2 + h2) >> 1;
+                        if (S.nb[mid] < c) l2 = mid + 1; else h2 = mid;
+                    }
+                    hit = l2 < s1 && S.nb[l2] == c;
+                }
+                unsigned long long p = reserve(hit, tri_n, lane);
+                if (hit) {
+                    int64_t ba_o = S.aoff[ow];
+                    int32_t s0 = S.seg[ow];
+                    put_triangle(p, (int32_t)(base + ow), S.nb[e], c, xS[ba_o + (e - s0)], xS[ba_o + (l2 - s0)],
+                                 xS[pb], tri, tri_cap, xoff, xcol, xS, xin, rec, acc, err);
+                }
             }
             __syncwarp();
-            int32_t W = pre[da];
-            for (int32_t wv = lane; wv < W; wv += 32) {
-                int32_t lo = 0, hi = da;               // last j with pre[j] <= wv
-                while (hi - lo > 1) {
-                    int32_t mid = (lo + hi) >> 1;
-                    if (pre[mid] <= wv) lo = mid; else hi = mid;
-                }
-                int32_t j = lo;
-                int64_t pb = boff[j] + (wv - pre[j]);
-                int32_t c = xcol[pb];
-                int32_t l2 = 0, h2 = da;
-                while (l2 < h2) {
-                    int32_t mid = (l2 + h2) >> 1;
-                    if (nb[mid] < c) l2 = mid + 1; else h2 = mid;
-                }
-                if (l2 < da && nb[l2] == c)
-                    emit_triangle(a, nb[j], c, xS[ba + j], xS[ba + l2], xS[pb], tri, tri_cap, tri_n, xoff, xcol,
-                                  xS, xin, rec, acc, err);
-            }
-            __syncwarp();
-        } else {
-            for (int32_t j = lane; j < da; j += 32) {
-                int32_t b = xcol[ba + j];
-                int64_t bb = xoff[b];
-                int32_t db = xout[b];
-                for (int32_t tb = 0; tb < db; ++tb) {
-                    int32_t c = xcol[bb + tb];
-                    int64_t p = find_out(xcol, ba, ba + da, c);
-                    if (p >= ba + da || xcol[p] != c) continue;
-                    emit_triangle(a, b, c, xS[ba + j], xS[p], xS[bb + tb], tri, tri_cap, tri_n, xoff, xcol, xS,
-                                  xin, rec, acc, err);
-                }
-            }
+        }
+        while (solo) {
+            int l = __ffs(solo) - 1;
+            solo &= solo - 1;
+            int32_t dA = __shfl_sync(FULL, da, l);
+            p3_node_warp((int32_t)(base + l), dA, xoff, xcol, xS, xout, xin, rec, tri, tri_cap, tri_n, acc, err, S,
+                         lane);
         }
     }
 }
@@ -1095,24 +1261,8 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_CUDA_TRY(cudaFuncSetAttribute(p2_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2_mid_smem));
         attr_done = true;
     }
-    // ---- P1
-    if (g->n_small) {
-        p1_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, s>>>(
-            g->off, g->col, g->lab, g->rows_small, g->n_small, g->k, g->LG, g->rec, g->Lall, g->wmax_bits,
-            g->rsum, g->cl_col, g->cl_lab);
-        RS_LAUNCHED(g, s, "p1_small");
-    }
-    if (g->n_mid) {
-        p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, 8), NT, 0, s>>>(
-            g->off, g->col, g->lab, g->rows_mid, g->n_mid, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err,
-            g->rsum, g->cl_col, g->cl_lab);
-        RS_LAUNCHED(g, s, "p1_mid");
-    }
-    if (g->n_large) {
-        p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, p1_smem, s>>>(
-            g->off, g->col, g->lab, g->rows_large, g->n_large, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err);
-        RS_LAUNCHED(g, s, "p1_large");
-    }
+    // ---- P1 (largest rows first: their weights seed w_max, so that most
+    //      smaller rows can skip their column maxima)
     if (g->n_hubs) {
         hub_p1_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, s>>>(
             g->off, g->col, g->lab, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->hkey,
@@ -1122,6 +1272,24 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->off, g->lab, g->hubs, g->n_hubs, g->k, g->LG, g->hkey, g->hcnt, g->hagg, g->rec, g->Lall,
             g->wmax_bits);
         RS_LAUNCHED(g, s, "hub_p1_finish");
+    }
+    if (g->n_large) {
+        p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, p1_smem, s>>>(
+            g->off, g->col, g->lab, g->rows_large, g->n_large, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err,
+            g->rsum, g->cl_col, g->cl_lab);
+        RS_LAUNCHED(g, s, "p1_large");
+    }
+    if (g->n_mid) {
+        p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, 8), NT, 0, s>>>(
+            g->off, g->col, g->lab, g->rows_mid, g->n_mid, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err,
+            g->rsum, g->cl_col, g->cl_lab);
+        RS_LAUNCHED(g, s, "p1_mid");
+    }
+    if (g->n_small) {
+        p1_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, s>>>(
+            g->off, g->col, g->lab, g->rows_small, g->n_small, g->k, g->LG, g->rec, g->Lall, g->wmax_bits,
+            g->rsum, g->cl_col, g->cl_lab);
+        RS_LAUNCHED(g, s, "p1_small");
     }
     // ---- G_x offsets
     gx_capacity_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->rec, n, g->xoff);
@@ -1145,8 +1313,8 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     }
     if (g->n_large) {
         p2_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, p2_smem, s>>>(
-            g->off, g->col, g->rows_large, g->n_large, g->k, g->LG, g->rec, g->acc, g->xoff, g->xcol, g->xS,
-            g->xout, g->xin, err);
+            g->off, g->rows_large, g->n_large, g->k, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
+            g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
         RS_LAUNCHED(g, s, "p2_large");
     }
     if (g->n_hubs) {
@@ -1166,7 +1334,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     // ---- P3
     unsigned long long *tri_n = (unsigned long long *)(g->d_flag + 48);
     RS_CUDA_TRY(cudaMemsetAsync(tri_n, 0, sizeof(unsigned long long), s));
-    p3_list_kernel<<<grid_for(n * 32, NT, 8), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->rec,
+    p3_list_kernel<<<grid_for(n, NT, 8), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->rec,
                                                            (Tri *)g->tri, g->tri_cap, tri_n, g->acc, err);
     RS_LAUNCHED(g, s, "p3_list");
     p3_terms_kernel<<<grid_for(g->tri_cap, NT, 8), NT, 0, s>>>((const Tri *)g->tri, g->tri_cap, tri_n, g->xoff,
