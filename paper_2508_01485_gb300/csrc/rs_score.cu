@@ -83,6 +83,25 @@ __device__ __forceinline__ int tab_insert(const Tab &t, int32_t c, uint32_t add,
     return -1;
 }
 
+// insert, returning the count before the add and whether the key is new
+__device__ __forceinline__ int tab_insert_old(const Tab &t, int32_t c, uint32_t add, uint32_t &old, bool &fresh,
+                                              int *err) {
+    uint32_t h = slot_of(c, t.mask);
+    for (uint32_t it = 0; it <= t.mask; ++it) {
+        int32_t prev = atomicCAS(&t.key[h], kEmpty, c);
+        if (prev == kEmpty || prev == c) {
+            fresh = prev == kEmpty;
+            old = atomicAdd(&t.cnt[h], add);
+            return (int)h;
+        }
+        h = (h + 1) & t.mask;
+    }
+    atomicOr(err, 1);
+    old = 0;
+    fresh = false;
+    return -1;
+}
+
 __device__ __forceinline__ int tab_find(const Tab &t, int32_t c) {
     uint32_t h = slot_of(c, t.mask);
     for (uint32_t it = 0; it <= t.mask; ++it) {
@@ -298,9 +317,12 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
     RowSum *__restrict__ rsum, int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab) {
     __shared__ int32_t skey[kMidWarps][kWarpCap];
     __shared__ uint32_t scnt[kMidWarps][kWarpCap];
+    __shared__ int16_t sused[kMidWarps][kWarpCap];    // slots taken by the current row
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint32_t j = lane; j < kWarpCap; j += 32) { skey[wid][j] = kEmpty; scnt[wid][j] = 0; }
+    __syncwarp();
     df best{0.0f, 0.0f};
     for (int64_t i = warp; i < nrows; i += nwarps) {
         int32_t v = rows[i];
@@ -309,10 +331,9 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
         int32_t cv = lab[v];
         uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(d, k));
         Tab t{skey[wid], scnt[wid], nullptr, nullptr, cap - 1};
-        for (uint32_t j = lane; j < cap; j += 32) { t.key[j] = kEmpty; t.cnt[j] = 0; }
-        __syncwarp();
-        uint32_t own = 0;
+        uint32_t own = 0, nused = 0;
         int32_t nx = 0;
+        u128 X = 0;                       // foreign part, from count deltas at insert time
         for (int base = 0; base < d; base += 32) {
             int e = base + lane;
             bool act = e < d;
@@ -321,30 +342,34 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
             own += (act && c == cv);
             bool foreign = act && c != cv;
             unsigned fm = __ballot_sync(FULL, foreign);
+            bool lead = false, fresh = false;
+            int sl = -1;
             if (foreign) {
                 int64_t p = b + nx + __popc(fm & lanemask_lt());
                 cl_col[p] = x;
                 cl_lab[p] = c;
                 unsigned grp = __match_any_sync(fm, c);
-                if (lane == __ffs(grp) - 1) tab_insert(t, c, __popc(grp), err);
+                lead = lane == __ffs(grp) - 1;
+                if (lead) {
+                    uint32_t old, g = __popc(grp);
+                    sl = tab_insert_old(t, c, g, old, fresh, err);
+                    X += (u128)(old + g) * LG[old + g] - (u128)old * LG[old];
+                }
             }
+            unsigned nm = __ballot_sync(FULL, fresh);
+            if (fresh) sused[wid][nused + __popc(nm & lanemask_lt())] = (int16_t)sl;
+            nused += __popc(nm);
             nx += __popc(fm);
         }
         __syncwarp();
         for (int o = 16; o; o >>= 1) own += __shfl_xor_sync(FULL, own, o);
-        uint32_t Lf = 0;
-        u128 X = 0;
-        for (uint32_t j = lane; j < cap; j += 32)
-            if (t.key[j] != kEmpty) { Lf++; X += (u128)t.cnt[j] * LG[t.cnt[j]]; }
-        for (int o = 16; o; o >>= 1) Lf += __shfl_xor_sync(FULL, Lf, o);
-        RowAgg a{(uint32_t)d, Lf + (own > 0 ? 1u : 0u), warp_sum_u128(X) + (u128)own * LG[own]};
+        RowAgg a{(uint32_t)d, nused + (own > 0 ? 1u : 0u), warp_sum_u128(X) + (u128)own * LG[own]};
         float wcur = 0.0f;
         if (lane == 0) wcur = fmaxf(current_wmax(wmax_bits), best.hi);
         bool want_max = __shfl_sync(FULL, (int)row_may_raise_max(a.L, wcur), 0);
         df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
         if (want_max)
-            for (uint32_t j = lane; j < cap; j += 32)
-                if (t.key[j] != kEmpty) cm = df_max(cm, column_weight(a, t.cnt[j], LG));
+            for (uint32_t j = lane; j < nused; j += 32) cm = df_max(cm, column_weight(a, t.cnt[sused[wid][j]], LG));
         if (own > 0 && lane == 0) { wown = column_weight(a, own, LG); cm = df_max(cm, wown); }
         cm = warp_max_df(cm);
         if (lane == 0) {
@@ -354,6 +379,8 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
             Lall[v] = (int32_t)a.L;
             store_rowsum(rsum, v, a);
         }
+        __syncwarp();
+        for (uint32_t j = lane; j < nused; j += 32) { int sl = sused[wid][j]; t.key[sl] = kEmpty; t.cnt[sl] = 0; }
         __syncwarp();
     }
     if (lane == 0 && best.hi > 0.0f) atomicMax(wmax_bits, double_bits(best));
@@ -628,7 +655,45 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
         NodeRec rw = rec[w];
         int dx = rw.dx;
         int32_t bo = 0, bi = 0;
-        if (dx > 0) {
+        if (dx > 0 && dx <= 32) {
+            // one chunk holds the whole cross list: warp matching gives each
+            // community's count and Type-II sum directly
+            RowSum rs = rsum[w];
+            RowAgg a{(uint32_t)d, rs.L, ((u128)rs.xhi << 64) | rs.xlo};
+            df sig1 = df_cbrt(column_weight(a, 1, LG));
+            bool act = lane < dx;
+            int32_t u = act ? cl_col[b + lane] : -1;
+            int32_t c = act ? cl_lab[b + lane] : -1;
+            NodeRec ru{0, -1, 0};
+            if (act) ru = rec[u];
+            st[lane] = ru.s_fix;
+            __syncwarp();
+            unsigned am = __ballot_sync(FULL, act);
+            unsigned grp = 0;
+            if (act) grp = __match_any_sync(am, c);
+            uint32_t f = __popc(grp);
+            df sig{0.0f, 0.0f};
+            if (act) {
+                sig = f == 1 ? sig1 : df_cbrt(column_weight(a, f, LG));
+                if (f > 1) {
+                    u128 rest = 0;
+                    unsigned m = grp & ~(1u << lane);
+                    while (m) { rest += st[__ffs(m) - 1]; m &= m - 1; }
+                    push_type2(acc, u, sig, rest);
+                }
+            }
+            __syncwarp();
+            if (dx >= 2) {
+                int64_t xb = xoff[w];
+                bool inx = act && ru.dx >= 2;
+                bool o = inx && rank_after(ru.dx, u, dx, w);
+                bool in = inx && !o;
+                unsigned mo = __ballot_sync(FULL, o), mi = __ballot_sync(FULL, in);
+                if (o) { int64_t p = xb + __popc(mo & lanemask_lt()); xcol[p] = u; xS[p] = sig; }
+                if (in) { int64_t p = xb + dx - 1 - __popc(mi & lanemask_lt()); xcol[p] = u; xS[p] = sig; }
+                bo = __popc(mo); bi = __popc(mi);
+            }
+        } else if (dx > 32) {
             uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(dx, k));
             Tab t;
             t.q = (unsigned long long *)base_w;
