@@ -345,7 +345,13 @@ __global__ void classify_kernel(const int64_t *off, int64_t n, int32_t k, int cl
 // small rows grouped by degree (so the threads of a warp run loops of equal length)
 __global__ void degree_hist_kernel(const int64_t *off, const int32_t *rows, int64_t m, int *hist) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) atomicAdd(&hist[off[rows[i] + 1] - off[rows[i]]], 1);
+    bool act = i < m;
+    int d = act ? (int)(off[rows[i] + 1] - off[rows[i]]) : 0;
+    unsigned am = __ballot_sync(0xFFFFFFFFu, act);
+    if (act) {
+        unsigned grp = __match_any_sync(am, d);
+        if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&hist[d], __popc(grp));
+    }
 }
 __global__ void degree_prefix_kernel(int *hist) {
     int acc = 0;
@@ -412,9 +418,10 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
         RS_CUDA_TRY(cudaGetLastError());
         degree_prefix_kernel<<<1, 1, 0, s>>>(hist);
         RS_CUDA_TRY(cudaGetLastError());
-        degree_scatter_kernel<<<sb, 256, 0, s>>>(g->off, g->rows_small, g->n_small, hist, g->xin);
+        degree_scatter_kernel<<<sb, 256, 0, s>>>(g->off, g->rows_small, g->n_small, hist, g->rows_small_deg);
         RS_CUDA_TRY(cudaGetLastError());
-        RS_CUDA_TRY(cudaMemcpyAsync(g->rows_small, g->xin, g->n_small * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    } else if (g->n_small == 1) {
+        RS_CUDA_TRY(cudaMemcpyAsync(g->rows_small_deg, g->rows_small, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     }
     // hubs: host-side work list (hubs are few)
     int nh = hdr[2];
@@ -492,6 +499,7 @@ static int alloc_workspace(rs_graph *g) {
     RS_CUDA_TRY(dmalloc(&g->rows_small, n));
     RS_CUDA_TRY(dmalloc(&g->rows_mid, n));
     RS_CUDA_TRY(dmalloc(&g->rows_large, n));
+    RS_CUDA_TRY(dmalloc(&g->rows_small_deg, n));
     RS_CUDA_TRY(dmalloc(&g->d_flag, 64));
     return 0;
 }
@@ -499,7 +507,7 @@ static int alloc_workspace(rs_graph *g) {
 static void free_graph(rs_graph *g) {
     if (!g) return;
     void *ptrs[] = {g->off, g->off_alt, g->col, g->col_alt, g->lab, g->removed, g->dead,
-                    g->rows_small, g->rows_mid, g->rows_large, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
+                    g->rows_small, g->rows_mid, g->rows_large, g->rows_small_deg, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
                     g->Lall, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->scan_tmp, g->tk_hist,
                     g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->tri, g->rsum, g->cl_col, g->cl_lab};
     for (void *p : ptrs) cudaFree(p);

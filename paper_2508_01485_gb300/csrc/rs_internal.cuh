@@ -87,6 +87,7 @@ struct rs_graph {
     uint8_t *dead = nullptr;          // nnz edge marks used by removals
     // row classes
     int32_t *rows_small = nullptr, *rows_mid = nullptr, *rows_large = nullptr;
+    int32_t *rows_small_deg = nullptr;   // the small rows grouped by degree
     int64_t n_small = 0, n_mid = 0, n_large = 0;
     int32_t large_cap = 0;            // largest table among large rows
     rs::HubInfo *hubs = nullptr;      // device copy

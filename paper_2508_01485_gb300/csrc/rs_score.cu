@@ -202,56 +202,7 @@ __device__ __forceinline__ df p1_row_result(const RowAgg &a, uint32_t own, df co
 // P1
 // ======================================================================================
 
-// Small rows, one thread per row.  Each thread keeps the foreign communities of
-// its row in a private column of a shared-memory table (slot-major, thread-minor,
-// so accesses never conflict); neighbours of its own community are counted
-// apart.  Column weights are evaluated once per distinct count.
 constexpr int kSlots = kSmallMax;
-constexpr int kPrefetch = 8;
-
-struct SmallTable {
-    int32_t lab[kSlots][kThreads];
-    uint8_t cnt[kSlots][kThreads];
-};
-
-// counts of row v's neighbour communities, and its cross list (neighbours of
-// another community, in id order) written to cl_col / cl_lab at b; returns the aggregates
-__device__ __forceinline__ RowAgg small_row_counts(const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
-                                                   int64_t b, int d, int32_t cv, const uint64_t *__restrict__ LG,
-                                                   SmallTable &T, int t, int &nf, uint32_t &own,
-                                                   uint64_t &seen, int32_t *__restrict__ cl_col,
-                                                   int32_t *__restrict__ cl_lab) {
-    nf = 0;
-    own = 0;
-    int nx = 0;
-    for (int j0 = 0; j0 < d; j0 += kPrefetch) {
-        int32_t x[kPrefetch], c[kPrefetch];
-#pragma unroll
-        for (int q = 0; q < kPrefetch; ++q) x[q] = (j0 + q < d) ? col[b + j0 + q] : -1;
-#pragma unroll
-        for (int q = 0; q < kPrefetch; ++q) c[q] = (x[q] >= 0) ? lab[x[q]] : -1;
-#pragma unroll
-        for (int q = 0; q < kPrefetch; ++q) {
-            if (j0 + q >= d) break;
-            if (c[q] == cv) { own++; continue; }
-            cl_col[b + nx] = x[q];
-            cl_lab[b + nx] = c[q];
-            ++nx;
-            int sl = 0;
-            while (sl < nf && T.lab[sl][t] != c[q]) ++sl;
-            if (sl == nf) { T.lab[sl][t] = c[q]; T.cnt[sl][t] = 1; ++nf; }
-            else T.cnt[sl][t]++;
-        }
-    }
-    u128 X = (u128)own * LG[own];
-    seen = own ? (1ull << own) : 0ull;
-    for (int sl = 0; sl < nf; ++sl) {
-        uint32_t f = T.cnt[sl][t];
-        X += (u128)f * LG[f];
-        seen |= 1ull << f;
-    }
-    return RowAgg{(uint32_t)d, (uint32_t)nf + (own > 0 ? 1u : 0u), X};
-}
 
 __device__ __forceinline__ void store_rowsum(RowSum *rsum, int32_t v, const RowAgg &a) {
     RowSum r;
@@ -262,49 +213,141 @@ __device__ __forceinline__ void store_rowsum(RowSum *rsum, int32_t v, const RowA
     rsum[v] = r;
 }
 
+// Small rows, tiles of 32 consecutive rows (id order) per warp: the union of
+// their CSR segments is streamed with one neighbour per lane (coalesced
+// columns, one label gather per lane), (row, community) groups come from warp
+// matching, and lane l then finishes row l of the tile.  A row of degree
+// <= 32 spans at most two chunks, so its foreign list holds at most 32
+// entries (a community seen in two chunks appears twice and is merged).
+struct SmallTile {
+    int32_t flab[kSlots][32];       // foreign (community, count) entries, entry-major
+    uint8_t fcnt[kSlots][32];
+    int32_t pre[33];                // prefix sums of the tile's degrees
+    int64_t rb[32];                 // row starts
+    int32_t cv[32];                 // row labels
+    uint32_t own[32], nf[32];
+    int32_t nx[32];                 // cross list fill
+};
+
 __global__ void __launch_bounds__(kThreads) p1_small_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
     const int32_t *__restrict__ rows, int64_t nrows, int32_t k, const uint64_t *__restrict__ LG,
     NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits,
     RowSum *__restrict__ rsum, int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab) {
-    __shared__ SmallTable T;
-    int t = threadIdx.x;
+    __shared__ SmallTile tiles[kThreads / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    SmallTile &T = tiles[wid];
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     df best{0.0f, 0.0f};
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < nrows; i0 += (int64_t)gridDim.x * blockDim.x) {
-        float wcur = 0.0f;
-        if ((t & 31) == 0) wcur = current_wmax(wmax_bits);
-        wcur = __shfl_sync(FULL, wcur, 0);
-        int64_t i = i0 + t;
-        if (i >= nrows) continue;
-        int32_t v = rows[i];
-        int64_t b = off[v];
-        int d = (int)(off[v + 1] - b);
-        int32_t cv = lab[v];
-        int nf;
-        uint32_t own;
-        uint64_t seen;
-        RowAgg a = small_row_counts(col, lab, b, d, cv, LG, T, t, nf, own, seen, cl_col, cl_lab);
-        store_rowsum(rsum, v, a);
-        bool want_max = row_may_raise_max(a.L, fmaxf(wcur, best.hi));
-        df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
-        if (want_max) {
-            while (seen) {
-                uint32_t f = (uint32_t)(__ffsll((long long)seen) - 1);
-                df w = column_weight(a, f, LG);
-                if (f == own) wown = w;
-                cm = df_max(cm, w);
-                seen &= seen - 1;
-            }
-        } else if (own > 0) {
-            wown = column_weight(a, own, LG);
+    for (int64_t t0 = warp * 32; t0 < nrows; t0 += nwarps * 32) {
+        int64_t i = t0 + lane;
+        bool have = i < nrows;
+        int32_t v = have ? rows[i] : 0;
+        int64_t b = have ? off[v] : 0;
+        int32_t d = have ? (int32_t)(off[v + 1] - b) : 0;
+        int32_t cv = have ? lab[v] : -1;
+        int32_t incl = d;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
         }
-        NodeRec r;
-        best = df_max(best, p1_row_result(a, own, cm, k, LG, r, cv, wown, want_max));
-        rec[v] = r;
-        Lall[v] = (int32_t)a.L;
+        int32_t D = __shfl_sync(FULL, incl, 31);
+        T.pre[lane + 1] = incl;
+        if (lane == 0) T.pre[0] = 0;
+        T.rb[lane] = b;
+        T.cv[lane] = cv;
+        T.own[lane] = 0;
+        T.nf[lane] = 0;
+        T.nx[lane] = 0;
+        __syncwarp();
+        for (int32_t e0 = 0; e0 < D; e0 += 32) {
+            int32_t e = e0 + lane;
+            bool act = e < D;
+            int32_t r = 0, x = -1, c = -1;
+            if (act) {
+                int32_t lo = 0, hi = 32;               // last r with pre[r] <= e
+                while (hi - lo > 1) {
+                    int32_t mid = (lo + hi) >> 1;
+                    if (T.pre[mid] <= e) lo = mid; else hi = mid;
+                }
+                r = lo;
+                x = col[T.rb[r] + (e - T.pre[r])];
+                c = lab[x];
+            }
+            bool own = act && c == T.cv[r];
+            bool foreign = act && !own;
+            unsigned om = __ballot_sync(FULL, own), fm = __ballot_sync(FULL, foreign);
+            unsigned gown = 0, grow = 0;
+            if (own) gown = __match_any_sync(om, r);
+            if (foreign) grow = __match_any_sync(fm, r);
+            int32_t xbase = foreign ? T.nx[r] : 0;
+            __syncwarp();
+            if (own && lane == __ffs(gown) - 1) T.own[r] += __popc(gown);
+            if (foreign) {
+                int64_t p = T.rb[r] + xbase + __popc(grow & lanemask_lt());
+                cl_col[p] = x;
+                cl_lab[p] = c;
+                if (lane == __ffs(grow) - 1) T.nx[r] = xbase + __popc(grow);
+                unsigned long long key = ((unsigned long long)(uint32_t)r << 32) | (uint32_t)c;
+                unsigned gc = __match_any_sync(fm, key);
+                if (lane == __ffs(gc) - 1) {
+                    uint32_t slot = atomicAdd(&T.nf[r], 1u);
+                    T.flab[slot][r] = c;
+                    T.fcnt[slot][r] = (uint8_t)__popc(gc);
+                }
+            }
+            __syncwarp();
+        }
+        // lane `lane` finishes row `lane` of the tile
+        float wcur = 0.0f;
+        if (lane == 0) wcur = current_wmax(wmax_bits);
+        wcur = __shfl_sync(FULL, wcur, 0);
+        if (have) {
+            uint32_t own = T.own[lane];
+            int nf = (int)T.nf[lane];
+            // merge a community listed from two chunks
+            for (int j = 1; j < nf; ++j)
+                for (int j2 = 0; j2 < j; ++j2)
+                    if (T.fcnt[j2][lane] && T.flab[j2][lane] == T.flab[j][lane]) {
+                        T.fcnt[j2][lane] += T.fcnt[j][lane];
+                        T.fcnt[j][lane] = 0;
+                        break;
+                    }
+            u128 X = (u128)own * LG[own];
+            uint64_t seen = own ? (1ull << own) : 0ull;
+            uint32_t L = own > 0 ? 1u : 0u;
+            for (int j = 0; j < nf; ++j) {
+                uint32_t f = T.fcnt[j][lane];
+                if (!f) continue;
+                X += (u128)f * LG[f];
+                seen |= 1ull << f;
+                ++L;
+            }
+            RowAgg a{(uint32_t)d, L, X};
+            store_rowsum(rsum, v, a);
+            bool want_max = row_may_raise_max(a.L, fmaxf(wcur, best.hi));
+            df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
+            if (want_max) {
+                while (seen) {
+                    uint32_t f = (uint32_t)(__ffsll((long long)seen) - 1);
+                    df w = column_weight(a, f, LG);
+                    if (f == own) wown = w;
+                    cm = df_max(cm, w);
+                    seen &= seen - 1;
+                }
+            } else if (own > 0) {
+                wown = column_weight(a, own, LG);
+            }
+            NodeRec rr;
+            best = df_max(best, p1_row_result(a, own, cm, k, LG, rr, cv, wown, want_max));
+            rec[v] = rr;
+            Lall[v] = (int32_t)a.L;
+        }
+        __syncwarp();
     }
     best = warp_max_df(best);
-    if ((t & 31) == 0 && best.hi > 0.0f) atomicMax(wmax_bits, double_bits(best));
+    if (lane == 0 && best.hi > 0.0f) atomicMax(wmax_bits, double_bits(best));
 }
 
 // Mid rows, one warp per row, a per-warp shared-memory table of kWarpCap slots.
@@ -1366,7 +1409,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     // ---- P2
     if (g->n_small) {
         p2_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, s>>>(
-            g->off, g->rows_small, g->n_small, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
+            g->off, g->rows_small_deg, g->n_small, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin);
         RS_LAUNCHED(g, s, "p2_small");
     }
