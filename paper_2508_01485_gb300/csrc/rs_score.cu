@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
 constexpr int kMidSlotBytes = 4 + 4 + 16;   // key, count, 2-word sum
 
 __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, int32_t k,
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, int32_t k, int32_t dx_max,
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
@@ -697,6 +697,7 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
         int d = (int)(off[w + 1] - b);
         NodeRec rw = rec[w];
         int dx = rw.dx;
+        if (dx > dx_max) continue;                 // left to the CTA-per-row kernel
         int32_t bo = 0, bi = 0;
         if (dx > 0 && dx <= 32) {
             // one chunk holds the whole cross list: warp matching gives each
@@ -842,7 +843,7 @@ __device__ __forceinline__ void gx_round(bool out, bool in, int64_t xb, int32_t 
 
 template <int NT>
 __global__ void __launch_bounds__(NT) p2_large_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, int32_t k,
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, int32_t k, int32_t dx_min,
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
@@ -858,6 +859,7 @@ __global__ void __launch_bounds__(NT) p2_large_kernel(
         int d = (int)(off[w + 1] - b);
         NodeRec rw = rec[w];
         int dx = rw.dx;
+        if (dx < dx_min) continue;                  // done by the warp-per-row kernel
         if (dx == 0) {
             if (tid == 0) { xout[w] = 0; xin[w] = 0; }
             continue;
@@ -1258,36 +1260,48 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
                 __syncwarp();
             }
             int32_t W = S.wpre[E];
-            for (int32_t w0 = 0; w0 < W; w0 += 32) {
-                int32_t wv = w0 + lane;
-                bool hit = false;
-                int32_t e = 0, l2 = 0, c = 0, ow = 0;
-                int64_t pb = 0;
-                if (wv < W) {
-                    int32_t lo = 0, hi = E;                 // last entry with wpre[e] <= wv
-                    while (hi - lo > 1) {
-                        int32_t mid = (lo + hi) >> 1;
-                        if (S.wpre[mid] <= wv) lo = mid; else hi = mid;
+            constexpr int U = 4;                       // wedges per lane per trip (loads in flight)
+            for (int32_t w0 = 0; w0 < W; w0 += 32 * U) {
+                int32_t e[U], c[U];
+                int64_t pb[U];
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    int32_t wv = w0 + q * 32 + lane;
+                    e[q] = -1;
+                    if (wv < W) {
+                        int32_t lo = 0, hi = E;             // last entry with wpre[e] <= wv
+                        while (hi - lo > 1) {
+                            int32_t mid = (lo + hi) >> 1;
+                            if (S.wpre[mid] <= wv) lo = mid; else hi = mid;
+                        }
+                        e[q] = lo;
+                        pb[q] = S.boff[lo] + (wv - S.wpre[lo]);
                     }
-                    e = lo;
-                    pb = S.boff[e] + (wv - S.wpre[e]);
-                    c = xcol[pb];
-                    ow = S.owner[e];
-                    int32_t s0 = S.seg[ow], s1 = S.seg[ow + 1];
-                    l2 = s0;
-                    int32_t h2 = s1;
-                    while (l2 < h2) {
-                        int32_t mid = (l2 + h2) >> 1;
-                        if (S.nb[mid] < c) l2 = mid + 1; else h2 = mid;
-                    }
-                    hit = l2 < s1 && S.nb[l2] == c;
                 }
-                unsigned long long p = reserve(hit, tri_n, lane);
-                if (hit) {
-                    int64_t ba_o = S.aoff[ow];
-                    int32_t s0 = S.seg[ow];
-                    put_triangle(p, (int32_t)(base + ow), S.nb[e], c, xS[ba_o + (e - s0)], xS[ba_o + (l2 - s0)],
-                                 xS[pb], tri, tri_cap, xoff, xcol, xS, xin, rec, acc, err);
+#pragma unroll
+                for (int q = 0; q < U; ++q) c[q] = e[q] >= 0 ? xcol[pb[q]] : 0;
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    bool hit = false;
+                    int32_t ow = 0, l2 = 0;
+                    if (e[q] >= 0) {
+                        ow = S.owner[e[q]];
+                        int32_t s0 = S.seg[ow], s1 = S.seg[ow + 1];
+                        l2 = s0;
+                        int32_t h2 = s1;
+                        while (l2 < h2) {
+                            int32_t mid = (l2 + h2) >> 1;
+                            if (S.nb[mid] < c[q]) l2 = mid + 1; else h2 = mid;
+                        }
+                        hit = l2 < s1 && S.nb[l2] == c[q];
+                    }
+                    unsigned long long p = reserve(hit, tri_n, lane);
+                    if (hit) {
+                        int64_t ba_o = S.aoff[ow];
+                        int32_t s0 = S.seg[ow];
+                        put_triangle(p, (int32_t)(base + ow), S.nb[e[q]], c[q], xS[ba_o + (e[q] - s0)],
+                                     xS[ba_o + (l2 - s0)], xS[pb[q]], tri, tri_cap, xoff, xcol, xS, xin, rec, acc, err);
+                    }
                 }
             }
             __syncwarp();
@@ -1415,13 +1429,18 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     }
     if (g->n_mid) {
         p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, p2_mid_smem, s>>>(
-            g->off, g->rows_mid, g->n_mid, g->k, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
+            g->off, g->rows_mid, g->n_mid, g->k, 1 << 30, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin, err);
         RS_LAUNCHED(g, s, "p2_mid");
     }
     if (g->n_large) {
+        // large rows whose cross list fits a per-warp table go warp-per-row too
+        p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, p2_mid_smem, s>>>(
+            g->off, g->rows_large, g->n_large, g->k, kWarpCap / 2, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab,
+            g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
+        RS_LAUNCHED(g, s, "p2_large_warp");
         p2_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, p2_smem, s>>>(
-            g->off, g->rows_large, g->n_large, g->k, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
+            g->off, g->rows_large, g->n_large, g->k, kWarpCap / 2 + 1, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
             g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
         RS_LAUNCHED(g, s, "p2_large");
     }
