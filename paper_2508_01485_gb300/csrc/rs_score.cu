@@ -617,60 +617,140 @@ __global__ void gx_capacity_kernel(const NodeRec *__restrict__ rec, int64_t n, i
 // another community, in id order) and the row aggregates; own-community
 // neighbours are never touched again.
 
-// Small rows, one thread per row.  The count f of a cross neighbour's
-// community is found by scanning the (short) cross list.
+// Small rows, tiles of 32 consecutive rows (id order) per warp.  The union of
+// the tile's cross lists is processed one entry per lane; lane l prepares and
+// closes row l.  A community's count f and Type-II sum come from warp matching
+// on (row, community); the rare row whose cross list straddles two chunks
+// rescans its own list instead.
+struct P2Tile {
+    int32_t pre[33];            // prefix sums of dx over the tile
+    int64_t rb[32], xb[32];     // cross list start (= CSR start), G_x row start
+    int32_t dx[32], w[32];
+    uint32_t d[32], L[32];
+    uint64_t xlo[32], xhi[32];
+    df sig1[32];
+    int32_t no[32], ni[32];
+    uint64_t st[32];
+};
+
 __global__ void __launch_bounds__(kThreads) p2_small_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows,
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
     int32_t *__restrict__ xout, int32_t *__restrict__ xin) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t w = rows[i];
-        int64_t b = off[w];
-        int d = (int)(off[w + 1] - b);
-        NodeRec rw = rec[w];
-        int dx = rw.dx;
-        int32_t no = 0, ni = 0;
-        if (dx > 0) {
-            RowSum rs = rsum[w];
-            RowAgg a{(uint32_t)d, rs.L, ((u128)rs.xhi << 64) | rs.xlo};
-            df sig1{-1.0f, 0.0f}, sigl{0.0f, 0.0f};
-            uint32_t fl = 0;
-            int64_t xb = xoff[w];
-            bool gx = dx >= 2;
-            for (int j = 0; j < dx; ++j) {
-                int32_t u = cl_col[b + j];
-                int32_t c = cl_lab[b + j];
-                uint32_t f = 0;
-                for (int j2 = 0; j2 < dx; ++j2) f += (cl_lab[b + j2] == c);
-                df sig;
-                if (f == 1) {
-                    if (sig1.hi < 0.0f) sig1 = df_cbrt(column_weight(a, 1, LG));
-                    sig = sig1;
-                } else {
-                    if (f != fl) { sigl = df_cbrt(column_weight(a, f, LG)); fl = f; }
-                    sig = sigl;
-                    // Type-II: the other cross neighbours of w in community c
-                    u128 rest = 0;
-                    for (int j2 = 0; j2 < dx; ++j2)
-                        if (j2 != j && cl_lab[b + j2] == c) rest += rec[cl_col[b + j2]].s_fix;
-                    push_type2(acc, u, sig, rest);
-                }
-                if (gx) {
-                    int32_t dxu = rec[u].dx;
-                    if (dxu >= 2) {
-                        int64_t p;
-                        if (rank_after(dxu, u, dx, w)) p = xb + no++;
-                        else p = xb + dx - 1 - ni++;
-                        xcol[p] = u;
-                        xS[p] = sig;
-                    }
-                }
+    __shared__ P2Tile tiles[kThreads / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    P2Tile &T = tiles[wid];
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t0 = warp * 32; t0 < nrows; t0 += nwarps * 32) {
+        int64_t i = t0 + lane;
+        bool have = i < nrows;
+        int32_t w = have ? rows[i] : 0;
+        int32_t dx = 0;
+        if (have) {
+            int64_t b = off[w];
+            NodeRec rw = rec[w];
+            dx = rw.dx;
+            T.rb[lane] = b;
+            T.d[lane] = (uint32_t)(off[w + 1] - b);
+            T.w[lane] = w;
+            if (dx > 0) {
+                RowSum rs = rsum[w];
+                T.xlo[lane] = rs.xlo; T.xhi[lane] = rs.xhi; T.L[lane] = rs.L;
+                RowAgg a{T.d[lane], rs.L, ((u128)rs.xhi << 64) | rs.xlo};
+                T.sig1[lane] = df_cbrt(column_weight(a, 1, LG));
+                T.xb[lane] = xoff[w];
             }
         }
-        xout[w] = no;
-        xin[w] = ni;
+        T.dx[lane] = dx;
+        T.no[lane] = 0;
+        T.ni[lane] = 0;
+        int32_t incl = dx;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int32_t DX = __shfl_sync(FULL, incl, 31);
+        T.pre[lane + 1] = incl;
+        if (lane == 0) T.pre[0] = 0;
+        __syncwarp();
+        for (int32_t e0 = 0; e0 < DX; e0 += 32) {
+            int32_t e = e0 + lane;
+            bool act = e < DX;
+            int32_t r = 0, u = -1, c = -1, j = 0;
+            NodeRec ru{0, -1, 0};
+            if (act) {
+                int32_t lo = 0, hi = 32;
+                while (hi - lo > 1) {
+                    int32_t mid = (lo + hi) >> 1;
+                    if (T.pre[mid] <= e) lo = mid; else hi = mid;
+                }
+                r = lo;
+                j = e - T.pre[r];
+                u = cl_col[T.rb[r] + j];
+                c = cl_lab[T.rb[r] + j];
+                ru = rec[u];
+            }
+            T.st[lane] = ru.s_fix;
+            __syncwarp();
+            unsigned am = __ballot_sync(FULL, act);
+            unsigned long long key = ((unsigned long long)(uint32_t)r << 32) | (uint32_t)c;
+            unsigned gc = 0;
+            if (act) gc = __match_any_sync(am, key);
+            df sig{0.0f, 0.0f};
+            if (act) {
+                int32_t rdx = T.dx[r];
+                bool whole = T.pre[r] >= e0 && T.pre[r] + rdx <= e0 + 32;   // row inside this chunk
+                uint32_t f;
+                u128 rest = 0;
+                if (whole) {
+                    f = __popc(gc);
+                    if (f > 1) {
+                        unsigned m = gc & ~(1u << lane);
+                        while (m) { rest += T.st[__ffs(m) - 1]; m &= m - 1; }
+                    }
+                } else {
+                    f = 0;
+                    int64_t rb = T.rb[r];
+                    for (int32_t j2 = 0; j2 < rdx; ++j2) {
+                        if (cl_lab[rb + j2] != c) continue;
+                        ++f;
+                        if (j2 != j) rest += rec[cl_col[rb + j2]].s_fix;
+                    }
+                }
+                if (f == 1) sig = T.sig1[r];
+                else {
+                    RowAgg a{T.d[r], T.L[r], ((u128)T.xhi[r] << 64) | T.xlo[r]};
+                    sig = df_cbrt(column_weight(a, f, LG));
+                    push_type2(acc, u, sig, rest);
+                }
+            }
+            // G_x entries of this chunk, in id order within each row
+            bool gx = act && T.dx[r] >= 2 && ru.dx >= 2;
+            bool o = gx && rank_after(ru.dx, u, T.dx[r], T.w[r]);
+            bool in = gx && !o;
+            unsigned om = __ballot_sync(FULL, o), im = __ballot_sync(FULL, in);
+            unsigned go = 0, gi = 0;
+            if (o) go = __match_any_sync(om, r);
+            if (in) gi = __match_any_sync(im, r);
+            int32_t bo = o ? T.no[r] : 0, bi = in ? T.ni[r] : 0;
+            __syncwarp();
+            if (o) {
+                int64_t p = T.xb[r] + bo + __popc(go & lanemask_lt());
+                xcol[p] = u; xS[p] = sig;
+                if (lane == __ffs(go) - 1) T.no[r] = bo + __popc(go);
+            }
+            if (in) {
+                int64_t p = T.xb[r] + T.dx[r] - 1 - (bi + __popc(gi & lanemask_lt()));
+                xcol[p] = u; xS[p] = sig;
+                if (lane == __ffs(gi) - 1) T.ni[r] = bi + __popc(gi);
+            }
+            __syncwarp();
+        }
+        if (have) { xout[w] = T.no[lane]; xin[w] = T.ni[lane]; }
+        __syncwarp();
     }
 }
 
@@ -1358,6 +1438,9 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(
 // ======================================================================================
 // host orchestration
 // ======================================================================================
+// rows of the large class take 1024-thread CTAs: their longest rows bound the kernel time
+constexpr int kLargeThreads = 1024;
+
 int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     int64_t n = g->n;
     if (n == 0) return 0;
@@ -1378,8 +1461,8 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     size_t p2_mid_smem = (size_t)kMidWarps * kWarpCap * kMidSlotBytes;
     static bool attr_done = false;
     if (!attr_done) {
-        RS_CUDA_TRY(cudaFuncSetAttribute(p1_large_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kMidCap));
-        RS_CUDA_TRY(cudaFuncSetAttribute(p2_large_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kMidCap));
+        RS_CUDA_TRY(cudaFuncSetAttribute(p1_large_kernel<kLargeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kMidCap));
+        RS_CUDA_TRY(cudaFuncSetAttribute(p2_large_kernel<kLargeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kMidCap));
         RS_CUDA_TRY(cudaFuncSetAttribute(p2_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2_mid_smem));
         attr_done = true;
     }
@@ -1396,7 +1479,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_LAUNCHED(g, s, "hub_p1_finish");
     }
     if (g->n_large) {
-        p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, p1_smem, s>>>(
+        p1_large_kernel<kLargeThreads><<<grid_for(g->n_large, 1, 2), kLargeThreads, p1_smem, s>>>(
             g->off, g->col, g->lab, g->rows_large, g->n_large, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err,
             g->rsum, g->cl_col, g->cl_lab);
         RS_LAUNCHED(g, s, "p1_large");
@@ -1423,7 +1506,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     // ---- P2
     if (g->n_small) {
         p2_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, s>>>(
-            g->off, g->rows_small_deg, g->n_small, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
+            g->off, g->rows_small, g->n_small, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin);
         RS_LAUNCHED(g, s, "p2_small");
     }
@@ -1439,7 +1522,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->off, g->rows_large, g->n_large, g->k, kWarpCap / 2, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab,
             g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
         RS_LAUNCHED(g, s, "p2_large_warp");
-        p2_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, p2_smem, s>>>(
+        p2_large_kernel<kLargeThreads><<<grid_for(g->n_large, 1, 2), kLargeThreads, p2_smem, s>>>(
             g->off, g->rows_large, g->n_large, g->k, kWarpCap / 2 + 1, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
             g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
         RS_LAUNCHED(g, s, "p2_large");
