@@ -754,42 +754,37 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
     }
 }
 
-// Mid rows, one warp per row: a per-warp table (community -> count, Type-II
-// sum) over the cross list, then the terms and the G_x entries in id order.
-constexpr int kMidSlotBytes = 4 + 4 + 16;   // key, count, 2-word sum
-
-__global__ void __launch_bounds__(kThreads) p2_mid_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, int32_t k, int32_t dx_max,
+// Rows with at most 32 cross neighbours, one warp per row: one chunk holds
+// the whole cross list, so warp matching gives each community's count and
+// Type-II sum directly; no table, no shared memory beyond a staging word per lane.
+__global__ void __launch_bounds__(kThreads) p2_warp_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows,
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
-    int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    int32_t *__restrict__ xout, int32_t *__restrict__ xin) {
     __shared__ uint64_t stage[kThreads];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int lane = threadIdx.x & 31;
     uint64_t *st = stage + (threadIdx.x & ~31);
-    unsigned char *base_w = smem + (size_t)wid * kWarpCap * kMidSlotBytes;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < nrows; i += nwarps) {
         int32_t w = rows[i];
-        int64_t b = off[w];
-        int d = (int)(off[w + 1] - b);
         NodeRec rw = rec[w];
         int dx = rw.dx;
-        if (dx > dx_max) continue;                 // left to the CTA-per-row kernel
+        if (dx > 32) continue;                     // left to the table kernel
         int32_t bo = 0, bi = 0;
-        if (dx > 0 && dx <= 32) {
-            // one chunk holds the whole cross list: warp matching gives each
-            // community's count and Type-II sum directly
+        if (dx > 0) {
+            int64_t b = off[w];
+            int d = (int)(off[w + 1] - b);
             RowSum rs = rsum[w];
             RowAgg a{(uint32_t)d, rs.L, ((u128)rs.xhi << 64) | rs.xlo};
-            df sig1 = df_cbrt(column_weight(a, 1, LG));
             bool act = lane < dx;
             int32_t u = act ? cl_col[b + lane] : -1;
             int32_t c = act ? cl_lab[b + lane] : -1;
             NodeRec ru{0, -1, 0};
             if (act) ru = rec[u];
+            df sig1 = df_cbrt(column_weight(a, 1, LG));
             st[lane] = ru.s_fix;
             __syncwarp();
             unsigned am = __ballot_sync(FULL, act);
@@ -817,7 +812,37 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
                 if (in) { int64_t p = xb + dx - 1 - __popc(mi & lanemask_lt()); xcol[p] = u; xS[p] = sig; }
                 bo = __popc(mo); bi = __popc(mi);
             }
-        } else if (dx > 32) {
+        }
+        if (lane == 0) { xout[w] = bo; xin[w] = bi; }
+    }
+}
+
+// Mid rows, one warp per row: a per-warp table (community -> count, Type-II
+// sum) over the cross list, then the terms and the G_x entries in id order.
+constexpr int kMidSlotBytes = 4 + 4 + 16;   // key, count, 2-word sum
+
+__global__ void __launch_bounds__(kThreads) p2_mid_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, int32_t k, int32_t dx_max,
+    const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
+    const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
+    const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
+    int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint64_t stage[kThreads];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t *st = stage + (threadIdx.x & ~31);
+    unsigned char *base_w = smem + (size_t)wid * kWarpCap * kMidSlotBytes;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < nrows; i += nwarps) {
+        int32_t w = rows[i];
+        int64_t b = off[w];
+        int d = (int)(off[w + 1] - b);
+        NodeRec rw = rec[w];
+        int dx = rw.dx;
+        if (dx > dx_max || dx <= 32) continue;     // the CTA-per-row kernel / p2_warp_kernel
+        int32_t bo = 0, bi = 0;
+        {
             uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(dx, k));
             Tab t;
             t.q = (unsigned long long *)base_w;
@@ -1340,49 +1365,51 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
                 __syncwarp();
             }
             int32_t W = S.wpre[E];
-            constexpr int U = 4;                       // wedges per lane per trip (loads in flight)
-            for (int32_t w0 = 0; w0 < W; w0 += 32 * U) {
-                int32_t e[U], c[U];
-                int64_t pb[U];
-#pragma unroll
-                for (int q = 0; q < U; ++q) {
-                    int32_t wv = w0 + q * 32 + lane;
-                    e[q] = -1;
-                    if (wv < W) {
-                        int32_t lo = 0, hi = E;             // last entry with wpre[e] <= wv
-                        while (hi - lo > 1) {
-                            int32_t mid = (lo + hi) >> 1;
-                            if (S.wpre[mid] <= wv) lo = mid; else hi = mid;
-                        }
-                        e[q] = lo;
-                        pb[q] = S.boff[lo] + (wv - S.wpre[lo]);
-                    }
+            // each lane walks a contiguous range of the group's wedges
+            int32_t per = (W + 31) >> 5;
+            int32_t wv = min(W, lane * per), wend = min(W, wv + per);
+            int32_t e = 0;
+            {
+                int32_t lo = 0, hi = E;                 // last entry with wpre[e] <= wv
+                while (hi - lo > 1) {
+                    int32_t mid = (lo + hi) >> 1;
+                    if (S.wpre[mid] <= wv) lo = mid; else hi = mid;
                 }
-#pragma unroll
-                for (int q = 0; q < U; ++q) c[q] = e[q] >= 0 ? xcol[pb[q]] : 0;
-#pragma unroll
-                for (int q = 0; q < U; ++q) {
-                    bool hit = false;
-                    int32_t ow = 0, l2 = 0;
-                    if (e[q] >= 0) {
-                        ow = S.owner[e[q]];
-                        int32_t s0 = S.seg[ow], s1 = S.seg[ow + 1];
+                e = lo;
+            }
+            int32_t t = wv - S.wpre[e];
+            for (int32_t it = 0; it < per; ++it) {
+                bool act = wv < wend;
+                bool hit = false;
+                int32_t ow = 0, l2 = 0, c = 0;
+                int64_t pb = 0;
+                if (act) {
+                    while (S.wpre[e] + t >= S.wpre[e + 1]) { ++e; t = 0; }   // skip finished / empty entries
+                    pb = S.boff[e] + t;
+                    c = xcol[pb];
+                    ow = S.owner[e];
+                    int32_t s0 = S.seg[ow], s1 = S.seg[ow + 1];
+                    if (s1 - s0 <= 8) {
+                        l2 = s0;
+                        while (l2 < s1 && S.nb[l2] < c) ++l2;
+                    } else {
                         l2 = s0;
                         int32_t h2 = s1;
                         while (l2 < h2) {
                             int32_t mid = (l2 + h2) >> 1;
-                            if (S.nb[mid] < c[q]) l2 = mid + 1; else h2 = mid;
+                            if (S.nb[mid] < c) l2 = mid + 1; else h2 = mid;
                         }
-                        hit = l2 < s1 && S.nb[l2] == c[q];
                     }
-                    unsigned long long p = reserve(hit, tri_n, lane);
-                    if (hit) {
-                        int64_t ba_o = S.aoff[ow];
-                        int32_t s0 = S.seg[ow];
-                        put_triangle(p, (int32_t)(base + ow), S.nb[e[q]], c[q], xS[ba_o + (e[q] - s0)],
-                                     xS[ba_o + (l2 - s0)], xS[pb[q]], tri, tri_cap, xoff, xcol, xS, xin, rec, acc, err);
-                    }
+                    hit = l2 < s1 && S.nb[l2] == c;
                 }
+                unsigned long long p = reserve(hit, tri_n, lane);
+                if (hit) {
+                    int64_t ba_o = S.aoff[ow];
+                    int32_t s0 = S.seg[ow];
+                    put_triangle(p, (int32_t)(base + ow), S.nb[e], c, xS[ba_o + (e - s0)], xS[ba_o + (l2 - s0)],
+                                 xS[pb], tri, tri_cap, xoff, xcol, xS, xin, rec, acc, err);
+                }
+                if (act) { ++wv; ++t; }
             }
             __syncwarp();
         }
@@ -1438,7 +1465,7 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(
 // ======================================================================================
 // host orchestration
 // ======================================================================================
-// rows of the large class take 1024-thread CTAs: their longest rows bound the kernel time
+// P2 of large rows takes 1024-thread CTAs: its longest cross lists bound the kernel time
 constexpr int kLargeThreads = 1024;
 
 int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
@@ -1461,7 +1488,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     size_t p2_mid_smem = (size_t)kMidWarps * kWarpCap * kMidSlotBytes;
     static bool attr_done = false;
     if (!attr_done) {
-        RS_CUDA_TRY(cudaFuncSetAttribute(p1_large_kernel<kLargeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kMidCap));
+        RS_CUDA_TRY(cudaFuncSetAttribute(p1_large_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kMidCap));
         RS_CUDA_TRY(cudaFuncSetAttribute(p2_large_kernel<kLargeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kMidCap));
         RS_CUDA_TRY(cudaFuncSetAttribute(p2_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2_mid_smem));
         attr_done = true;
@@ -1479,7 +1506,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_LAUNCHED(g, s, "hub_p1_finish");
     }
     if (g->n_large) {
-        p1_large_kernel<kLargeThreads><<<grid_for(g->n_large, 1, 2), kLargeThreads, p1_smem, s>>>(
+        p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, p1_smem, s>>>(
             g->off, g->col, g->lab, g->rows_large, g->n_large, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err,
             g->rsum, g->cl_col, g->cl_lab);
         RS_LAUNCHED(g, s, "p1_large");
@@ -1511,6 +1538,10 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_LAUNCHED(g, s, "p2_small");
     }
     if (g->n_mid) {
+        p2_warp_kernel<<<grid_for(g->n_mid * 32, NT, 8), NT, 0, s>>>(
+            g->off, g->rows_mid, g->n_mid, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff, g->xcol,
+            g->xS, g->xout, g->xin);
+        RS_LAUNCHED(g, s, "p2_warp");
         p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, p2_mid_smem, s>>>(
             g->off, g->rows_mid, g->n_mid, g->k, 1 << 30, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin, err);
@@ -1518,6 +1549,10 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     }
     if (g->n_large) {
         // large rows whose cross list fits a per-warp table go warp-per-row too
+        p2_warp_kernel<<<grid_for(g->n_large * 32, NT, 8), NT, 0, s>>>(
+            g->off, g->rows_large, g->n_large, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
+            g->xcol, g->xS, g->xout, g->xin);
+        RS_LAUNCHED(g, s, "p2_warp");
         p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, p2_mid_smem, s>>>(
             g->off, g->rows_large, g->n_large, g->k, kWarpCap / 2, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab,
             g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
