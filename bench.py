@@ -74,6 +74,10 @@ def peaks():
 # ---- algorithmic bytes (model stated in the design doc) ---------------------------------
 
 def graph_stats(g):
+    """Per row class (the library's classes: small d <= 32, mid/large by hash-table
+    size 2 min(d, k) <= 512 / 2048, hub above) the rows R, CSR entries E, cross
+    entries X (neighbours of another community) and G_x slots G; and the
+    oriented G_x out-slots O."""
     import numpy as np
     deg = np.diff(g.offsets)
     n, E = g.n, g.nnz
@@ -82,30 +86,57 @@ def graph_stats(g):
     cross = lab[rows] != lab[g.cols]
     dx = np.bincount(rows[cross], minlength=n)
     keep = cross & (dx[rows] >= 2) & (dx[g.cols] >= 2)
-    small = deg <= 32
-    return {
-        "n": n, "E": E, "m": E // 2, "k": g.k,
-        "n_small": int(small.sum()), "E_small": int(deg[small].sum()),
-        "gx_slots": int(keep.sum()), "gx_slots_small": int((keep & small[rows]).sum()),
-        "dmax": int(deg.max()) if n else 0,
-    }
+    a, b = rows[keep], g.cols[keep].astype(np.int64)
+    out = (dx[b] > dx[a]) | ((dx[b] == dx[a]) & (b > a))
+    m = np.minimum(deg, g.k)
+    cap = np.where(m > 0, 2 ** np.ceil(np.log2(np.maximum(2 * m, 1))), 1)
+    cls = np.where(deg <= 32, 0, np.where(cap <= 512, 1, np.where(cap <= 2048, 2, 3)))
+    st = {"n": n, "E": E, "m": E // 2, "k": g.k, "dmax": int(deg.max()) if n else 0,
+          "gx_slots": int(keep.sum()), "out_slots": int(out.sum()), "cross": int(cross.sum())}
+    def put(name, sel):
+        st["R_" + name] = int(sel.sum())
+        st["E_" + name] = int(deg[sel].sum())
+        st["X_" + name] = int(dx[sel].sum())
+        st["G_" + name] = int((keep & sel[rows]).sum())
+    for c, name in enumerate(["small", "mid", "large", "hub"]):
+        put(name, cls == c)
+    # P2 splits mid and large rows by cross degree: <= 32 (no table), <= 256 (warp table), more (CTA)
+    put("mid_w", (cls == 1) & (dx <= 32))
+    put("mid_t", (cls == 1) & (dx > 32))
+    put("large_w", (cls == 2) & (dx <= 32))
+    put("large_t", (cls == 2) & (dx > 32) & (dx <= 256))
+    put("large_c", (cls == 2) & (dx > 256))
+    # compatibility names used by the JSON line
+    st["n_small"], st["E_small"] = st["R_small"], st["E_small"]
+    st["gx_slots_small"] = st["G_small"]
+    return st
 
 
 def kernel_bytes(name, st):
-    """Compulsory HBM bytes of one launch of a kernel (gathered arrays once)."""
-    n, E = st["n"], st["E"]
-    Rs, Es = st["n_small"], st["E_small"]
-    if name == "p1_small":
-        # row ids, offsets, columns, own label, node record + L written; the
-        # labels gathered by the columns (4 n bytes) are L2-resident after first touch
-        return 4 * Rs + 8 * Rs + 4 * Es + 4 * Rs + 20 * Rs + 4 * n * Es / max(E, 1)
-    if name == "p2_small":
-        # row ids, offsets, columns, own record, G_x slots (4 + 8 B) and counts;
-        # node records gathered (16 n B once)
-        return 4 * Rs + 8 * Rs + 4 * Es + 16 * Rs + 12 * st["gx_slots_small"] + 8 * Rs + 16 * n * Es / max(E, 1)
-    if name == "finalize":
-        return 16 * n + 16 * n + 8 * n
-    return None
+    """Algorithmic (compulsory) bytes of a kernel per step (all its launches): every array it
+    must touch, once; arrays it gathers at random are counted once in full,
+    shared among the kernels that gather them in proportion to their rows' entries."""
+    n, E, X = st["n"], st["E"], max(st["cross"], 1)
+    def p1(c):
+        R, Ec, Xc = st["R_" + c], st["E_" + c], st["X_" + c]
+        # row ids, offsets, own label; columns; labels gathered; record + sums + L; cross list
+        return 16 * R + 4 * Ec + 4 * n * Ec / max(E, 1) + (16 + 24 + 4) * R + 8 * Xc
+    def p2(c):
+        R, Xc, Gc = st["R_" + c], st["X_" + c], st["G_" + c]
+        # row ids, offsets, own record, sums, G_x offset, counts; cross list; records gathered; G_x slots
+        return (4 + 8 + 16 + 24 + 8 + 8) * R + 8 * Xc + 16 * n * Xc / X + 12 * Gc
+    table = {
+        "p1_small": lambda: p1("small"), "p1_mid": lambda: p1("mid"), "p1_large": lambda: p1("large"),
+        "p2_small": lambda: p2("small"), "p2_warp": lambda: p2("mid_w") + p2("large_w"),
+        "p2_mid": lambda: p2("mid_t"), "p2_large_warp": lambda: p2("large_t"), "p2_large": lambda: p2("large_c"),
+        # out-lists and the out/in counts and offsets of every node
+        "p3_list": lambda: 4 * st["out_slots"] + (4 + 8) * n,
+        "finalize": lambda: (8 + 16 + 8) * n,
+        "tk_select": lambda: 8 * n,
+        "gx_capacity": lambda: 16 * n + 8 * n,
+    }
+    f = table.get(name)
+    return f() if f else None
 
 
 def step_bytes(st):
@@ -272,7 +303,7 @@ def run_ours(args):
     prof_sum = sum(d["ms"] for d in per.values())
     top_name = max((k for k in per if per[k]["kernel"]), key=lambda k: per[k]["ms"])
     top = per[top_name]
-    avg_ms = top["ms"] / top["launches"]
+    avg_ms = top["ms"] / args.steps            # the kernel's device time per step (all its launches)
     hbm, peak_kind = peaks()
     kb = kernel_bytes(top_name, st)
     traffic = None
@@ -288,7 +319,8 @@ def run_ours(args):
         "peak": hbm, "unit": "GB/s",
         "frac": (kb / (avg_ms / 1e3) / 1e9 / hbm) if kb else None,
         "traffic": traffic, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-        "kernel_ms": avg_ms, "kernel_share": top["ms"] / prof_sum if prof_sum else None,
+        "kernel_ms": avg_ms, "launches_per_step": top["launches"] / args.steps,
+        "kernel_share": top["ms"] / prof_sum if prof_sum else None,
         "algorithmic_bytes": kb,
         "step_achieved": step_bytes(st) / (statistics.mean(step_ms) / 1e3) / 1e9,
         "step_frac": step_bytes(st) / (statistics.mean(step_ms) / 1e3) / 1e9 / hbm,

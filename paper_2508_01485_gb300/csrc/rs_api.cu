@@ -134,10 +134,18 @@ static void prof_record(rs_graph *g, cudaStream_t s, const char *name, bool is_k
         g->prof_ev.push_back(e);
         g->prof_name.push_back(nullptr);
         g->prof_is_kernel.push_back(0);
+        g->prof_prev.push_back(-1);
+        g->prof_stream.push_back(nullptr);
     }
-    cudaEventRecord(g->prof_ev[g->prof_used], s);
-    g->prof_name[g->prof_used] = name;
-    g->prof_is_kernel[g->prof_used] = is_kernel ? 1 : 0;
+    size_t i = g->prof_used;
+    int prev = -1;
+    for (size_t j = i; j-- > 0;)
+        if (g->prof_stream[j] == s) { prev = (int)j; break; }
+    cudaEventRecord(g->prof_ev[i], s);
+    g->prof_name[i] = name;
+    g->prof_is_kernel[i] = is_kernel ? 1 : 0;
+    g->prof_prev[i] = prev;
+    g->prof_stream[i] = s;
     g->prof_used++;
 }
 void rs::prof_begin(rs_graph *g, cudaStream_t s) {
@@ -146,6 +154,23 @@ void rs::prof_begin(rs_graph *g, cudaStream_t s) {
 void rs::prof_mark(rs_graph *g, cudaStream_t s, const char *name, bool is_kernel) {
     if (is_kernel) g->launches++;
     if (g->prof_on) prof_record(g, s, name, is_kernel);
+}
+
+int rs::fork_aux(rs_graph *g, cudaStream_t s) {
+    RS_CUDA_TRY(cudaEventRecord(g->ev_fork, s));
+    for (int i = 0; i < rs_graph::kAux; ++i) {
+        RS_CUDA_TRY(cudaStreamWaitEvent(g->aux[i], g->ev_fork, 0));
+        prof_begin(g, g->aux[i]);
+    }
+    return 0;
+}
+int rs::join_aux(rs_graph *g, cudaStream_t s, int used) {
+    for (int i = 0; i < used; ++i) {
+        RS_CUDA_TRY(cudaEventRecord(g->ev_join[i], g->aux[i]));
+        RS_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_join[i], 0));
+    }
+    prof_begin(g, s);
+    return 0;
 }
 
 extern "C" rs_status rs_profile_enable(rs_graph *g, int enable) {
@@ -164,10 +189,10 @@ extern "C" rs_status rs_profile_read(rs_graph *g, int32_t *n_out, const char **n
             return (rs_status)cuda_fail(e, "rs_profile_read");
     }
     for (size_t i = 1; i < g->prof_used; ++i) {
-        if (!g->prof_name[i]) continue;            // a segment start: nothing ran before it
+        if (!g->prof_name[i] || g->prof_prev[i] < 0) continue;   // a segment start: nothing ran before it
         if (n < cap) {
             float t = 0.0f;
-            cudaEventElapsedTime(&t, g->prof_ev[i - 1], g->prof_ev[i]);
+            cudaEventElapsedTime(&t, g->prof_ev[g->prof_prev[i]], g->prof_ev[i]);
             if (names) names[n] = g->prof_name[i];
             if (ms) ms[n] = t;
             if (is_kernel) is_kernel[n] = g->prof_is_kernel[i];
@@ -481,6 +506,11 @@ static int build_tables(rs_graph *g, cudaStream_t s) {
 
 static int alloc_workspace(rs_graph *g) {
     int64_t n = g->n, nnz = g->nnz;
+    for (int i = 0; i < rs_graph::kAux; ++i) {
+        RS_CUDA_TRY(cudaStreamCreateWithFlags(&g->aux[i], cudaStreamNonBlocking));
+        RS_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_join[i], cudaEventDisableTiming));
+    }
+    RS_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
     RS_CUDA_TRY(dmalloc(&g->rec, n));
     RS_CUDA_TRY(dmalloc(&g->acc, 2 * n));
     RS_CUDA_TRY(dmalloc(&g->wmax_bits, 1));
@@ -513,6 +543,11 @@ static void free_graph(rs_graph *g) {
     for (void *p : ptrs) cudaFree(p);
     free_hub_tables(g);
     for (cudaEvent_t e : g->prof_ev) cudaEventDestroy(e);
+    for (int i = 0; i < rs_graph::kAux; ++i) {
+        if (g->aux[i]) cudaStreamDestroy(g->aux[i]);
+        if (g->ev_join[i]) cudaEventDestroy(g->ev_join[i]);
+    }
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
     delete g;
 }
 

@@ -132,7 +132,14 @@ struct rs_graph {
     std::vector<cudaEvent_t> prof_ev;         // event pool (created on demand)
     std::vector<const char *> prof_name;      // per recorded event: kernel name, or nullptr (segment start)
     std::vector<char> prof_is_kernel;
+    std::vector<int> prof_prev;               // index of the previous event on the same stream
+    std::vector<cudaStream_t> prof_stream;
     size_t prof_used = 0;
+    // auxiliary streams for independent row classes (fork / join by events)
+    static constexpr int kAux = 4;
+    cudaStream_t aux[kAux] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kAux] = {};
 };
 
 namespace rs {
@@ -157,6 +164,9 @@ int inclusive_scan_i64(int64_t *a, int64_t m, int64_t *tmp, cudaStream_t s, int6
 // and, when profiling is on, record an event after it on the stream
 void prof_begin(rs_graph *g, cudaStream_t s);
 void prof_mark(rs_graph *g, cudaStream_t s, const char *name, bool is_kernel);
+// make the auxiliary streams wait for s / make s wait for the first `used` auxiliary streams
+int fork_aux(rs_graph *g, cudaStream_t s);
+int join_aux(rs_graph *g, cudaStream_t s, int used);
 #define RS_LAUNCHED(g, s, name)                        \
     do {                                               \
         RS_CUDA_TRY(cudaGetLastError());               \

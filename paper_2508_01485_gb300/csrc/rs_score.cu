@@ -1365,51 +1365,49 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
                 __syncwarp();
             }
             int32_t W = S.wpre[E];
-            // each lane walks a contiguous range of the group's wedges
-            int32_t per = (W + 31) >> 5;
-            int32_t wv = min(W, lane * per), wend = min(W, wv + per);
-            int32_t e = 0;
-            {
-                int32_t lo = 0, hi = E;                 // last entry with wpre[e] <= wv
-                while (hi - lo > 1) {
-                    int32_t mid = (lo + hi) >> 1;
-                    if (S.wpre[mid] <= wv) lo = mid; else hi = mid;
+            constexpr int U = 4;                       // wedges per lane per trip (loads in flight)
+            for (int32_t w0 = 0; w0 < W; w0 += 32 * U) {
+                int32_t e[U], c[U];
+                int64_t pb[U];
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    int32_t wv = w0 + q * 32 + lane;
+                    e[q] = -1;
+                    if (wv < W) {
+                        int32_t lo = 0, hi = E;             // last entry with wpre[e] <= wv
+                        while (hi - lo > 1) {
+                            int32_t mid = (lo + hi) >> 1;
+                            if (S.wpre[mid] <= wv) lo = mid; else hi = mid;
+                        }
+                        e[q] = lo;
+                        pb[q] = S.boff[lo] + (wv - S.wpre[lo]);
+                    }
                 }
-                e = lo;
-            }
-            int32_t t = wv - S.wpre[e];
-            for (int32_t it = 0; it < per; ++it) {
-                bool act = wv < wend;
-                bool hit = false;
-                int32_t ow = 0, l2 = 0, c = 0;
-                int64_t pb = 0;
-                if (act) {
-                    while (S.wpre[e] + t >= S.wpre[e + 1]) { ++e; t = 0; }   // skip finished / empty entries
-                    pb = S.boff[e] + t;
-                    c = xcol[pb];
-                    ow = S.owner[e];
-                    int32_t s0 = S.seg[ow], s1 = S.seg[ow + 1];
-                    if (s1 - s0 <= 8) {
-                        l2 = s0;
-                        while (l2 < s1 && S.nb[l2] < c) ++l2;
-                    } else {
+#pragma unroll
+                for (int q = 0; q < U; ++q) c[q] = e[q] >= 0 ? xcol[pb[q]] : 0;
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    bool hit = false;
+                    int32_t ow = 0, l2 = 0;
+                    if (e[q] >= 0) {
+                        ow = S.owner[e[q]];
+                        int32_t s0 = S.seg[ow], s1 = S.seg[ow + 1];
                         l2 = s0;
                         int32_t h2 = s1;
                         while (l2 < h2) {
                             int32_t mid = (l2 + h2) >> 1;
-                            if (S.nb[mid] < c) l2 = mid + 1; else h2 = mid;
+                            if (S.nb[mid] < c[q]) l2 = mid + 1; else h2 = mid;
                         }
+                        hit = l2 < s1 && S.nb[l2] == c[q];
                     }
-                    hit = l2 < s1 && S.nb[l2] == c;
+                    unsigned long long p = reserve(hit, tri_n, lane);
+                    if (hit) {
+                        int64_t ba_o = S.aoff[ow];
+                        int32_t s0 = S.seg[ow];
+                        put_triangle(p, (int32_t)(base + ow), S.nb[e[q]], c[q], xS[ba_o + (e[q] - s0)],
+                                     xS[ba_o + (l2 - s0)], xS[pb[q]], tri, tri_cap, xoff, xcol, xS, xin, rec, acc, err);
+                    }
                 }
-                unsigned long long p = reserve(hit, tri_n, lane);
-                if (hit) {
-                    int64_t ba_o = S.aoff[ow];
-                    int32_t s0 = S.seg[ow];
-                    put_triangle(p, (int32_t)(base + ow), S.nb[e], c, xS[ba_o + (e - s0)], xS[ba_o + (l2 - s0)],
-                                 xS[pb], tri, tri_cap, xoff, xcol, xS, xin, rec, acc, err);
-                }
-                if (act) { ++wv; ++t; }
             }
             __syncwarp();
         }
@@ -1493,30 +1491,32 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_CUDA_TRY(cudaFuncSetAttribute(p2_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2_mid_smem));
         attr_done = true;
     }
-    // ---- P1 (largest rows first: their weights seed w_max, so that most
-    //      smaller rows can skip their column maxima)
+    // ---- P1: the larger row classes run concurrently on auxiliary streams and
+    //      seed w_max; then the small rows, most of which skip their column maxima
+    if (int rc = fork_aux(g, s)) return rc;
     if (g->n_hubs) {
-        hub_p1_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, s>>>(
+        hub_p1_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[0]>>>(
             g->off, g->col, g->lab, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->hkey,
             g->hcnt, g->hagg, err);
-        RS_LAUNCHED(g, s, "hub_p1_insert");
-        hub_p1_finish_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, s>>>(
+        RS_LAUNCHED(g, g->aux[0], "hub_p1_insert");
+        hub_p1_finish_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, g->aux[0]>>>(
             g->off, g->lab, g->hubs, g->n_hubs, g->k, g->LG, g->hkey, g->hcnt, g->hagg, g->rec, g->Lall,
             g->wmax_bits);
-        RS_LAUNCHED(g, s, "hub_p1_finish");
+        RS_LAUNCHED(g, g->aux[0], "hub_p1_finish");
     }
     if (g->n_large) {
-        p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, p1_smem, s>>>(
+        p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, p1_smem, g->aux[1]>>>(
             g->off, g->col, g->lab, g->rows_large, g->n_large, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err,
             g->rsum, g->cl_col, g->cl_lab);
-        RS_LAUNCHED(g, s, "p1_large");
+        RS_LAUNCHED(g, g->aux[1], "p1_large");
     }
     if (g->n_mid) {
-        p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, 8), NT, 0, s>>>(
+        p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, 8), NT, 0, g->aux[2]>>>(
             g->off, g->col, g->lab, g->rows_mid, g->n_mid, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err,
             g->rsum, g->cl_col, g->cl_lab);
-        RS_LAUNCHED(g, s, "p1_mid");
+        RS_LAUNCHED(g, g->aux[2], "p1_mid");
     }
+    if (int rc = join_aux(g, s, 3)) return rc;
     if (g->n_small) {
         p1_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, s>>>(
             g->off, g->col, g->lab, g->rows_small, g->n_small, g->k, g->LG, g->rec, g->Lall, g->wmax_bits,
@@ -1530,52 +1530,54 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     if (int rc = inclusive_scan_i64(g->xoff + 1, n, g->scan_tmp, s, &scan_launches)) return rc;
     g->launches += scan_launches - 1;
     prof_mark(g, s, "gx_scan", true);
-    // ---- P2
+    // ---- P2: every row class on its own stream
+    if (int rc = fork_aux(g, s)) return rc;
     if (g->n_small) {
-        p2_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, s>>>(
+        p2_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, g->aux[0]>>>(
             g->off, g->rows_small, g->n_small, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin);
-        RS_LAUNCHED(g, s, "p2_small");
+        RS_LAUNCHED(g, g->aux[0], "p2_small");
     }
     if (g->n_mid) {
-        p2_warp_kernel<<<grid_for(g->n_mid * 32, NT, 8), NT, 0, s>>>(
+        p2_warp_kernel<<<grid_for(g->n_mid * 32, NT, 8), NT, 0, g->aux[1]>>>(
             g->off, g->rows_mid, g->n_mid, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff, g->xcol,
             g->xS, g->xout, g->xin);
-        RS_LAUNCHED(g, s, "p2_warp");
-        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, p2_mid_smem, s>>>(
+        RS_LAUNCHED(g, g->aux[1], "p2_warp");
+        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, p2_mid_smem, g->aux[1]>>>(
             g->off, g->rows_mid, g->n_mid, g->k, 1 << 30, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin, err);
-        RS_LAUNCHED(g, s, "p2_mid");
+        RS_LAUNCHED(g, g->aux[1], "p2_mid");
     }
     if (g->n_large) {
         // large rows whose cross list fits a per-warp table go warp-per-row too
-        p2_warp_kernel<<<grid_for(g->n_large * 32, NT, 8), NT, 0, s>>>(
+        p2_warp_kernel<<<grid_for(g->n_large * 32, NT, 8), NT, 0, g->aux[2]>>>(
             g->off, g->rows_large, g->n_large, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin);
-        RS_LAUNCHED(g, s, "p2_warp");
-        p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, p2_mid_smem, s>>>(
+        RS_LAUNCHED(g, g->aux[2], "p2_warp");
+        p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, p2_mid_smem, g->aux[2]>>>(
             g->off, g->rows_large, g->n_large, g->k, kWarpCap / 2, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab,
             g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
-        RS_LAUNCHED(g, s, "p2_large_warp");
-        p2_large_kernel<kLargeThreads><<<grid_for(g->n_large, 1, 2), kLargeThreads, p2_smem, s>>>(
+        RS_LAUNCHED(g, g->aux[2], "p2_large_warp");
+        p2_large_kernel<kLargeThreads><<<grid_for(g->n_large, 1, 2), kLargeThreads, p2_smem, g->aux[2]>>>(
             g->off, g->rows_large, g->n_large, g->k, kWarpCap / 2 + 1, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
             g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
-        RS_LAUNCHED(g, s, "p2_large");
+        RS_LAUNCHED(g, g->aux[2], "p2_large");
     }
     if (g->n_hubs) {
-        hub_p2_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, s>>>(
+        hub_p2_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
             g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->rec, g->hkey, g->hq,
             g->hitem_out, g->hitem_in, err);
-        RS_LAUNCHED(g, s, "hub_p2_insert");
-        hub_p2_sigma_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, s>>>(
+        RS_LAUNCHED(g, g->aux[3], "hub_p2_insert");
+        hub_p2_sigma_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, g->aux[3]>>>(
             g->hubs, g->n_hubs, g->LG, g->hagg, g->off, g->hkey, g->hcnt, g->hsig, g->hitem_out, g->hitem_in,
             g->xout, g->xin);
-        RS_LAUNCHED(g, s, "hub_p2_sigma");
-        hub_p2_emit_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, s>>>(
+        RS_LAUNCHED(g, g->aux[3], "hub_p2_sigma");
+        hub_p2_emit_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
             g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->rec, g->hkey, g->hcnt,
             g->hq, g->hsig, g->hitem_out, g->hitem_in, g->acc, g->xoff, g->xcol, g->xS, err);
-        RS_LAUNCHED(g, s, "hub_p2_emit");
+        RS_LAUNCHED(g, g->aux[3], "hub_p2_emit");
     }
+    if (int rc = join_aux(g, s, 4)) return rc;
     // ---- P3
     unsigned long long *tri_n = (unsigned long long *)(g->d_flag + 48);
     RS_CUDA_TRY(cudaMemsetAsync(tri_n, 0, sizeof(unsigned long long), s));
