@@ -387,6 +387,11 @@ __global__ void degree_scatter_kernel(const int64_t *off, const int32_t *rows, i
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m) out[atomicAdd(&cursor[off[rows[i] + 1] - off[rows[i]]], 1)] = rows[i];
 }
+__global__ void hub_bounds_kernel(const int64_t *off, const int32_t *hubs, int64_t nh, int64_t *bounds) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nh) { bounds[2 * i] = off[hubs[i]]; bounds[2 * i + 1] = off[hubs[i] + 1]; }
+}
+
 __global__ void scatter_class_kernel(const int64_t *a, int64_t n, int32_t *rows) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
@@ -452,10 +457,28 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
     int nh = hdr[2];
     std::vector<int32_t> hl(nh);
     std::vector<int64_t> offs(2 * (size_t)nh);
-    if (nh) RS_CUDA_TRY(cudaMemcpy(hl.data(), hub_list, nh * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    std::sort(hl.begin(), hl.end());
-    for (int i = 0; i < nh; ++i)
-        RS_CUDA_TRY(cudaMemcpy(&offs[2 * i], g->off + hl[i], 2 * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (nh) {
+        // the hubs' row bounds in one gather and one copy
+        int64_t *d_bounds = g->xoff;   // 2 nh <= n + 1 int64 of scratch
+        hub_bounds_kernel<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(g->off, hub_list, nh, d_bounds);
+        RS_CUDA_TRY(cudaGetLastError());
+        RS_CUDA_TRY(cudaMemcpyAsync(hl.data(), hub_list, nh * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        RS_CUDA_TRY(cudaMemcpyAsync(offs.data(), d_bounds, 2 * nh * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        RS_CUDA_TRY(cudaStreamSynchronize(s));
+        // sort the hubs by row id, keeping their bounds
+        std::vector<int> order(nh);
+        for (int i = 0; i < nh; ++i) order[i] = i;
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return hl[a] < hl[b]; });
+        std::vector<int32_t> hl2(nh);
+        std::vector<int64_t> offs2(2 * (size_t)nh);
+        for (int i = 0; i < nh; ++i) {
+            hl2[i] = hl[order[i]];
+            offs2[2 * i] = offs[2 * order[i]];
+            offs2[2 * i + 1] = offs[2 * order[i] + 1];
+        }
+        hl.swap(hl2);
+        offs.swap(offs2);
+    }
     std::vector<HubInfo> info(nh);
     std::vector<int32_t> items, chunks;
     int64_t slots = 0;
