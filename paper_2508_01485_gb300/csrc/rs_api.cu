@@ -459,12 +459,15 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
     std::vector<int64_t> offs(2 * (size_t)nh);
     if (nh) {
         // the hubs' row bounds in one gather and one copy
-        int64_t *d_bounds = g->xoff;   // 2 nh <= n + 1 int64 of scratch
+        int64_t *d_bounds = nullptr;
+        RS_CUDA_TRY(dmalloc(&d_bounds, 2 * (size_t)nh));
         hub_bounds_kernel<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(g->off, hub_list, nh, d_bounds);
-        RS_CUDA_TRY(cudaGetLastError());
-        RS_CUDA_TRY(cudaMemcpyAsync(hl.data(), hub_list, nh * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        RS_CUDA_TRY(cudaMemcpyAsync(offs.data(), d_bounds, 2 * nh * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        RS_CUDA_TRY(cudaStreamSynchronize(s));
+        cudaError_t e = cudaGetLastError();
+        if (!e) e = cudaMemcpyAsync(hl.data(), hub_list, nh * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaMemcpyAsync(offs.data(), d_bounds, 2 * nh * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        cudaFree(d_bounds);
+        if (e) return cuda_fail(e, "hub bounds");
         // sort the hubs by row id, keeping their bounds
         std::vector<int> order(nh);
         for (int i = 0; i < nh; ++i) order[i] = i;
