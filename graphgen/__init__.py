@@ -135,3 +135,70 @@ def dcsbm_small(n: int, seed: int, dmax: int = 1000, mu: float = 0.2, gamma: flo
     k = max(2, n // 100)
     return dcsbm(n, k, 50.0 if n >= 100 * 50 else 1.0, gamma, dmin, dmax, mu, seed,
                  name="dcsbm-%d" % n)
+
+
+# ---- batches of independent graphs -----------------------------------------
+
+@dataclass
+class Batch:
+    """Independent graphs packed into one CSR (node ids global, labels local)."""
+    graph_node_offsets: np.ndarray  # int64[G+1]
+    graph_k: np.ndarray             # int32[G]
+    offsets: np.ndarray             # int64[N+1]
+    cols: np.ndarray                # int32[nnz]
+    labels: np.ndarray              # int32[N], local to each graph
+    name: str = ""
+
+    @property
+    def n_graphs(self) -> int:
+        return int(self.graph_k.shape[0])
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets.shape[0] - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.cols.shape[0])
+
+    def graph(self, i: int) -> Graph:
+        """Graph i alone (node ids renumbered from 0)."""
+        a, b = int(self.graph_node_offsets[i]), int(self.graph_node_offsets[i + 1])
+        off = self.offsets[a:b + 1] - self.offsets[a]
+        cols = self.cols[self.offsets[a]:self.offsets[b]] - a
+        return Graph(n=b - a, k=int(self.graph_k[i]), offsets=off.astype(np.int64), cols=cols.astype(np.int32),
+                     labels=self.labels[a:b].copy(), name="%s[%d]" % (self.name, i))
+
+
+def pack(graphs, name="batch") -> Batch:
+    """Pack independent graphs into one CSR."""
+    gno = np.zeros(len(graphs) + 1, np.int64)
+    for i, g in enumerate(graphs):
+        gno[i + 1] = gno[i] + g.n
+    off_parts, col_parts, lab_parts, base_e = [np.zeros(1, np.int64)], [], [], 0
+    for i, g in enumerate(graphs):
+        off_parts.append(g.offsets[1:] + base_e)
+        col_parts.append(g.cols.astype(np.int64) + gno[i])
+        lab_parts.append(g.labels)
+        base_e += g.nnz
+    return Batch(graph_node_offsets=gno, graph_k=np.array([g.k for g in graphs], np.int32),
+                 offsets=np.concatenate(off_parts).astype(np.int64),
+                 cols=np.concatenate(col_parts).astype(np.int32) if col_parts else np.zeros(0, np.int32),
+                 labels=np.concatenate(lab_parts).astype(np.int32) if lab_parts else np.zeros(0, np.int32),
+                 name=name)
+
+
+def dcsbm_batch(n_graphs: int, n_min: int, n_max: int, seed: int, dmax: int = 5000) -> Batch:
+    """Batched workload: graph sizes log-uniform on [n_min, n_max], each a DC-SBM shaped like
+    the 1M workload (k = n/100 communities, min size 50 where possible; degrees power law 2.5
+    on [8, dmax]; mixing 0.2).  Graph i uses seed (seed, i)."""
+    import math
+    graphs = []
+    for i in range(n_graphs):
+        r = _load()  # ensure built
+        u = ((i * 0x9E3779B97F4A7C15 + seed * 0xBF58476D1CE4E5B9) % (1 << 64)) / float(1 << 64)
+        n = int(round(math.exp(math.log(n_min) + u * (math.log(n_max) - math.log(n_min)))))
+        k = max(2, n // 100)
+        graphs.append(dcsbm(n, k, 50.0 if n >= 100 * 50 else 1.0, 2.5, 8, min(dmax, n - 1), 0.2,
+                            seed * 1_000_003 + i, name="g%d" % i))
+    return pack(graphs, name="dcsbm-batch-%d" % n_graphs)

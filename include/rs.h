@@ -79,6 +79,33 @@ rs_status rs_build_graph(int64_t n, int64_t nnz, const void *row_offsets, int of
                          int inputs_on_device, uint32_t flags, void *stream, rs_graph **out);
 
 /*
+ * rs_build_batch -- many independent community-labelled graphs packed into one
+ * CSR and scored together: every graph keeps its own labels, its own w_max
+ * and therefore its own scores, exactly as if built alone.
+ *
+ *   n_graphs              >= 1.
+ *   graph_node_offsets    host int64[n_graphs+1]: graph i owns nodes
+ *                         [graph_node_offsets[i], graph_node_offsets[i+1]); starts at 0.
+ *   graph_k               host int32[n_graphs]: communities of each graph (>= 1);
+ *                         their sum must stay below 2^31.
+ *   nnz, row_offsets, offsets_are_i64, cols, inputs_on_device, flags, stream
+ *                         as rs_build_graph, over the packed node ids; every
+ *                         neighbour lies in its row's graph.
+ *   labels                int32[n]: each node's label local to its graph, in [0, k_i).
+ * RS_VALIDATE adds the per-graph checks (neighbours inside the graph, labels
+ * below its k).  rs_score then normalises each node by its own graph's w_max;
+ * rs_get_interaction reports community ids offset by the sum of the k of the
+ * graphs before (graph i's community c is reported as k_0 + .. + k_{i-1} + c).
+ */
+rs_status rs_build_batch(int32_t n_graphs, const int64_t *graph_node_offsets, const int32_t *graph_k, int64_t nnz,
+                         const void *row_offsets, int offsets_are_i64, const int32_t *cols, const int32_t *labels,
+                         int inputs_on_device, uint32_t flags, void *stream, rs_graph **out);
+
+/* rs_batch_omega_max -- w_max of each graph of the last rs_score call, to host
+ * double[n_graphs] (one entry for a single graph).  Synchronises `stream`. */
+rs_status rs_batch_omega_max(rs_graph *g, double *wmax_out, void *stream);
+
+/*
  * rs_score -- Robust Spanning Index of every node (Alg. 1 Steps 1-3, Eq. RSI).
  *
  *   scores          device buffer of n doubles, written with R(u) in node-id

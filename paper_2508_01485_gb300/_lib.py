@@ -57,6 +57,10 @@ def lib():
         L.rs_profile_read.argtypes = [P, ctypes.POINTER(I32), P, P, P, I32]
         L.rs_launch_count.restype = I
         L.rs_launch_count.argtypes = [P, ctypes.POINTER(I64)]
+        L.rs_build_batch.restype = I
+        L.rs_build_batch.argtypes = [I32, P, P, I64, P, I, P, P, I, U32, P, ctypes.POINTER(P)]
+        L.rs_batch_omega_max.restype = I
+        L.rs_batch_omega_max.argtypes = [P, P, P]
         L.rs_free_graph.restype = None
         L.rs_free_graph.argtypes = [P]
         L.rs_last_error.restype = ctypes.c_char_p
@@ -119,6 +123,30 @@ class Graph:
                                     int(k), 1 if on_dev else 0, RS_VALIDATE if validate else 0, s,
                                     ctypes.byref(h)))
         return cls(h, n, k)
+
+    @classmethod
+    def build_batch(cls, graph_node_offsets, graph_k, offsets, cols, labels, validate=True, stream=None):
+        """rs_build_batch from host numpy arrays: graphs packed into one CSR, local labels."""
+        gno = np.ascontiguousarray(graph_node_offsets, dtype=np.int64)
+        gk = np.ascontiguousarray(graph_k, dtype=np.int32)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        col = np.ascontiguousarray(cols, dtype=np.int32)
+        lab = np.ascontiguousarray(labels, dtype=np.int32)
+        n, nnz = off.shape[0] - 1, col.shape[0]
+        h = ctypes.c_void_p()
+        _check(lib().rs_build_batch(gk.shape[0], gno.ctypes.data, gk.ctypes.data, nnz, ctypes.c_void_p(off.ctypes.data), 1,
+                                    ctypes.c_void_p(col.ctypes.data if nnz else None),
+                                    ctypes.c_void_p(lab.ctypes.data if n else None), 0,
+                                    RS_VALIDATE if validate else 0, _stream(stream), ctypes.byref(h)))
+        G = cls(h, n, int(gk.sum()))
+        G.n_graphs = int(gk.shape[0])
+        return G
+
+    def batch_omega_max(self, stream=None):
+        """w_max of every graph of the batch (numpy float64[n_graphs])."""
+        out = np.zeros(getattr(self, "n_graphs", 1), np.float64)
+        _check(lib().rs_batch_omega_max(self._h, out.ctypes.data, _stream(stream)))
+        return out
 
     @classmethod
     def from_generated(cls, g, validate=True, stream=None):

@@ -539,7 +539,8 @@ static int alloc_workspace(rs_graph *g) {
     RS_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
     RS_CUDA_TRY(dmalloc(&g->rec, n));
     RS_CUDA_TRY(dmalloc(&g->acc, 2 * n));
-    RS_CUDA_TRY(dmalloc(&g->wmax_bits, 1));
+    RS_CUDA_TRY(dmalloc(&g->wmax_bits, g->n_graphs));
+    RS_CUDA_TRY(dmalloc(&g->winv, g->n_graphs));
     RS_CUDA_TRY(dmalloc(&g->Lall, n));
     RS_CUDA_TRY(dmalloc(&g->rsum, n));
     RS_CUDA_TRY(dmalloc(&g->cl_col, nnz));
@@ -565,7 +566,8 @@ static void free_graph(rs_graph *g) {
     void *ptrs[] = {g->off, g->off_alt, g->col, g->col_alt, g->lab, g->removed, g->dead,
                     g->rows_small, g->rows_mid, g->rows_large, g->rows_small_deg, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
                     g->Lall, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->scan_tmp, g->tk_hist,
-                    g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->tri, g->rsum, g->cl_col, g->cl_lab};
+                    g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->tri, g->rsum, g->cl_col, g->cl_lab,
+                    g->winv, g->gid, g->gk, g->gnode};
     for (void *p : ptrs) cudaFree(p);
     free_hub_tables(g);
     for (cudaEvent_t e : g->prof_ev) cudaEventDestroy(e);
@@ -592,10 +594,10 @@ static int finish_graph(rs_graph *g, cudaStream_t s) {
     return 0;
 }
 
-extern "C" rs_status rs_build_graph(int64_t n, int64_t nnz, const void *row_offsets, int offsets_are_i64,
-                                    const int32_t *cols, const int32_t *labels, int32_t num_communities,
-                                    int inputs_on_device, uint32_t flags, void *stream, rs_graph **out) {
-    cudaStream_t s = as_stream(stream);
+static rs_status rs_build_graph_impl(int64_t n, int64_t nnz, const void *row_offsets, int offsets_are_i64,
+                                     const int32_t *cols, const int32_t *labels, int32_t num_communities,
+                                     int inputs_on_device, uint32_t flags, cudaStream_t s, rs_graph **out,
+                                     bool finish) {
     if (!out) return (rs_status)fail(RS_EINVAL, "rs_build_graph: out is NULL");
     if (n < 0 || n >= (1LL << 31)) return (rs_status)fail(RS_EINVAL, "rs_build_graph: n must be in [0, 2^31)");
     if (nnz < 0 || nnz >= (1LL << 40)) return (rs_status)fail(RS_EINVAL, "rs_build_graph: nnz must be in [0, 2^40)");
@@ -644,10 +646,145 @@ extern "C" rs_status rs_build_graph(int64_t n, int64_t nnz, const void *row_offs
     if (flags & RS_VALIDATE) {
         if (int rc = validate_graph(g, s)) return bail(rc);
     }
+    if (!finish) {                 // the caller completes the graph (batches)
+        *out = g;
+        return RS_OK;
+    }
     cudaFree(g->d_flag);
     g->d_flag = nullptr;
     if (int rc = finish_graph(g, s)) return bail(rc);
     *out = g;
+    return RS_OK;
+}
+
+extern "C" rs_status rs_build_graph(int64_t n, int64_t nnz, const void *row_offsets, int offsets_are_i64,
+                                    const int32_t *cols, const int32_t *labels, int32_t num_communities,
+                                    int inputs_on_device, uint32_t flags, void *stream, rs_graph **out) {
+    return rs_build_graph_impl(n, nnz, row_offsets, offsets_are_i64, cols, labels, num_communities,
+                               inputs_on_device, flags, as_stream(stream), out, true);
+}
+
+// ---------------------------------------------------------------------------
+// batches of independent graphs packed into one CSR
+// ---------------------------------------------------------------------------
+__global__ void batch_gid_kernel(const int64_t *gnode, int32_t ng, int64_t n, int32_t *gid) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t lo = 0, hi = ng;                    // last graph with gnode[g] <= v
+    while (hi - lo > 1) {
+        int32_t mid = (lo + hi) >> 1;
+        if (gnode[mid] <= v) lo = mid; else hi = mid;
+    }
+    gid[v] = lo;
+}
+
+// every neighbour inside the row's graph, every label inside [0, k of the graph)
+__global__ void batch_validate_kernel(const int64_t *off, const int32_t *col, const int32_t *lab,
+                                      const int32_t *gid, const int64_t *gnode, const int32_t *gk, int64_t n,
+                                      int *flag) {
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = w; v < n; v += nw) {
+        int32_t gi = gid[v];
+        int64_t lo = gnode[gi], hi = gnode[gi + 1];
+        int bad = 0;
+        if (lane == 0 && (lab[v] < 0 || lab[v] >= gk[gi])) bad |= 1;
+        for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32)
+            if (col[e] < lo || col[e] >= hi) bad |= 2;
+        if (bad) atomicOr(flag, bad);
+    }
+}
+
+__global__ void batch_labels_kernel(int32_t *lab, const int32_t *gid, const int64_t *koff, int64_t n) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) lab[v] = (int32_t)(lab[v] + koff[gid[v]]);
+}
+
+extern "C" rs_status rs_build_batch(int32_t n_graphs, const int64_t *graph_node_offsets, const int32_t *graph_k,
+                                    int64_t nnz, const void *row_offsets, int offsets_are_i64, const int32_t *cols,
+                                    const int32_t *labels, int inputs_on_device, uint32_t flags, void *stream,
+                                    rs_graph **out) {
+    cudaStream_t s = as_stream(stream);
+    if (!out || !graph_node_offsets || !graph_k || n_graphs < 1)
+        return (rs_status)fail(RS_EINVAL, "rs_build_batch: bad arguments");
+    if (graph_node_offsets[0] != 0) return (rs_status)fail(RS_EINVAL, "rs_build_batch: graph offsets must start at 0");
+    int64_t ksum = 0;
+    std::vector<int64_t> koff(n_graphs);
+    for (int32_t i = 0; i < n_graphs; ++i) {
+        if (graph_node_offsets[i + 1] < graph_node_offsets[i])
+            return (rs_status)fail(RS_EINVAL, "rs_build_batch: graph offsets decrease");
+        if (graph_k[i] < 1) return (rs_status)fail(RS_EINVAL, "rs_build_batch: every graph needs k >= 1");
+        koff[i] = ksum;
+        ksum += graph_k[i];
+    }
+    if (ksum >= (1LL << 31)) return (rs_status)fail(RS_EINVAL, "rs_build_batch: too many communities in total");
+    int64_t n = graph_node_offsets[n_graphs];
+    // load the packed CSR as one graph; labels are still local to their graph here
+    rs_graph *g = nullptr;
+    int32_t kmax = 1;
+    for (int32_t i = 0; i < n_graphs; ++i) kmax = std::max(kmax, graph_k[i]);
+    rs_status st = rs_build_graph_impl(n, nnz, row_offsets, offsets_are_i64, cols, labels, kmax, inputs_on_device,
+                                       flags & ~RS_VALIDATE, s, &g, /*finish=*/false);
+    if (st != RS_OK) return st;
+    auto bail = [&](int rc) { free_graph(g); return (rs_status)rc; };
+    g->n_graphs = n_graphs;
+    if (cudaError_t e = dmalloc(&g->gid, n)) return bail(cuda_fail(e, "alloc batch"));
+    if (cudaError_t e = dmalloc(&g->gk, n_graphs)) return bail(cuda_fail(e, "alloc batch"));
+    if (cudaError_t e = dmalloc(&g->gnode, n_graphs + 1)) return bail(cuda_fail(e, "alloc batch"));
+    int64_t *d_koff = nullptr;
+    if (cudaError_t e = dmalloc(&d_koff, n_graphs)) return bail(cuda_fail(e, "alloc batch"));
+    cudaError_t e = cudaMemcpyAsync(g->gnode, graph_node_offsets, (n_graphs + 1) * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(g->gk, graph_k, n_graphs * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d_koff, koff.data(), n_graphs * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (!e && n > 0) {
+        batch_gid_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->gnode, n_graphs, n, g->gid);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) { cudaFree(d_koff); return bail(cuda_fail(e, "batch set-up")); }
+    if (flags & RS_VALIDATE) {
+        g->k = (int32_t)std::min<int64_t>(kmax, INT32_MAX);
+        int rc = validate_graph(g, s);
+        int flag = 0;
+        if (!rc) {
+            e = cudaMemsetAsync(g->d_flag, 0, sizeof(int), s);
+            if (!e && n > 0) {
+                batch_validate_kernel<<<grid_for(n * 32, kThreads, 16), kThreads, 0, s>>>(
+                    g->off, g->col, g->lab, g->gid, g->gnode, g->gk, n, g->d_flag);
+                e = cudaGetLastError();
+            }
+            if (!e) rc = read_flag(g, s, &flag); else rc = cuda_fail(e, "batch validation");
+        }
+        if (!rc && (flag & 2)) rc = fail(RS_EINVAL, "invalid batch: an edge leaves its graph");
+        if (!rc && (flag & 1)) rc = fail(RS_EINVAL, "invalid batch: a label outside [0, k of its graph)");
+        if (rc) { cudaFree(d_koff); return bail(rc); }
+    }
+    if (n > 0) {
+        batch_labels_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->lab, g->gid, d_koff, n);
+        e = cudaGetLastError();
+        if (!e) e = cudaStreamSynchronize(s);
+    }
+    cudaFree(d_koff);
+    if (e) return bail(cuda_fail(e, "batch labels"));
+    g->k = (int32_t)ksum;
+    cudaFree(g->d_flag);
+    g->d_flag = nullptr;
+    if (int rc = finish_graph(g, s)) return bail(rc);
+    *out = g;
+    return RS_OK;
+}
+
+extern "C" rs_status rs_batch_omega_max(rs_graph *g, double *wmax_out, void *stream) {
+    if (!g || !wmax_out) return (rs_status)fail(RS_EINVAL, "rs_batch_omega_max: NULL argument");
+    std::vector<unsigned long long> bits(g->n_graphs);
+    cudaStream_t s = as_stream(stream);
+    if (cudaError_t e = cudaMemcpyAsync(bits.data(), g->wmax_bits, g->n_graphs * sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, s))
+        return (rs_status)cuda_fail(e, "read w_max");
+    if (cudaError_t e = cudaStreamSynchronize(s)) return (rs_status)cuda_fail(e, "read w_max");
+    for (int32_t i = 0; i < g->n_graphs; ++i) memcpy(&wmax_out[i], &bits[i], sizeof(double));
     return RS_OK;
 }
 
@@ -684,6 +821,16 @@ extern "C" rs_status rs_clone_graph(const rs_graph *src, rs_graph **out, void *s
     if (!e && n) e = cudaMemcpyAsync(g->lab, src->lab, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
     if (!e && n) e = cudaMemcpyAsync(g->removed, src->removed, 4 * n, cudaMemcpyDeviceToDevice, s);
     if (e) return bail(cuda_fail(e, "copy graph"));
+    g->n_graphs = src->n_graphs;
+    if (src->gid) {
+        if ((e = dmalloc(&g->gid, n))) return bail(cuda_fail(e, "alloc batch"));
+        if ((e = dmalloc(&g->gk, g->n_graphs))) return bail(cuda_fail(e, "alloc batch"));
+        if ((e = dmalloc(&g->gnode, g->n_graphs + 1))) return bail(cuda_fail(e, "alloc batch"));
+        e = cudaMemcpyAsync(g->gid, src->gid, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        if (!e) e = cudaMemcpyAsync(g->gk, src->gk, g->n_graphs * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        if (!e) e = cudaMemcpyAsync(g->gnode, src->gnode, (g->n_graphs + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+        if (e) return bail(cuda_fail(e, "copy batch"));
+    }
     if (int rc = finish_graph(g, s)) return bail(rc);
     *out = g;
     return RS_OK;

@@ -47,6 +47,18 @@ struct __align__(16) HubAgg {
     uint32_t pad[2];
 };
 
+// Graphs of a batch (many independent graphs packed into one CSR): each node's
+// graph, each graph's number of communities and its own w_max slot.  For a
+// single graph gid is null and k / wmax[0] apply to every node.
+struct Batch {
+    const int32_t *gid;
+    const int32_t *gk;
+    int32_t k;
+    unsigned long long *wmax;
+};
+__device__ __forceinline__ int32_t graph_of(const Batch &B, int32_t v) { return B.gid ? B.gid[v] : 0; }
+__device__ __forceinline__ int32_t k_of(const Batch &B, int32_t gi) { return B.gid ? B.gk[gi] : B.k; }
+
 // row aggregates kept from P1 for P2: X = sum_c f_c LG[f_c] (exact) and the
 // number of distinct neighbour communities L
 struct __align__(8) RowSum {
@@ -77,7 +89,12 @@ __device__ __forceinline__ bool rank_after(int32_t dxu, int32_t u, int32_t dxw, 
 
 struct rs_graph {
     int64_t n = 0, nnz = 0;
-    int32_t k = 0, dmax = 0;
+    int32_t k = 0, dmax = 0;               // k: communities (batch: the sum over its graphs)
+    int32_t n_graphs = 1;                  // > 1 for a batch of packed graphs
+    int32_t *gid = nullptr;                // batch: graph of each node
+    int32_t *gk = nullptr;                 // batch: communities of each graph
+    int64_t *gnode = nullptr;              // batch: first node of each graph (n_graphs + 1)
+    double *winv = nullptr;                // 1 / w_max per graph (0 when w_max = 0)
     int device = 0;
     // CSR (int64 offsets) and labels; *_alt are the compaction targets of removals
     int64_t *off = nullptr, *off_alt = nullptr;
@@ -106,7 +123,7 @@ struct rs_graph {
     // scoring workspace
     rs::NodeRec *rec = nullptr;
     unsigned long long *acc = nullptr;        // 2 words per node
-    unsigned long long *wmax_bits = nullptr;  // double bits of w_max
+    unsigned long long *wmax_bits = nullptr;  // double bits of w_max, one per graph
     int32_t *Lall = nullptr;                  // distinct neighbour communities per node
     rs::RowSum *rsum = nullptr;               // per-node aggregates from P1
     int32_t *cl_col = nullptr;                // cross lists: row v's cross neighbours at
@@ -136,7 +153,7 @@ struct rs_graph {
     std::vector<cudaStream_t> prof_stream;
     size_t prof_used = 0;
     // auxiliary streams for independent row classes (fork / join by events)
-    static constexpr int kAux = 4;
+    static constexpr int kAux = 6;
     cudaStream_t aux[kAux] = {};
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kAux] = {};

@@ -180,6 +180,12 @@ __device__ __forceinline__ float current_wmax(const unsigned long long *wmax_bit
     return __double2float_rd(__longlong_as_double((long long)b));
 }
 
+// publish a row's largest weight when it may raise its graph's w_max (wcur is
+// the w_max read earlier, rounded down: any m above w_max has m.hi >= wcur)
+__device__ __forceinline__ void publish_max(const Batch &B, int32_t gi, df m, float wcur) {
+    if (m.hi > 0.0f && m.hi >= wcur) atomicMax(&B.wmax[gi], double_bits(m));
+}
+
 // finishing a row in P1: the row's largest weight, s_v and the node record;
 // w_own is the weight of the row's own community when own > 0 (else ignored)
 __device__ __forceinline__ df p1_row_result(const RowAgg &a, uint32_t own, df col_max, int32_t k,
@@ -231,15 +237,14 @@ struct SmallTile {
 
 __global__ void __launch_bounds__(kThreads) p1_small_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
-    const int32_t *__restrict__ rows, int64_t nrows, int32_t k, const uint64_t *__restrict__ LG,
-    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits,
+    const int32_t *__restrict__ rows, int64_t nrows, Batch B, const uint64_t *__restrict__ LG,
+    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall,
     RowSum *__restrict__ rsum, int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab) {
     __shared__ SmallTile tiles[kThreads / 32];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     SmallTile &T = tiles[wid];
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    df best{0.0f, 0.0f};
     for (int64_t t0 = warp * 32; t0 < nrows; t0 += nwarps * 32) {
         int64_t i = t0 + lane;
         bool have = i < nrows;
@@ -300,10 +305,9 @@ __global__ void __launch_bounds__(kThreads) p1_small_kernel(
             __syncwarp();
         }
         // lane `lane` finishes row `lane` of the tile
-        float wcur = 0.0f;
-        if (lane == 0) wcur = current_wmax(wmax_bits);
-        wcur = __shfl_sync(FULL, wcur, 0);
         if (have) {
+            int32_t gi = graph_of(B, v);
+            float wcur = current_wmax(&B.wmax[gi]);
             uint32_t own = T.own[lane];
             int nf = (int)T.nf[lane];
             // merge a community listed from two chunks
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(kThreads) p1_small_kernel(
             }
             RowAgg a{(uint32_t)d, L, X};
             store_rowsum(rsum, v, a);
-            bool want_max = row_may_raise_max(a.L, fmaxf(wcur, best.hi));
+            bool want_max = row_may_raise_max(a.L, wcur);
             df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
             if (want_max) {
                 while (seen) {
@@ -340,14 +344,13 @@ __global__ void __launch_bounds__(kThreads) p1_small_kernel(
                 wown = column_weight(a, own, LG);
             }
             NodeRec rr;
-            best = df_max(best, p1_row_result(a, own, cm, k, LG, rr, cv, wown, want_max));
+            df m = p1_row_result(a, own, cm, k_of(B, gi), LG, rr, cv, wown, want_max);
+            publish_max(B, gi, m, wcur);
             rec[v] = rr;
             Lall[v] = (int32_t)a.L;
         }
         __syncwarp();
     }
-    best = warp_max_df(best);
-    if (lane == 0 && best.hi > 0.0f) atomicMax(wmax_bits, double_bits(best));
 }
 
 // Mid rows, one warp per row, a per-warp shared-memory table of kWarpCap slots.
@@ -355,8 +358,8 @@ constexpr int kMidWarps = kThreads / 32;
 
 __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
-    const int32_t *__restrict__ rows, int64_t nrows, int32_t k, const uint64_t *__restrict__ LG,
-    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits, int *err,
+    const int32_t *__restrict__ rows, int64_t nrows, Batch B, const uint64_t *__restrict__ LG,
+    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, int *err,
     RowSum *__restrict__ rsum, int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab) {
     __shared__ int32_t skey[kMidWarps][kWarpCap];
     __shared__ uint32_t scnt[kMidWarps][kWarpCap];
@@ -366,12 +369,13 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (uint32_t j = lane; j < kWarpCap; j += 32) { skey[wid][j] = kEmpty; scnt[wid][j] = 0; }
     __syncwarp();
-    df best{0.0f, 0.0f};
+    const int32_t k = B.k;
     for (int64_t i = warp; i < nrows; i += nwarps) {
         int32_t v = rows[i];
         int64_t b = off[v];
         int d = (int)(off[v + 1] - b);
         int32_t cv = lab[v];
+        int32_t gi = graph_of(B, v);
         uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(d, k));
         Tab t{skey[wid], scnt[wid], nullptr, nullptr, cap - 1};
         uint32_t own = 0, nused = 0;
@@ -408,8 +412,9 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
         for (int o = 16; o; o >>= 1) own += __shfl_xor_sync(FULL, own, o);
         RowAgg a{(uint32_t)d, nused + (own > 0 ? 1u : 0u), warp_sum_u128(X) + (u128)own * LG[own]};
         float wcur = 0.0f;
-        if (lane == 0) wcur = fmaxf(current_wmax(wmax_bits), best.hi);
-        bool want_max = __shfl_sync(FULL, (int)row_may_raise_max(a.L, wcur), 0);
+        if (lane == 0) wcur = current_wmax(&B.wmax[gi]);
+        wcur = __shfl_sync(FULL, wcur, 0);
+        bool want_max = row_may_raise_max(a.L, wcur);
         df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
         if (want_max)
             for (uint32_t j = lane; j < nused; j += 32) cm = df_max(cm, column_weight(a, t.cnt[sused[wid][j]], LG));
@@ -417,7 +422,8 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
         cm = warp_max_df(cm);
         if (lane == 0) {
             NodeRec r;
-            best = df_max(best, p1_row_result(a, own, cm, k, LG, r, cv, wown, want_max));
+            df m = p1_row_result(a, own, cm, k_of(B, gi), LG, r, cv, wown, want_max);
+            publish_max(B, gi, m, wcur);
             rec[v] = r;
             Lall[v] = (int32_t)a.L;
             store_rowsum(rsum, v, a);
@@ -426,7 +432,6 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
         for (uint32_t j = lane; j < nused; j += 32) { int sl = sused[wid][j]; t.key[sl] = kEmpty; t.cnt[sl] = 0; }
         __syncwarp();
     }
-    if (lane == 0 && best.hi > 0.0f) atomicMax(wmax_bits, double_bits(best));
 }
 
 // Large rows, one CTA per row, a per-CTA table of up to kMidCap slots
@@ -451,8 +456,8 @@ __device__ __forceinline__ int32_t cta_rank(bool flag, int32_t &base, int32_t *s
 template <int NT>
 __global__ void __launch_bounds__(NT) p1_large_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
-    const int32_t *__restrict__ rows, int64_t nrows, int32_t k, const uint64_t *__restrict__ LG,
-    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits, int *err,
+    const int32_t *__restrict__ rows, int64_t nrows, Batch B, const uint64_t *__restrict__ LG,
+    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, int *err,
     RowSum *__restrict__ rsum, int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t sh_u32[NT / 32];
@@ -460,12 +465,13 @@ __global__ void __launch_bounds__(NT) p1_large_kernel(
     __shared__ df sh_df[NT / 32];
     __shared__ int32_t sh_cnt[NT / 32];
     int tid = threadIdx.x, lane = tid & 31;
-    df best{0.0f, 0.0f};
+    const int32_t k = B.k;
     for (int64_t i = blockIdx.x; i < nrows; i += gridDim.x) {
         int32_t v = rows[i];
         int64_t b = off[v];
         int d = (int)(off[v + 1] - b);
         int32_t cv = lab[v];
+        int32_t gi = graph_of(B, v);
         uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(d, k));
         Tab t{(int32_t *)smem, (uint32_t *)(smem + 4 * cap), nullptr, nullptr, cap - 1};
         for (uint32_t j = tid; j < cap; j += NT) { t.key[j] = kEmpty; t.cnt[j] = 0; }
@@ -495,8 +501,8 @@ __global__ void __launch_bounds__(NT) p1_large_kernel(
         Lf = block_sum_u32<NT>(Lf, sh_u32);
         X = block_sum_u128<NT>(X, sh_u128);
         RowAgg a{(uint32_t)d, Lf + (own > 0 ? 1u : 0u), X + (u128)own * LG[own]};
-        bool want_max = row_may_raise_max(a.L, fmaxf(current_wmax(wmax_bits), 0.0f));
-        want_max = __syncthreads_or(want_max);
+        float wcur = current_wmax(&B.wmax[gi]);
+        bool want_max = __syncthreads_or(row_may_raise_max(a.L, wcur));
         df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
         if (want_max)
             for (uint32_t j = tid; j < cap; j += NT)
@@ -505,15 +511,14 @@ __global__ void __launch_bounds__(NT) p1_large_kernel(
         cm = block_max_df<NT>(cm, sh_df);
         if (tid == 0) {
             NodeRec r;
-            df m = p1_row_result(a, own, cm, k, LG, r, cv, wown, want_max);
+            df m = p1_row_result(a, own, cm, k_of(B, gi), LG, r, cv, wown, want_max);
+            publish_max(B, gi, m, wcur);
             rec[v] = r;
             Lall[v] = (int32_t)a.L;
             store_rowsum(rsum, v, a);
-            best = df_max(best, m);
         }
         __syncthreads();                              // table reuse
     }
-    if (tid == 0 && best.hi > 0.0f) atomicMax(wmax_bits, double_bits(best));
 }
 
 // hub rows: chunks insert foreign communities into the row's global table
@@ -554,15 +559,15 @@ __global__ void __launch_bounds__(NT) hub_p1_insert_kernel(
 template <int NT>
 __global__ void __launch_bounds__(NT) hub_p1_finish_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ lab, const HubInfo *__restrict__ hubs,
-    int64_t nhubs, int32_t k, const uint64_t *__restrict__ LG, const int32_t *hkey, const uint32_t *hcnt,
-    HubAgg *hagg, NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, unsigned long long *wmax_bits) {
+    int64_t nhubs, Batch B, const uint64_t *__restrict__ LG, const int32_t *hkey, const uint32_t *hcnt,
+    HubAgg *hagg, NodeRec *__restrict__ rec, int32_t *__restrict__ Lall) {
     __shared__ uint32_t sh_u32[NT / 32];
     __shared__ u128 sh_u128[NT / 32];
     __shared__ df sh_df[NT / 32];
     int tid = threadIdx.x;
-    df best{0.0f, 0.0f};
     for (int64_t hi = blockIdx.x; hi < nhubs; hi += gridDim.x) {
         HubInfo h = hubs[hi];
+        int32_t gi = graph_of(B, h.row);
         int64_t d = off[h.row + 1] - off[h.row];
         uint32_t own = hagg[hi].own;
         uint32_t Lf = 0;
@@ -588,14 +593,13 @@ __global__ void __launch_bounds__(NT) hub_p1_finish_kernel(
             g.L = a.L;
             hagg[hi] = g;
             NodeRec r;
-            df m = p1_row_result(a, own, cm, k, LG, r, lab[h.row], wown, want_max);
+            df m = p1_row_result(a, own, cm, k_of(B, gi), LG, r, lab[h.row], wown, want_max);
+            publish_max(B, gi, m, current_wmax(&B.wmax[gi]));
             rec[h.row] = r;
             Lall[h.row] = (int32_t)a.L;
-            best = df_max(best, m);
         }
         __syncthreads();
     }
-    if (tid == 0 && best.hi > 0.0f) atomicMax(wmax_bits, double_bits(best));
 }
 
 // ======================================================================================
@@ -1437,22 +1441,24 @@ __global__ void __launch_bounds__(kThreads) p3_terms_kernel(
 // ======================================================================================
 // finalize: R(u) = acc(u) / (w_max d (d - 1))
 // ======================================================================================
+__global__ void graph_scale_kernel(const unsigned long long *__restrict__ wmax_bits, int32_t ng, double *winv) {
+    int32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= ng) return;
+    double wm = __longlong_as_double((long long)wmax_bits[gi]);
+    winv[gi] = wm > 0.0 ? 1.0 / wm : 0.0;
+}
+
 __global__ void __launch_bounds__(kThreads) finalize_kernel(
     int64_t n, const int64_t *__restrict__ off, const unsigned long long *__restrict__ acc,
-    const unsigned long long *__restrict__ wmax_bits, const double *__restrict__ RD, double *scores) {
-    __shared__ double sW;
-    if (threadIdx.x == 0) {
-        double wm = __longlong_as_double((long long)*wmax_bits);
-        sW = wm > 0.0 ? 1.0 / wm : 0.0;
-    }
-    __syncthreads();
-    double W = sW;
+    const int32_t *__restrict__ gid, const double *__restrict__ winv, const double *__restrict__ RD,
+    double *scores) {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
         int64_t d = off[u + 1] - off[u];
         double r = 0.0;
-        if (d >= 2 && W > 0.0) {
+        if (d >= 2) {
+            double W = winv[gid ? gid[u] : 0];
             u128 s = ((u128)acc[2 * u + 1] << 64) | acc[2 * u];
-            if (s) r = u128_to_double(s, -kAccFrac) * W * RD[d];
+            if (s && W > 0.0) r = u128_to_double(s, -kAccFrac) * W * RD[d];
         }
         scores[u] = r;
     }
@@ -1472,7 +1478,8 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     constexpr int NT = kThreads;
     int *err = g->d_flag + 4;
     prof_begin(g, s);
-    RS_CUDA_TRY(cudaMemsetAsync(g->wmax_bits, 0, sizeof(unsigned long long), s));
+    RS_CUDA_TRY(cudaMemsetAsync(g->wmax_bits, 0, g->n_graphs * sizeof(unsigned long long), s));
+    Batch B{g->gid, g->gk, g->k, g->wmax_bits};
     RS_CUDA_TRY(cudaMemsetAsync(g->acc, 0, 2 * n * sizeof(unsigned long long), s));
     RS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
     if (g->n_hubs) {
@@ -1500,26 +1507,25 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->hcnt, g->hagg, err);
         RS_LAUNCHED(g, g->aux[0], "hub_p1_insert");
         hub_p1_finish_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, g->aux[0]>>>(
-            g->off, g->lab, g->hubs, g->n_hubs, g->k, g->LG, g->hkey, g->hcnt, g->hagg, g->rec, g->Lall,
-            g->wmax_bits);
+            g->off, g->lab, g->hubs, g->n_hubs, B, g->LG, g->hkey, g->hcnt, g->hagg, g->rec, g->Lall);
         RS_LAUNCHED(g, g->aux[0], "hub_p1_finish");
     }
     if (g->n_large) {
         p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, p1_smem, g->aux[1]>>>(
-            g->off, g->col, g->lab, g->rows_large, g->n_large, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err,
+            g->off, g->col, g->lab, g->rows_large, g->n_large, B, g->LG, g->rec, g->Lall, err,
             g->rsum, g->cl_col, g->cl_lab);
         RS_LAUNCHED(g, g->aux[1], "p1_large");
     }
     if (g->n_mid) {
         p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, 8), NT, 0, g->aux[2]>>>(
-            g->off, g->col, g->lab, g->rows_mid, g->n_mid, g->k, g->LG, g->rec, g->Lall, g->wmax_bits, err,
+            g->off, g->col, g->lab, g->rows_mid, g->n_mid, B, g->LG, g->rec, g->Lall, err,
             g->rsum, g->cl_col, g->cl_lab);
         RS_LAUNCHED(g, g->aux[2], "p1_mid");
     }
     if (int rc = join_aux(g, s, 3)) return rc;
     if (g->n_small) {
         p1_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, s>>>(
-            g->off, g->col, g->lab, g->rows_small, g->n_small, g->k, g->LG, g->rec, g->Lall, g->wmax_bits,
+            g->off, g->col, g->lab, g->rows_small, g->n_small, B, g->LG, g->rec, g->Lall,
             g->rsum, g->cl_col, g->cl_lab);
         RS_LAUNCHED(g, s, "p1_small");
     }
@@ -1543,10 +1549,10 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->off, g->rows_mid, g->n_mid, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff, g->xcol,
             g->xS, g->xout, g->xin);
         RS_LAUNCHED(g, g->aux[1], "p2_warp");
-        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, p2_mid_smem, g->aux[1]>>>(
+        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, p2_mid_smem, g->aux[5]>>>(
             g->off, g->rows_mid, g->n_mid, g->k, 1 << 30, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin, err);
-        RS_LAUNCHED(g, g->aux[1], "p2_mid");
+        RS_LAUNCHED(g, g->aux[5], "p2_mid");
     }
     if (g->n_large) {
         // large rows whose cross list fits a per-warp table go warp-per-row too
@@ -1558,10 +1564,10 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->off, g->rows_large, g->n_large, g->k, kWarpCap / 2, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab,
             g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
         RS_LAUNCHED(g, g->aux[2], "p2_large_warp");
-        p2_large_kernel<kLargeThreads><<<grid_for(g->n_large, 1, 2), kLargeThreads, p2_smem, g->aux[2]>>>(
+        p2_large_kernel<kLargeThreads><<<grid_for(g->n_large, 1, 2), kLargeThreads, p2_smem, g->aux[4]>>>(
             g->off, g->rows_large, g->n_large, g->k, kWarpCap / 2 + 1, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
             g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
-        RS_LAUNCHED(g, g->aux[2], "p2_large");
+        RS_LAUNCHED(g, g->aux[4], "p2_large");
     }
     if (g->n_hubs) {
         hub_p2_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
@@ -1577,7 +1583,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->hq, g->hsig, g->hitem_out, g->hitem_in, g->acc, g->xoff, g->xcol, g->xS, err);
         RS_LAUNCHED(g, g->aux[3], "hub_p2_emit");
     }
-    if (int rc = join_aux(g, s, 4)) return rc;
+    if (int rc = join_aux(g, s, rs_graph::kAux)) return rc;
     // ---- P3
     unsigned long long *tri_n = (unsigned long long *)(g->d_flag + 48);
     RS_CUDA_TRY(cudaMemsetAsync(tri_n, 0, sizeof(unsigned long long), s));
@@ -1588,7 +1594,9 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
                                                                g->xcol, g->xS, g->xin, g->rec, g->acc, err);
     RS_LAUNCHED(g, s, "p3_terms");
     // ---- finalize
-    finalize_kernel<<<grid_for(n, NT, 8), NT, 0, s>>>(n, g->off, g->acc, g->wmax_bits, g->RD, scores);
+    graph_scale_kernel<<<(g->n_graphs + 255) / 256, 256, 0, s>>>(g->wmax_bits, g->n_graphs, g->winv);
+    RS_LAUNCHED(g, s, "graph_scale");
+    finalize_kernel<<<grid_for(n, NT, 8), NT, 0, s>>>(n, g->off, g->acc, g->gid, g->winv, g->RD, scores);
     RS_LAUNCHED(g, s, "finalize");
     return 0;
 }
