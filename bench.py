@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-json", default="")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch parameters")
+    ap.add_argument("--gen-workers", type=int, default=0, help="processes generating a batch (0: all cores)")
     return ap.parse_args()
 
 
@@ -62,6 +64,114 @@ def workload(name):
     raise SystemExit("unknown workload " + name)
 
 
+# ---- workloads: one resident graph, or many graphs packed into one CSR ------------------
+
+class Single:
+    """One graph: the step is rs_score + rs_topk(1000)."""
+    tune_reps = 5
+
+    def __init__(self, g):
+        self.g = g
+        self.name, self.n, self.k = g.name, g.n, g.k
+        self.st = graph_stats(g)
+        self.m = self.st["m"]
+        self.topk = TOPK
+        self.host = (g.offsets, g.cols, g.labels)
+        self.e2e_step = "rs_build_graph (pinned host CSR, RS_VALIDATE) + rs_score + rs_topk + top-K to host"
+
+    def build(self, rsgpu, arrays=None):
+        off, col, lab = arrays or self.host
+        return rsgpu.Graph.build(off, col, lab, self.k, validate=True)
+
+    def cpu(self, budget):
+        return cpu_oracle_rate(self.g, budget)
+
+    def config(self):
+        return {"workload": self.name, "n": self.n, "m": self.m, "k": self.k, "max_degree": self.st["dmax"],
+                "topk": TOPK, "step": "rs_score + rs_topk on a resident graph"}
+
+
+# independent graphs of the batched workload: node counts log-uniform on [500, 200000],
+# each a DC-SBM shaped like the 1M graph (k = n/100, degrees 2.5 on [8, 5000], mixing 0.2)
+BATCH_N_MIN, BATCH_N_MAX, BATCH_SEED, BATCH_DMAX = 500, 200_000, 4, 5000
+
+
+def _batch_job(job):
+    """Generate one graph of the batch and its row-class statistics (runs in a worker)."""
+    import graphgen
+    member, k_class = job
+    g = graphgen._batch_member(member)
+    return g, graph_stats(g, k_class)
+
+
+class Packed:
+    """Many graphs packed into one CSR: the step is rs_score over all of them at once."""
+    tune_reps = 3
+
+    def __init__(self, n_graphs, workers):
+        import graphgen
+        sizes = graphgen._batch_sizes(n_graphs, BATCH_N_MIN, BATCH_N_MAX, BATCH_SEED)
+        K = sum(max(2, n // 100) for n in sizes)
+        jobs = [((n, BATCH_SEED, i, BATCH_DMAX), K) for i, n in enumerate(sizes)]
+        workers = workers or min(32, os.cpu_count() or 1)
+        if workers > 1 and n_graphs > 1:
+            import concurrent.futures as cf
+            import multiprocessing as mp
+            with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+                res = list(ex.map(_batch_job, jobs, chunksize=max(1, n_graphs // (8 * workers))))
+        else:
+            res = [_batch_job(j) for j in jobs]
+        graphs = [r[0] for r in res]
+        st = {}
+        for _, s in res:
+            for key, v in s.items():
+                st[key] = max(st.get(key, 0), v) if key == "dmax" else st.get(key, 0) + v
+        st["k"] = K
+        self.st = st
+        # the oracle's sample: the smallest and largest graphs and six seeded others
+        import numpy as np
+        rng = np.random.default_rng(BATCH_SEED)
+        pick = {int(np.argmin(sizes)), int(np.argmax(sizes))} | set(int(i) for i in rng.choice(n_graphs, min(6, n_graphs), replace=False))
+        self.sample = [graphs[i] for i in sorted(pick)]
+        del res
+        self.b = graphgen.pack(graphs, name="dcsbm-batch-%d" % n_graphs)
+        del graphs
+        self.name, self.n, self.k, self.m = self.b.name, self.b.n, K, st["m"]
+        self.n_graphs = n_graphs
+        self.topk = 0
+        self.host = (self.b.offsets, self.b.cols, self.b.labels)
+        self.e2e_step = "rs_build_batch (pinned host CSR, RS_VALIDATE) + rs_score + all scores to host"
+
+    def build(self, rsgpu, arrays=None):
+        off, col, lab = arrays or self.host
+        return rsgpu.Graph.build_batch(self.b.graph_node_offsets, self.b.graph_k, off, col, lab, validate=True)
+
+    def cpu(self, budget):
+        m_sum, t_sum, parts = 0, 0.0, []
+        for g in self.sample:
+            r = cpu_oracle_rate(g, budget / len(self.sample))
+            m_sum += g.m
+            t_sum += r["est_full_seconds"]
+            parts.append("%s (n=%d)" % (g.name, g.n))
+        return {"value": m_sum / t_sum, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                "sample": "%d graphs of the batch (%s), each: weight tables for the whole graph + literal R(u) "
+                          "for seeded random nodes, full time extrapolated; value = their edges / their "
+                          "extrapolated time" % (len(self.sample), ", ".join(parts))}
+
+    def config(self):
+        return {"workload": self.name, "graphs": self.n_graphs, "n": self.n, "m": self.m, "k": self.k,
+                "max_degree": self.st["dmax"],
+                "sizes": "log-uniform n on [%d, %d], k = n/100, degrees 2.5 on [8, %d], mixing 0.2"
+                         % (BATCH_N_MIN, BATCH_N_MAX, BATCH_DMAX),
+                "step": "rs_score over the packed batch (per-graph w_max)"}
+
+
+def make_workload(args):
+    if args.workload.startswith("batch-"):
+        return Packed(int(args.workload.split("-")[1]), args.gen_workers)
+    return Single(workload(args.workload))
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -73,11 +183,12 @@ def peaks():
 
 # ---- algorithmic bytes (model stated in the design doc) ---------------------------------
 
-def graph_stats(g):
-    """Per row class (the library's classes: small d <= 32, mid/large by hash-table
-    size 2 min(d, k) <= 512 / 2048, hub above) the rows R, CSR entries E, cross
-    entries X (neighbours of another community) and G_x slots G; and the
-    oriented G_x out-slots O."""
+def graph_stats(g, k_class=None):
+    """Per row class (the library's default classes: small d <= 32, mid/large by
+    hash-table size 2 min(d, k) <= 512 / 2048, hub above) the rows R, CSR entries
+    E, cross entries X (neighbours of another community) and G_x slots G; and the
+    oriented G_x out-slots O.  k_class replaces g.k in the class rule (a packed
+    batch sizes tables by its total number of communities)."""
     import numpy as np
     deg = np.diff(g.offsets)
     n, E = g.n, g.nnz
@@ -88,7 +199,7 @@ def graph_stats(g):
     keep = cross & (dx[rows] >= 2) & (dx[g.cols] >= 2)
     a, b = rows[keep], g.cols[keep].astype(np.int64)
     out = (dx[b] > dx[a]) | ((dx[b] == dx[a]) & (b > a))
-    m = np.minimum(deg, g.k)
+    m = np.minimum(deg, k_class or g.k)
     cap = np.where(m > 0, 2 ** np.ceil(np.log2(np.maximum(2 * m, 1))), 1)
     cls = np.where(deg <= 32, 0, np.where(cap <= 512, 1, np.where(cap <= 2048, 2, 3)))
     st = {"n": n, "E": E, "m": E // 2, "k": g.k, "dmax": int(deg.max()) if n else 0,
@@ -129,8 +240,12 @@ def kernel_bytes(name, st):
         "p1_small": lambda: p1("small"), "p1_mid": lambda: p1("mid"), "p1_large": lambda: p1("large"),
         "p2_small": lambda: p2("small"), "p2_warp": lambda: p2("mid_w") + p2("large_w"),
         "p2_mid": lambda: p2("mid_t"), "p2_large_warp": lambda: p2("large_t"), "p2_large": lambda: p2("large_c"),
-        # out-lists and the out/in counts and offsets of every node
-        "p3_list": lambda: 4 * st["out_slots"] + (4 + 8) * n,
+        # out-lists (ids, forward and reverse values are read only for triangles), out counts,
+        # offsets and ranks of every node
+        "p3_list": lambda: 4 * st["out_slots"] + (4 + 8 + 4) * n,
+        # every in-slot (id, value) read once, its out-slot's reverse value written once;
+        # in counts, offsets and ranks of every node
+        "gx_mirror": lambda: (4 + 8 + 8) * st["out_slots"] + (4 + 8 + 4) * n,
         "finalize": lambda: (8 + 16 + 8) * n,
         "tk_select": lambda: 8 * n,
         "gx_capacity": lambda: 16 * n + 8 * n,
@@ -248,23 +363,29 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    W = make_workload(args)              # host-side generation before the first CUDA call
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    g = workload(args.workload)
-    st = graph_stats(g)
-    G = rsgpu.Graph.from_generated(g, validate=True)
-    stream = torch.cuda.current_stream()
-    scores = torch.empty(g.n, dtype=torch.float64, device=dev)
-    ids = torch.empty(TOPK, dtype=torch.int32, device=dev)
-    vals = torch.empty(TOPK, dtype=torch.float64, device=dev)
+    st = W.st
+    G = W.build(rsgpu)
+    scores = torch.empty(max(W.n, 1), dtype=torch.float64, device=dev)
+    kk = W.topk
+    ids = torch.empty(max(kk, 1), dtype=torch.int32, device=dev)
+    vals = torch.empty(max(kk, 1), dtype=torch.float64, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step():
         G.score_into(scores)
-        G.topk_into(scores, TOPK, ids, vals)
+        if kk:
+            G.topk_into(scores, kk, ids, vals)
+
+    tuning, autotune = G.tuning(), None
+    if not args.no_autotune:
+        tuning, best_ms, tried = G.autotune(topk=kk, reps=W.tune_reps)
+        autotune = {"candidates": tried, "best_step_ms": best_ms, "reps": W.tune_reps}
 
     for i in range(args.warmup):
         flush.fill_(i & 0xFF)
@@ -281,9 +402,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     for i in range(args.steps):
         flush.fill_((i + 7) & 0xFF)
-        ev[i][0].record(stream)
+        ev[i][0].record()
         step()
-        ev[i][1].record(stream)
+        ev[i][1].record()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -327,22 +448,46 @@ def run_ours(args):
         "step_bytes": step_bytes(st),
     }
 
+    # the same step captured once as a CUDA graph and replayed (rs_step_capture / rs_step_launch)
+    graph_replay = None
+    try:
+        cap = G.capture_step(scores, kk, ids if kk else None, vals if kk else None)
+        for i in range(2):
+            flush.fill_(i & 0xFF)
+            cap.launch()
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_((i + 3) & 0xFF)
+            gev[i][0].record()
+            cap.launch()
+            gev[i][1].record()
+        torch.cuda.synchronize()
+        g_ms = [a.elapsed_time(b) for a, b in gev]
+        g_value, g_total = aggregate(sum(g_ms), st["m"] * args.steps, world, dev)
+        graph_replay = {"value": g_value, "ms_per_step": g_total / args.steps}
+        cap.close()
+    except rsgpu.RSError as e:
+        graph_replay = {"error": str(e)}
+
     # end to end through the C ABI from pinned host buffers
-    pin_off = torch.from_numpy(g.offsets).pin_memory().numpy()
-    pin_col = torch.from_numpy(g.cols).pin_memory().numpy()
-    pin_lab = torch.from_numpy(g.labels).pin_memory().numpy()
-    host_ids = torch.empty(TOPK, dtype=torch.int32).pin_memory()
-    host_vals = torch.empty(TOPK, dtype=torch.float64).pin_memory()
+    pinned = tuple(torch.from_numpy(a).pin_memory().numpy() for a in W.host)
+    d2h = torch.empty(max(kk, 1), dtype=torch.int32).pin_memory(), torch.empty(max(kk, 1), dtype=torch.float64).pin_memory()
+    if not kk:
+        d2h = (torch.empty(max(W.n, 1), dtype=torch.float64).pin_memory(),)
     e2e_ms = []
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        G2 = rsgpu.Graph.build(pin_off, pin_col, pin_lab, g.k, validate=True)
+        G2 = W.build(rsgpu, pinned)
         G2.score_into(scores)
-        G2.topk_into(scores, TOPK, ids, vals)
-        host_ids.copy_(ids, non_blocking=True)
-        host_vals.copy_(vals, non_blocking=True)
+        if kk:
+            G2.topk_into(scores, kk, ids, vals)
+            d2h[0].copy_(ids, non_blocking=True)
+            d2h[1].copy_(vals, non_blocking=True)
+        else:
+            d2h[0].copy_(scores, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         G2.close()
@@ -351,26 +496,28 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_oracle_rate(g, args.cpu_seconds)
+        cpu = W.cpu(args.cpu_seconds)
         cpu.pop("est_full_seconds", None)
 
+    config = W.config()
+    config.update({"l2": "flushed between timed steps (512 MB write outside the events)",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "tuning": tuning, "autotune": autotune})
     out = {
         "metric": "RS-scored edges/s", "value": value, "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "arith": "int128 fixed-point sums + double-float (2 x f32) products; fp64 outputs",
         "data": "synthetic",
-        "config": {"workload": g.name, "n": g.n, "m": st["m"], "k": g.k, "max_degree": st["dmax"],
-                   "topk": TOPK, "step": "rs_score + rs_topk on a resident graph",
-                   "l2": "flushed between timed steps (512 MB write outside the events)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": config,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "edges/s",
-                "h2d_bytes_per_step": int(g.offsets.nbytes + g.cols.nbytes + g.labels.nbytes),
-                "d2h_bytes_per_step": int(host_ids.numel() * 4 + host_vals.numel() * 8),
+                "h2d_bytes_per_step": int(sum(a.nbytes for a in W.host)),
+                "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in d2h)),
                 "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None,
-                "step": "rs_build_graph (pinned host CSR, RS_VALIDATE) + rs_score + rs_topk + top-K to host"},
+                "step": W.e2e_step},
+        "graph_replay": graph_replay,
         "gpu_launches": launches,
         "clocks": clk,
     }

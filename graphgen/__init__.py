@@ -171,34 +171,57 @@ class Batch:
 
 
 def pack(graphs, name="batch") -> Batch:
-    """Pack independent graphs into one CSR."""
-    gno = np.zeros(len(graphs) + 1, np.int64)
+    """Pack independent graphs into one CSR (arrays filled in place, no int64 copies of the columns)."""
+    G = len(graphs)
+    gno = np.zeros(G + 1, np.int64)
     for i, g in enumerate(graphs):
         gno[i + 1] = gno[i] + g.n
-    off_parts, col_parts, lab_parts, base_e = [np.zeros(1, np.int64)], [], [], 0
+    nnz = int(sum(g.nnz for g in graphs))
+    N = int(gno[-1])
+    offsets = np.zeros(N + 1, np.int64)
+    cols = np.empty(nnz, np.int32)
+    labels = np.empty(N, np.int32)
+    base_e = 0
     for i, g in enumerate(graphs):
-        off_parts.append(g.offsets[1:] + base_e)
-        col_parts.append(g.cols.astype(np.int64) + gno[i])
-        lab_parts.append(g.labels)
+        a, b = int(gno[i]), int(gno[i + 1])
+        offsets[a + 1:b + 1] = g.offsets[1:] + base_e
+        np.add(g.cols, np.int32(a), out=cols[base_e:base_e + g.nnz], dtype=np.int32)
+        labels[a:b] = g.labels
         base_e += g.nnz
     return Batch(graph_node_offsets=gno, graph_k=np.array([g.k for g in graphs], np.int32),
-                 offsets=np.concatenate(off_parts).astype(np.int64),
-                 cols=np.concatenate(col_parts).astype(np.int32) if col_parts else np.zeros(0, np.int32),
-                 labels=np.concatenate(lab_parts).astype(np.int32) if lab_parts else np.zeros(0, np.int32),
-                 name=name)
+                 offsets=offsets, cols=cols, labels=labels, name=name)
 
 
-def dcsbm_batch(n_graphs: int, n_min: int, n_max: int, seed: int, dmax: int = 5000) -> Batch:
+def _batch_sizes(n_graphs: int, n_min: int, n_max: int, seed: int):
+    """Graph i's node count, log-uniform on [n_min, n_max] from a hash of (seed, i)."""
+    import math
+    out = []
+    for i in range(n_graphs):
+        u = ((i * 0x9E3779B97F4A7C15 + seed * 0xBF58476D1CE4E5B9) % (1 << 64)) / float(1 << 64)
+        out.append(int(round(math.exp(math.log(n_min) + u * (math.log(n_max) - math.log(n_min))))))
+    return out
+
+
+def _batch_member(args):
+    n, seed, i, dmax = args
+    k = max(2, n // 100)
+    return dcsbm(n, k, 50.0 if n >= 100 * 50 else 1.0, 2.5, 8, min(dmax, n - 1), 0.2,
+                 seed * 1_000_003 + i, name="g%d" % i)
+
+
+def dcsbm_batch(n_graphs: int, n_min: int, n_max: int, seed: int, dmax: int = 5000, workers: int = 0) -> Batch:
     """Batched workload: graph sizes log-uniform on [n_min, n_max], each a DC-SBM shaped like
     the 1M workload (k = n/100 communities, min size 50 where possible; degrees power law 2.5
-    on [8, dmax]; mixing 0.2).  Graph i uses seed (seed, i)."""
-    import math
-    graphs = []
-    for i in range(n_graphs):
-        r = _load()  # ensure built
-        u = ((i * 0x9E3779B97F4A7C15 + seed * 0xBF58476D1CE4E5B9) % (1 << 64)) / float(1 << 64)
-        n = int(round(math.exp(math.log(n_min) + u * (math.log(n_max) - math.log(n_min)))))
-        k = max(2, n // 100)
-        graphs.append(dcsbm(n, k, 50.0 if n >= 100 * 50 else 1.0, 2.5, 8, min(dmax, n - 1), 0.2,
-                            seed * 1_000_003 + i, name="g%d" % i))
+    on [8, dmax]; mixing 0.2).  Graph i uses seed (seed, i), so the batch does not depend on
+    `workers` (> 1: generated by that many spawned processes)."""
+    _load()
+    jobs = [(n, seed, i, dmax) for i, n in enumerate(_batch_sizes(n_graphs, n_min, n_max, seed))]
+    if workers and workers > 1 and n_graphs > 1:
+        # spawned (not forked) workers; a worker that dies raises instead of being replaced
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            graphs = list(ex.map(_batch_member, jobs, chunksize=max(1, n_graphs // (8 * workers))))
+    else:
+        graphs = [_batch_member(j) for j in jobs]
     return pack(graphs, name="dcsbm-batch-%d" % n_graphs)

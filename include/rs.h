@@ -208,6 +208,81 @@ rs_status rs_profile_read(rs_graph *g, int32_t *n_out, const char **names, float
                           int32_t cap);
 rs_status rs_launch_count(const rs_graph *g, int64_t *launches);
 
+/*
+ * Launch parameters of the scoring kernels.  None of them changes a result:
+ * every sum is accumulated in exact fixed point, so scores are bit-identical
+ * under any valid setting (the paper has no counterpart; its kernels use
+ * fixed launch shapes, Sec. V).  Rows are split by degree d and by the hash
+ * capacity cap = smallest power of two >= 2 min(d, k):
+ *   small_max    rows with d <= small_max take the 32-row tile kernels    [1, 32]
+ *   warp_cap     other rows with cap <= warp_cap take one warp each       {64,...,512}
+ *   cta_cap      then rows with cap <= cta_cap take one CTA each;         {warp_cap,...,2048}
+ *                larger rows are hubs (global table, split into chunks)
+ *   hub_chunk    neighbours per hub work item                             {512,...,65536}
+ *   p2_cta_dx    CTA rows with more cross neighbours than this take a     [32, 256]
+ *                CTA in the second pass (else one warp)
+ *   p1_cta_threads  threads per CTA row in the first pass                 {128, 256, 512}
+ *   p2_cta_threads  threads per CTA row in the second pass                {256, 512, 1024}
+ *   ctas_per_sm  grid size of the grid-stride kernels, in CTAs per SM     [1, 32]
+ * Powers of two are required where a set is given.
+ */
+typedef struct {
+    int32_t small_max;
+    int32_t warp_cap;
+    int32_t cta_cap;
+    int32_t hub_chunk;
+    int32_t p2_cta_dx;
+    int32_t p1_cta_threads;
+    int32_t p2_cta_threads;
+    int32_t ctas_per_sm;
+} rs_tuning;
+
+/* rs_default_tuning -- the parameters a new graph starts with. */
+void rs_default_tuning(rs_tuning *out);
+/* rs_get_tuning -- the parameters g uses now. */
+rs_status rs_get_tuning(const rs_graph *g, rs_tuning *out);
+/*
+ * rs_set_tuning -- validate t (RS_EINVAL, g unchanged, if a field is outside
+ *   its range) and re-split g's rows by it.  Synchronises `stream`.
+ */
+rs_status rs_set_tuning(rs_graph *g, const rs_tuning *t, void *stream);
+/*
+ * rs_autotune -- time one scoring step (rs_score, plus rs_topk(topk_k) when
+ *   topk_k > 0) under a coordinate sweep of the parameters above, starting
+ *   from the current ones, and leave g on the fastest.  Each candidate is
+ *   timed as the median of `reps` steps (>= 1) with CUDA events on `stream`
+ *   after one untimed step.  `scores` (device, n doubles), `ids_out` and
+ *   `vals_out` (device, topk_k each; may be NULL when topk_k == 0) are
+ *   scratch.  best_out / best_ms_out (host, nullable) receive the choice and
+ *   its median step time; n_tried_out (nullable) the candidates timed.
+ */
+rs_status rs_autotune(rs_graph *g, double *scores, int32_t topk_k, int32_t *ids_out, double *vals_out,
+                      int32_t reps, void *stream, rs_tuning *best_out, float *best_ms_out,
+                      int32_t *n_tried_out);
+
+/*
+ * A captured scoring step: rs_score(g, scores) followed, when topk_k > 0, by
+ * rs_topk(g, scores, topk_k, ids_out, vals_out), recorded once as a CUDA graph
+ * and replayed by rs_step_launch on any stream with one launch call.  The
+ * graph holds g's current buffers and launch parameters: a later
+ * rs_apply_removals or rs_set_tuning on g invalidates it (rs_step_launch then
+ * returns RS_EINVAL).  Profiling must be off while capturing.
+ */
+typedef struct rs_step rs_step;
+rs_status rs_step_capture(rs_graph *g, double *scores, int32_t topk_k, int32_t *ids_out, double *vals_out,
+                          rs_step **out);
+rs_status rs_step_launch(rs_step *st, void *stream);
+void rs_step_free(rs_step *st);
+
+/*
+ * rs_device_errors -- synchronise `stream` and return in *flags_out the
+ *   internal consistency checks that failed in g's kernels during the last
+ *   rs_score (bit flags; 0 when none).  A non-zero value means a library bug
+ *   (a hash table found full, a G_x slot not found), not bad input: inputs are
+ *   checked before any kernel runs.
+ */
+rs_status rs_device_errors(rs_graph *g, int32_t *flags_out, void *stream);
+
 /* rs_free_graph -- release a graph and its device memory (NULL is a no-op). */
 void rs_free_graph(rs_graph *g);
 

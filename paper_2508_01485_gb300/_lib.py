@@ -19,6 +19,23 @@ RS_VALIDATE = 1
 
 _lib = None
 
+TUNING_FIELDS = ("small_max", "warp_cap", "cta_cap", "hub_chunk", "p2_cta_dx", "p1_cta_threads",
+                 "p2_cta_threads", "ctas_per_sm")
+
+
+class Tuning(ctypes.Structure):
+    """rs_tuning: the scoring kernels' launch parameters (no effect on results)."""
+    _fields_ = [(f, ctypes.c_int32) for f in TUNING_FIELDS]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f in TUNING_FIELDS}
+
+
+def default_tuning():
+    t = Tuning()
+    lib().rs_default_tuning(ctypes.byref(t))
+    return t.as_dict()
+
 
 class RSError(RuntimeError):
     def __init__(self, status, msg):
@@ -61,6 +78,23 @@ def lib():
         L.rs_build_batch.argtypes = [I32, P, P, I64, P, I, P, P, I, U32, P, ctypes.POINTER(P)]
         L.rs_batch_omega_max.restype = I
         L.rs_batch_omega_max.argtypes = [P, P, P]
+        L.rs_default_tuning.restype = None
+        L.rs_default_tuning.argtypes = [ctypes.POINTER(Tuning)]
+        L.rs_get_tuning.restype = I
+        L.rs_get_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
+        L.rs_set_tuning.restype = I
+        L.rs_set_tuning.argtypes = [P, ctypes.POINTER(Tuning), P]
+        L.rs_autotune.restype = I
+        L.rs_autotune.argtypes = [P, P, I32, P, P, I32, P, ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_float),
+                                  ctypes.POINTER(I32)]
+        L.rs_step_capture.restype = I
+        L.rs_step_capture.argtypes = [P, P, I32, P, P, ctypes.POINTER(P)]
+        L.rs_step_launch.restype = I
+        L.rs_step_launch.argtypes = [P, P]
+        L.rs_step_free.restype = None
+        L.rs_step_free.argtypes = [P]
+        L.rs_device_errors.restype = I
+        L.rs_device_errors.argtypes = [P, ctypes.POINTER(I32), P]
         L.rs_free_graph.restype = None
         L.rs_free_graph.argtypes = [P]
         L.rs_last_error.restype = ctypes.c_char_p
@@ -234,6 +268,12 @@ class Graph:
         _check(lib().rs_profile_read(self._h, ctypes.byref(n), names, ms, isk, cap))
         return [(names[i].decode(), float(ms[i]), bool(isk[i])) for i in range(min(cap, n.value))]
 
+    def device_errors(self, stream=None):
+        """Internal consistency flags raised by the kernels of the last rs_score (0: none)."""
+        f = ctypes.c_int32(0)
+        _check(lib().rs_device_errors(self._h, ctypes.byref(f), _stream(stream)))
+        return f.value
+
     def launch_count(self):
         c = ctypes.c_int64(0)
         _check(lib().rs_launch_count(self._h, ctypes.byref(c)))
@@ -243,3 +283,64 @@ class Graph:
         h = ctypes.c_void_p()
         _check(lib().rs_clone_graph(self._h, ctypes.byref(h), _stream(stream)))
         return Graph(h, self.n, self.k)
+
+    # ---- launch parameters, autotuner, captured steps ---------------------------------
+
+    def tuning(self):
+        t = Tuning()
+        _check(lib().rs_get_tuning(self._h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, stream=None, **fields):
+        """rs_set_tuning with the current parameters updated by ``fields``."""
+        cur = self.tuning()
+        for k in fields:
+            if k not in cur:
+                raise KeyError(k)
+        cur.update(fields)
+        t = Tuning(**cur)
+        _check(lib().rs_set_tuning(self._h, ctypes.byref(t), _stream(stream)))
+
+    def autotune(self, topk=0, reps=5, stream=None):
+        """rs_autotune: returns (chosen parameters, median step ms, candidates timed)."""
+        import torch
+        scores = torch.empty(max(self.n, 1), dtype=torch.float64, device="cuda")
+        ids = torch.empty(max(topk, 1), dtype=torch.int32, device="cuda")
+        vals = torch.empty(max(topk, 1), dtype=torch.float64, device="cuda")
+        best = Tuning()
+        ms = ctypes.c_float(0.0)
+        tried = ctypes.c_int32(0)
+        _check(lib().rs_autotune(self._h, _ptr(scores), int(topk), _ptr(ids), _ptr(vals), int(reps), _stream(stream),
+                                 ctypes.byref(best), ctypes.byref(ms), ctypes.byref(tried)))
+        return best.as_dict(), float(ms.value), int(tried.value)
+
+    def capture_step(self, scores, k=0, ids=None, vals=None):
+        """rs_step_capture: a CUDA graph of rs_score(scores) [+ rs_topk(k) into ids / vals]."""
+        h = ctypes.c_void_p()
+        _check(lib().rs_step_capture(self._h, _ptr(scores), int(k), _ptr(ids), _ptr(vals), ctypes.byref(h)))
+        return Step(h, self, (scores, ids, vals))
+
+
+class Step:
+    """A captured scoring step (owns an rs_step); keeps its graph and buffers alive."""
+
+    def __init__(self, handle, graph, buffers):
+        self._h = handle
+        self._graph = graph
+        self._buffers = buffers
+
+    def launch(self, stream=None):
+        if self._h is None or self._graph._h is None:
+            raise RSError(RS_EINVAL, "step or its graph is closed")
+        _check(lib().rs_step_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().rs_step_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -344,21 +344,25 @@ __device__ __forceinline__ uint32_t row_cap(int64_t d, int32_t k) {
     while ((int64_t)cap < 2 * m) cap <<= 1;
     return cap;
 }
-// 0 small, 1 mid (warp), 2 large (CTA), 3 hub
-__device__ __forceinline__ int row_class(int64_t d, int32_t k) {
-    if (d <= kSmallMax) return 0;
+// 0 small, 1 mid (warp), 2 large (CTA), 3 hub, by the split points of rs_tuning
+struct ClassSplit { int32_t small_max, warp_cap, cta_cap; };
+__device__ __forceinline__ int row_class(int64_t d, int32_t k, const ClassSplit &cs) {
+    if (d <= cs.small_max) return 0;
     uint32_t cap = row_cap(d, k);
-    if (cap <= (uint32_t)kWarpCap) return 1;
-    return cap <= (uint32_t)kMidCap ? 2 : 3;
+    if (cap <= (uint32_t)cs.warp_cap) return 1;
+    return cap <= (uint32_t)cs.cta_cap ? 2 : 3;
 }
 
 // flags for one class into a[v], plus dmax / large cap / hub list on the first pass
-__global__ void classify_kernel(const int64_t *off, int64_t n, int32_t k, int cls, int64_t *a,
-                                int *dmax, int *largecap, int32_t *hub_list, int *n_hub) {
+// (a batch bounds each row's table by the communities of the row's own graph)
+__global__ void classify_kernel(const int64_t *off, int64_t n, int32_t k, const int32_t *gid, const int32_t *gk,
+                                ClassSplit cs, int cls, int64_t *a, int *dmax, int *largecap, int32_t *hub_list,
+                                int *n_hub) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     int64_t d = off[v + 1] - off[v];
-    int c = row_class(d, k);
+    if (gid) k = gk[gid[v]];
+    int c = row_class(d, k, cs);
     a[v] = (c == cls) ? 1 : 0;
     if (cls == 0) {
         atomicMax(dmax, (int)d);
@@ -387,9 +391,16 @@ __global__ void degree_scatter_kernel(const int64_t *off, const int32_t *rows, i
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m) out[atomicAdd(&cursor[off[rows[i] + 1] - off[rows[i]]], 1)] = rows[i];
 }
-__global__ void hub_bounds_kernel(const int64_t *off, const int32_t *hubs, int64_t nh, int64_t *bounds) {
+// per hub: row bounds and the communities of its graph
+__global__ void hub_bounds_kernel(const int64_t *off, const int32_t *hubs, int64_t nh, int32_t k, const int32_t *gid,
+                                  const int32_t *gk, int64_t *bounds) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nh) { bounds[2 * i] = off[hubs[i]]; bounds[2 * i + 1] = off[hubs[i] + 1]; }
+    if (i < nh) {
+        int32_t h = hubs[i];
+        bounds[3 * i] = off[h];
+        bounds[3 * i + 1] = off[h + 1];
+        bounds[3 * i + 2] = gid ? gk[gid[h]] : k;
+    }
 }
 
 __global__ void scatter_class_kernel(const int64_t *a, int64_t n, int32_t *rows) {
@@ -417,6 +428,8 @@ static cudaError_t dmalloc(T **p, size_t count) {
 // builds rows_small / rows_mid / rows_large / hub tables from the current offsets; syncs
 static int classify_rows(rs_graph *g, cudaStream_t s) {
     int64_t n = g->n;
+    g->version++;                  // row lists and hub tables are rebuilt: captured steps are stale
+    const ClassSplit cs{g->tune.small_max, g->tune.warp_cap, g->tune.cta_cap};
     int hdr[4] = {0, 0, 0, 0};   // dmax, large cap, n_hub, unused
     int *d_hdr = g->d_flag;      // d_flag has room for 4 ints
     RS_CUDA_TRY(cudaMemsetAsync(d_hdr, 0, 4 * sizeof(int), s));
@@ -427,7 +440,8 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
     int64_t counts[3] = {0, 0, 0};
     for (int cls = 0; cls < 3; ++cls) {
         if (n > 0) {
-            classify_kernel<<<blocks, 256, 0, s>>>(g->off, n, g->k, cls, a, d_hdr, d_hdr + 1, hub_list, d_hdr + 2);
+            classify_kernel<<<blocks, 256, 0, s>>>(g->off, n, g->k, g->gid, g->gk, cs, cls, a, d_hdr, d_hdr + 1,
+                                                   hub_list, d_hdr + 2);
             RS_CUDA_TRY(cudaGetLastError());
             if (int rc = inclusive_scan_i64(a, n, g->scan_tmp, s)) return rc;
             scatter_class_kernel<<<blocks, 256, 0, s>>>(a, n, lists[cls]);
@@ -456,15 +470,16 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
     // hubs: host-side work list (hubs are few)
     int nh = hdr[2];
     std::vector<int32_t> hl(nh);
-    std::vector<int64_t> offs(2 * (size_t)nh);
+    std::vector<int64_t> offs(3 * (size_t)nh);
     if (nh) {
-        // the hubs' row bounds in one gather and one copy
+        // the hubs' row bounds and graph sizes in one gather and one copy
         int64_t *d_bounds = nullptr;
-        RS_CUDA_TRY(dmalloc(&d_bounds, 2 * (size_t)nh));
-        hub_bounds_kernel<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(g->off, hub_list, nh, d_bounds);
+        RS_CUDA_TRY(dmalloc(&d_bounds, 3 * (size_t)nh));
+        hub_bounds_kernel<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(g->off, hub_list, nh, g->k, g->gid, g->gk,
+                                                                     d_bounds);
         cudaError_t e = cudaGetLastError();
         if (!e) e = cudaMemcpyAsync(hl.data(), hub_list, nh * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-        if (!e) e = cudaMemcpyAsync(offs.data(), d_bounds, 2 * nh * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaMemcpyAsync(offs.data(), d_bounds, 3 * nh * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
         if (!e) e = cudaStreamSynchronize(s);
         cudaFree(d_bounds);
         if (e) return cuda_fail(e, "hub bounds");
@@ -473,11 +488,10 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
         for (int i = 0; i < nh; ++i) order[i] = i;
         std::sort(order.begin(), order.end(), [&](int a, int b) { return hl[a] < hl[b]; });
         std::vector<int32_t> hl2(nh);
-        std::vector<int64_t> offs2(2 * (size_t)nh);
+        std::vector<int64_t> offs2(3 * (size_t)nh);
         for (int i = 0; i < nh; ++i) {
             hl2[i] = hl[order[i]];
-            offs2[2 * i] = offs[2 * order[i]];
-            offs2[2 * i + 1] = offs[2 * order[i] + 1];
+            for (int j = 0; j < 3; ++j) offs2[3 * i + j] = offs[3 * order[i] + j];
         }
         hl.swap(hl2);
         offs.swap(offs2);
@@ -486,13 +500,13 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
     std::vector<int32_t> items, chunks;
     int64_t slots = 0;
     for (int i = 0; i < nh; ++i) {
-        int64_t d = offs[2 * i + 1] - offs[2 * i];
-        int64_t m = std::min<int64_t>(d, g->k);
+        int64_t d = offs[3 * i + 1] - offs[3 * i];
+        int64_t m = std::min<int64_t>(d, offs[3 * i + 2]);
         info[i].row = hl[i];
         info[i].cap = (int32_t)pow2_at_least((uint64_t)(2 * m));
         info[i].tab = slots;
         info[i].first_item = (int32_t)items.size();
-        int nc = (int)((d + kHubChunk - 1) / kHubChunk);
+        int nc = (int)((d + g->tune.hub_chunk - 1) / g->tune.hub_chunk);
         info[i].n_items = nc;
         for (int c = 0; c < nc; ++c) { items.push_back(i); chunks.push_back(c); }
         slots += info[i].cap;
@@ -516,6 +530,12 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
         RS_CUDA_TRY(cudaMemcpy(g->hub_items, items.data(), items.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
         RS_CUDA_TRY(cudaMemcpy(g->hub_item_chunk, chunks.data(), chunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     }
+    return 0;
+}
+
+int rs::reclassify(rs_graph *g, cudaStream_t s) {
+    if (int rc = classify_rows(g, s)) return rc;
+    RS_CUDA_TRY(cudaStreamSynchronize(s));
     return 0;
 }
 
@@ -550,8 +570,7 @@ static int alloc_workspace(rs_graph *g) {
     RS_CUDA_TRY(dmalloc(&g->xS, nnz));
     RS_CUDA_TRY(dmalloc(&g->xout, n));
     RS_CUDA_TRY(dmalloc(&g->xin, n));
-    g->tri_cap = std::max<int64_t>(1 << 20, nnz / 8);
-    RS_CUDA_TRY(cudaMalloc(&g->tri, g->tri_cap * sizeof(rs::Tri)));
+    RS_CUDA_TRY(dmalloc(&g->xR, nnz));
     RS_CUDA_TRY(dmalloc(&g->scan_tmp, scan_tmp_words(std::max<int64_t>(n + 1, 1)) + 64));
     RS_CUDA_TRY(dmalloc(&g->rows_small, n));
     RS_CUDA_TRY(dmalloc(&g->rows_mid, n));
@@ -566,7 +585,7 @@ static void free_graph(rs_graph *g) {
     void *ptrs[] = {g->off, g->off_alt, g->col, g->col_alt, g->lab, g->removed, g->dead,
                     g->rows_small, g->rows_mid, g->rows_large, g->rows_small_deg, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
                     g->Lall, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->scan_tmp, g->tk_hist,
-                    g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->tri, g->rsum, g->cl_col, g->cl_lab,
+                    g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->xR, g->rsum, g->cl_col, g->cl_lab,
                     g->winv, g->gid, g->gk, g->gnode};
     for (void *p : ptrs) cudaFree(p);
     free_hub_tables(g);
@@ -804,6 +823,7 @@ extern "C" rs_status rs_clone_graph(const rs_graph *src, rs_graph **out, void *s
     if (!src || !out) return (rs_status)fail(RS_EINVAL, "rs_clone_graph: NULL argument");
     rs_graph *g = new rs_graph();
     g->n = src->n; g->nnz = src->nnz; g->k = src->k; g->device = src->device;
+    g->tune = src->tune;
     auto bail = [&](int rc) { free_graph(g); return (rs_status)rc; };
     int64_t n = g->n, nnz = g->nnz;
     if (cudaError_t e = dmalloc(&g->off, n + 1)) return bail(cuda_fail(e, "alloc"));
@@ -1128,6 +1148,19 @@ extern "C" rs_status rs_score(rs_graph *g, double *scores, double *omega_max_out
         memcpy(&w, &bits, sizeof(w));
         *omega_max_out = w;
     }
+    return RS_OK;
+}
+
+extern "C" rs_status rs_device_errors(rs_graph *g, int32_t *flags_out, void *stream) {
+    if (!g || !flags_out) return (rs_status)fail(RS_EINVAL, "rs_device_errors: NULL argument");
+    cudaStream_t s = as_stream(stream);
+    int32_t f = 0;
+    if (g->n > 0) {
+        if (cudaError_t e = cudaMemcpyAsync(&f, g->d_flag + 4, sizeof(int32_t), cudaMemcpyDeviceToHost, s))
+            return (rs_status)cuda_fail(e, "rs_device_errors");
+        if (cudaError_t e = cudaStreamSynchronize(s)) return (rs_status)cuda_fail(e, "rs_device_errors");
+    }
+    *flags_out = f;
     return RS_OK;
 }
 

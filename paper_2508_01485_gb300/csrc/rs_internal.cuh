@@ -6,23 +6,26 @@
 #include <string>
 #include <vector>
 
+#include "rs.h"
 #include "rs_numeric.cuh"
 
 namespace rs {
 
 // Row classes by degree d and by the hash-table size cap = pow2 >= 2 min(d, k)
-// (k bounds the number of distinct neighbour communities):
-//   small: d <= 32, one thread per row (rows sorted by degree so that the
-//          threads of a warp loop alike), a private table in shared memory;
-//   mid:   cap <= kWarpCap, one warp per row, a per-warp shared-memory table;
-//   large: cap <= kMidCap, one CTA per row, a per-CTA shared-memory table;
+// (k bounds the number of distinct neighbour communities).  The split points
+// are launch parameters (rs_tuning in rs.h); these are their upper limits,
+// which size the shared-memory tables:
+//   small: d <= small_max (<= kSmallMax), tiles of 32 rows per warp;
+//   mid:   cap <= warp_cap (<= kWarpCap), one warp per row, a per-warp
+//          shared-memory table;
+//   large: cap <= cta_cap (<= kMidCap), one CTA per row, a per-CTA
+//          shared-memory table;
 //   hub:   larger rows; a hash table in global memory, rows split into chunks
-//          of kHubChunk neighbours processed by separate CTAs and merged by
+//          of hub_chunk neighbours processed by separate CTAs and merged by
 //          atomics into the row's table.
 constexpr int kSmallMax = 32;
 constexpr int kWarpCap = 512;
 constexpr int kMidCap = 2048;
-constexpr int kHubChunk = 4096;
 constexpr int32_t kEmpty = -1;
 
 // per-node record written by the first pass and gathered by the second
@@ -67,11 +70,6 @@ struct __align__(8) RowSum {
 };
 
 // a G_x triangle (a, b, c), rank a < b < c, with its three out-direction values
-struct __align__(8) Tri {
-    int32_t a, b, c, pad;
-    df Sab, Sac, Sbc;
-};
-
 inline uint32_t pow2_at_least(uint64_t x) {
     uint32_t c = 1;
     while (c < x) c <<= 1;
@@ -85,6 +83,22 @@ __device__ __forceinline__ bool rank_after(int32_t dxu, int32_t u, int32_t dxw, 
     return dxu > dxw || (dxu == dxw && u > w);
 }
 
+}  // namespace rs
+
+namespace rs {
+// the launch parameters a new graph starts with (see rs_tuning in rs.h)
+inline rs_tuning default_tuning_value() {
+    rs_tuning t;
+    t.small_max = kSmallMax;
+    t.warp_cap = kWarpCap;
+    t.cta_cap = kMidCap;
+    t.hub_chunk = 4096;
+    t.p2_cta_dx = kWarpCap / 2;
+    t.p1_cta_threads = 256;
+    t.p2_cta_threads = 1024;
+    t.ctas_per_sm = 8;
+    return t;
+}
 }  // namespace rs
 
 struct rs_graph {
@@ -132,8 +146,7 @@ struct rs_graph {
     int32_t *xcol = nullptr;                  // G_x neighbours (capacity nnz)
     rs::df *xS = nullptr;                     // S(w -> u) = w_w(C(u))^(1/3)
     int32_t *xout = nullptr, *xin = nullptr;  // out / in counts per node
-    void *tri = nullptr;                      // triangle records (rs::Tri) found by P3a
-    int64_t tri_cap = 0;
+    rs::df *xR = nullptr;                     // at out-slot (w -> u): the reverse value S(u -> w)
     int64_t *scan_tmp = nullptr;              // block sums for scans
     // top-k workspace
     uint32_t *tk_hist = nullptr;
@@ -157,6 +170,9 @@ struct rs_graph {
     cudaStream_t aux[kAux] = {};
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kAux] = {};
+    // launch parameters and a counter bumped whenever buffers or row classes change
+    rs_tuning tune = rs::default_tuning_value();
+    uint64_t version = 0;
 };
 
 namespace rs {
@@ -199,5 +215,11 @@ int topk_scores(rs_graph *g, const double *scores, int64_t n, int32_t k, int32_t
                 double *out_scores, cudaStream_t s);
 int interaction_table(rs_graph *g, int64_t *t_out, int64_t *row_ptr, int32_t *comm,
                       int32_t *count, cudaStream_t s);
+// one-time kernel attributes / launch shapes and workspaces, so that a step can
+// be captured into a CUDA graph without allocating or configuring inside it
+int prepare_score_kernels();
+int topk_prepare(rs_graph *g, int64_t n);
+// re-split g's rows by g->tune (rs_api.cu); synchronises s
+int reclassify(rs_graph *g, cudaStream_t s);
 
 }  // namespace rs

@@ -26,8 +26,8 @@
 //   P2  per row w: counts and Q_w again, sigma_w per column, the Type-II
 //       terms pushed to the neighbours, and the G_x rows of w (out-neighbours
 //       of higher (dx, id) rank first, in-neighbours from the back);
-//   P3  per node a: oriented triangle listing on G_x (merge by binary search),
-//       the Type-I terms of the three apexes;
+//   P3  per node a: oriented triangle listing on G_x (pairs of out-neighbours,
+//       closing edge by binary search), the Type-I terms of the three apexes;
 //   FIN R(u) = acc(u) / (w_max d(u)(d(u)-1)), 0 when d(u) < 2 or w_max = 0.
 // All terms are added into 128-bit fixed-point accumulators, so the scores do
 // not depend on the order in which threads run.
@@ -369,14 +369,13 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (uint32_t j = lane; j < kWarpCap; j += 32) { skey[wid][j] = kEmpty; scnt[wid][j] = 0; }
     __syncwarp();
-    const int32_t k = B.k;
     for (int64_t i = warp; i < nrows; i += nwarps) {
         int32_t v = rows[i];
         int64_t b = off[v];
         int d = (int)(off[v + 1] - b);
         int32_t cv = lab[v];
         int32_t gi = graph_of(B, v);
-        uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(d, k));
+        uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(d, k_of(B, gi)));
         Tab t{skey[wid], scnt[wid], nullptr, nullptr, cap - 1};
         uint32_t own = 0, nused = 0;
         int32_t nx = 0;
@@ -465,14 +464,13 @@ __global__ void __launch_bounds__(NT) p1_large_kernel(
     __shared__ df sh_df[NT / 32];
     __shared__ int32_t sh_cnt[NT / 32];
     int tid = threadIdx.x, lane = tid & 31;
-    const int32_t k = B.k;
     for (int64_t i = blockIdx.x; i < nrows; i += gridDim.x) {
         int32_t v = rows[i];
         int64_t b = off[v];
         int d = (int)(off[v + 1] - b);
         int32_t cv = lab[v];
         int32_t gi = graph_of(B, v);
-        uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(d, k));
+        uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(d, k_of(B, gi)));
         Tab t{(int32_t *)smem, (uint32_t *)(smem + 4 * cap), nullptr, nullptr, cap - 1};
         for (uint32_t j = tid; j < cap; j += NT) { t.key[j] = kEmpty; t.cnt[j] = 0; }
         __syncthreads();
@@ -526,15 +524,15 @@ template <int NT>
 __global__ void __launch_bounds__(NT) hub_p1_insert_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
     const HubInfo *__restrict__ hubs, const int32_t *__restrict__ items, const int32_t *__restrict__ chunks,
-    int64_t nitems, int32_t *hkey, uint32_t *hcnt, HubAgg *hagg, int *err) {
+    int64_t nitems, int32_t chunk_len, int32_t *hkey, uint32_t *hcnt, HubAgg *hagg, int *err) {
     __shared__ uint32_t sh_u32[NT / 32];
     int tid = threadIdx.x, lane = tid & 31;
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
         HubInfo h = hubs[items[it]];
         int64_t b = off[h.row];
         int64_t d = off[h.row + 1] - b;
-        int64_t lo = (int64_t)chunks[it] * kHubChunk;
-        int64_t hi = min(d, lo + kHubChunk);
+        int64_t lo = (int64_t)chunks[it] * chunk_len;
+        int64_t hi = min(d, lo + chunk_len);
         int32_t cv = lab[h.row];
         Tab t{hkey + h.tab, hcnt + h.tab, nullptr, nullptr, (uint32_t)h.cap - 1};
         uint32_t own = 0;
@@ -826,7 +824,7 @@ __global__ void __launch_bounds__(kThreads) p2_warp_kernel(
 constexpr int kMidSlotBytes = 4 + 4 + 16;   // key, count, 2-word sum
 
 __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, int32_t k, int32_t dx_max,
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, Batch B, int32_t dx_max,
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
@@ -847,7 +845,7 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
         if (dx > dx_max || dx <= 32) continue;     // the CTA-per-row kernel / p2_warp_kernel
         int32_t bo = 0, bi = 0;
         {
-            uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(dx, k));
+            uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(dx, k_of(B, graph_of(B, w))));
             Tab t;
             t.q = (unsigned long long *)base_w;
             t.key = (int32_t *)(base_w + 16 * kWarpCap);
@@ -952,7 +950,7 @@ __device__ __forceinline__ void gx_round(bool out, bool in, int64_t xb, int32_t 
 
 template <int NT>
 __global__ void __launch_bounds__(NT) p2_large_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, int32_t k, int32_t dx_min,
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, Batch B, int32_t dx_min,
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
@@ -973,7 +971,7 @@ __global__ void __launch_bounds__(NT) p2_large_kernel(
             if (tid == 0) { xout[w] = 0; xin[w] = 0; }
             continue;
         }
-        uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(dx, k));
+        uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(dx, k_of(B, graph_of(B, w))));
         Tab t = p2_table(smem, cap);
         for (uint32_t j = tid; j < cap; j += NT) {
             t.key[j] = kEmpty; t.cnt[j] = 0; t.q[2 * j] = 0; t.q[2 * j + 1] = 0;
@@ -1037,7 +1035,7 @@ __global__ void __launch_bounds__(NT) p2_large_kernel(
 template <int NT>
 __global__ void __launch_bounds__(NT) hub_p2_insert_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const HubInfo *__restrict__ hubs,
-    const int32_t *__restrict__ items, const int32_t *__restrict__ chunks, int64_t nitems,
+    const int32_t *__restrict__ items, const int32_t *__restrict__ chunks, int64_t nitems, int32_t chunk_len,
     const NodeRec *__restrict__ rec, const int32_t *hkey, unsigned long long *hq,
     int32_t *hitem_out, int32_t *hitem_in, int *err) {
     __shared__ uint32_t sh_u32[NT / 32];
@@ -1048,8 +1046,8 @@ __global__ void __launch_bounds__(NT) hub_p2_insert_kernel(
         HubInfo h = hubs[items[it]];
         int64_t b = off[h.row];
         int64_t d = off[h.row + 1] - b;
-        int64_t lo = (int64_t)chunks[it] * kHubChunk;
-        int64_t hi = min(d, lo + kHubChunk);
+        int64_t lo = (int64_t)chunks[it] * chunk_len;
+        int64_t hi = min(d, lo + chunk_len);
         NodeRec rw = rec[h.row];
         Tab t{(int32_t *)hkey + h.tab, nullptr, hq + 2 * h.tab, nullptr, (uint32_t)h.cap - 1};
         uint32_t no = 0, ni = 0;
@@ -1113,7 +1111,7 @@ __global__ void __launch_bounds__(NT) hub_p2_sigma_kernel(
 template <int NT>
 __global__ void __launch_bounds__(NT) hub_p2_emit_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const HubInfo *__restrict__ hubs,
-    const int32_t *__restrict__ items, const int32_t *__restrict__ chunks, int64_t nitems,
+    const int32_t *__restrict__ items, const int32_t *__restrict__ chunks, int64_t nitems, int32_t chunk_len,
     const NodeRec *__restrict__ rec, const int32_t *hkey, const uint32_t *hcnt,
     const unsigned long long *hq, const df *hsig, const int32_t *hitem_out, const int32_t *hitem_in,
     unsigned long long *acc, const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol,
@@ -1126,8 +1124,8 @@ __global__ void __launch_bounds__(NT) hub_p2_emit_kernel(
         int64_t b = off[h.row];
         int64_t d = off[h.row + 1] - b;
         int32_t ch = chunks[it];
-        int64_t lo = (int64_t)ch * kHubChunk;
-        int64_t hi = min(d, lo + kHubChunk);
+        int64_t lo = (int64_t)ch * chunk_len;
+        int64_t hi = min(d, lo + chunk_len);
         NodeRec rw = rec[h.row];
         Tab t{(int32_t *)hkey + h.tab, (uint32_t *)hcnt + h.tab, nullptr, nullptr, (uint32_t)h.cap - 1};
         int32_t bo = 0, bi = 0;
@@ -1165,37 +1163,124 @@ __global__ void __launch_bounds__(NT) hub_p2_emit_kernel(
 // ======================================================================================
 // P3: Type-I triads from G_x triangles
 // ======================================================================================
-__device__ __forceinline__ int64_t find_out(const int32_t *xcol, int64_t lo, int64_t hi, int32_t key) {
-    while (lo < hi) {
+// P3m (mirror): every G_x out-slot (w -> u) receives the reverse value
+// S(u -> w), which row u wrote at its in-slot for w.  Node u's slots are
+// [xoff[u], xoff[u] + dx(u)), its in-slots the last xin(u) of them.  The slot
+// space [0, xoff[n]) is cut into tiles of kMirTile consecutive slots, one
+// tile per CTA trip, so the work per CTA does not depend on the in-degrees.
+// A tile stages the offsets of the nodes it spans in shared memory, counts
+// their in-slots inside the tile and spreads only those over the threads; a
+// slot's out-slot twin is found by binary search in w's out-list, which is
+// short (w has the lower rank).  A tile spanning more than kMirNodes nodes
+// (long runs of nodes outside G_x) searches the offsets in global memory.
+constexpr int kMirTile = 2048;
+constexpr int kMirNodes = 1024;
+
+__device__ __forceinline__ int64_t last_leq(const int64_t *xoff, int64_t lo, int64_t hi, int64_t key) {
+    // last index i in [lo, hi) with xoff[i] <= key (xoff[lo] <= key)
+    while (hi - lo > 1) {
         int64_t mid = lo + ((hi - lo) >> 1);
-        if (xcol[mid] < key) lo = mid + 1; else hi = mid;
+        if (xoff[mid] <= key) lo = mid; else hi = mid;
     }
     return lo;
 }
-// S(x -> y) for an in-neighbour y of x: the in-list sits at the back of x's
-// slots in descending position order of ascending ids
-__device__ __forceinline__ df in_value(const int64_t *xoff, const int32_t *xcol, const df *xS,
-                                       const int32_t *xin, const NodeRec *rec, int32_t x, int32_t y,
-                                       int *err) {
-    int64_t end = xoff[x] + rec[x].dx - 1;      // position of in-rank 0
-    int32_t lo = 0, hi = xin[x];
-    while (lo < hi) {
-        int32_t mid = (lo + hi) >> 1;
-        if (xcol[end - mid] < y) lo = mid + 1; else hi = mid;
+
+// copy S(u -> w) from u's in-slot sl to w's out-slot for u
+__device__ __forceinline__ void mirror_one(int64_t sl, int32_t u, const int64_t *xoff, const int32_t *xcol,
+                                           const df *xS, const int32_t *xout, df *xR, int *err) {
+    int32_t w = xcol[sl];
+    int64_t wb = xoff[w];
+    int32_t len = xout[w], l = 0, h = len;
+    while (l < h) {
+        int32_t mid = (l + h) >> 1;
+        if (xcol[wb + mid] < u) l = mid + 1; else h = mid;
     }
-    if (lo < xin[x] && xcol[end - lo] == y) return xS[end - lo];
-    atomicOr(err, 16);
-    return df{0.0f, 0.0f};
+    if (l < len && xcol[wb + l] == u) xR[wb + l] = xS[sl];
+    else atomicOr(err, 16);
 }
 
-// the three apex terms of triangle (a, b, c), rank a < b < c
-__device__ __forceinline__ void triangle_terms(int32_t a, int32_t b, int32_t c, df Sab, df Sac, df Sbc,
-                                               const int64_t *xoff, const int32_t *xcol, const df *xS,
-                                               const int32_t *xin, const NodeRec *rec,
-                                               unsigned long long *acc, int *err) {
-    df Sba = in_value(xoff, xcol, xS, xin, rec, b, a, err);
-    df Sca = in_value(xoff, xcol, xS, xin, rec, c, a, err);
-    df Scb = in_value(xoff, xcol, xS, xin, rec, c, b, err);
+__global__ void __launch_bounds__(kThreads) gx_mirror_kernel(
+    int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
+    const int32_t *__restrict__ xout, const int32_t *__restrict__ xin, df *__restrict__ xR, int *err) {
+    __shared__ int64_t range[2];
+    __shared__ int64_t s_lo[kMirNodes];          // first in-slot of each staged node inside the tile
+    __shared__ int32_t s_pre[kMirNodes + 1];     // prefix sums of the staged nodes' in-slots in the tile
+    __shared__ int32_t s_wsum[kThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t S = xoff[n];
+    const int64_t tiles = (S + kMirTile - 1) / kMirTile;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        int64_t s0 = t * kMirTile, s1 = min(S, s0 + kMirTile);
+        __syncthreads();
+        if (tid == 0) {
+            int64_t u0 = last_leq(xoff, 0, n + 1, s0);
+            range[0] = u0;
+            range[1] = last_leq(xoff, u0, n + 1, s1 - 1) + 1;
+        }
+        __syncthreads();
+        int64_t ulo = range[0], uhi = range[1];
+        int32_t nn = (int32_t)(uhi - ulo);
+        if (nn > kMirNodes) {
+            for (int64_t sl = s0 + tid; sl < s1; sl += blockDim.x) {
+                int64_t u = last_leq(xoff, ulo, uhi, sl);
+                if (sl >= xoff[u + 1] - xin[u]) mirror_one(sl, (int32_t)u, xoff, xcol, xS, xout, xR, err);
+            }
+            continue;
+        }
+        // in-slots of each staged node inside [s0, s1): four consecutive nodes per thread
+        constexpr int kPer = kMirNodes / kThreads;
+        int32_t cnt[kPer];
+        int32_t mine = 0;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            int32_t i = tid * kPer + j;
+            cnt[j] = 0;
+            if (i < nn) {
+                int64_t end = xoff[ulo + i + 1];
+                int64_t lo = max(end - (int64_t)xin[ulo + i], s0);
+                int64_t hi = min(end, s1);
+                s_lo[i] = lo;
+                cnt[j] = hi > lo ? (int32_t)(hi - lo) : 0;
+            }
+            mine += cnt[j];
+        }
+        int32_t incl = mine;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[wid] = incl;
+        __syncthreads();
+        int32_t before = 0, total = 0;
+        for (int j = 0; j < kThreads / 32; ++j) {
+            if (j < wid) before += s_wsum[j];
+            total += s_wsum[j];
+        }
+        int32_t run = before + incl - mine;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            int32_t i = tid * kPer + j;
+            if (i < nn) s_pre[i] = run;
+            run += cnt[j];
+        }
+        if (tid == 0) s_pre[nn] = total;
+        __syncthreads();
+        for (int32_t q = tid; q < total; q += blockDim.x) {
+            int32_t lo = 0, hi = nn;                    // last staged node with s_pre <= q
+            while (hi - lo > 1) {
+                int32_t mid = (lo + hi) >> 1;
+                if (s_pre[mid] <= q) lo = mid; else hi = mid;
+            }
+            mirror_one(s_lo[lo] + (q - s_pre[lo]), (int32_t)(ulo + lo), xoff, xcol, xS, xout, xR, err);
+        }
+    }
+}
+
+// the three apex terms of triangle (a, b, c) from its six directed values
+// S(x -> y) = w_x(C(y))^(1/3): at apex a the ordered pairs (w, v) = (b, c) and
+// (c, b) give S(c->a) S(b->c) S(b->a) + S(b->a) S(c->b) S(c->a)
+__device__ __forceinline__ void triangle_terms(int32_t a, int32_t b, int32_t c, df Sab, df Sba, df Sac, df Sca,
+                                               df Sbc, df Scb, unsigned long long *acc) {
     df ta = df_mul(df_mul(Sba, Sca), df_add(Sbc, Scb));
     df tb = df_mul(df_mul(Sab, Scb), df_add(Sac, Sca));
     df tc = df_mul(df_mul(Sac, Sbc), df_add(Sab, Sba));
@@ -1204,124 +1289,93 @@ __device__ __forceinline__ void triangle_terms(int32_t a, int32_t b, int32_t c, 
     atomic_add_u128(acc + 2 * (int64_t)c, df_to_fixed(tc, kAccFrac));
 }
 
-// P3a lists the triangles of G_x once each, from their lowest-ranked node a
-// (out-lists are sorted by id).  A warp takes 32 consecutive nodes and stages
-// their out-lists in shared memory, with, per entry b, the prefix sums of
-// d+(b).  All wedges a -> b -> c of the group then form one flat index space
-// that the lanes share evenly; c closes a triangle iff it is in N+(a)
-// (binary search in shared memory).  Nodes with an out-list longer than
-// kGroupDa, or groups with more than kGroupCap out-entries, take a per-node
-// warp path (staged N+(a), or global binary searches beyond kP3Cap).
-// Triangles go to a buffer for P3b, slots reserved once per warp iteration;
-// when the buffer is full they are finished on the spot.
-constexpr int kP3Cap = 256;
-constexpr int kGroupDa = 64;
-constexpr int kGroupCap = 256;
+// P3 lists the triangles of G_x once each, from their lowest-ranked node a
+// (rank = (dx, id); a node's out-list holds its higher-ranked G_x neighbours,
+// sorted by id).  Every pair {b, c} of a's out-neighbours is a candidate, and
+// it closes a triangle iff the higher-ranked of the two is in the out-list of
+// the lower-ranked one.  There are sum_a d+(a)(d+(a)-1)/2 candidates, several
+// times fewer than the wedges a -> b -> c on these graphs.
+//
+// A warp takes 32 consecutive nodes and stages their out-lists (with each
+// entry's G_x offset, out-degree and rank) in shared memory, window by window
+// of at most kWinCap entries.  All candidate pairs of a window form one flat
+// index space that the lanes share evenly (four per lane per trip): entry e
+// owns the pairs (e, f > e) of its node.  The closing edge is looked up by
+// binary search in the lower-ranked node's out-list in global memory (short:
+// the out-degree of a low-ranked node).  Each of the three slots of a
+// triangle holds both directed values (xS forward, xR reverse), so the
+// triangle's terms are added where it is found.  Nodes with more than kWinCap
+// out-neighbours take a lane-strided path over global memory.
+constexpr int kWinCap = 128;
 constexpr int kP3Warps = kThreads / 32;
 
 struct P3Stage {
-    int32_t nb[kGroupCap];          // out-entries b of the group, node after node
-    int64_t boff[kGroupCap];        // xoff[b]
-    int32_t wpre[kGroupCap + 1];    // prefix sums of d+(b) over the entries
-    uint8_t owner[kGroupCap];       // lane (node) of the entry
-    int32_t seg[33];                // first entry of each node
+    int64_t boff[kWinCap];          // xoff[b]
+    int32_t nb[kWinCap];            // b
+    int32_t bdeg[kWinCap];          // d+(b)
+    int32_t bdx[kWinCap];           // dx(b): rank(b) = (dx(b), b)
+    uint16_t ppre[kWinCap + 1];     // prefix sums of the pairs (e, f > e) owned by the entries
+    uint8_t owner[kWinCap];         // lane (node) of the entry
+    int32_t seg[33];                // first entry of each lane's node in the window
     int64_t aoff[32];               // xoff[a]
+    // triangles found and not yet finished: the closing slot, the owner lane
+    // and the window entries of the lower- and higher-ranked neighbours
+    int64_t qpos[64];
+    uint8_t qow[64], qlo[64], qhi[64];
 };
 
-__device__ __forceinline__ void put_triangle(unsigned long long p, int32_t a, int32_t b, int32_t c, df Sab, df Sac,
-                                             df Sbc, Tri *tri, int64_t tri_cap, const int64_t *xoff,
-                                             const int32_t *xcol, const df *xS, const int32_t *xin,
-                                             const NodeRec *rec, unsigned long long *acc, int *err) {
-    if ((int64_t)p < tri_cap) {
-        Tri t;
-        t.a = a; t.b = b; t.c = c; t.pad = 0;
-        t.Sab = Sab; t.Sac = Sac; t.Sbc = Sbc;
-        tri[p] = t;
-    } else {
-        triangle_terms(a, b, c, Sab, Sac, Sbc, xoff, xcol, xS, xin, rec, acc, err);
+// finish the first m (<= 32) queued triangles of the window, one per lane
+__device__ __forceinline__ void p3_flush(const P3Stage &S, int m, int64_t base, const df *xS, const df *xR,
+                                         unsigned long long *acc, int lane) {
+    if (lane < m) {
+        int ow = S.qow[lane], el = S.qlo[lane], eh = S.qhi[lane];
+        int64_t ao = S.aoff[ow] - S.seg[ow];
+        int64_t il = ao + el, ih = ao + eh, pc = S.qpos[lane];
+        triangle_terms((int32_t)(base + ow), S.nb[el], S.nb[eh], xS[il], xR[il], xS[ih], xR[ih], xS[pc], xR[pc],
+                       acc);
     }
 }
 
-// reserve slots for this iteration's hits, one atomic per warp
-__device__ __forceinline__ unsigned long long reserve(bool hit, unsigned long long *tri_n, int lane) {
-    unsigned hm = __ballot_sync(FULL, hit);
-    unsigned long long hb = 0;
-    if (hm && lane == 0) hb = atomicAdd(tri_n, (unsigned long long)__popc(hm));
-    hb = __shfl_sync(FULL, hb, 0);
-    return hb + __popc(hm & lanemask_lt());
+__device__ __forceinline__ bool rank_less(int32_t dx1, int32_t id1, int32_t dx2, int32_t id2) {
+    return dx1 < dx2 || (dx1 == dx2 && id1 < id2);
 }
 
-// the whole warp on one node a (out-list longer than kGroupDa)
-__device__ void p3_node_warp(int32_t a, int32_t dA, const int64_t *xoff, const int32_t *xcol, const df *xS,
-                             const int32_t *xout, const int32_t *xin, const NodeRec *rec, Tri *tri,
-                             int64_t tri_cap, unsigned long long *tri_n, unsigned long long *acc, int *err,
-                             P3Stage &S, int lane) {
+// position of key in the sorted list xcol[lo, lo + len), or -1
+__device__ __forceinline__ int64_t find_in_list(const int32_t *xcol, int64_t lo, int32_t len, int32_t key) {
+    int32_t l = 0, h = len;
+    while (l < h) {
+        int32_t mid = (l + h) >> 1;
+        if (xcol[lo + mid] < key) l = mid + 1; else h = mid;
+    }
+    return (l < len && xcol[lo + l] == key) ? lo + l : -1;
+}
+
+// a node with more than kWinCap out-neighbours: lanes stride over its first entries
+__device__ void p3_node_global(int32_t a, int32_t dA, const int64_t *xoff, const int32_t *xcol, const df *xS,
+                               const df *xR, const int32_t *xout, const NodeRec *rec, unsigned long long *acc,
+                               int lane) {
     int64_t bA = xoff[a];
-    if (dA <= kP3Cap && dA <= kGroupCap) {
-        int32_t carry = 0;
-        if (lane == 0) S.wpre[0] = 0;
-        for (int32_t j0 = 0; j0 < dA; j0 += 32) {
-            int32_t j = j0 + lane;
-            int32_t b = j < dA ? xcol[bA + j] : 0;
-            int32_t db = j < dA ? xout[b] : 0;
-            if (j < dA) { S.nb[j] = b; S.boff[j] = xoff[b]; }
-            int32_t x = db;
-            for (int o = 1; o < 32; o <<= 1) {
-                int32_t y = __shfl_up_sync(FULL, x, o);
-                if (lane >= o) x += y;
-            }
-            if (j < dA) S.wpre[j + 1] = carry + x;
-            carry += __shfl_sync(FULL, x, 31);
-        }
-        __syncwarp();
-        int32_t W = S.wpre[dA];
-        for (int32_t w0 = 0; w0 < W; w0 += 32) {
-            int32_t wv = w0 + lane;
-            bool hit = false;
-            int32_t j = 0, l2 = 0, c = 0;
-            int64_t pb = 0;
-            if (wv < W) {
-                int32_t lo = 0, hi = dA;
-                while (hi - lo > 1) {
-                    int32_t mid = (lo + hi) >> 1;
-                    if (S.wpre[mid] <= wv) lo = mid; else hi = mid;
-                }
-                j = lo;
-                pb = S.boff[j] + (wv - S.wpre[j]);
-                c = xcol[pb];
-                int32_t h2 = dA;
-                while (l2 < h2) {
-                    int32_t mid = (l2 + h2) >> 1;
-                    if (S.nb[mid] < c) l2 = mid + 1; else h2 = mid;
-                }
-                hit = l2 < dA && S.nb[l2] == c;
-            }
-            unsigned long long p = reserve(hit, tri_n, lane);
-            if (hit)
-                put_triangle(p, a, S.nb[j], c, xS[bA + j], xS[bA + l2], xS[pb], tri, tri_cap, xoff, xcol, xS, xin,
-                             rec, acc, err);
-        }
-        __syncwarp();
-    } else {
-        for (int32_t j = lane; j < dA; j += 32) {
-            int32_t b = xcol[bA + j];
-            int64_t bb = xoff[b];
-            int32_t db = xout[b];
-            for (int32_t tb = 0; tb < db; ++tb) {
-                int32_t c = xcol[bb + tb];
-                int64_t p = find_out(xcol, bA, bA + dA, c);
-                if (p >= bA + dA || xcol[p] != c) continue;
-                put_triangle(atomicAdd(tri_n, 1ull), a, b, c, xS[bA + j], xS[p], xS[bb + tb], tri, tri_cap, xoff,
-                             xcol, xS, xin, rec, acc, err);
-            }
+    for (int32_t i = lane; i < dA; i += 32) {
+        int32_t b = xcol[bA + i];
+        int32_t dxb = rec[b].dx;
+        int64_t ob = xoff[b];
+        int32_t db = xout[b];
+        for (int32_t j = i + 1; j < dA; ++j) {
+            int32_t c = xcol[bA + j];
+            int32_t dxc = rec[c].dx;
+            bool b_low = rank_less(dxb, b, dxc, c);
+            int64_t pos = b_low ? find_in_list(xcol, ob, db, c) : find_in_list(xcol, xoff[c], xout[c], b);
+            if (pos < 0) continue;
+            int64_t il = bA + (b_low ? i : j), ih = bA + (b_low ? j : i);
+            triangle_terms(a, b_low ? b : c, b_low ? c : b, xS[il], xR[il], xS[ih], xR[ih], xS[pos], xR[pos], acc);
         }
     }
 }
 
 __global__ void __launch_bounds__(kThreads) p3_list_kernel(
     int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
-    const int32_t *__restrict__ xout, const int32_t *__restrict__ xin, const NodeRec *__restrict__ rec,
-    Tri *tri, int64_t tri_cap, unsigned long long *tri_n, unsigned long long *acc, int *err) {
+    const df *__restrict__ xR, const int32_t *__restrict__ xout, const NodeRec *__restrict__ rec,
+    unsigned long long *acc) {
     __shared__ P3Stage stage[kP3Warps];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     P3Stage &S = stage[wid];
@@ -1330,111 +1384,127 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
     for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
         int64_t av = base + lane;
         int32_t da = av < n ? xout[av] : 0;
-        bool grp = da >= 2 && da <= kGroupDa;
+        bool grp = da >= 2 && da <= kWinCap;
         int32_t mine = grp ? da : 0;
         int32_t incl = mine;
         for (int o = 1; o < 32; o <<= 1) {
             int32_t y = __shfl_up_sync(FULL, incl, o);
             if (lane >= o) incl += y;
         }
-        int32_t E = __shfl_sync(FULL, incl, 31);
-        bool fits = E <= kGroupCap;
-        unsigned solo = __ballot_sync(FULL, da > kGroupDa || (!fits && da >= 2));
-        if (fits && E > 0) {
-            int32_t e0 = incl - mine;
-            S.seg[lane] = e0;
-            if (lane == 31) S.seg[32] = E;
-            int64_t ba = grp ? xoff[av] : 0;
-            S.aoff[lane] = ba;
-            for (int32_t j = 0; j < mine; ++j) {
-                int32_t b = xcol[ba + j];
-                S.nb[e0 + j] = b;
-                S.boff[e0 + j] = xoff[b];
-                S.wpre[e0 + j + 1] = xout[b];          // counts; turned into prefix sums below
-                S.owner[e0 + j] = (uint8_t)lane;
-            }
-            __syncwarp();
-            int32_t carry = 0;
-            if (lane == 0) S.wpre[0] = 0;
-            for (int32_t j0 = 0; j0 < E; j0 += 32) {
-                int32_t j = j0 + lane;
-                int32_t x = j < E ? S.wpre[j + 1] : 0;
-                for (int o = 1; o < 32; o <<= 1) {
-                    int32_t y = __shfl_up_sync(FULL, x, o);
-                    if (lane >= o) x += y;
-                }
+        int64_t ba = grp ? xoff[av] : 0;
+        // windows of consecutive nodes whose entries fit kWinCap
+        int32_t start = 0;
+        while (true) {
+            int32_t excl0 = start > 0 ? __shfl_sync(FULL, incl, start - 1) : 0;
+            unsigned fitm = __ballot_sync(FULL, lane >= start && incl - excl0 <= kWinCap);
+            if (start >= 32 || fitm == 0) break;
+            int32_t end = 32 - __clz(fitm);               // lanes [start, end) fit
+            int32_t Ew = __shfl_sync(FULL, incl, end - 1) - excl0;
+            bool inwin = lane >= start && lane < end;
+            int32_t e0 = incl - mine - excl0;              // this lane's first entry in the window
+            if (Ew > 0) {
+                // seg is nondecreasing over all 32 lanes: the entry j belongs to the
+                // last lane o with seg[o] <= j (lanes without entries share the next seg)
+                S.seg[lane] = lane < start ? 0 : (inwin ? e0 : Ew);
+                if (lane == 0) S.seg[32] = Ew;
+                S.aoff[lane] = ba;
                 __syncwarp();
-                if (j < E) S.wpre[j + 1] = carry + x;
-                carry += __shfl_sync(FULL, x, 31);
-                __syncwarp();
-            }
-            int32_t W = S.wpre[E];
-            constexpr int U = 4;                       // wedges per lane per trip (loads in flight)
-            for (int32_t w0 = 0; w0 < W; w0 += 32 * U) {
-                int32_t e[U], c[U];
-                int64_t pb[U];
-#pragma unroll
-                for (int q = 0; q < U; ++q) {
-                    int32_t wv = w0 + q * 32 + lane;
-                    e[q] = -1;
-                    if (wv < W) {
-                        int32_t lo = 0, hi = E;             // last entry with wpre[e] <= wv
+                // entries, their data and the pair prefix sums, lanes over entries
+                uint32_t carry = 0;
+                if (lane == 0) S.ppre[0] = 0;
+                for (int32_t j0 = 0; j0 < Ew; j0 += 32) {
+                    int32_t j = j0 + lane;
+                    uint32_t x = 0;
+                    if (j < Ew) {
+                        int32_t lo = 0, hi = 32;
                         while (hi - lo > 1) {
                             int32_t mid = (lo + hi) >> 1;
-                            if (S.wpre[mid] <= wv) lo = mid; else hi = mid;
+                            if (S.seg[mid] <= j) lo = mid; else hi = mid;
                         }
-                        e[q] = lo;
-                        pb[q] = S.boff[lo] + (wv - S.wpre[lo]);
+                        int32_t loc = j - S.seg[lo];
+                        int32_t b = xcol[S.aoff[lo] + loc];
+                        S.nb[j] = b;
+                        S.owner[j] = (uint8_t)lo;
+                        S.boff[j] = xoff[b];
+                        S.bdeg[j] = xout[b];
+                        S.bdx[j] = rec[b].dx;
+                        x = (uint32_t)(S.seg[lo + 1] - S.seg[lo] - 1 - loc);   // pairs (j, f > j) of the node
+                    }
+                    for (int o = 1; o < 32; o <<= 1) {
+                        uint32_t y = __shfl_up_sync(FULL, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    if (j < Ew) S.ppre[j + 1] = (uint16_t)(carry + x);
+                    carry += __shfl_sync(FULL, x, 31);
+                }
+                __syncwarp();
+                int32_t P = S.ppre[Ew];
+                int qn = 0;                                // queued triangles (warp-uniform)
+                constexpr int U = 4;                       // pairs per lane per trip
+                for (int32_t p0 = 0; p0 < P; p0 += 32 * U) {
+                    int32_t lo_e[U], hi_e[U];
+                    int64_t pos[U];
+#pragma unroll
+                    for (int q = 0; q < U; ++q) {
+                        int32_t pv = p0 + q * 32 + lane;
+                        lo_e[q] = -1;
+                        hi_e[q] = 0;
+                        if (pv < P) {
+                            int32_t lo = 0, hi = Ew;        // last entry with ppre[e] <= pv
+                            while (hi - lo > 1) {
+                                int32_t mid = (lo + hi) >> 1;
+                                if (S.ppre[mid] <= pv) lo = mid; else hi = mid;
+                            }
+                            int32_t f = lo + 1 + (pv - S.ppre[lo]);
+                            bool e_low = rank_less(S.bdx[lo], S.nb[lo], S.bdx[f], S.nb[f]);
+                            lo_e[q] = e_low ? lo : f;
+                            hi_e[q] = e_low ? f : lo;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < U; ++q)
+                        pos[q] = lo_e[q] >= 0 ? find_in_list(xcol, S.boff[lo_e[q]], S.bdeg[lo_e[q]], S.nb[hi_e[q]]) : -1;
+#pragma unroll
+                    for (int q = 0; q < U; ++q) {
+                        bool hit = pos[q] >= 0;
+                        unsigned hm = __ballot_sync(FULL, hit);
+                        if (hit) {
+                            int slot = qn + __popc(hm & lanemask_lt());
+                            S.qpos[slot] = pos[q];
+                            S.qow[slot] = S.owner[lo_e[q]];
+                            S.qlo[slot] = (uint8_t)lo_e[q];
+                            S.qhi[slot] = (uint8_t)hi_e[q];
+                        }
+                        qn += __popc(hm);
+                        if (qn >= 32) {                        // a full warp of triangles
+                            __syncwarp();
+                            p3_flush(S, 32, base, xS, xR, acc, lane);
+                            __syncwarp();
+                            if (lane < qn - 32) {
+                                S.qpos[lane] = S.qpos[32 + lane];
+                                S.qow[lane] = S.qow[32 + lane];
+                                S.qlo[lane] = S.qlo[32 + lane];
+                                S.qhi[lane] = S.qhi[32 + lane];
+                            }
+                            qn -= 32;
+                            __syncwarp();
+                        }
                     }
                 }
-#pragma unroll
-                for (int q = 0; q < U; ++q) c[q] = e[q] >= 0 ? xcol[pb[q]] : 0;
-#pragma unroll
-                for (int q = 0; q < U; ++q) {
-                    bool hit = false;
-                    int32_t ow = 0, l2 = 0;
-                    if (e[q] >= 0) {
-                        ow = S.owner[e[q]];
-                        int32_t s0 = S.seg[ow], s1 = S.seg[ow + 1];
-                        l2 = s0;
-                        int32_t h2 = s1;
-                        while (l2 < h2) {
-                            int32_t mid = (l2 + h2) >> 1;
-                            if (S.nb[mid] < c[q]) l2 = mid + 1; else h2 = mid;
-                        }
-                        hit = l2 < s1 && S.nb[l2] == c[q];
-                    }
-                    unsigned long long p = reserve(hit, tri_n, lane);
-                    if (hit) {
-                        int64_t ba_o = S.aoff[ow];
-                        int32_t s0 = S.seg[ow];
-                        put_triangle(p, (int32_t)(base + ow), S.nb[e[q]], c[q], xS[ba_o + (e[q] - s0)],
-                                     xS[ba_o + (l2 - s0)], xS[pb[q]], tri, tri_cap, xoff, xcol, xS, xin, rec, acc, err);
-                    }
-                }
+                __syncwarp();
+                p3_flush(S, qn, base, xS, xR, acc, lane);   // the window's stage is reused next
+                qn = 0;
+                __syncwarp();
             }
-            __syncwarp();
+            start = end;
         }
-        while (solo) {
-            int l = __ffs(solo) - 1;
-            solo &= solo - 1;
+        unsigned big = __ballot_sync(FULL, da > kWinCap);
+        while (big) {
+            int l = __ffs(big) - 1;
+            big &= big - 1;
             int32_t dA = __shfl_sync(FULL, da, l);
-            p3_node_warp((int32_t)(base + l), dA, xoff, xcol, xS, xout, xin, rec, tri, tri_cap, tri_n, acc, err, S,
-                         lane);
+            p3_node_global((int32_t)(base + l), dA, xoff, xcol, xS, xR, xout, rec, acc, lane);
         }
-    }
-}
-
-// P3b: one thread per listed triangle
-__global__ void __launch_bounds__(kThreads) p3_terms_kernel(
-    const Tri *__restrict__ tri, int64_t tri_cap, const unsigned long long *tri_n,
-    const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
-    const int32_t *__restrict__ xin, const NodeRec *__restrict__ rec, unsigned long long *acc, int *err) {
-    int64_t m = (int64_t)*tri_n;
-    if (m > tri_cap) m = tri_cap;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-        Tri t = tri[i];
-        triangle_terms(t.a, t.b, t.c, t.Sab, t.Sac, t.Sbc, xoff, xcol, xS, xin, rec, acc, err);
     }
 }
 
@@ -1469,14 +1539,43 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(
 // ======================================================================================
 // host orchestration
 // ======================================================================================
-// P2 of large rows takes 1024-thread CTAs: its longest cross lists bound the kernel time
-constexpr int kLargeThreads = 1024;
+// dynamic shared memory limits of the table kernels, set once per process
+int rs::prepare_score_kernels() {
+    static int done = 0;
+    if (done) return 0;
+    const int p2_mid_smem = kMidWarps * kWarpCap * kMidSlotBytes;
+    RS_CUDA_TRY(cudaFuncSetAttribute(p1_large_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kMidCap));
+    RS_CUDA_TRY(cudaFuncSetAttribute(p1_large_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kMidCap));
+    RS_CUDA_TRY(cudaFuncSetAttribute(p1_large_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kMidCap));
+    RS_CUDA_TRY(cudaFuncSetAttribute(p2_large_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kMidCap));
+    RS_CUDA_TRY(cudaFuncSetAttribute(p2_large_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kMidCap));
+    RS_CUDA_TRY(cudaFuncSetAttribute(p2_large_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kMidCap));
+    RS_CUDA_TRY(cudaFuncSetAttribute(p2_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, p2_mid_smem));
+    done = 1;
+    return 0;
+}
+
+// the CTA-per-row kernels at the tuned CTA size
+template <int NT>
+static void launch_p1_large(rs_graph *g, const Batch &B, int *err, size_t smem) {
+    p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, smem, g->aux[1]>>>(
+        g->off, g->col, g->lab, g->rows_large, g->n_large, B, g->LG, g->rec, g->Lall, err,
+        g->rsum, g->cl_col, g->cl_lab);
+}
+template <int NT>
+static void launch_p2_large(rs_graph *g, const Batch &B, int *err, size_t smem) {
+    p2_large_kernel<NT><<<grid_for(g->n_large, 1, 2), NT, smem, g->aux[4]>>>(
+        g->off, g->rows_large, g->n_large, B, g->tune.p2_cta_dx + 1, g->LG, g->rec, g->rsum, g->cl_col,
+        g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
+}
 
 int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     int64_t n = g->n;
     if (n == 0) return 0;
     constexpr int NT = kThreads;
     int *err = g->d_flag + 4;
+    const int cps = g->tune.ctas_per_sm;
+    if (int rc = prepare_score_kernels()) return rc;
     prof_begin(g, s);
     RS_CUDA_TRY(cudaMemsetAsync(g->wmax_bits, 0, g->n_graphs * sizeof(unsigned long long), s));
     Batch B{g->gid, g->gk, g->k, g->wmax_bits};
@@ -1491,40 +1590,35 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     prof_mark(g, s, "memset", false);
     size_t p1_smem = 8 * (size_t)g->large_cap, p2_smem = 32 * (size_t)g->large_cap;
     size_t p2_mid_smem = (size_t)kMidWarps * kWarpCap * kMidSlotBytes;
-    static bool attr_done = false;
-    if (!attr_done) {
-        RS_CUDA_TRY(cudaFuncSetAttribute(p1_large_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kMidCap));
-        RS_CUDA_TRY(cudaFuncSetAttribute(p2_large_kernel<kLargeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kMidCap));
-        RS_CUDA_TRY(cudaFuncSetAttribute(p2_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2_mid_smem));
-        attr_done = true;
-    }
     // ---- P1: the larger row classes run concurrently on auxiliary streams and
     //      seed w_max; then the small rows, most of which skip their column maxima
     if (int rc = fork_aux(g, s)) return rc;
     if (g->n_hubs) {
         hub_p1_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[0]>>>(
-            g->off, g->col, g->lab, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->hkey,
-            g->hcnt, g->hagg, err);
+            g->off, g->col, g->lab, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items,
+            g->tune.hub_chunk, g->hkey, g->hcnt, g->hagg, err);
         RS_LAUNCHED(g, g->aux[0], "hub_p1_insert");
         hub_p1_finish_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, g->aux[0]>>>(
             g->off, g->lab, g->hubs, g->n_hubs, B, g->LG, g->hkey, g->hcnt, g->hagg, g->rec, g->Lall);
         RS_LAUNCHED(g, g->aux[0], "hub_p1_finish");
     }
     if (g->n_large) {
-        p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, p1_smem, g->aux[1]>>>(
-            g->off, g->col, g->lab, g->rows_large, g->n_large, B, g->LG, g->rec, g->Lall, err,
-            g->rsum, g->cl_col, g->cl_lab);
+        switch (g->tune.p1_cta_threads) {
+        case 128: launch_p1_large<128>(g, B, err, p1_smem); break;
+        case 512: launch_p1_large<512>(g, B, err, p1_smem); break;
+        default: launch_p1_large<256>(g, B, err, p1_smem); break;
+        }
         RS_LAUNCHED(g, g->aux[1], "p1_large");
     }
     if (g->n_mid) {
-        p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, 8), NT, 0, g->aux[2]>>>(
+        p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, cps), NT, 0, g->aux[2]>>>(
             g->off, g->col, g->lab, g->rows_mid, g->n_mid, B, g->LG, g->rec, g->Lall, err,
             g->rsum, g->cl_col, g->cl_lab);
         RS_LAUNCHED(g, g->aux[2], "p1_mid");
     }
     if (int rc = join_aux(g, s, 3)) return rc;
     if (g->n_small) {
-        p1_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, s>>>(
+        p1_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, s>>>(
             g->off, g->col, g->lab, g->rows_small, g->n_small, B, g->LG, g->rec, g->Lall,
             g->rsum, g->cl_col, g->cl_lab);
         RS_LAUNCHED(g, s, "p1_small");
@@ -1539,39 +1633,42 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     // ---- P2: every row class on its own stream
     if (int rc = fork_aux(g, s)) return rc;
     if (g->n_small) {
-        p2_small_kernel<<<grid_for(g->n_small, NT, 8), NT, 0, g->aux[0]>>>(
+        p2_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[0]>>>(
             g->off, g->rows_small, g->n_small, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin);
         RS_LAUNCHED(g, g->aux[0], "p2_small");
     }
     if (g->n_mid) {
-        p2_warp_kernel<<<grid_for(g->n_mid * 32, NT, 8), NT, 0, g->aux[1]>>>(
+        p2_warp_kernel<<<grid_for(g->n_mid * 32, NT, cps), NT, 0, g->aux[1]>>>(
             g->off, g->rows_mid, g->n_mid, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff, g->xcol,
             g->xS, g->xout, g->xin);
         RS_LAUNCHED(g, g->aux[1], "p2_warp");
         p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, p2_mid_smem, g->aux[5]>>>(
-            g->off, g->rows_mid, g->n_mid, g->k, 1 << 30, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
+            g->off, g->rows_mid, g->n_mid, B, 1 << 30, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin, err);
         RS_LAUNCHED(g, g->aux[5], "p2_mid");
     }
     if (g->n_large) {
         // large rows whose cross list fits a per-warp table go warp-per-row too
-        p2_warp_kernel<<<grid_for(g->n_large * 32, NT, 8), NT, 0, g->aux[2]>>>(
+        p2_warp_kernel<<<grid_for(g->n_large * 32, NT, cps), NT, 0, g->aux[2]>>>(
             g->off, g->rows_large, g->n_large, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin);
         RS_LAUNCHED(g, g->aux[2], "p2_warp");
         p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, p2_mid_smem, g->aux[2]>>>(
-            g->off, g->rows_large, g->n_large, g->k, kWarpCap / 2, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab,
+            g->off, g->rows_large, g->n_large, B, g->tune.p2_cta_dx, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab,
             g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
         RS_LAUNCHED(g, g->aux[2], "p2_large_warp");
-        p2_large_kernel<kLargeThreads><<<grid_for(g->n_large, 1, 2), kLargeThreads, p2_smem, g->aux[4]>>>(
-            g->off, g->rows_large, g->n_large, g->k, kWarpCap / 2 + 1, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
-            g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
+        switch (g->tune.p2_cta_threads) {
+        case 256: launch_p2_large<256>(g, B, err, p2_smem); break;
+        case 512: launch_p2_large<512>(g, B, err, p2_smem); break;
+        default: launch_p2_large<1024>(g, B, err, p2_smem); break;
+        }
         RS_LAUNCHED(g, g->aux[4], "p2_large");
     }
     if (g->n_hubs) {
         hub_p2_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
-            g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->rec, g->hkey, g->hq,
+            g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
+            g->hkey, g->hq,
             g->hitem_out, g->hitem_in, err);
         RS_LAUNCHED(g, g->aux[3], "hub_p2_insert");
         hub_p2_sigma_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, g->aux[3]>>>(
@@ -1579,24 +1676,22 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->xout, g->xin);
         RS_LAUNCHED(g, g->aux[3], "hub_p2_sigma");
         hub_p2_emit_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
-            g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->rec, g->hkey, g->hcnt,
+            g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
+            g->hkey, g->hcnt,
             g->hq, g->hsig, g->hitem_out, g->hitem_in, g->acc, g->xoff, g->xcol, g->xS, err);
         RS_LAUNCHED(g, g->aux[3], "hub_p2_emit");
     }
     if (int rc = join_aux(g, s, rs_graph::kAux)) return rc;
-    // ---- P3
-    unsigned long long *tri_n = (unsigned long long *)(g->d_flag + 48);
-    RS_CUDA_TRY(cudaMemsetAsync(tri_n, 0, sizeof(unsigned long long), s));
-    p3_list_kernel<<<grid_for(n, NT, 8), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->rec,
-                                                           (Tri *)g->tri, g->tri_cap, tri_n, g->acc, err);
+    // ---- P3: reverse values, then triangles
+    gx_mirror_kernel<<<grid_for(g->nnz, kMirTile, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xout, g->xin,
+                                                                   g->xR, err);
+    RS_LAUNCHED(g, s, "gx_mirror");
+    p3_list_kernel<<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xR, g->xout, g->rec, g->acc);
     RS_LAUNCHED(g, s, "p3_list");
-    p3_terms_kernel<<<grid_for(g->tri_cap, NT, 8), NT, 0, s>>>((const Tri *)g->tri, g->tri_cap, tri_n, g->xoff,
-                                                               g->xcol, g->xS, g->xin, g->rec, g->acc, err);
-    RS_LAUNCHED(g, s, "p3_terms");
     // ---- finalize
     graph_scale_kernel<<<(g->n_graphs + 255) / 256, 256, 0, s>>>(g->wmax_bits, g->n_graphs, g->winv);
     RS_LAUNCHED(g, s, "graph_scale");
-    finalize_kernel<<<grid_for(n, NT, 8), NT, 0, s>>>(n, g->off, g->acc, g->gid, g->winv, g->RD, scores);
+    finalize_kernel<<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->off, g->acc, g->gid, g->winv, g->RD, scores);
     RS_LAUNCHED(g, s, "finalize");
     return 0;
 }

@@ -220,6 +220,24 @@ static int ensure_topk_workspace(rs_graph *g, int64_t n) {
     RS_CUDA_TRY(cudaMalloc(&g->tk_keys, (2 * cap + kSortMax) * sizeof(unsigned long long)));
     RS_CUDA_TRY(cudaMalloc(&g->tk_ids, (2 * cap + kSortMax) * sizeof(uint32_t)));
     g->tk_cap = cap;
+    g->version++;                     // captured steps hold the old buffers
+    return 0;
+}
+
+static int tk_grid = 0;   // one CTA per SM (or what fits), found once per process
+
+// workspace for n scores and the selection kernel's launch shape
+int rs::topk_prepare(rs_graph *g, int64_t n) {
+    if (int rc = ensure_topk_workspace(g, n)) return rc;
+    if (!tk_grid) {
+        RS_CUDA_TRY(cudaFuncSetAttribute(tk_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTkSmem));
+        int dev = 0, sms = 0, per_sm = 0;
+        RS_CUDA_TRY(cudaGetDevice(&dev));
+        RS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        RS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tk_select_kernel, kTkThreads, kTkSmem));
+        if (per_sm < 1) return fail(RS_ECUDA, "rs_topk: selection kernel does not fit an SM");
+        tk_grid = sms * per_sm;
+    }
     return 0;
 }
 
@@ -227,17 +245,8 @@ int rs::topk_scores(rs_graph *g, const double *scores, int64_t n, int32_t k, int
                     cudaStream_t s) {
     if (k > kSortMax) return fail(RS_EINVAL, "rs_topk: k above 16384 is not supported");
     if (n > 2147483647LL) return fail(RS_EINVAL, "rs_topk: n too large");
-    if (int rc = ensure_topk_workspace(g, n)) return rc;
-    static int grid = 0;
-    if (!grid) {
-        RS_CUDA_TRY(cudaFuncSetAttribute(tk_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTkSmem));
-        int dev = 0, sms = 0, per_sm = 0;
-        RS_CUDA_TRY(cudaGetDevice(&dev));
-        RS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        RS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tk_select_kernel, kTkThreads, kTkSmem));
-        if (per_sm < 1) return fail(RS_ECUDA, "rs_topk: selection kernel does not fit an SM");
-        grid = sms * per_sm;
-    }
+    if (int rc = topk_prepare(g, n)) return rc;
+    const int grid = tk_grid;
     int64_t cap = g->tk_cap;
     TkArgs A;
     A.scores = scores; A.n = n; A.k = k; A.ids_out = ids; A.scores_out = out_scores;

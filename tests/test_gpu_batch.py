@@ -23,6 +23,7 @@ def test_batch_matches_oracle_and_single_graphs(rs):
     b = graphgen.dcsbm_batch(24, 500, 20000, seed=9, dmax=2000)
     G = rs.Graph.build_batch(b.graph_node_offsets, b.graph_k, b.offsets, b.cols, b.labels)
     s = G.score().cpu().numpy()
+    assert G.device_errors() == 0
     wmax = G.batch_omega_max()
     koff = np.concatenate([[0], np.cumsum(b.graph_k)[:-1]])
     rp, comm, cnt = [x.cpu().numpy() for x in G.interaction()]
