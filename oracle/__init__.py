@@ -159,8 +159,8 @@ def remove(offsets, cols, removed, nodes=(), edges=()):
     col = _c(cols, np.int32) if len(cols) else np.zeros(1, np.int32)
     n = off.shape[0] - 1
     assert removed.dtype == np.uint8 and removed.shape[0] == n and removed.flags.c_contiguous
-    nodes = _c(nodes, np.int32) if len(nodes) else np.zeros(1, np.int32)
-    nn = len(nodes) if len(nodes) and nodes.size else 0
+    nn = len(nodes)
+    nodes = _c(nodes, np.int32) if nn else np.zeros(1, np.int32)   # a valid pointer; nn = 0 removes none
     e = np.asarray(edges, dtype=np.int32).reshape(-1, 2) if len(edges) else np.zeros((0, 2), np.int32)
     es = _c(e[:, 0], np.int32) if e.shape[0] else np.zeros(1, np.int32)
     ed = _c(e[:, 1], np.int32) if e.shape[0] else np.zeros(1, np.int32)

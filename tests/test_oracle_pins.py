@@ -333,3 +333,25 @@ def test_pins_catch_planted_mistake(monkeypatch, mistake):
         mod.scores = scores
     del src_scores
     assert not _pins_pass(mod)
+
+
+def test_edge_only_removal_touches_no_node():
+    """Removing only edges flags no node and deletes exactly those edges (both directions)."""
+    rng = np.random.default_rng(19)
+    off, cols, labels = random_tiny_graph(rng, 30, 3, 0.3)
+    removed = np.zeros(30, np.uint8)
+    u = int(np.flatnonzero(np.diff(off) > 0)[0])
+    v = int(cols[off[u]])
+    new_off, new_cols, applied = oracle.remove(off, cols, removed, (), [(u, v)])
+    assert applied == 1
+    assert not removed.any()
+    adj = brute.adjacency(off, cols)
+    adj[u].discard(v); adj[v].discard(u)
+    e_off, e_cols = csr_from_edges(30, [(a, b) for a in range(30) for b in adj[a]])
+    np.testing.assert_array_equal(new_off, e_off)
+    np.testing.assert_array_equal(new_cols, e_cols)
+    # and nothing at all removes nothing
+    same_off, same_cols, none = oracle.remove(off, cols, np.zeros(30, np.uint8), (), ())
+    assert none == 0
+    np.testing.assert_array_equal(same_off, off)
+    np.testing.assert_array_equal(same_cols, cols)
