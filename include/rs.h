@@ -275,6 +275,66 @@ rs_status rs_step_launch(rs_step *st, void *stream);
 void rs_step_free(rs_step *st);
 
 /*
+ * Serving: what-if rescoring of resident graphs.  The paper has no counterpart
+ * (its dynamic networks are future work, Sec. VII; its removal experiments,
+ * Sec. VI-C, remove nodes cumulatively and rescore from scratch).
+ *
+ * A request removes nodes (with every incident edge) and undirected edges from
+ * one resident graph and asks for the top_k nodes of the changed graph's
+ * scores.  Every request applies to the resident (base) graph, never to
+ * another request's result, so a result does not depend on what else runs.
+ *
+ * rs_server_create -- take ownership of n_graphs graphs (single graphs, not
+ *   batches; rs_server_free frees them), score each once (its base state,
+ *   kept on the device) and create up to max_slots request slots: the requests
+ *   that run concurrently, each on its own stream.  Slots are created while
+ *   their device memory stays within budget_bytes (RS_EBUDGET if not even one
+ *   fits); full copies of graphs made by the full path count against the
+ *   budget too.  max_top_k bounds top_k (<= 16384).  mode:
+ *     RS_SERVE_INCREMENTAL  a request recounts only the rows it touches and
+ *                           updates the exact fixed-point sums by the terms that
+ *                           change (bit-identical to a full rescoring); requests
+ *                           whose touched rows exceed a slot's buffers, or touch
+ *                           more than a quarter of the CSR entries, are rescored
+ *                           in full instead;
+ *     RS_SERVE_FULL         every request restores a full copy of its graph,
+ *                           applies the removals and rescores it completely.
+ * rs_server_submit -- queue a request (lists are copied, ids are checked);
+ *   returns its ticket.  No device work starts before rs_server_poll.
+ * rs_server_poll -- start queued requests, in order, on free slots when the
+ *   memory budget allows, and collect finished ones without waiting (block = 0)
+ *   or until at least one finished or nothing is left (block != 0).  For each
+ *   of at most `max` finished requests: tickets[i], status[i] (RS_OK, or
+ *   RS_EBUDGET when it could not fit), path[i] (1 incremental, 0 full; may be
+ *   NULL), and its min(kmax, top_k) best (id, score) pairs at ids[i*kmax] and
+ *   scores[i*kmax] (host arrays, may be NULL); *n_done = how many.
+ * rs_server_info -- slots, device bytes held by slots and full copies, queued
+ *   and running requests (any out-pointer may be NULL).
+ * rs_server_whatif -- run one request at once (no request may be in flight) and
+ *   write the changed graph's scores for all n nodes to scores_out (device);
+ *   full != 0 forces the full path; *path_out (nullable) tells which ran.
+ *   Synchronises `stream`.
+ * rs_server_base_scores -- the base scores of a resident graph (device double[n]).
+ */
+typedef struct rs_server rs_server;
+#define RS_SERVE_INCREMENTAL 0
+#define RS_SERVE_FULL 1
+rs_status rs_server_create(rs_graph *const *graphs, int32_t n_graphs, int32_t max_slots, int64_t budget_bytes,
+                           int32_t max_top_k, int32_t mode, rs_server **out);
+rs_status rs_server_submit(rs_server *srv, int32_t graph, const int32_t *nodes, int64_t n_nodes,
+                           const int32_t *edge_src, const int32_t *edge_dst, int64_t n_edges, int32_t top_k,
+                           int64_t *ticket_out);
+rs_status rs_server_poll(rs_server *srv, int32_t max, int32_t kmax, int64_t *tickets, int32_t *status,
+                         int32_t *path, int32_t *ids, double *scores, int32_t *n_done, int32_t block);
+rs_status rs_server_info(const rs_server *srv, int32_t *slots, int64_t *bytes_used, int64_t *queued,
+                         int32_t *in_flight);
+rs_status rs_server_whatif(rs_server *srv, int32_t graph, const int32_t *nodes, int64_t n_nodes,
+                           const int32_t *edge_src, const int32_t *edge_dst, int64_t n_edges, int32_t full,
+                           double *scores_out, int32_t *path_out, void *stream);
+rs_status rs_server_base_scores(rs_server *srv, int32_t graph, double *scores_out, void *stream);
+void rs_server_free(rs_server *srv);
+
+/*
  * rs_device_errors -- synchronise `stream` and return in *flags_out the
  *   internal consistency checks that failed in g's kernels during the last
  *   rs_score (bit flags; 0 when none).  A non-zero value means a library bug

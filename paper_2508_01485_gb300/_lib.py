@@ -93,6 +93,21 @@ def lib():
         L.rs_step_launch.argtypes = [P, P]
         L.rs_step_free.restype = None
         L.rs_step_free.argtypes = [P]
+        L.rs_server_create.restype = I
+        L.rs_server_create.argtypes = [P, I32, I32, I64, I32, I32, ctypes.POINTER(P)]
+        L.rs_server_submit.restype = I
+        L.rs_server_submit.argtypes = [P, I32, P, I64, P, P, I64, I32, ctypes.POINTER(I64)]
+        L.rs_server_poll.restype = I
+        L.rs_server_poll.argtypes = [P, I32, I32, P, P, P, P, P, ctypes.POINTER(I32), I32]
+        L.rs_server_info.restype = I
+        L.rs_server_info.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                     ctypes.POINTER(I32)]
+        L.rs_server_whatif.restype = I
+        L.rs_server_whatif.argtypes = [P, I32, P, I64, P, P, I64, I32, P, ctypes.POINTER(I32), P]
+        L.rs_server_base_scores.restype = I
+        L.rs_server_base_scores.argtypes = [P, I32, P, P]
+        L.rs_server_free.restype = None
+        L.rs_server_free.argtypes = [P]
         L.rs_device_errors.restype = I
         L.rs_device_errors.argtypes = [P, ctypes.POINTER(I32), P]
         L.rs_free_graph.restype = None
@@ -337,6 +352,95 @@ class Step:
     def close(self):
         if self._h is not None and self._h.value:
             lib().rs_step_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- serving ------------------------------------------------------------------------------
+
+RS_SERVE_INCREMENTAL, RS_SERVE_FULL = 0, 1
+
+
+def _removal_arrays(nodes, edges):
+    nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.int32).reshape(-1))
+    e = np.asarray(edges, dtype=np.int32).reshape(-1, 2) if len(edges) else np.zeros((0, 2), np.int32)
+    return nodes, np.ascontiguousarray(e[:, 0]), np.ascontiguousarray(e[:, 1])
+
+
+def _cp(a):
+    return ctypes.c_void_p(a.ctypes.data if a.size else None)
+
+
+class Server:
+    """rs_server: what-if removal requests served concurrently on resident graphs.
+
+    Takes ownership of the given Graph objects (they must not be used afterwards)."""
+
+    def __init__(self, graphs, max_slots=8, budget_bytes=120 << 30, max_top_k=100, mode="incremental"):
+        handles = (ctypes.c_void_p * len(graphs))(*[g._h for g in graphs])
+        h = ctypes.c_void_p()
+        m = {"incremental": RS_SERVE_INCREMENTAL, "full": RS_SERVE_FULL}[mode]
+        _check(lib().rs_server_create(ctypes.cast(handles, ctypes.c_void_p), len(graphs), int(max_slots),
+                                      int(budget_bytes), int(max_top_k), m, ctypes.byref(h)))
+        self._h = h
+        self.n = [g.n for g in graphs]
+        self.max_top_k = int(max_top_k)
+        for g in graphs:                      # the server owns them now
+            g._h = None
+
+    def submit(self, graph, nodes=(), edges=(), top_k=100):
+        nd, es, ed = _removal_arrays(nodes, edges)
+        t = ctypes.c_int64(0)
+        _check(lib().rs_server_submit(self._h, int(graph), _cp(nd), nd.size, _cp(es), _cp(ed), es.size, int(top_k),
+                                      ctypes.byref(t)))
+        return t.value
+
+    def poll(self, max_results=256, block=False):
+        """[(ticket, status, path, ids, scores)] of the requests that finished."""
+        k = self.max_top_k
+        tickets = np.zeros(max_results, np.int64)
+        status = np.zeros(max_results, np.int32)
+        path = np.zeros(max_results, np.int32)
+        ids = np.zeros(max_results * k, np.int32)
+        vals = np.zeros(max_results * k, np.float64)
+        n = ctypes.c_int32(0)
+        _check(lib().rs_server_poll(self._h, max_results, k, tickets.ctypes.data, status.ctypes.data,
+                                    path.ctypes.data, ids.ctypes.data, vals.ctypes.data, ctypes.byref(n),
+                                    1 if block else 0))
+        return [(int(tickets[i]), int(status[i]), int(path[i]), ids[i * k:(i + 1) * k].copy(),
+                 vals[i * k:(i + 1) * k].copy()) for i in range(n.value)]
+
+    def info(self):
+        sl, b, q, f = ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
+        _check(lib().rs_server_info(self._h, ctypes.byref(sl), ctypes.byref(b), ctypes.byref(q), ctypes.byref(f)))
+        return {"slots": sl.value, "bytes": b.value, "queued": q.value, "in_flight": f.value}
+
+    def whatif(self, graph, nodes=(), edges=(), full=False, out=None, stream=None):
+        """The changed graph's scores for every node (a float64 CUDA tensor) and the path taken."""
+        import torch
+        nd, es, ed = _removal_arrays(nodes, edges)
+        if out is None:
+            out = torch.empty(max(self.n[graph], 1), dtype=torch.float64, device="cuda")
+        p = ctypes.c_int32(-1)
+        _check(lib().rs_server_whatif(self._h, int(graph), _cp(nd), nd.size, _cp(es), _cp(ed), es.size,
+                                      1 if full else 0, _ptr(out), ctypes.byref(p), _stream(stream)))
+        return out[: self.n[graph]], p.value
+
+    def base_scores(self, graph, stream=None):
+        import torch
+        out = torch.empty(max(self.n[graph], 1), dtype=torch.float64, device="cuda")
+        _check(lib().rs_server_base_scores(self._h, int(graph), _ptr(out), _stream(stream)))
+        torch.cuda.synchronize()
+        return out[: self.n[graph]]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rs_server_free(self._h)
         self._h = None
 
     def __del__(self):

@@ -69,7 +69,6 @@ struct __align__(8) RowSum {
     uint32_t L, pad;
 };
 
-// a G_x triangle (a, b, c), rank a < b < c, with its three out-direction values
 inline uint32_t pow2_at_least(uint64_t x) {
     uint32_t c = 1;
     while (c < x) c <<= 1;
