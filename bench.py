@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--profile-json", default="")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch parameters")
     ap.add_argument("--gen-workers", type=int, default=0, help="processes generating a batch (0: all cores)")
+    ap.add_argument("--serve-requests", type=int, default=20000, help="serve: requests per incremental pass")
+    ap.add_argument("--serve-plain", type=int, default=1500, help="serve: requests per plain (full) pass")
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-load", type=float, default=0.5, help="serve: open-loop rate as a fraction of capacity")
     return ap.parse_args()
 
 
@@ -541,6 +545,158 @@ def csrc_sha():
     return h.hexdigest()[:16]
 
 
+# ---- serving (config 5): what-if removal requests on resident graphs ----------------------
+
+SERVE_SEED, SERVE_GRAPHS, SERVE_N_MIN, SERVE_N_MAX = 5, 64, 10_000, 2_000_000
+SERVE_BUDGET = 120 << 30
+SERVE_TOPK = 100
+
+
+def _serve_graph(job):
+    """One resident graph: the 1M-node graph shape scaled (1 community per 1,000 nodes)."""
+    import graphgen
+    i, n = job
+    if n == 1_000_000 and i == SERVE_GRAPHS:
+        return graphgen.dcsbm_1m()
+    return graphgen.dcsbm(n, max(2, n // 1000), 50.0, 2.5, 8, min(5000, n - 1), 0.2, SERVE_SEED * 1_000_003 + i,
+                          name="serve-%d" % i)
+
+
+def serve_graphs(workers):
+    import graphgen
+    sizes = graphgen._batch_sizes(SERVE_GRAPHS, SERVE_N_MIN, SERVE_N_MAX, SERVE_SEED) + [1_000_000]
+    jobs = list(enumerate(sizes))
+    workers = workers or min(32, os.cpu_count() or 1)
+    if workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_serve_graph, jobs))
+    return [_serve_graph(j) for j in jobs]
+
+
+def serve_requests(graphs, base_scores, count, seed):
+    """Seeded request stream: a graph uniformly; k log-uniform on [1, 10000] (at most n/10);
+    half node removals, half edge removals; 70% of the targets among the graph's top-1% scorers
+    (edges: incident to one), 30% uniform."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    tops = [np.argsort(-s, kind="stable")[: max(1, len(s) // 100)] for s in base_scores]
+    degs = [np.diff(g.offsets) for g in graphs]
+    out = []
+    for _ in range(count):
+        gi = int(rng.integers(0, len(graphs)))
+        g, top, deg = graphs[gi], tops[gi], degs[gi]
+        k = int(min(round(np.exp(rng.random() * np.log(10000.0))), max(1, g.n // 10)))
+        hot = rng.random(k) < 0.7
+        pick = np.where(hot, top[rng.integers(0, len(top), k)], rng.integers(0, g.n, k)).astype(np.int64)
+        if rng.random() < 0.5:
+            out.append((gi, pick.astype(np.int32), np.zeros((0, 2), np.int32)))
+        else:
+            pick = pick[deg[pick] > 0]
+            nb = g.cols[g.offsets[pick] + (rng.random(len(pick)) * deg[pick]).astype(np.int64)]
+            out.append((gi, np.zeros(0, np.int32), np.stack([pick, nb], 1).astype(np.int32)))
+    return out
+
+
+def serve_pass(srv, reqs, rate):
+    """Submit the requests (all at once when rate is None, else at Poisson arrival times of
+    that rate) and collect them.  Returns (wall seconds, latencies in ms, paths, statuses)."""
+    import ctypes
+    import numpy as np
+    from paper_2508_01485_gb300._lib import lib, _check
+    L = lib()
+    m = 512
+    tickets = np.zeros(m, np.int64)
+    status = np.zeros(m, np.int32)
+    path = np.zeros(m, np.int32)
+    n_done = ctypes.c_int32(0)
+    arrive = {}
+    lat, paths, stats = [], [], []
+    rng = np.random.default_rng(77)
+    gaps = rng.exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
+    due = np.cumsum(gaps)
+    t0 = time.perf_counter()
+    i = 0
+    while len(lat) < len(reqs):
+        now = time.perf_counter() - t0
+        while i < len(reqs) and due[i] <= now:
+            gi, nodes, edges = reqs[i]
+            arrive[srv.submit(gi, nodes, edges, top_k=SERVE_TOPK)] = t0 + due[i]
+            i += 1
+        _check(L.rs_server_poll(srv._h, m, 0, tickets.ctypes.data, status.ctypes.data, path.ctypes.data, None, None,
+                                ctypes.byref(n_done), 0))
+        if n_done.value:
+            t = time.perf_counter()
+            for j in range(n_done.value):
+                lat.append((t - arrive.pop(int(tickets[j]))) * 1e3)
+                paths.append(int(path[j]))
+                stats.append(int(status[j]))
+    return time.perf_counter() - t0, np.array(lat), np.array(paths), np.array(stats)
+
+
+def serve_mode(rsgpu, gens, mode, reqs_cap, reqs_open, args):
+    import numpy as np
+    srv = rsgpu.Server([rsgpu.Graph.from_generated(g, validate=False) for g in gens], max_slots=args.serve_slots,
+                       budget_bytes=SERVE_BUDGET, max_top_k=SERVE_TOPK, mode=mode)
+    serve_pass(srv, reqs_cap[:64], None)                  # warm-up: kernels, copies, slots
+    wall, lat_c, paths_c, st_c = serve_pass(srv, reqs_cap, None)
+    capacity = len(reqs_cap) / wall
+    rate = args.serve_load * capacity
+    wall_o, lat, paths, st = serve_pass(srv, reqs_open, rate)
+    info = srv.info()
+    srv.close()
+    pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
+    return {"mode": mode, "slots": info["slots"], "device_bytes": info["bytes"],
+            "closed_loop": {"requests": len(reqs_cap), "requests_per_s": capacity,
+                            "incremental_share": float(paths_c.mean()) if len(paths_c) else None,
+                            "errors": int((st_c != 0).sum())},
+            "open_loop": {"requests": len(reqs_open), "offered_rps": rate, "achieved_rps": len(reqs_open) / wall_o,
+                          "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "p999_ms": pct(lat, 99.9),
+                          "incremental_share": float(paths.mean()) if len(paths) else None,
+                          "errors": int((st != 0).sum())}}
+
+
+def run_serve(args):
+    import numpy as np
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    gens = serve_graphs(args.gen_workers)                # before the first CUDA call
+    import paper_2508_01485_gb300 as rsgpu
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    # base scores for the request generator (the server computes its own, identical)
+    base = []
+    for g in gens:
+        G = rsgpu.Graph.from_generated(g, validate=False)
+        base.append(G.score().cpu().numpy())
+        G.close()
+    n_inc, n_plain = args.serve_requests, args.serve_plain
+    reqs_inc_c = serve_requests(gens, base, n_inc, 501)
+    reqs_inc_o = serve_requests(gens, base, n_inc, 502)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    inc = serve_mode(rsgpu, gens, "incremental", reqs_inc_c, reqs_inc_o, args)
+    plain = serve_mode(rsgpu, gens, "full", reqs_inc_c[:n_plain], reqs_inc_o[:n_plain], args)
+    clk = clocks.stop()
+    out = {
+        "metric": "served what-if requests/s (removals + rescoring + top-100), closed loop",
+        "value": inc["closed_loop"]["requests_per_s"], "unit": "requests/s", "n_gpus": 1,
+        "steps": n_inc, "warmup": 64, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "serve-%d-graphs" % len(gens), "graphs": len(gens),
+                   "n_total": int(sum(g.n for g in gens)), "m_total": int(sum(g.m for g in gens)),
+                   "sizes": "64 graphs with n log-uniform on [10000, 2000000] (1 community per 1,000 nodes, "
+                            "degrees 2.5 on [8, 5000], mixing 0.2) + the 1M-node graph",
+                   "requests": "k log-uniform on [1, 10000] (<= n/10), half nodes / half edges, 70% of targets "
+                               "among the graph's top-1% scorers; top-100 each; what-if on the base graph",
+                   "budget_bytes": SERVE_BUDGET, "slots": args.serve_slots, "open_loop_load": args.serve_load},
+        "serving": {"incremental": inc, "plain_full_rescoring": plain},
+        "vs_plain_closed_loop": inc["closed_loop"]["requests_per_s"] / plain["closed_loop"]["requests_per_s"],
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+
+
 # ---- reference arm: the CPU oracle ----------------------------------------------------------
 
 def run_reference(args):
@@ -582,6 +738,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

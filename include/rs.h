@@ -294,9 +294,10 @@ void rs_step_free(rs_step *st);
  *     RS_SERVE_INCREMENTAL  a request recounts only the rows it touches and
  *                           updates the exact fixed-point sums by the terms that
  *                           change (bit-identical to a full rescoring); requests
- *                           whose touched rows exceed a slot's buffers, or touch
- *                           more than a quarter of the CSR entries, are rescored
- *                           in full instead;
+ *                           whose touched rows exceed a slot's buffers, or whose
+ *                           touched rows' degrees (bounded from the removed
+ *                           nodes' 2-hop degree sums) exceed 1/48 of the CSR
+ *                           entries, are rescored in full instead;
  *     RS_SERVE_FULL         every request restores a full copy of its graph,
  *                           applies the removals and rescores it completely.
  * rs_server_submit -- queue a request (lists are copied, ids are checked);
@@ -312,7 +313,9 @@ void rs_step_free(rs_step *st);
  *   and running requests (any out-pointer may be NULL).
  * rs_server_whatif -- run one request at once (no request may be in flight) and
  *   write the changed graph's scores for all n nodes to scores_out (device);
- *   full != 0 forces the full path; *path_out (nullable) tells which ran.
+ *   full = 0 chooses as the server does, 1 forces the full path, 2 takes the
+ *   incremental path whenever the slot's buffers hold the request (whatever
+ *   its cost); *path_out (nullable) tells which ran.
  *   Synchronises `stream`.
  * rs_server_base_scores -- the base scores of a resident graph (device double[n]).
  */

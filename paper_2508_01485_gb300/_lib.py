@@ -421,14 +421,18 @@ class Server:
         return {"slots": sl.value, "bytes": b.value, "queued": q.value, "in_flight": f.value}
 
     def whatif(self, graph, nodes=(), edges=(), full=False, out=None, stream=None):
-        """The changed graph's scores for every node (a float64 CUDA tensor) and the path taken."""
+        """The changed graph's scores for every node (a float64 CUDA tensor) and the path taken.
+
+        full: False (as the server chooses), True (full rescoring) or "incremental" (the
+        incremental path whenever a slot's buffers hold the request)."""
         import torch
         nd, es, ed = _removal_arrays(nodes, edges)
         if out is None:
             out = torch.empty(max(self.n[graph], 1), dtype=torch.float64, device="cuda")
         p = ctypes.c_int32(-1)
         _check(lib().rs_server_whatif(self._h, int(graph), _cp(nd), nd.size, _cp(es), _cp(ed), es.size,
-                                      1 if full else 0, _ptr(out), ctypes.byref(p), _stream(stream)))
+                                      2 if full == "incremental" else (1 if full else 0), _ptr(out), ctypes.byref(p),
+                                      _stream(stream)))
         return out[: self.n[graph]], p.value
 
     def base_scores(self, graph, stream=None):

@@ -80,7 +80,7 @@ struct BaseView {
 };
 
 // counters of a slot
-enum { C_T = 0, C_WS, C_WB, C_TAB, C_X, C_WMAX, C_ERR, C_NCTR = 8 };
+enum { C_T = 0, C_WS, C_WB, C_TAB, C_X, C_WMAX, C_PAIR, C_TRI, C_NCTR = 8 };
 
 // per-request device state of a slot
 struct SlotView {
@@ -102,6 +102,9 @@ struct SlotView {
     uint32_t *hcnt;
     unsigned long long *hq;
     int64_t hub_cap;                 // slots per CTA
+    int32_t *pairs;                  // (x, y): a touched node and a G_x neighbour (2 words each)
+    int32_t *tris;                   // (x, y, z): base triangles through touched nodes (3 words each)
+    int64_t pair_cap, tri_cap;
     int32_t *err;
 };
 
@@ -305,15 +308,12 @@ __device__ __forceinline__ void add_W(const BaseView &B, const SlotView &S, int3
     else atomicOr(S.err, 4);
 }
 
-__global__ void sv_mark_w(BaseView B, SlotView S) {
-    int lane = threadIdx.x & 31;
-    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+__global__ void __launch_bounds__(kSvThreads) sv_mark_w(BaseView B, SlotView S) {
     int64_t nT = min((int64_t)S.ctr[C_T], S.tcap);
-    for (int64_t i = w; i < nT; i += nw) {
+    for (int64_t i = blockIdx.x; i < nT; i += gridDim.x) {          // a CTA per touched row
         int32_t x = S.tlist[i];
-        if (lane == 0) add_W(B, S, x);
-        for (int64_t e = B.off[x] + lane; e < B.off[x + 1]; e += 32) add_W(B, S, B.col[e]);
+        if (threadIdx.x == 0) add_W(B, S, x);
+        for (int64_t e = B.off[x] + threadIdx.x; e < B.off[x + 1]; e += blockDim.x) add_W(B, S, B.col[e]);
     }
 }
 
@@ -339,21 +339,47 @@ __device__ __forceinline__ uint64_t s_new(const BaseView &B, const SlotView &S, 
     return (S.flag[x] & kInT) ? S.trow[S.tidx[x]].rec.s_fix : B.rec[x].s_fix;
 }
 
+// A row w of W that is not touched keeps its cross list and weights; only the
+// communities of its touched cross neighbours get new group sums Q_w(c), so only
+// the terms it pushes to those communities change.  Such rows mark these
+// communities in the table first (count 0) and both sides then take only the
+// entries of marked communities.  A touched row redoes every entry.
+
+// warp: mark the affected communities of an untouched row
+__device__ __forceinline__ void mark_affected_warp(const SlotView &S, const RowSide &R, Tab t, uint32_t cap,
+                                                   int lane) {
+    for (uint32_t j = lane; j < cap; j += 32) t.key[j] = kEmpty;
+    __syncwarp();
+    for (int32_t e = lane; e < R.len; e += 32)
+        if (S.flag[R.ucol[e]] & kInT) tab_insert(t, R.ulab[e], 0, S.err);
+    __syncwarp();
+}
+
 // one side of a row on a warp: group sums by community, then every pushed term
-__device__ void type2_side_warp(const BaseView &B, const SlotView &S, const RowSide &R, bool neg, Tab t,
-                                uint32_t cap, int lane) {
-    for (uint32_t j = lane; j < cap; j += 32) { t.key[j] = kEmpty; t.cnt[j] = 0; t.q[2 * j] = 0; t.q[2 * j + 1] = 0; }
+__device__ void type2_side_warp(const BaseView &B, const SlotView &S, const RowSide &R, bool neg, bool filter,
+                                Tab t, uint32_t cap, int lane) {
+    for (uint32_t j = lane; j < cap; j += 32) {
+        if (!filter) t.key[j] = kEmpty;
+        t.cnt[j] = 0; t.q[2 * j] = 0; t.q[2 * j + 1] = 0;
+    }
     __syncwarp();
     for (int32_t e = lane; e < R.len; e += 32) {
         int32_t x = R.ucol[e];
-        int sl = tab_insert(t, R.ulab[e], 1, S.err);
+        int sl;
+        if (filter) {
+            sl = tab_find(t, R.ulab[e]);
+            if (sl < 0) continue;
+            atomicAdd(&t.cnt[sl], 1u);
+        } else {
+            sl = tab_insert(t, R.ulab[e], 1, S.err);
+        }
         if (sl >= 0) atomic_add_u128(t.q + 2 * sl, (u128)(neg ? B.rec[x].s_fix : s_new(B, S, x)));
     }
     __syncwarp();
     for (int32_t e = lane; e < R.len; e += 32) {
         int32_t u = R.ucol[e];
         int sl = tab_find(t, R.ulab[e]);
-        if (sl < 0) { atomicOr(S.err, 8); continue; }
+        if (sl < 0) { if (!filter) atomicOr(S.err, 8); continue; }
         uint32_t f = t.cnt[sl];
         if (f < 2) continue;                           // Q - s_u = 0
         u128 q = ((u128)t.q[2 * sl + 1] << 64) | t.q[2 * sl];
@@ -373,31 +399,41 @@ __global__ void __launch_bounds__(kSvThreads) sv_type2_warp(BaseView B, SlotView
     int64_t nW = min((int64_t)S.ctr[C_WS], S.wcap);
     for (int64_t i = w0; i < nW; i += nw) {
         int32_t w = S.wsmall[i];
+        bool touched = S.flag[w] & kInT;
         RowSide ro = old_side(B, w);
-        RowSide rn = new_side(B, S, w);
+        RowSide rn = touched ? new_side(B, S, w) : ro;
         uint32_t cap = table_cap(max(ro.len, rn.len), B.k);
         Tab t{skey[wid], scnt[wid], sq[wid], nullptr, cap - 1};
-        type2_side_warp(B, S, ro, true, t, cap, lane);
-        type2_side_warp(B, S, rn, false, t, cap, lane);
+        if (!touched) mark_affected_warp(S, ro, t, cap, lane);
+        type2_side_warp(B, S, ro, true, !touched, t, cap, lane);
+        type2_side_warp(B, S, rn, false, !touched, t, cap, lane);
     }
 }
 
-__device__ void type2_side_cta(const BaseView &B, const SlotView &S, const RowSide &R, bool neg, Tab t,
+__device__ void type2_side_cta(const BaseView &B, const SlotView &S, const RowSide &R, bool neg, bool filter, Tab t,
                                uint32_t cap) {
     for (uint32_t j = threadIdx.x; j < cap; j += blockDim.x) {
-        t.key[j] = kEmpty; t.cnt[j] = 0; t.q[2 * j] = 0; t.q[2 * j + 1] = 0;
+        if (!filter) t.key[j] = kEmpty;
+        t.cnt[j] = 0; t.q[2 * j] = 0; t.q[2 * j + 1] = 0;
     }
     __syncthreads();
     for (int32_t e = threadIdx.x; e < R.len; e += blockDim.x) {
         int32_t x = R.ucol[e];
-        int sl = tab_insert(t, R.ulab[e], 1, S.err);
+        int sl;
+        if (filter) {
+            sl = tab_find(t, R.ulab[e]);
+            if (sl < 0) continue;
+            atomicAdd(&t.cnt[sl], 1u);
+        } else {
+            sl = tab_insert(t, R.ulab[e], 1, S.err);
+        }
         if (sl >= 0) atomic_add_u128(t.q + 2 * sl, (u128)(neg ? B.rec[x].s_fix : s_new(B, S, x)));
     }
     __syncthreads();
     for (int32_t e = threadIdx.x; e < R.len; e += blockDim.x) {
         int32_t u = R.ucol[e];
         int sl = tab_find(t, R.ulab[e]);
-        if (sl < 0) { atomicOr(S.err, 8); continue; }
+        if (sl < 0) { if (!filter) atomicOr(S.err, 8); continue; }
         uint32_t f = t.cnt[sl];
         if (f < 2) continue;
         u128 q = ((u128)t.q[2 * sl + 1] << 64) | t.q[2 * sl];
@@ -414,8 +450,9 @@ __global__ void __launch_bounds__(kSvThreads) sv_type2_cta(BaseView B, SlotView 
     int64_t nW = min((int64_t)S.ctr[C_WB], S.wcap);
     for (int64_t i = blockIdx.x; i < nW; i += gridDim.x) {
         int32_t w = S.wbig[i];
+        bool touched = S.flag[w] & kInT;
         RowSide ro = old_side(B, w);
-        RowSide rn = new_side(B, S, w);
+        RowSide rn = touched ? new_side(B, S, w) : ro;
         uint32_t cap = table_cap(max(ro.len, rn.len), B.k);
         Tab t;
         if (cap <= (uint32_t)kCtaTab) {
@@ -425,8 +462,16 @@ __global__ void __launch_bounds__(kSvThreads) sv_type2_cta(BaseView B, SlotView 
             int64_t o = (int64_t)blockIdx.x * S.hub_cap;
             t = Tab{S.hkey + o, S.hcnt + o, S.hq + 2 * o, nullptr, cap - 1};
         }
-        type2_side_cta(B, S, ro, true, t, cap);
-        type2_side_cta(B, S, rn, false, t, cap);
+        if (!touched) {                                  // mark the affected communities
+            __syncthreads();
+            for (uint32_t j = threadIdx.x; j < cap; j += blockDim.x) t.key[j] = kEmpty;
+            __syncthreads();
+            for (int32_t e = threadIdx.x; e < ro.len; e += blockDim.x)
+                if (S.flag[ro.ucol[e]] & kInT) tab_insert(t, ro.ulab[e], 0, S.err);
+            __syncthreads();
+        }
+        type2_side_cta(B, S, ro, true, !touched, t, cap);
+        type2_side_cta(B, S, rn, false, !touched, t, cap);
     }
 }
 
@@ -516,30 +561,71 @@ __device__ __forceinline__ int32_t gx_nbr(const BaseView &B, int32_t p, int32_t 
     return B.xcol[base + B.rec[p].dx - 1 - (j - nout)];
 }
 
-// a warp per touched node x: every base triangle {x, y, z} (y < z), taken by the
-// smallest touched vertex of the triangle
-__global__ void __launch_bounds__(kSvThreads) sv_type1(BaseView B, SlotView S) {
+// 5a. pairs (x, y): x touched, y a base G_x neighbour of x; a triangle through
+//     several touched nodes belongs to the smallest of them, so y is skipped when
+//     it is touched and smaller than x
+__global__ void __launch_bounds__(kSvThreads) sv_tri_pairs(BaseView B, SlotView S) {
     int lane = threadIdx.x & 31;
-    int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t nT = min((int64_t)S.ctr[C_T], S.tcap);
-    for (int64_t i = w0; i < nT; i += nw) {
+    for (int64_t i = blockIdx.x; i < nT; i += gridDim.x) {              // a CTA per touched row
         int32_t x = S.tlist[i];
         if (B.rec[x].dx < 2) continue;                  // not in G_x: no base triangle
         int32_t xo = B.xout[x], xi = B.xin[x];
-        for (int32_t j = lane; j < xo + xi; j += 32) {
-            int32_t y = gx_nbr(B, x, j, xo);
-            if ((S.flag[y] & kInT) && y < x) continue;
-            int32_t yo = B.xout[y], yi = B.xin[y];
-            for (int32_t jj = 0; jj < yo + yi; ++jj) {
-                int32_t z = gx_nbr(B, y, jj, yo);
-                if (z <= y || z == x) continue;
-                if ((S.flag[z] & kInT) && z < x) continue;
-                if (gx_slot(B, x, z) < 0) continue;
-                triangle_delta(B, S, x, y, z);
+        for (int32_t j0 = 0; j0 < xo + xi; j0 += blockDim.x) {
+            int32_t j = j0 + threadIdx.x;
+            bool keep = false;
+            int32_t y = 0;
+            if (j < xo + xi) {
+                y = gx_nbr(B, x, j, xo);
+                keep = !((S.flag[y] & kInT) && y < x);
+            }
+            unsigned m = __ballot_sync(FULL, keep);
+            unsigned long long b0 = 0;
+            if (lane == 0 && m) b0 = atomicAdd(&S.ctr[C_PAIR], (unsigned long long)__popc(m));
+            b0 = __shfl_sync(FULL, b0, 0);
+            if (keep) {
+                unsigned long long p = b0 + __popc(m & ((1u << lane) - 1));
+                if ((int64_t)p < S.pair_cap) { S.pairs[2 * p] = x; S.pairs[2 * p + 1] = y; }
+                else atomicOr(S.err, 64);
             }
         }
     }
+}
+
+// is q a base G_x neighbour of p (either list)
+__device__ __forceinline__ bool gx_adj(const BaseView &B, int32_t p, int32_t q) { return gx_slot(B, p, q) >= 0; }
+
+// 5b. a warp per pair (x, y): the common G_x neighbours z > y of x and y (the
+//     lanes walk the shorter list, each z searched in the longer), each a base
+//     triangle {x, y, z}
+__global__ void __launch_bounds__(kSvThreads) sv_tri_find(BaseView B, SlotView S) {
+    int lane = threadIdx.x & 31;
+    int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t nP = min((int64_t)S.ctr[C_PAIR], S.pair_cap);
+    for (int64_t i = w0; i < nP; i += nwp) {
+        int32_t x = S.pairs[2 * i], y = S.pairs[2 * i + 1];
+        int32_t nx = B.xout[x] + B.xin[x], ny = B.xout[y] + B.xin[y];
+        bool walk_x = nx <= ny;
+        int32_t w = walk_x ? x : y, o = walk_x ? y : x;
+        int32_t wo = B.xout[w], len = walk_x ? nx : ny;
+        for (int32_t j = lane; j < len; j += 32) {
+            int32_t z = gx_nbr(B, w, j, wo);
+            if (z <= y || z == x) continue;
+            if ((S.flag[z] & kInT) && z < x) continue;
+            if (!gx_adj(B, o, z)) continue;
+            unsigned long long t = atomicAdd(&S.ctr[C_TRI], 1ull);
+            if ((int64_t)t < S.tri_cap) { S.tris[3 * t] = x; S.tris[3 * t + 1] = y; S.tris[3 * t + 2] = z; }
+            else triangle_delta(B, S, x, y, z);          // buffer full: finish it here
+        }
+    }
+}
+
+// 5c. one thread per triangle: old terms away, new ones back if it survives
+__global__ void __launch_bounds__(kSvThreads) sv_tri_delta(BaseView B, SlotView S) {
+    int64_t nt = min((int64_t)S.ctr[C_TRI], S.tri_cap);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x)
+        triangle_delta(B, S, S.tris[3 * i], S.tris[3 * i + 1], S.tris[3 * i + 2]);
 }
 
 // ---- 6. w_max, finalize ----------------------------------------------------------------
@@ -701,10 +787,8 @@ struct Slot {
     double *h_vals = nullptr;
     int32_t *h_err = nullptr;
     rs_graph *tk = nullptr;            // holds the top-K workspace
-    // full-path copy of one base graph
-    rs_graph *full = nullptr;
-    int32_t full_graph = -1;
-    int64_t full_bytes = 0;
+    // full path: the copy of the base graph the request in flight uses (index in the pool)
+    int32_t copy = -1;
     // the request in flight
     bool busy = false;
     Request req;
@@ -714,9 +798,20 @@ struct Slot {
 
 }  // namespace
 
+// a full copy of a base graph, for the full path
+struct Copy {
+    rs_graph *g = nullptr;
+    int32_t graph = -1;
+    int64_t bytes = 0;
+    bool busy = false;
+    uint64_t last_use = 0;
+};
+
 struct rs_server {
     std::vector<Base> bases;
     std::vector<Slot> slots;
+    std::vector<Copy> copies;
+    uint64_t clock = 0;
     std::deque<Request> queue;
     int32_t mode = RS_SERVE_INCREMENTAL;
     int32_t max_top_k = 0;
@@ -785,10 +880,9 @@ void free_slot(Slot &sl) {
     cudaFree(sl.v.dead); cudaFree(sl.v.flag); cudaFree(sl.v.tidx); cudaFree(sl.v.tlist); cudaFree(sl.v.wsmall);
     cudaFree(sl.v.wbig); cudaFree(sl.v.trow); cudaFree(sl.v.tkey); cudaFree(sl.v.tcnt); cudaFree(sl.v.xnew_col);
     cudaFree(sl.v.xnew_lab); cudaFree(sl.v.ctr); cudaFree(sl.v.acc); cudaFree(sl.v.scores); cudaFree(sl.v.hkey);
-    cudaFree(sl.v.hcnt); cudaFree(sl.v.hq); cudaFree(sl.v.err); cudaFree(sl.d_req); cudaFree(sl.ids); cudaFree(sl.vals);
+    cudaFree(sl.v.hcnt); cudaFree(sl.v.hq); cudaFree(sl.v.pairs); cudaFree(sl.v.tris); cudaFree(sl.v.err); cudaFree(sl.d_req); cudaFree(sl.ids); cudaFree(sl.vals);
     cudaFreeHost(sl.h_req); cudaFreeHost(sl.h_ids); cudaFreeHost(sl.h_vals); cudaFreeHost(sl.h_err);
     if (sl.tk) rs_free_graph(sl.tk);
-    if (sl.full) rs_free_graph(sl.full);
     if (sl.done) cudaEventDestroy(sl.done);
     if (sl.s) cudaStreamDestroy(sl.s);
     sl = Slot();
@@ -823,6 +917,10 @@ int alloc_slot(rs_server *srv, Slot &sl) {
     RS_CUDA_TRY(dalloc(&v.hkey, (size_t)hub_slots, b));
     RS_CUDA_TRY(dalloc(&v.hcnt, (size_t)hub_slots, b));
     RS_CUDA_TRY(dalloc(&v.hq, 2 * (size_t)hub_slots, b));
+    v.pair_cap = srv->xcap;
+    v.tri_cap = srv->xcap;
+    RS_CUDA_TRY(dalloc(&v.pairs, 2 * (size_t)v.pair_cap, b));
+    RS_CUDA_TRY(dalloc(&v.tris, 3 * (size_t)v.tri_cap, b));
     RS_CUDA_TRY(dalloc(&v.err, 1, b));
     sl.req_cap = 1 << 16;
     RS_CUDA_TRY(dalloc(&sl.d_req, (size_t)sl.req_cap, b));
@@ -852,11 +950,18 @@ Bounds request_bounds(const Base &b, const Request &r) {
     return x;
 }
 
-bool fits_incremental(const rs_server *srv, const Base &b, const Request &r) {
+bool fits_buffers(const rs_server *srv, const Base &b, const Request &r) {
     if ((int64_t)(r.nodes.size() + 2 * r.src.size()) > (int64_t)(1 << 16)) return false;
     Bounds x = request_bounds(b, r);
-    if (x.t > srv->tcap || x.dt > srv->xcap) return false;
-    return x.dt <= b.nnz / 4;            // beyond that a full rescoring is as cheap
+    return x.t <= srv->tcap && x.dt <= srv->xcap;
+}
+
+bool fits_incremental(const rs_server *srv, const Base &b, const Request &r) {
+    if (!fits_buffers(srv, b, r)) return false;
+    Bounds x = request_bounds(b, r);
+    // measured on the 1M-node graph: the delta kernels cost about as much as a full
+    // rescoring once the touched rows' degrees sum to ~1/40 of the CSR entries
+    return x.dt <= b.nnz / 48;
 }
 
 // stage the removal lists on the slot's stream; returns the device pointers
@@ -897,10 +1002,12 @@ int launch_incremental(rs_server *srv, Slot &sl, const Request &r) {
     int64_t tb = std::max<int64_t>(x.t, 1);
     int64_t wb = std::min<int64_t>(b.n, x.t + x.dt + 1);
     sv_trows<<<(int)std::min<int64_t>(tb, sms * 8), kSvThreads, 0, s>>>(B, S);
-    sv_mark_w<<<warps_grid(tb, 8), kSvThreads, 0, s>>>(B, S);
+    sv_mark_w<<<(int)std::min<int64_t>(tb, sms * 8), kSvThreads, 0, s>>>(B, S);
     sv_type2_warp<<<warps_grid(wb, 4), kSvThreads, 0, s>>>(B, S);
     sv_type2_cta<<<(int)std::min<int64_t>(wb, sms * 4), kSvThreads, 0, s>>>(B, S);
-    sv_type1<<<warps_grid(tb, 8), kSvThreads, 0, s>>>(B, S);
+    sv_tri_pairs<<<(int)std::min<int64_t>(tb, sms * 8), kSvThreads, 0, s>>>(B, S);
+    sv_tri_find<<<sms * 8, kSvThreads, 0, s>>>(B, S);
+    sv_tri_delta<<<sms * 8, kSvThreads, 0, s>>>(B, S);
     sv_wmax<<<grid_for(b.n, kSvThreads, 8), kSvThreads, 0, s>>>(B, S);
     sv_finalize<<<grid_for(b.n, kSvThreads, 8), kSvThreads, 0, s>>>(B, S);
     RS_CUDA_TRY(cudaGetLastError());
@@ -911,19 +1018,15 @@ int launch_incremental(rs_server *srv, Slot &sl, const Request &r) {
 // with both values, per-node records and workspaces)
 int64_t full_bytes_estimate(const Base &b) { return 37 * b.nnz + 170 * b.n + (16 << 20); }
 
-// full path: restore the slot's copy of the base graph, apply the removals, rescore
+// full path: restore a copy of the base graph, apply the removals, rescore
 int launch_full(rs_server *srv, Slot &sl, const Request &r) {
     Base &b = srv->bases[r.graph];
     cudaStream_t s = sl.s;
-    if (sl.full_graph != r.graph) {
-        if (sl.full) { rs_free_graph(sl.full); sl.full = nullptr; srv->used -= sl.full_bytes; sl.full_bytes = 0; }
-        sl.full_graph = -1;
-        if (int rc = rs_clone_graph(b.g, &sl.full, s)) return rc;
-        sl.full_bytes = full_bytes_estimate(b);
-        srv->used += sl.full_bytes;
-        sl.full_graph = r.graph;
+    Copy &cp = srv->copies[sl.copy];
+    if (!cp.g) {
+        if (int rc = rs_clone_graph(b.g, &cp.g, s)) return rc;
     }
-    rs_graph *g = sl.full;
+    rs_graph *g = cp.g;
     RS_CUDA_TRY(cudaMemcpyAsync(g->off, b.g->off, (b.n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     if (b.nnz) RS_CUDA_TRY(cudaMemcpyAsync(g->col, b.g->col, b.nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     if (b.n) RS_CUDA_TRY(cudaMemsetAsync(g->removed, 0, 4 * b.n, s));
@@ -936,9 +1039,49 @@ int launch_full(rs_server *srv, Slot &sl, const Request &r) {
     return 0;
 }
 
+// a copy of graph gi for the full path: an idle one, or a new one within the budget
+// (idle copies of other graphs are released, least recently used first); -1 if
+// none can be had now, -2 if none ever can (nothing else holds memory)
+int acquire_copy(rs_server *srv, int32_t gi) {
+    for (size_t i = 0; i < srv->copies.size(); ++i) {
+        Copy &c = srv->copies[i];
+        if (c.graph == gi && !c.busy) { c.busy = true; c.last_use = ++srv->clock; return (int)i; }
+    }
+    int64_t need = full_bytes_estimate(srv->bases[gi]);
+    while (srv->used + need > srv->budget) {
+        int victim = -1;
+        for (size_t i = 0; i < srv->copies.size(); ++i) {
+            Copy &c = srv->copies[i];
+            if (c.g && !c.busy && (victim < 0 || c.last_use < srv->copies[victim].last_use)) victim = (int)i;
+        }
+        if (victim < 0) break;
+        Copy &v = srv->copies[victim];
+        rs_free_graph(v.g);
+        srv->used -= v.bytes;
+        v = Copy();
+    }
+    if (srv->used + need > srv->budget) {
+        bool any = false;
+        for (auto &c : srv->copies) any |= c.busy;
+        for (auto &sl : srv->slots) any |= sl.busy;
+        return any ? -1 : -2;
+    }
+    int idx = -1;
+    for (size_t i = 0; i < srv->copies.size(); ++i)
+        if (!srv->copies[i].g && srv->copies[i].graph < 0) { idx = (int)i; break; }
+    if (idx < 0) { srv->copies.push_back(Copy()); idx = (int)srv->copies.size() - 1; }
+    Copy &c = srv->copies[idx];
+    c.graph = gi;
+    c.bytes = need;
+    c.busy = true;
+    c.last_use = ++srv->clock;
+    srv->used += need;
+    return idx;                    // the copy itself is made on the slot's stream
+}
+
 int start_request(rs_server *srv, Slot &sl, Request &&r, int refuse = 0) {
     const Base &b = srv->bases[r.graph];
-    bool inc = srv->mode == RS_SERVE_INCREMENTAL && fits_incremental(srv, b, r);
+    bool inc = sl.copy < 0;
     int rc = refuse ? refuse : inc ? launch_incremental(srv, sl, r) : launch_full(srv, sl, r);
     if (!rc && b.n > 0) rc = topk_scores(sl.tk, sl.v.scores, b.n, r.top_k, sl.ids, sl.vals, sl.s);
     if (!rc) {
@@ -1052,6 +1195,7 @@ extern "C" rs_status rs_server_poll(rs_server *srv, int32_t max, int32_t kmax, i
             if (ids) for (int32_t j = 0; j < k; ++j) ids[(int64_t)done * kmax + j] = st ? -1 : sl.h_ids[j];
             if (scores) for (int32_t j = 0; j < k; ++j) scores[(int64_t)done * kmax + j] = st ? 0.0 : sl.h_vals[j];
             sl.busy = false;
+            if (sl.copy >= 0) { srv->copies[sl.copy].busy = false; sl.copy = -1; }
             ++done;
         }
         // admit queued requests, in order, into free slots within the memory budget
@@ -1062,24 +1206,12 @@ extern "C" rs_status rs_server_poll(rs_server *srv, int32_t max, int32_t kmax, i
             const Base &b = srv->bases[front.graph];
             bool need_full = srv->mode == RS_SERVE_FULL || !fits_incremental(srv, b, front);
             int refuse = 0;
-            if (need_full && sl.full_graph != front.graph) {
-                // a full copy of the graph must fit: release the copies idle slots hold
-                int64_t need = full_bytes_estimate(b) - sl.full_bytes;
-                for (auto &o : srv->slots) {
-                    if (srv->used + need <= srv->budget) break;
-                    if (o.busy || !o.full || &o == &sl) continue;
-                    rs_free_graph(o.full);
-                    o.full = nullptr;
-                    o.full_graph = -1;
-                    srv->used -= o.full_bytes;
-                    o.full_bytes = 0;
-                }
-                if (srv->used + need > srv->budget) {
-                    bool any_busy = false;
-                    for (auto &o : srv->slots) any_busy |= o.busy;
-                    if (any_busy) break;                     // wait for memory to free up
-                    refuse = fail(RS_EBUDGET, "rs_server: the request does not fit the memory budget");
-                }
+            sl.copy = -1;
+            if (need_full) {
+                int c = acquire_copy(srv, front.graph);
+                if (c == -1) break;                          // wait for memory to free up
+                if (c == -2) refuse = fail(RS_EBUDGET, "rs_server: the request does not fit the memory budget");
+                else sl.copy = c;
             }
             Request r = std::move(srv->queue.front());
             srv->queue.pop_front();
@@ -1129,8 +1261,15 @@ extern "C" rs_status rs_server_whatif(rs_server *srv, int32_t graph, const int32
         if (r.src[i] < 0 || r.src[i] >= b.n || r.dst[i] < 0 || r.dst[i] >= b.n)
             return (rs_status)fail(RS_EINVAL, "rs_server_whatif: edge endpoint out of range");
     Slot &sl = srv->slots[0];
-    bool inc = !full && fits_incremental(srv, b, r);
+    bool inc = full == 2 ? fits_buffers(srv, b, r) : (!full && fits_incremental(srv, b, r));
+    sl.copy = -1;
+    if (!inc) {
+        int c = acquire_copy(srv, graph);
+        if (c < 0) return (rs_status)fail(RS_EBUDGET, "rs_server_whatif: a full copy does not fit the memory budget");
+        sl.copy = c;
+    }
     int rc = inc ? launch_incremental(srv, sl, r) : launch_full(srv, sl, r);
+    if (sl.copy >= 0) { srv->copies[sl.copy].busy = false; sl.copy = -1; }
     if (rc) return (rs_status)rc;
     int32_t err = 0;
     cudaError_t e = cudaMemcpyAsync(&err, sl.v.err, sizeof(int32_t), cudaMemcpyDeviceToHost, sl.s);
@@ -1161,6 +1300,8 @@ extern "C" void rs_server_free(rs_server *srv) {
         if (sl.busy) cudaEventSynchronize(sl.done);
         free_slot(sl);
     }
+    for (auto &c : srv->copies)
+        if (c.g) rs_free_graph(c.g);
     for (auto &b : srv->bases) {
         cudaFree(b.acc); cudaFree(b.scores); cudaFree(b.rowmax);
         rs_free_graph(b.g);

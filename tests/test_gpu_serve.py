@@ -78,20 +78,19 @@ def _requests(g, base_scores, seed):
 
 def test_incremental_equals_full_rescoring(served):
     srv, gens = served
-    n_inc = n_all = 0
     for gi, g in enumerate(gens):
         base = srv.base_scores(gi).cpu().numpy()
         for ri, (nodes, edges) in enumerate(_requests(g, base, 100 + gi)):
-            inc, p_inc = srv.whatif(gi, nodes, edges)
+            inc, p_inc = srv.whatif(gi, nodes, edges, full="incremental")
+            assert p_inc == 1, (gi, ri)
             inc = _bits(inc)
             full, p_full = srv.whatif(gi, nodes, edges, full=True)
             assert p_full == 0
             np.testing.assert_array_equal(inc, _bits(full), err_msg="graph %d request %d" % (gi, ri))
-            if ri in (0, 4, 8):                 # empty, one edge, absent edges: always incremental
-                assert p_inc == 1, (gi, ri)
-            n_inc += p_inc
-            n_all += 1
-    assert n_inc >= 0.75 * n_all
+            auto, p_auto = srv.whatif(gi, nodes, edges)
+            np.testing.assert_array_equal(_bits(auto), inc)
+            if ri in (0, 4, 8):                 # empty, one edge, absent edges: cheap, always incremental
+                assert p_auto == 1, (gi, ri)
 
 
 def test_empty_request_gives_base_scores(served):
@@ -108,7 +107,8 @@ def test_incremental_matches_oracle(served):
     base = srv.base_scores(1).cpu().numpy()
     rng = np.random.default_rng(7)
     for nodes, edges in _requests(g, base, 7)[1:7]:
-        got, p = srv.whatif(1, nodes, edges)
+        got, p = srv.whatif(1, nodes, edges, full="incremental")
+        assert p == 1
         got = got.cpu().numpy()
         removed = np.zeros(g.n, np.uint8)
         off, col, _ = oracle.remove(g.offsets, g.cols, removed, nodes, edges)
