@@ -275,6 +275,20 @@ rs_status rs_step_launch(rs_step *st, void *stream);
 void rs_step_free(rs_step *st);
 
 /*
+ * rs_target_subset -- the graph restricted to target communities.  The paper
+ * searches spanners in user-provided (large) communities only and counts only
+ * neighbours in them (T = sum of f_l over the k targets, Sec. V-A); its
+ * experiments take the k largest communities (Sec. VI).  targets: host
+ * int32[n_targets], distinct labels of g in [0, k).  The new graph (free with
+ * rs_free_graph) keeps every node id; every edge with an endpoint outside the
+ * targets is dropped, so such nodes are isolated and score 0; target i becomes
+ * community i and k = n_targets (so w_max ranges over the target columns).
+ * Not for batches.  Synchronises `stream`.
+ */
+rs_status rs_target_subset(const rs_graph *g, const int32_t *targets, int32_t n_targets, void *stream,
+                           rs_graph **out);
+
+/*
  * Serving: what-if rescoring of resident graphs.  The paper has no counterpart
  * (its dynamic networks are future work, Sec. VII; its removal experiments,
  * Sec. VI-C, remove nodes cumulatively and rescore from scratch).

@@ -93,6 +93,8 @@ def lib():
         L.rs_step_launch.argtypes = [P, P]
         L.rs_step_free.restype = None
         L.rs_step_free.argtypes = [P]
+        L.rs_target_subset.restype = I
+        L.rs_target_subset.argtypes = [P, P, I32, P, ctypes.POINTER(P)]
         L.rs_server_create.restype = I
         L.rs_server_create.argtypes = [P, I32, I32, I64, I32, I32, ctypes.POINTER(P)]
         L.rs_server_submit.restype = I
@@ -293,6 +295,13 @@ class Graph:
         c = ctypes.c_int64(0)
         _check(lib().rs_launch_count(self._h, ctypes.byref(c)))
         return c.value
+
+    def target_subset(self, targets, stream=None):
+        """rs_target_subset: a new Graph restricted to the target communities (target i -> community i)."""
+        t = np.ascontiguousarray(np.asarray(targets, dtype=np.int32).reshape(-1))
+        h = ctypes.c_void_p()
+        _check(lib().rs_target_subset(self._h, ctypes.c_void_p(t.ctypes.data), t.size, _stream(stream), ctypes.byref(h)))
+        return Graph(h, self.n, t.size)
 
     def clone(self, stream=None):
         h = ctypes.c_void_p()

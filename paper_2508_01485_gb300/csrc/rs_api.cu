@@ -991,6 +991,75 @@ extern "C" rs_status rs_apply_removals(rs_graph *g, const int32_t *nodes, int64_
 }
 
 // ---------------------------------------------------------------------------
+// target-community subset: drop every edge with an endpoint outside the targets
+// ---------------------------------------------------------------------------
+__global__ void mark_nontarget_kernel(const int64_t *off, const int32_t *col, const int32_t *lab, const int32_t *map,
+                                      int64_t n, uint32_t *dead) {
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = w; v < n; v += nw) {
+        bool out_v = map[lab[v]] < 0;
+        for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32)
+            if (out_v || map[lab[col[e]]] < 0) mark_dead(dead, e);
+    }
+}
+__global__ void relabel_kernel(int32_t *lab, const int32_t *map, int64_t n) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) { int32_t m = map[lab[v]]; lab[v] = m >= 0 ? m : 0; }
+}
+
+extern "C" rs_status rs_target_subset(const rs_graph *g, const int32_t *targets, int32_t n_targets, void *stream,
+                                      rs_graph **out) {
+    cudaStream_t s = as_stream(stream);
+    if (!g || !targets || !out || n_targets < 1) return (rs_status)fail(RS_EINVAL, "rs_target_subset: bad arguments");
+    if (g->n_graphs != 1) return (rs_status)fail(RS_EINVAL, "rs_target_subset: not for batches");
+    std::vector<int32_t> map(std::max(g->k, 1), -1);
+    for (int32_t i = 0; i < n_targets; ++i) {
+        if (targets[i] < 0 || targets[i] >= g->k) return (rs_status)fail(RS_EINVAL, "rs_target_subset: target outside [0, k)");
+        if (map[targets[i]] >= 0) return (rs_status)fail(RS_EINVAL, "rs_target_subset: repeated target");
+        map[targets[i]] = i;
+    }
+    rs_graph *c = nullptr;
+    if (rs_status st = rs_clone_graph(g, &c, stream)) return st;
+    auto bail = [&](int rc) { free_graph(c); return (rs_status)rc; };
+    int32_t *d_map = nullptr;
+    int64_t n = c->n;
+    cudaError_t e = dmalloc(&d_map, map.size());
+    if (!e) e = cudaMemcpyAsync(d_map, map.data(), map.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (!e && c->nnz) e = cudaMemsetAsync(c->dead, 0, 4 * ((c->nnz + 31) / 32), s);
+    if (!e && n > 0) {
+        int grid = grid_for(n * 32, kThreads, 16);
+        mark_nontarget_kernel<<<grid, kThreads, 0, s>>>(c->off, c->col, c->lab, d_map, n, (uint32_t *)c->dead);
+        e = cudaGetLastError();
+        if (!e) {
+            alive_degree_kernel<<<grid, kThreads, 0, s>>>(c->off, (uint32_t *)c->dead, n, c->off_alt);
+            e = cudaGetLastError();
+        }
+        if (!e) {
+            if (int rc = inclusive_scan_i64(c->off_alt + 1, n, c->scan_tmp, s)) { cudaFree(d_map); return bail(rc); }
+            compact_rows_kernel<<<grid, kThreads, 0, s>>>(c->off, c->col, (uint32_t *)c->dead, n, c->off_alt, c->col_alt);
+            e = cudaGetLastError();
+        }
+        if (!e) {
+            std::swap(c->off, c->off_alt);
+            std::swap(c->col, c->col_alt);
+            relabel_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->lab, d_map, n);
+            e = cudaGetLastError();
+        }
+    }
+    if (!e) e = cudaStreamSynchronize(s);
+    cudaFree(d_map);
+    if (e) return bail(cuda_fail(e, "rs_target_subset"));
+    c->k = n_targets;
+    if (int rc = classify_rows(c, s)) return bail(rc);
+    if (int rc = build_tables(c, s)) return bail(rc);
+    if ((e = cudaStreamSynchronize(s))) return bail(cuda_fail(e, "rs_target_subset"));
+    *out = c;
+    return RS_OK;
+}
+
+// ---------------------------------------------------------------------------
 // interaction table (sorted per row): labels of each row are sorted in place
 // in a scratch copy, then run-length encoded
 // ---------------------------------------------------------------------------
