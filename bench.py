@@ -431,13 +431,16 @@ def run_ours(args):
     avg_ms = top["ms"] / args.steps            # the kernel's device time per step (all its launches)
     hbm, peak_kind = peaks()
     kb = kernel_bytes(top_name, st)
+    # DRAM bytes of the dominant kernel per step, from the committed ncu summary of the
+    # same sources (null when the kernels changed since it was taken)
     traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
+    for tr_path in glob.glob(os.path.join(ROOT, "profiles", "traffic_*.md")):
         with open(tr_path) as f:
-            tr = json.load(f)
-        if tr.get("csrc_sha") == csrc_sha() and tr.get("workload") == args.workload:
-            traffic = tr.get("kernels", {}).get(top_name)
+            for line in f:
+                if line.startswith("traffic-json:"):
+                    tr = json.loads(line.split(":", 1)[1])
+                    if tr.get("csrc_sha") == csrc_sha() and tr.get("workload") == args.workload:
+                        traffic = tr.get("kernels", {}).get(top_name)
     roofline = {
         "bound": "hbm", "kernel": top_name,
         "achieved": (kb / (avg_ms / 1e3) / 1e9) if kb else None,
