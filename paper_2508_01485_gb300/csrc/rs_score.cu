@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
 // the whole cross list, so warp matching gives each community's count and
 // Type-II sum directly; no table, no shared memory beyond a staging word per lane.
 __global__ void __launch_bounds__(kThreads) p2_warp_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows,
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_dev,
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
@@ -673,6 +673,7 @@ __global__ void __launch_bounds__(kThreads) p2_warp_kernel(
     uint64_t *st = stage + (threadIdx.x & ~31);
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nrows = *nrows_dev;               // rows of this kernel, counted by p2_split
     for (int64_t i = warp; i < nrows; i += nwarps) {
         int32_t w = rows[i];
         NodeRec rw = rec[w];
@@ -727,7 +728,7 @@ __global__ void __launch_bounds__(kThreads) p2_warp_kernel(
 constexpr int kMidSlotBytes = 4 + 4 + 16;   // key, count, 2-word sum
 
 __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, Batch B, int32_t dx_max,
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_dev, Batch B, int32_t dx_max,
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
@@ -739,6 +740,7 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
     unsigned char *base_w = smem + (size_t)wid * kWarpCap * kMidSlotBytes;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nrows = *nrows_dev;               // rows of this kernel, counted by p2_split
     for (int64_t i = warp; i < nrows; i += nwarps) {
         int32_t w = rows[i];
         int64_t b = off[w];
@@ -853,7 +855,7 @@ __device__ __forceinline__ void gx_round(bool out, bool in, int64_t xb, int32_t 
 
 template <int NT>
 __global__ void __launch_bounds__(NT) p2_large_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows, Batch B, int32_t dx_min,
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_dev, Batch B, int32_t dx_min,
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
@@ -863,6 +865,7 @@ __global__ void __launch_bounds__(NT) p2_large_kernel(
     __shared__ uint64_t stage[NT];
     int tid = threadIdx.x, lane = tid & 31;
     uint64_t *st = stage + (tid & ~31);
+    const int64_t nrows = *nrows_dev;               // rows of this kernel, counted by p2_split
     for (int64_t i = blockIdx.x; i < nrows; i += gridDim.x) {
         int32_t w = rows[i];
         int64_t b = off[w];
@@ -1405,6 +1408,38 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
 }
 
 // ======================================================================================
+// P2 row lists by cross degree (known after P1): each P2 kernel then walks only its rows
+//   0 mid rows, dx <= 32 (p2_warp)      1 mid rows, dx > 32 (p2_mid)
+//   2 large rows, dx <= 32 (p2_warp)    3 large rows, 32 < dx <= dx_cta (p2_mid)
+//   4 large rows, dx > dx_cta (p2_large)
+// ======================================================================================
+__device__ __forceinline__ void append_row(int32_t *list, int32_t *cnt, bool take, int32_t v) {
+    unsigned m = __ballot_sync(FULL, take);
+    int lane = threadIdx.x & 31;
+    int32_t base = 0;
+    if (m && lane == __ffs(m) - 1) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(FULL, base, __ffs(m ? m : 1u) - 1);
+    if (take) list[base + __popc(m & lanemask_lt())] = v;
+}
+
+__global__ void p2_split_kernel(const int32_t *__restrict__ rows_mid, int64_t n_mid,
+                                const int32_t *__restrict__ rows_large, int64_t n_large,
+                                const NodeRec *__restrict__ rec, int32_t dx_cta, int32_t *lists, int32_t *cnt) {
+    int64_t total = n_mid + n_large;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < total; i0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = i0 + threadIdx.x;
+        bool act = i < total;
+        bool mid = i < n_mid;
+        int32_t v = act ? (mid ? rows_mid[i] : rows_large[i - n_mid]) : 0;
+        int32_t dx = act ? rec[v].dx : 0;
+        int cls = !act ? -1 : mid ? (dx <= 32 ? 0 : 1) : (dx <= 32 ? 2 : dx <= dx_cta ? 3 : 4);
+        int32_t *base[5] = {lists, lists + n_mid, lists + 2 * n_mid, lists + 2 * n_mid + n_large,
+                            lists + 2 * n_mid + 2 * n_large};
+        for (int c = 0; c < 5; ++c) append_row(base[c], cnt + c, cls == c, v);
+    }
+}
+
+// ======================================================================================
 // finalize: R(u) = acc(u) / (w_max d (d - 1))
 // ======================================================================================
 __global__ void graph_scale_kernel(const unsigned long long *__restrict__ wmax_bits, int32_t ng, double *winv) {
@@ -1460,8 +1495,9 @@ static void launch_p1_large(rs_graph *g, const Batch &B, int *err, size_t smem) 
 }
 template <int NT>
 static void launch_p2_large(rs_graph *g, const Batch &B, int *err, size_t smem) {
+    int32_t *L4 = g->p2rows + 2 * g->n_mid + 2 * g->n_large;
     p2_large_kernel<NT><<<grid_for(g->n_large, 1, 2), NT, smem, g->aux[4]>>>(
-        g->off, g->rows_large, g->n_large, B, g->tune.p2_cta_dx + 1, g->LG, g->rec, g->rsum, g->cl_col,
+        g->off, L4, g->p2cnt + 4, B, g->tune.p2_cta_dx + 1, g->LG, g->rec, g->rsum, g->cl_col,
         g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
 }
 
@@ -1526,6 +1562,14 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     if (int rc = inclusive_scan_i64(g->xoff + 1, n, g->scan_tmp, s, &scan_launches)) return rc;
     g->launches += scan_launches - 1;
     prof_mark(g, s, "gx_scan", true);
+    const int64_t nm = g->n_mid, nl = g->n_large;
+    int32_t *L0 = g->p2rows, *L1 = L0 + nm, *L2 = L0 + 2 * nm, *L3 = L2 + nl;
+    if (nm + nl) {
+        RS_CUDA_TRY(cudaMemsetAsync(g->p2cnt, 0, 8 * sizeof(int32_t), s));
+        p2_split_kernel<<<grid_for(nm + nl, 256, 8), 256, 0, s>>>(g->rows_mid, nm, g->rows_large, nl, g->rec,
+                                                                  g->tune.p2_cta_dx, g->p2rows, g->p2cnt);
+        RS_LAUNCHED(g, s, "p2_split");
+    }
     // ---- P2: every row class on its own stream
     if (int rc = fork_aux(g, s)) return rc;
     if (g->n_small) {
@@ -1536,22 +1580,22 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     }
     if (g->n_mid) {
         p2_warp_kernel<<<grid_for(g->n_mid * 32, NT, cps), NT, 0, g->aux[1]>>>(
-            g->off, g->rows_mid, g->n_mid, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff, g->xcol,
+            g->off, L0, g->p2cnt + 0, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff, g->xcol,
             g->xS, g->xout, g->xin);
         RS_LAUNCHED(g, g->aux[1], "p2_warp");
         p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, p2_mid_smem, g->aux[5]>>>(
-            g->off, g->rows_mid, g->n_mid, B, 1 << 30, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
+            g->off, L1, g->p2cnt + 1, B, 1 << 30, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin, err);
         RS_LAUNCHED(g, g->aux[5], "p2_mid");
     }
     if (g->n_large) {
         // large rows whose cross list fits a per-warp table go warp-per-row too
         p2_warp_kernel<<<grid_for(g->n_large * 32, NT, cps), NT, 0, g->aux[2]>>>(
-            g->off, g->rows_large, g->n_large, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
+            g->off, L2, g->p2cnt + 2, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin);
         RS_LAUNCHED(g, g->aux[2], "p2_warp");
         p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, p2_mid_smem, g->aux[2]>>>(
-            g->off, g->rows_large, g->n_large, B, g->tune.p2_cta_dx, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab,
+            g->off, L3, g->p2cnt + 3, B, g->tune.p2_cta_dx, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab,
             g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
         RS_LAUNCHED(g, g->aux[2], "p2_large_warp");
         switch (g->tune.p2_cta_threads) {
