@@ -48,7 +48,7 @@ def _load():
         lib = ctypes.CDLL(build())
         P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         lib.rso_new.restype = P
-        lib.rso_new.argtypes = [I64, I32, P, P, P, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
+        lib.rso_new.argtypes = [I64, I32, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
         lib.rso_free.argtypes = [P]
         lib.rso_wmax.restype = D; lib.rso_wmax.argtypes = [P]
         lib.rso_table_size.restype = I64; lib.rso_table_size.argtypes = [P]
@@ -72,7 +72,7 @@ def _c(a, dtype):
 class Oracle:
     """Oracle state for one graph: community tables, weights and w_max."""
 
-    def __init__(self, offsets, cols, labels, k, validate=True):
+    def __init__(self, offsets, cols, labels, k, validate=True, alg2=False):
         lib = _load()
         self._off = _c(offsets, np.int64)
         self._col = _c(cols, np.int32) if len(cols) else np.zeros(1, np.int32)
@@ -81,13 +81,13 @@ class Oracle:
         self.k = int(k)
         err = ctypes.create_string_buffer(256)
         self._h = lib.rso_new(self.n, self.k, self._off.ctypes.data, self._col.ctypes.data,
-                              self._lab.ctypes.data, 1 if validate else 0, err, 256)
+                              self._lab.ctypes.data, 1 if validate else 0, 1 if alg2 else 0, err, 256)
         if not self._h:
             raise ValueError("oracle: " + err.value.decode())
 
     @classmethod
-    def from_graph(cls, g, validate=True):
-        return cls(g.offsets, g.cols, g.labels, g.k, validate)
+    def from_graph(cls, g, validate=True, alg2=False):
+        return cls(g.offsets, g.cols, g.labels, g.k, validate, alg2)
 
     def close(self):
         if getattr(self, "_h", None):

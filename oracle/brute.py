@@ -37,11 +37,14 @@ def entropy_bits(freqs):
     return -math.fsum((f / total) * math.log2(f / total) for f in freqs)
 
 
-def weight(adj, labels, u_comm, v):
+def weight(adj, labels, u_comm, v, alg2=False):
+    """w_v(u) with |L| = the communities left (Eq. weight), or, with alg2, the number of
+    communities in N(v) minus one for every column (the convention of Alg. 2)."""
     L = diversity(adj, labels, u_comm, v)
-    if len(L) < 2:
+    size = len(set(labels[x] for x in adj[v])) - 1 if alg2 else len(L)
+    if size < 2:
         return 0.0
-    return entropy_bits(list(L.values())) * len(L)
+    return entropy_bits(list(L.values())) * size
 
 
 def is_valid_triad(adj, labels, u, w, v, strict=False):
@@ -60,12 +63,12 @@ def is_valid_triad(adj, labels, u, w, v, strict=False):
     return type1 or type2 or same_comm_closed
 
 
-def scores(offsets, cols, labels, k, strict=False):
+def scores(offsets, cols, labels, k, strict=False, alg2=False):
     """All R(u) by enumeration of node triples (tiny graphs only)."""
     labels = [int(x) for x in labels]
     adj = adjacency(offsets, cols)
     n = len(adj)
-    wmax = max((weight(adj, labels, c, v) for v in range(n) for c in range(k)), default=0.0)
+    wmax = max((weight(adj, labels, c, v, alg2) for v in range(n) for c in range(k)), default=0.0)
     out = []
     for u in range(n):
         d = len(adj[u])
@@ -76,9 +79,9 @@ def scores(offsets, cols, labels, k, strict=False):
         for w in range(n):
             for v in range(n):
                 if is_valid_triad(adj, labels, u, w, v, strict):
-                    a = weight(adj, labels, labels[u], v)   # w_v(u)
-                    b = weight(adj, labels, labels[v], w)   # w_w(v)
-                    c = weight(adj, labels, labels[u], w)   # w_w(u)
+                    a = weight(adj, labels, labels[u], v, alg2)   # w_v(u)
+                    b = weight(adj, labels, labels[v], w, alg2)   # w_w(v)
+                    c = weight(adj, labels, labels[u], w, alg2)   # w_w(u)
                     terms.append(math.cbrt(a * b * c))
         out.append(math.fsum(terms) / wmax / (d * (d - 1)))
     return out, wmax

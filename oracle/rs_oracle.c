@@ -23,7 +23,8 @@
  *   - ordered pairs (w,v): a Type-I triangle counts twice at each apex (the
  *     worked example of Sec. V-B lists (u,v1,w) and (u,w,v1));
  *   - |L| is the number of distinct communities in L (Eq. weight), and a
- *     weight with |L| < 2 is 0 (Alg. 1 Step 2 keeps only |L| > 1);
+ *     weight with |L| < 2 is 0 (Alg. 1 Step 2 keeps only |L| > 1); an option
+ *     takes Alg. 2's |L| = L_all - 1 for every column instead;
  *   - w_max is the largest w_v(c) over every node v and every community
  *     c in [0,k) (Alg. 1 Step 2 / normalize_weights), so it includes the
  *     value for communities absent from N(v);
@@ -42,6 +43,7 @@
 typedef struct {
     int64_t n;
     int32_t k;
+    int alg2;          /* weights with |L| = L_all - 1 for every column (Alg. 2) */
     int64_t *off;      /* n+1 */
     int32_t *col;      /* nnz */
     int32_t *lab;      /* n */
@@ -106,10 +108,11 @@ static int validate(rso_graph *g) {
 
 /* H of the count multiset cnt[0..m) with one copy of the value `skip` left out
    (skip < 0: nothing left out).  cnt must be sorted ascending so that equal
-   multisets are summed in the same order.  Returns w = H * |L|, or 0 if the
-   multiset left has fewer than two entries. */
-static double weight_of_counts(const int32_t *cnt, int m, int32_t skip) {
-    int L = m - (skip >= 0 ? 1 : 0);
+   multisets are summed in the same order.  Returns w = H * |L|, or 0 if |L| < 2,
+   where |L| is the number of entries left (Eq. weight), or m - 1 for every
+   column when alg2 is set (the convention of Alg. 2, compute_weights). */
+static double weight_of_counts(const int32_t *cnt, int m, int32_t skip, int alg2) {
+    int L = m - ((skip >= 0 || alg2) ? 1 : 0);     /* alg2: |L| = L_all - 1 for every column */
     if (L < 2) return 0.0;
     double Y = 0.0;
     int skipped = 0;
@@ -180,7 +183,7 @@ static int build_tables(rso_graph *g) {
            removing one copy of f_v(c) is the same for equal counts */
         int nd = 0;
         for (int i = 0; i < m; ++i)
-            if (i == 0 || cs[i] != cs[i - 1]) { dist[nd] = cs[i]; dw[nd] = weight_of_counts(cs, m, cs[i]); nd++; }
+            if (i == 0 || cs[i] != cs[i - 1]) { dist[nd] = cs[i]; dw[nd] = weight_of_counts(cs, m, cs[i], g->alg2); nd++; }
         for (int i = 0; i < m; ++i) {
             int32_t f = g->tcnt[g->tptr[v] + i];
             int lo = 0, hi = nd - 1;
@@ -189,7 +192,7 @@ static int build_tables(rso_graph *g) {
             g->tw[g->tptr[v] + i] = w;
             if (w > g->wmax) g->wmax = w;
         }
-        g->wabs[v] = weight_of_counts(cs, m, -1);
+        g->wabs[v] = weight_of_counts(cs, m, -1, g->alg2);
         if (m < g->k && g->wabs[v] > g->wmax) g->wmax = g->wabs[v];
     }
     free(buf); free(cs); free(dist); free(dw);
@@ -244,10 +247,10 @@ static double score_sum(const rso_graph *g, int32_t u, int strict) {
 /* ---- exported API ------------------------------------------------------------ */
 
 rso_graph *rso_new(int64_t n, int32_t k, const int64_t *off, const int32_t *col, const int32_t *lab,
-                   int do_validate, char *err, int errlen) {
+                   int do_validate, int alg2, char *err, int errlen) {
     rso_graph *g = (rso_graph *)calloc(1, sizeof(rso_graph));
     if (!g) return NULL;
-    g->n = n; g->k = k;
+    g->n = n; g->k = k; g->alg2 = alg2 ? 1 : 0;
     int64_t nnz = off[n];
     g->off = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
     g->col = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));

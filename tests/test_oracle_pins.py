@@ -355,3 +355,42 @@ def test_edge_only_removal_touches_no_node():
     assert none == 0
     np.testing.assert_array_equal(same_off, off)
     np.testing.assert_array_equal(same_cols, cols)
+
+
+# Alg. 2 convention (|L| = L_all - 1 for every column).  In the pendant triangle the
+# absent column of a, b, c (their own community) weighs H(1,1,1)(3 - 1) = 2 log2 3,
+# which becomes w_max, and the triangle terms are unchanged (2 each, two per apex):
+# R = 4 / (2 log2 3 * 3 * 2) = 1 / (3 log2 3).
+ALG2_PENDANT_R = 1.0 / (3.0 * math.log2(3.0))
+
+
+def test_alg2_pendant_triangle_closed_form():
+    off, cols, labels, k = pendant_triangle()
+    o = oracle.Oracle(off, cols, labels, k, alg2=True)
+    assert o.wmax == pytest.approx(2.0 * math.log2(3.0), rel=1e-15)
+    np.testing.assert_allclose(o.scores(), [ALG2_PENDANT_R] * 3 + [0, 0, 0], rtol=1e-14, atol=0)
+    b, wmax = brute.scores(off, cols, labels, k, alg2=True)
+    np.testing.assert_allclose(b, [ALG2_PENDANT_R] * 3 + [0, 0, 0], rtol=1e-13, atol=0)
+
+
+def test_alg2_oracle_matches_brute_force():
+    rng = np.random.default_rng(23)
+    for _ in range(15):
+        off, cols, labels = random_tiny_graph(rng, 12, 4, 0.35)
+        o = oracle.Oracle(off, cols, labels, 4, alg2=True)
+        b, wmax = brute.scores(off, cols, labels, 4, alg2=True)
+        assert o.wmax == pytest.approx(wmax, rel=1e-13, abs=0)
+        np.testing.assert_allclose(o.scores(), b, rtol=1e-12, atol=1e-300)
+
+
+def test_alg2_changes_only_absent_columns():
+    """With every community present around every node and no own-community gaps, the
+    two conventions give the same weights."""
+    off, cols = csr_from_edges(6, [(0, 1), (0, 2), (0, 3), (1, 2), (1, 4), (2, 5), (3, 4), (3, 5), (4, 5)])
+    labels = np.array([0, 1, 2, 0, 1, 2], np.int32)
+    a = oracle.Oracle(off, cols, labels, 3)
+    b = oracle.Oracle(off, cols, labels, 3, alg2=True)
+    np.testing.assert_array_equal(a.table()[0], b.table()[0])
+    for v in range(6):
+        for c in range(3):
+            assert a.omega(v, c) == b.omega(v, c)
