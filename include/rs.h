@@ -51,7 +51,12 @@ typedef enum {
 } rs_status;
 
 /* rs_build_graph flags */
-#define RS_VALIDATE 1u  /* check the CSR on the device (see rs_build_graph) */
+#define RS_VALIDATE 1u      /* check the CSR on the device (see rs_build_graph) */
+#define RS_ALG2_COMPAT 2u   /* weights with |L| = L_all - 1 for every column, as Alg. 2
+                               (compute_weights) takes it, instead of the definition's number of
+                               communities left (Eq. weight); differs only for communities
+                               absent from N(v): w_max and s of nodes without own-community
+                               neighbours */
 
 /*
  * rs_build_graph -- load a community-labelled graph (Sec. II; CSR of Sec. V-A).
@@ -287,6 +292,19 @@ void rs_step_free(rs_step *st);
  */
 rs_status rs_target_subset(const rs_graph *g, const int32_t *targets, int32_t n_targets, void *stream,
                            rs_graph **out);
+
+/*
+ * rs_awcc -- the community-spanning diversity of a node set S (Sec. VI-C):
+ *   AWCC(S) = 1/|S| sum_{v in S} |zeta(v)| / d(v), zeta(v) = the communities of
+ *   v's neighbours.  nodes: host int32[m] (S).  deg_ref: host int64[m] or NULL;
+ *   when given, d(v) = deg_ref[i] (the paper's "absolute" AWCC after a
+ *   disruption: only |zeta(v)| follows the changed graph), else the current
+ *   degree; nodes with d(v) = 0 add 0.  zeta_out: host int32[m] or NULL.
+ *   |zeta(v)| is counted by rs_score: the graph must have been scored since its
+ *   last change (RS_EINVAL otherwise).  Synchronises `stream`.
+ */
+rs_status rs_awcc(rs_graph *g, const int32_t *nodes, int64_t m, const int64_t *deg_ref, double *awcc_out,
+                  int32_t *zeta_out, void *stream);
 
 /*
  * Serving: what-if rescoring of resident graphs.  The paper has no counterpart

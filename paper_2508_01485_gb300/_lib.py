@@ -16,6 +16,7 @@ from . import build as _build
 
 RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ETIMEOUT, RS_EBUDGET = range(6)
 RS_VALIDATE = 1
+RS_ALG2_COMPAT = 2
 
 _lib = None
 
@@ -93,6 +94,8 @@ def lib():
         L.rs_step_launch.argtypes = [P, P]
         L.rs_step_free.restype = None
         L.rs_step_free.argtypes = [P]
+        L.rs_awcc.restype = I
+        L.rs_awcc.argtypes = [P, P, I64, P, ctypes.POINTER(ctypes.c_double), P, P]
         L.rs_target_subset.restype = I
         L.rs_target_subset.argtypes = [P, P, I32, P, ctypes.POINTER(P)]
         L.rs_server_create.restype = I
@@ -145,10 +148,11 @@ class Graph:
         self.k = int(k)
 
     @classmethod
-    def build(cls, offsets, cols, labels, k, validate=True, stream=None):
+    def build(cls, offsets, cols, labels, k, validate=True, stream=None, alg2=False):
         """rs_build_graph from numpy arrays (host) or torch CUDA tensors (device).
 
         offsets: int64 or int32 [n+1]; cols: int32 [nnz]; labels: int32 [n].
+        alg2: RS_ALG2_COMPAT (weights with |L| = L_all - 1 for every column).
         """
         import torch
         on_dev = isinstance(offsets, torch.Tensor) and offsets.is_cuda
@@ -171,7 +175,8 @@ class Graph:
         s = _stream(stream)
         _check(lib().rs_build_graph(n, nnz, ctypes.c_void_p(p_off), 1 if is64 else 0,
                                     ctypes.c_void_p(p_col if nnz else None), ctypes.c_void_p(p_lab if n else None),
-                                    int(k), 1 if on_dev else 0, RS_VALIDATE if validate else 0, s,
+                                    int(k), 1 if on_dev else 0,
+                                    (RS_VALIDATE if validate else 0) | (RS_ALG2_COMPAT if alg2 else 0), s,
                                     ctypes.byref(h)))
         return cls(h, n, k)
 
@@ -200,8 +205,8 @@ class Graph:
         return out
 
     @classmethod
-    def from_generated(cls, g, validate=True, stream=None):
-        return cls.build(g.offsets, g.cols, g.labels, g.k, validate=validate, stream=stream)
+    def from_generated(cls, g, validate=True, stream=None, alg2=False):
+        return cls.build(g.offsets, g.cols, g.labels, g.k, validate=validate, stream=stream, alg2=alg2)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -295,6 +300,17 @@ class Graph:
         c = ctypes.c_int64(0)
         _check(lib().rs_launch_count(self._h, ctypes.byref(c)))
         return c.value
+
+    def awcc(self, nodes, deg_ref=None, stream=None):
+        """rs_awcc: (AWCC of the node set, |zeta(v)| per node); deg_ref fixes d(v) (absolute AWCC)."""
+        v = np.ascontiguousarray(np.asarray(nodes, dtype=np.int32).reshape(-1))
+        d = None if deg_ref is None else np.ascontiguousarray(np.asarray(deg_ref, dtype=np.int64).reshape(-1))
+        z = np.zeros(max(v.size, 1), np.int32)
+        a = ctypes.c_double(0.0)
+        _check(lib().rs_awcc(self._h, ctypes.c_void_p(v.ctypes.data if v.size else None), v.size,
+                             ctypes.c_void_p(d.ctypes.data) if d is not None else None, ctypes.byref(a),
+                             ctypes.c_void_p(z.ctypes.data), _stream(stream)))
+        return a.value, z[: v.size]
 
     def target_subset(self, targets, stream=None):
         """rs_target_subset: a new Graph restricted to the target communities (target i -> community i)."""

@@ -234,7 +234,9 @@ __device__ uint64_t atanh_fixed(uint64_t z) {  // z < 1/2 in 2^-64 units
     }
     return s;
 }
-__global__ void init_tables_kernel(uint64_t *LG, double *RD, int32_t dmax) {
+// LG[0] is never used as a logarithm (it only multiplies a zero count); it holds the
+// weight convention instead: 1 = Alg. 2's |L| = L_all - 1 for every column
+__global__ void init_tables_kernel(uint64_t *LG, double *RD, int32_t dmax, int alg2) {
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f > dmax) return;
     uint64_t lg = 0;
@@ -251,7 +253,7 @@ __global__ void init_tables_kernel(uint64_t *LG, double *RD, int32_t dmax) {
             lg = ((uint64_t)e << kLogFrac) + (l2m >> drop) + ((l2m >> (drop - 1)) & 1);
         }
     }
-    LG[f] = lg;
+    LG[f] = f == 0 ? (uint64_t)(alg2 ? 1 : 0) : lg;
     RD[f] = f >= 2 ? 1.0 / ((double)f * (double)(f - 1)) : 0.0;
 }
 
@@ -545,7 +547,7 @@ static int build_tables(rs_graph *g, cudaStream_t s) {
     int64_t m = (int64_t)g->dmax + 1;
     RS_CUDA_TRY(dmalloc(&g->LG, m));
     RS_CUDA_TRY(dmalloc(&g->RD, m));
-    init_tables_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(g->LG, g->RD, g->dmax);
+    init_tables_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(g->LG, g->RD, g->dmax, g->alg2 ? 1 : 0);
     RS_CUDA_TRY(cudaGetLastError());
     return 0;
 }
@@ -629,6 +631,7 @@ static rs_status rs_build_graph_impl(int64_t n, int64_t nnz, const void *row_off
         return (rs_status)fail(RS_EINVAL, "rs_build_graph: NULL input array");
     rs_graph *g = new rs_graph();
     g->n = n; g->nnz = nnz; g->k = num_communities;
+    g->alg2 = (flags & RS_ALG2_COMPAT) != 0;
     cudaGetDevice(&g->device);
     auto bail = [&](int rc) { free_graph(g); return (rs_status)rc; };
     cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -826,6 +829,7 @@ extern "C" rs_status rs_clone_graph(const rs_graph *src, rs_graph **out, void *s
     rs_graph *g = new rs_graph();
     g->n = src->n; g->nnz = src->nnz; g->k = src->k; g->device = src->device;
     g->tune = src->tune;
+    g->alg2 = src->alg2;
     auto bail = [&](int rc) { free_graph(g); return (rs_status)rc; };
     int64_t n = g->n, nnz = g->nnz;
     if (cudaError_t e = dmalloc(&g->off, n + 1)) return bail(cuda_fail(e, "alloc"));
@@ -1219,6 +1223,48 @@ extern "C" rs_status rs_score(rs_graph *g, double *scores, double *omega_max_out
         memcpy(&w, &bits, sizeof(w));
         *omega_max_out = w;
     }
+    return RS_OK;
+}
+
+__global__ void gather_awcc_kernel(const int32_t *nodes, int64_t m, const int32_t *Lall, const int64_t *off,
+                                   int32_t *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) {
+        int32_t v = nodes[i];
+        out[2 * i] = Lall[v];
+        out[2 * i + 1] = (int32_t)(off[v + 1] - off[v]);
+    }
+}
+
+extern "C" rs_status rs_awcc(rs_graph *g, const int32_t *nodes, int64_t m, const int64_t *deg_ref, double *awcc_out,
+                             int32_t *zeta_out, void *stream) {
+    cudaStream_t s = as_stream(stream);
+    if (!g || (m > 0 && !nodes) || m < 0 || !awcc_out) return (rs_status)fail(RS_EINVAL, "rs_awcc: bad arguments");
+    if (g->scored_version != g->version)
+        return (rs_status)fail(RS_EINVAL, "rs_awcc: call rs_score after the last change of the graph");
+    for (int64_t i = 0; i < m; ++i)
+        if (nodes[i] < 0 || nodes[i] >= g->n) return (rs_status)fail(RS_EINVAL, "rs_awcc: node id out of range");
+    if (m == 0) { *awcc_out = 0.0; return RS_OK; }
+    int32_t *d_buf = nullptr;
+    std::vector<int32_t> h(2 * (size_t)m);
+    cudaError_t e = dmalloc(&d_buf, 3 * (size_t)m);
+    if (!e) e = cudaMemcpyAsync(d_buf, nodes, m * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (!e) {
+        gather_awcc_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(d_buf, m, g->Lall, g->off, d_buf + m);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaMemcpyAsync(h.data(), d_buf + m, 2 * m * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    cudaFree(d_buf);
+    if (e) return (rs_status)cuda_fail(e, "rs_awcc");
+    double sum = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t d = deg_ref ? deg_ref[i] : h[2 * i + 1];
+        int32_t z = h[2 * i + 1] > 0 ? h[2 * i] : 0;       // an isolated node reaches no community
+        if (zeta_out) zeta_out[i] = z;
+        if (d > 0) sum += (double)z / (double)d;
+    }
+    *awcc_out = sum / (double)m;
     return RS_OK;
 }
 

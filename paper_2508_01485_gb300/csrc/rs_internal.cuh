@@ -174,6 +174,8 @@ struct rs_graph {
     // launch parameters and a counter bumped whenever buffers or row classes change
     rs_tuning tune = rs::default_tuning_value();
     uint64_t version = 0;
+    bool alg2 = false;                        // RS_ALG2_COMPAT: |L| = L_all - 1 for every column
+    uint64_t scored_version = ~0ull;          // version of the last rs_score (Lall and the scores are current)
 };
 
 namespace rs {

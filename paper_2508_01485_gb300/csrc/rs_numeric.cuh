@@ -207,7 +207,9 @@ __device__ __forceinline__ df warp_max_df(df v) {
 // of distinct communities, X = sum_c f_c LG[f_c] (exact).  The weight of column
 // c with count f (f = 0 for a community absent from N(v)) is
 //     w = H(L_c) |L_c|,  H(L_c) = E / Y,  Y = T - f,  E = Y LG[Y] - (X - f LG[f]),
-// |L_c| = L - [f > 0], and w = 0 when |L_c| < 2.
+// |L_c| = L - [f > 0], and w = 0 when |L_c| < 2.  Under the convention of Alg. 2
+// (|L| = L_all - 1 for every column, also when c is absent from N(v)), which the
+// table flags with LG[0] = 1, |L_c| = L - 1 for every column.
 struct RowAgg {
     uint32_t T;      // degree
     uint32_t L;      // distinct communities among the neighbours
@@ -215,8 +217,9 @@ struct RowAgg {
 };
 
 __device__ __forceinline__ df column_weight(const RowAgg &a, uint32_t f, const uint64_t *LG) {
-    uint32_t Lc = a.L - (f > 0 ? 1u : 0u);
-    if (Lc < 2) return df{0.0f, 0.0f};
+    uint32_t drop = (f > 0 || (LG[0] & 1)) ? 1u : 0u;
+    if (a.L < drop + 2) return df{0.0f, 0.0f};
+    uint32_t Lc = a.L - drop;
     uint32_t Y = a.T - f;
     u128 rest = a.X - (u128)f * LG[f];
     u128 yy = (u128)Y * LG[Y];

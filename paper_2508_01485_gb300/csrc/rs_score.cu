@@ -1503,6 +1503,7 @@ static void launch_p2_large(rs_graph *g, const Batch &B, int *err, size_t smem) 
 
 int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     int64_t n = g->n;
+    g->scored_version = g->version;
     if (n == 0) return 0;
     constexpr int NT = kThreads;
     int *err = g->d_flag + 4;
