@@ -57,6 +57,11 @@ typedef enum {
                                communities left (Eq. weight); differs only for communities
                                absent from N(v): w_max and s of nodes without own-community
                                neighbours */
+#define RS_TRIAD_STRICT 4u  /* the strict reading of the triad types (Sec. III-A): a closed
+                               triangle (u, w, v) with C(v) = C(u) != C(w) is not a triad for
+                               u (by default it counts once, as an augmented-edge triad).
+                               Needs 16 bytes per CSR entry more; resident graphs served by
+                               rs_server take the full path with it */
 
 /*
  * rs_build_graph -- load a community-labelled graph (Sec. II; CSR of Sec. V-A).

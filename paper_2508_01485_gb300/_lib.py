@@ -17,6 +17,7 @@ from . import build as _build
 RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ETIMEOUT, RS_EBUDGET = range(6)
 RS_VALIDATE = 1
 RS_ALG2_COMPAT = 2
+RS_TRIAD_STRICT = 4
 
 _lib = None
 
@@ -148,11 +149,12 @@ class Graph:
         self.k = int(k)
 
     @classmethod
-    def build(cls, offsets, cols, labels, k, validate=True, stream=None, alg2=False):
+    def build(cls, offsets, cols, labels, k, validate=True, stream=None, alg2=False, strict=False):
         """rs_build_graph from numpy arrays (host) or torch CUDA tensors (device).
 
         offsets: int64 or int32 [n+1]; cols: int32 [nnz]; labels: int32 [n].
         alg2: RS_ALG2_COMPAT (weights with |L| = L_all - 1 for every column).
+        strict: RS_TRIAD_STRICT (no closed triad with C(v) = C(u) != C(w)).
         """
         import torch
         on_dev = isinstance(offsets, torch.Tensor) and offsets.is_cuda
@@ -176,7 +178,8 @@ class Graph:
         _check(lib().rs_build_graph(n, nnz, ctypes.c_void_p(p_off), 1 if is64 else 0,
                                     ctypes.c_void_p(p_col if nnz else None), ctypes.c_void_p(p_lab if n else None),
                                     int(k), 1 if on_dev else 0,
-                                    (RS_VALIDATE if validate else 0) | (RS_ALG2_COMPAT if alg2 else 0), s,
+                                    (RS_VALIDATE if validate else 0) | (RS_ALG2_COMPAT if alg2 else 0)
+                                    | (RS_TRIAD_STRICT if strict else 0), s,
                                     ctypes.byref(h)))
         return cls(h, n, k)
 
@@ -205,8 +208,9 @@ class Graph:
         return out
 
     @classmethod
-    def from_generated(cls, g, validate=True, stream=None, alg2=False):
-        return cls.build(g.offsets, g.cols, g.labels, g.k, validate=validate, stream=stream, alg2=alg2)
+    def from_generated(cls, g, validate=True, stream=None, alg2=False, strict=False):
+        return cls.build(g.offsets, g.cols, g.labels, g.k, validate=validate, stream=stream, alg2=alg2,
+                         strict=strict)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

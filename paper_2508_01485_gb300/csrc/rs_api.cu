@@ -575,6 +575,7 @@ static int alloc_workspace(rs_graph *g) {
     RS_CUDA_TRY(dmalloc(&g->xR, nnz));
     RS_CUDA_TRY(dmalloc(&g->p2rows, 3 * (size_t)n));
     RS_CUDA_TRY(dmalloc(&g->p2cnt, 8));
+    if (g->strict) RS_CUDA_TRY(dmalloc(&g->sx, 2 * (size_t)nnz));
     RS_CUDA_TRY(dmalloc(&g->scan_tmp, scan_tmp_words(std::max<int64_t>(n + 1, 1)) + 64));
     RS_CUDA_TRY(dmalloc(&g->rows_small, n));
     RS_CUDA_TRY(dmalloc(&g->rows_mid, n));
@@ -590,7 +591,7 @@ static void free_graph(rs_graph *g) {
                     g->rows_small, g->rows_mid, g->rows_large, g->rows_small_deg, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
                     g->Lall, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->scan_tmp, g->tk_hist,
                     g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->xR, g->rsum, g->cl_col, g->cl_lab,
-                    g->winv, g->gid, g->gk, g->gnode, g->p2rows, g->p2cnt};
+                    g->winv, g->gid, g->gk, g->gnode, g->p2rows, g->p2cnt, g->sx};
     for (void *p : ptrs) cudaFree(p);
     free_hub_tables(g);
     for (cudaEvent_t e : g->prof_ev) cudaEventDestroy(e);
@@ -632,6 +633,7 @@ static rs_status rs_build_graph_impl(int64_t n, int64_t nnz, const void *row_off
     rs_graph *g = new rs_graph();
     g->n = n; g->nnz = nnz; g->k = num_communities;
     g->alg2 = (flags & RS_ALG2_COMPAT) != 0;
+    g->strict = (flags & RS_TRIAD_STRICT) != 0;
     cudaGetDevice(&g->device);
     auto bail = [&](int rc) { free_graph(g); return (rs_status)rc; };
     cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -830,6 +832,7 @@ extern "C" rs_status rs_clone_graph(const rs_graph *src, rs_graph **out, void *s
     g->n = src->n; g->nnz = src->nnz; g->k = src->k; g->device = src->device;
     g->tune = src->tune;
     g->alg2 = src->alg2;
+    g->strict = src->strict;
     auto bail = [&](int rc) { free_graph(g); return (rs_status)rc; };
     int64_t n = g->n, nnz = g->nnz;
     if (cudaError_t e = dmalloc(&g->off, n + 1)) return bail(cuda_fail(e, "alloc"));

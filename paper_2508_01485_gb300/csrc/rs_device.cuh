@@ -96,6 +96,30 @@ __device__ __forceinline__ void push_type2(unsigned long long *acc, int32_t u, d
     if (v) atomic_add_u128(acc + 2 * (int64_t)u, neg ? (u128)0 - v : v);
 }
 
+// The strict reading of the triad indicator (RS_TRIAD_STRICT) drops the closed
+// triads (u, w, v) with C(v) = C(u) != C(w) and v in N(u): the Type-II sum
+// Q_w(C(u)) - s_u pushed by w to u then leaves out X(w, u), the s of u's
+// same-community neighbours that are also neighbours of w.  X is summed exactly
+// per pushed pair beforehand, two words per CSR entry, at u's entry in w's row
+// (sx null: the default reading).
+struct Strict {
+    const int32_t *col;
+    const unsigned long long *sx;
+};
+__device__ __forceinline__ u128 strict_rest(const Strict &SX, const int64_t *off, int32_t w, int32_t u, u128 rest,
+                                            int64_t pos = -1) {
+    if (!SX.sx || rest == 0) return rest;
+    if (pos < 0) {
+        int64_t lo = off[w], hi = off[w + 1];
+        while (lo < hi) {
+            int64_t mid = lo + ((hi - lo) >> 1);
+            if (SX.col[mid] < u) lo = mid + 1; else hi = mid;
+        }
+        pos = lo;
+    }
+    return rest - (((u128)SX.sx[2 * pos + 1] << 64) | SX.sx[2 * pos]);
+}
+
 // the three apex terms of triangle (a, b, c) from its six directed values
 // S(x -> y) = w_x(C(y))^(1/3): at apex a the ordered pairs (w, v) = (b, c) and
 // (c, b) give S(c->a) S(b->c) S(b->a) + S(b->a) S(c->b) S(c->a)

@@ -175,6 +175,8 @@ struct rs_graph {
     rs_tuning tune = rs::default_tuning_value();
     uint64_t version = 0;
     bool alg2 = false;                        // RS_ALG2_COMPAT: |L| = L_all - 1 for every column
+    bool strict = false;                      // RS_TRIAD_STRICT: no closed triad with C(v) = C(u)
+    unsigned long long *sx = nullptr;         // strict: X(w, u) per CSR entry (2 words), else null
     uint64_t scored_version = ~0ull;          // version of the last rs_score (Lall and the scores are current)
 };
 

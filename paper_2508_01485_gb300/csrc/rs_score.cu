@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
-    int32_t *__restrict__ xout, int32_t *__restrict__ xin) {
+    int32_t *__restrict__ xout, int32_t *__restrict__ xin, Strict SX) {
     __shared__ P2Tile tiles[kThreads / 32];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     P2Tile &T = tiles[wid];
@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
                 else {
                     RowAgg a{T.d[r], T.L[r], ((u128)T.xhi[r] << 64) | T.xlo[r]};
                     sig = df_cbrt(column_weight(a, f, LG));
-                    push_type2(acc, u, sig, rest);
+                    push_type2(acc, u, sig, strict_rest(SX, off, T.w[r], u, rest));
                 }
             }
             // G_x entries of this chunk, in id order within each row
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(kThreads) p2_warp_kernel(
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
-    int32_t *__restrict__ xout, int32_t *__restrict__ xin) {
+    int32_t *__restrict__ xout, int32_t *__restrict__ xin, Strict SX) {
     __shared__ uint64_t stage[kThreads];
     int lane = threadIdx.x & 31;
     uint64_t *st = stage + (threadIdx.x & ~31);
@@ -704,7 +704,7 @@ __global__ void __launch_bounds__(kThreads) p2_warp_kernel(
                     u128 rest = 0;
                     unsigned m = grp & ~(1u << lane);
                     while (m) { rest += st[__ffs(m) - 1]; m &= m - 1; }
-                    push_type2(acc, u, sig, rest);
+                    push_type2(acc, u, sig, strict_rest(SX, off, w, u, rest));
                 }
             }
             __syncwarp();
@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
-    int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err) {
+    int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err, Strict SX) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t stage[kThreads];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
                         sig = f == 1 ? sig1 : df_cbrt(column_weight(a, f, LG));
                         if (f > 1) {
                             u128 q = ((u128)t.q[2 * sl + 1] << 64) | t.q[2 * sl];
-                            push_type2(acc, u, sig, q - ru.s_fix);
+                            push_type2(acc, u, sig, strict_rest(SX, off, w, u, q - ru.s_fix));
                         }
                     }
                 }
@@ -859,7 +859,7 @@ __global__ void __launch_bounds__(NT) p2_large_kernel(
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
-    int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err) {
+    int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err, Strict SX) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int32_t sh_cnt[2 * NT / 32];
     __shared__ uint64_t stage[NT];
@@ -922,7 +922,7 @@ __global__ void __launch_bounds__(NT) p2_large_kernel(
                     sig = t.sig[sl];
                     if (t.cnt[sl] > 1) {
                         u128 q = ((u128)t.q[2 * sl + 1] << 64) | t.q[2 * sl];
-                        push_type2(acc, u, sig, q - ru.s_fix);
+                        push_type2(acc, u, sig, strict_rest(SX, off, w, u, q - ru.s_fix));
                     }
                 }
             }
@@ -1021,7 +1021,7 @@ __global__ void __launch_bounds__(NT) hub_p2_emit_kernel(
     const NodeRec *__restrict__ rec, const int32_t *hkey, const uint32_t *hcnt,
     const unsigned long long *hq, const df *hsig, const int32_t *hitem_out, const int32_t *hitem_in,
     unsigned long long *acc, const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol,
-    df *__restrict__ xS, int *err) {
+    df *__restrict__ xS, int *err, Strict SX) {
     __shared__ int32_t sh_cnt[2 * NT / 32];
     int tid = threadIdx.x;
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -1053,7 +1053,7 @@ __global__ void __launch_bounds__(NT) hub_p2_emit_kernel(
                     sig = hsig[gs];
                     if (hcnt[gs] > 1) {
                         u128 q = ((u128)hq[2 * gs + 1] << 64) | hq[2 * gs];
-                        push_type2(acc, u, sig, q - ru.s_fix);
+                        push_type2(acc, u, sig, strict_rest(SX, off, h.row, u, q - ru.s_fix, b + e));
                     }
                 }
             }
@@ -1408,6 +1408,53 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
 }
 
 // ======================================================================================
+// Strict reading: X(w, u) for every pushed pair, from the closed triads (u, w, v)
+// with C(v) = C(u) != C(w): for every intra-community edge {u, v} (u < v) and
+// every common neighbour w of another community, s_v is added at u's entry in
+// w's row and s_u at v's.  The shorter row of u, v is walked; w is looked up in
+// the other row and the entries in w's row by binary search (rows are sorted).
+// ======================================================================================
+__device__ __forceinline__ int64_t csr_find(const int64_t *off, const int32_t *col, int32_t row, int32_t key) {
+    int64_t lo = off[row], hi = off[row + 1], end = hi;
+    while (lo < hi) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (col[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return (lo < end && col[lo] == key) ? lo : -1;
+}
+
+__global__ void __launch_bounds__(kThreads) strict_pairs_kernel(int64_t n, const int64_t *__restrict__ off,
+                                                                const int32_t *__restrict__ col,
+                                                                const int32_t *__restrict__ lab,
+                                                                const NodeRec *__restrict__ rec,
+                                                                unsigned long long *sx) {
+    int lane = threadIdx.x & 31;
+    int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = w0; u < n; u += nw) {                 // a warp per row u, lanes over its entries v
+        int32_t cu = lab[u];
+        int64_t bu = off[u], du = off[u + 1] - bu;
+        for (int64_t e = lane; e < du; e += 32) {
+            int32_t v = col[bu + e];
+            if (v <= u || lab[v] != cu) continue;
+            int64_t bv = off[v], dv = off[v + 1] - bv;
+            bool walk_u = du <= dv;
+            int32_t o = walk_u ? v : (int32_t)u;
+            int64_t ba = walk_u ? bu : bv, da = walk_u ? du : dv;
+            uint64_t su = rec[u].s_fix, sv = rec[v].s_fix;
+            for (int64_t j = 0; j < da; ++j) {
+                int32_t w = col[ba + j];
+                if (w == o || lab[w] == cu) continue;
+                if (csr_find(off, col, o, w) < 0) continue;
+                int64_t pu = csr_find(off, col, w, (int32_t)u), pv = csr_find(off, col, w, v);
+                if (sv && pu >= 0) atomic_add_u128(sx + 2 * pu, (u128)sv);
+                if (su && pv >= 0) atomic_add_u128(sx + 2 * pv, (u128)su);
+            }
+        }
+    }
+}
+
+// ======================================================================================
 // P2 row lists by cross degree (known after P1): each P2 kernel then walks only its rows
 //   0 mid rows, dx <= 32 (p2_warp)      1 mid rows, dx > 32 (p2_mid)
 //   2 large rows, dx <= 32 (p2_warp)    3 large rows, 32 < dx <= dx_cta (p2_mid)
@@ -1498,7 +1545,7 @@ static void launch_p2_large(rs_graph *g, const Batch &B, int *err, size_t smem) 
     int32_t *L4 = g->p2rows + 2 * g->n_mid + 2 * g->n_large;
     p2_large_kernel<NT><<<grid_for(g->n_large, 1, 2), NT, smem, g->aux[4]>>>(
         g->off, L4, g->p2cnt + 4, B, g->tune.p2_cta_dx + 1, g->LG, g->rec, g->rsum, g->cl_col,
-        g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
+        g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, Strict{g->col, g->sx});
 }
 
 int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
@@ -1563,6 +1610,12 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     if (int rc = inclusive_scan_i64(g->xoff + 1, n, g->scan_tmp, s, &scan_launches)) return rc;
     g->launches += scan_launches - 1;
     prof_mark(g, s, "gx_scan", true);
+    const Strict SX{g->col, g->strict ? g->sx : nullptr};
+    if (g->strict) {
+        RS_CUDA_TRY(cudaMemsetAsync(g->sx, 0, 2 * g->nnz * sizeof(unsigned long long), s));
+        strict_pairs_kernel<<<grid_for(n * 32, NT, cps), NT, 0, s>>>(n, g->off, g->col, g->lab, g->rec, g->sx);
+        RS_LAUNCHED(g, s, "strict_pairs");
+    }
     const int64_t nm = g->n_mid, nl = g->n_large;
     int32_t *L0 = g->p2rows, *L1 = L0 + nm, *L2 = L0 + 2 * nm, *L3 = L2 + nl;
     if (nm + nl) {
@@ -1576,28 +1629,28 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     if (g->n_small) {
         p2_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[0]>>>(
             g->off, g->rows_small, g->n_small, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
-            g->xcol, g->xS, g->xout, g->xin);
+            g->xcol, g->xS, g->xout, g->xin, SX);
         RS_LAUNCHED(g, g->aux[0], "p2_small");
     }
     if (g->n_mid) {
         p2_warp_kernel<<<grid_for(g->n_mid * 32, NT, cps), NT, 0, g->aux[1]>>>(
             g->off, L0, g->p2cnt + 0, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff, g->xcol,
-            g->xS, g->xout, g->xin);
+            g->xS, g->xout, g->xin, SX);
         RS_LAUNCHED(g, g->aux[1], "p2_warp");
         p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, p2_mid_smem, g->aux[5]>>>(
             g->off, L1, g->p2cnt + 1, B, 1 << 30, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
-            g->xcol, g->xS, g->xout, g->xin, err);
+            g->xcol, g->xS, g->xout, g->xin, err, SX);
         RS_LAUNCHED(g, g->aux[5], "p2_mid");
     }
     if (g->n_large) {
         // large rows whose cross list fits a per-warp table go warp-per-row too
         p2_warp_kernel<<<grid_for(g->n_large * 32, NT, cps), NT, 0, g->aux[2]>>>(
             g->off, L2, g->p2cnt + 2, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
-            g->xcol, g->xS, g->xout, g->xin);
+            g->xcol, g->xS, g->xout, g->xin, SX);
         RS_LAUNCHED(g, g->aux[2], "p2_warp");
         p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, p2_mid_smem, g->aux[2]>>>(
             g->off, L3, g->p2cnt + 3, B, g->tune.p2_cta_dx, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab,
-            g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err);
+            g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX);
         RS_LAUNCHED(g, g->aux[2], "p2_large_warp");
         switch (g->tune.p2_cta_threads) {
         case 256: launch_p2_large<256>(g, B, err, p2_smem); break;
@@ -1619,7 +1672,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         hub_p2_emit_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
             g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
             g->hkey, g->hcnt,
-            g->hq, g->hsig, g->hitem_out, g->hitem_in, g->acc, g->xoff, g->xcol, g->xS, err);
+            g->hq, g->hsig, g->hitem_out, g->hitem_in, g->acc, g->xoff, g->xcol, g->xS, err, SX);
         RS_LAUNCHED(g, g->aux[3], "hub_p2_emit");
     }
     if (int rc = join_aux(g, s, rs_graph::kAux)) return rc;

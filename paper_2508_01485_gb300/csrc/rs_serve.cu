@@ -951,6 +951,7 @@ Bounds request_bounds(const Base &b, const Request &r) {
 }
 
 bool fits_buffers(const rs_server *srv, const Base &b, const Request &r) {
+    if (b.g->strict) return false;       // the delta kernels follow the default triad reading
     if ((int64_t)(r.nodes.size() + 2 * r.src.size()) > (int64_t)(1 << 16)) return false;
     Bounds x = request_bounds(b, r);
     return x.t <= srv->tcap && x.dt <= srv->xcap;
