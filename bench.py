@@ -215,11 +215,14 @@ def graph_stats(g, k_class=None):
         st["G_" + name] = int((keep & sel[rows]).sum())
     for c, name in enumerate(["small", "mid", "large", "hub"]):
         put(name, cls == c)
-    # P2 splits mid and large rows by cross degree: <= 32 (no table), <= 256 (warp table), more (CTA)
+    # P2 splits mid and large rows by cross degree: <= 32 (no table), <= 128 (256-slot warp table),
+    # <= 256 (512-slot warp table), more (CTA)
     put("mid_w", (cls == 1) & (dx <= 32))
-    put("mid_t", (cls == 1) & (dx > 32))
+    put("mid_t", (cls == 1) & (dx > 32) & (dx <= 128))
+    put("mid_tw", (cls == 1) & (dx > 128))
     put("large_w", (cls == 2) & (dx <= 32))
-    put("large_t", (cls == 2) & (dx > 32) & (dx <= 256))
+    put("large_t", (cls == 2) & (dx > 32) & (dx <= 128))
+    put("large_tw", (cls == 2) & (dx > 128) & (dx <= 256))
     put("large_c", (cls == 2) & (dx > 256))
     # compatibility names used by the JSON line
     st["n_small"], st["E_small"] = st["R_small"], st["E_small"]
@@ -243,7 +246,9 @@ def kernel_bytes(name, st):
     table = {
         "p1_small": lambda: p1("small"), "p1_mid": lambda: p1("mid"), "p1_large": lambda: p1("large"),
         "p2_small": lambda: p2("small"), "p2_warp": lambda: p2("mid_w") + p2("large_w"),
-        "p2_mid": lambda: p2("mid_t"), "p2_large_warp": lambda: p2("large_t"), "p2_large": lambda: p2("large_c"),
+        "p2_mid": lambda: p2("mid_t"), "p2_mid_wide": lambda: p2("mid_tw"),
+        "p2_large_warp": lambda: p2("large_t"), "p2_large_warp_wide": lambda: p2("large_tw"),
+        "p2_large": lambda: p2("large_c"),
         # out-lists (ids, forward and reverse values are read only for triangles), out counts,
         # offsets and ranks of every node
         "p3_list": lambda: 4 * st["out_slots"] + (4 + 8 + 4) * n,

@@ -573,7 +573,7 @@ static int alloc_workspace(rs_graph *g) {
     RS_CUDA_TRY(dmalloc(&g->xout, n));
     RS_CUDA_TRY(dmalloc(&g->xin, n));
     RS_CUDA_TRY(dmalloc(&g->xR, nnz));
-    RS_CUDA_TRY(dmalloc(&g->p2rows, 3 * (size_t)n));
+    RS_CUDA_TRY(dmalloc(&g->p2rows, 4 * (size_t)n));
     RS_CUDA_TRY(dmalloc(&g->p2cnt, 8));
     if (g->strict) RS_CUDA_TRY(dmalloc(&g->sx, 2 * (size_t)nnz));
     RS_CUDA_TRY(dmalloc(&g->scan_tmp, scan_tmp_words(std::max<int64_t>(n + 1, 1)) + 64));

@@ -146,7 +146,7 @@ struct rs_graph {
     rs::df *xS = nullptr;                     // S(w -> u) = w_w(C(u))^(1/3)
     int32_t *xout = nullptr, *xin = nullptr;  // out / in counts per node
     rs::df *xR = nullptr;                     // at out-slot (w -> u): the reverse value S(u -> w)
-    int32_t *p2rows = nullptr;                // P2 row lists by cross degree (3 n), counted in p2cnt[5]
+    int32_t *p2rows = nullptr;                // P2 row lists by cross degree (4 n), counted in p2cnt
     int32_t *p2cnt = nullptr;
     int64_t *scan_tmp = nullptr;              // block sums for scans
     // top-k workspace

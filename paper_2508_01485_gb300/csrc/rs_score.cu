@@ -728,7 +728,7 @@ __global__ void __launch_bounds__(kThreads) p2_warp_kernel(
 constexpr int kMidSlotBytes = 4 + 4 + 16;   // key, count, 2-word sum
 
 __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_dev, Batch B, int32_t dx_max,
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_dev, Batch B, int32_t dx_max, int32_t wslots,
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
@@ -737,7 +737,7 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
     __shared__ uint64_t stage[kThreads];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t *st = stage + (threadIdx.x & ~31);
-    unsigned char *base_w = smem + (size_t)wid * kWarpCap * kMidSlotBytes;
+    unsigned char *base_w = smem + (size_t)wid * wslots * kMidSlotBytes;   // wslots >= every row's table
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nrows = *nrows_dev;               // rows of this kernel, counted by p2_split
@@ -753,8 +753,8 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
             uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(dx, k_of(B, graph_of(B, w))));
             Tab t;
             t.q = (unsigned long long *)base_w;
-            t.key = (int32_t *)(base_w + 16 * kWarpCap);
-            t.cnt = (uint32_t *)(base_w + 20 * kWarpCap);
+            t.key = (int32_t *)(base_w + 16 * wslots);
+            t.cnt = (uint32_t *)(base_w + 20 * wslots);
             t.sig = nullptr;
             t.mask = cap - 1;
             for (uint32_t j = lane; j < cap; j += 32) { t.key[j] = kEmpty; t.cnt[j] = 0; t.q[2 * j] = 0; t.q[2 * j + 1] = 0; }
@@ -1456,10 +1456,14 @@ __global__ void __launch_bounds__(kThreads) strict_pairs_kernel(int64_t n, const
 
 // ======================================================================================
 // P2 row lists by cross degree (known after P1): each P2 kernel then walks only its rows
-//   0 mid rows, dx <= 32 (p2_warp)      1 mid rows, dx > 32 (p2_mid)
-//   2 large rows, dx <= 32 (p2_warp)    3 large rows, 32 < dx <= dx_cta (p2_mid)
-//   4 large rows, dx > dx_cta (p2_large)
+//   0 mid rows, dx <= 32 (p2_warp)           1 mid rows, 32 < dx <= 128 (p2_mid, 256 slots)
+//   2 large rows, dx <= 32 (p2_warp)         3 large rows, 32 < dx <= min(128, dx_cta) (p2_mid, 256)
+//   4 large rows, dx > dx_cta (p2_large)     5 mid rows, dx > 128 (p2_mid, 512 slots)
+//   6 large rows, 128 < dx <= dx_cta (p2_mid, 512 slots)
 // ======================================================================================
+constexpr int kP2Lists = 7;
+constexpr int32_t kSmallTableDx = 128;        // rows up to this cross degree fit 256-slot tables
+
 __device__ __forceinline__ void append_row(int32_t *list, int32_t *cnt, bool take, int32_t v) {
     unsigned m = __ballot_sync(FULL, take);
     int lane = threadIdx.x & 31;
@@ -1467,6 +1471,13 @@ __device__ __forceinline__ void append_row(int32_t *list, int32_t *cnt, bool tak
     if (m && lane == __ffs(m) - 1) base = atomicAdd(cnt, __popc(m));
     base = __shfl_sync(FULL, base, __ffs(m ? m : 1u) - 1);
     if (take) list[base + __popc(m & lanemask_lt())] = v;
+}
+
+// list c starts at p2_list_start(c) * (its class size): mid lists have n_mid entries, large ones n_large
+__host__ __device__ __forceinline__ int64_t p2_list_start(int c, int64_t n_mid, int64_t n_large) {
+    const int mids_before[kP2Lists] = {0, 1, 2, 2, 2, 2, 3};
+    const int larges_before[kP2Lists] = {0, 0, 0, 1, 2, 3, 3};
+    return mids_before[c] * n_mid + larges_before[c] * n_large;
 }
 
 __global__ void p2_split_kernel(const int32_t *__restrict__ rows_mid, int64_t n_mid,
@@ -1479,10 +1490,13 @@ __global__ void p2_split_kernel(const int32_t *__restrict__ rows_mid, int64_t n_
         bool mid = i < n_mid;
         int32_t v = act ? (mid ? rows_mid[i] : rows_large[i - n_mid]) : 0;
         int32_t dx = act ? rec[v].dx : 0;
-        int cls = !act ? -1 : mid ? (dx <= 32 ? 0 : 1) : (dx <= 32 ? 2 : dx <= dx_cta ? 3 : 4);
-        int32_t *base[5] = {lists, lists + n_mid, lists + 2 * n_mid, lists + 2 * n_mid + n_large,
-                            lists + 2 * n_mid + 2 * n_large};
-        for (int c = 0; c < 5; ++c) append_row(base[c], cnt + c, cls == c, v);
+        int cls = -1;
+        if (act) {
+            if (mid) cls = dx <= 32 ? 0 : dx <= kSmallTableDx ? 1 : 5;
+            else cls = dx <= 32 ? 2 : dx > dx_cta ? 4 : dx <= kSmallTableDx ? 3 : 6;
+        }
+        for (int c = 0; c < kP2Lists; ++c)
+            append_row(lists + p2_list_start(c, n_mid, n_large), cnt + c, cls == c, v);
     }
 }
 
@@ -1542,7 +1556,7 @@ static void launch_p1_large(rs_graph *g, const Batch &B, int *err, size_t smem) 
 }
 template <int NT>
 static void launch_p2_large(rs_graph *g, const Batch &B, int *err, size_t smem) {
-    int32_t *L4 = g->p2rows + 2 * g->n_mid + 2 * g->n_large;
+    int32_t *L4 = g->p2rows + p2_list_start(4, g->n_mid, g->n_large);
     p2_large_kernel<NT><<<grid_for(g->n_large, 1, 2), NT, smem, g->aux[4]>>>(
         g->off, L4, g->p2cnt + 4, B, g->tune.p2_cta_dx + 1, g->LG, g->rec, g->rsum, g->cl_col,
         g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, Strict{g->col, g->sx});
@@ -1569,9 +1583,8 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     }
     prof_mark(g, s, "memset", false);
     size_t p1_smem = 8 * (size_t)g->large_cap, p2_smem = 32 * (size_t)g->large_cap;
-    size_t p2_mid_smem = (size_t)kMidWarps * kWarpCap * kMidSlotBytes;
-    // ---- P1: the larger row classes run concurrently on auxiliary streams and
-    //      seed w_max; then the small rows, most of which skip their column maxima
+    // ---- P1: every row class on its own stream; the larger classes are launched
+    //      first, so their maxima seed w_max early and most small rows skip theirs
     if (int rc = fork_aux(g, s)) return rc;
     if (g->n_hubs) {
         hub_p1_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[0]>>>(
@@ -1596,13 +1609,13 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->rsum, g->cl_col, g->cl_lab);
         RS_LAUNCHED(g, g->aux[2], "p1_mid");
     }
-    if (int rc = join_aux(g, s, 3)) return rc;
     if (g->n_small) {
-        p1_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, s>>>(
+        p1_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[3]>>>(
             g->off, g->col, g->lab, g->rows_small, g->n_small, B, g->LG, g->rec, g->Lall,
             g->rsum, g->cl_col, g->cl_lab);
-        RS_LAUNCHED(g, s, "p1_small");
+        RS_LAUNCHED(g, g->aux[3], "p1_small");
     }
+    if (int rc = join_aux(g, s, 4)) return rc;
     // ---- G_x offsets
     gx_capacity_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->rec, n, g->xoff);
     RS_LAUNCHED(g, s, "gx_capacity");
@@ -1617,9 +1630,9 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_LAUNCHED(g, s, "strict_pairs");
     }
     const int64_t nm = g->n_mid, nl = g->n_large;
-    int32_t *L0 = g->p2rows, *L1 = L0 + nm, *L2 = L0 + 2 * nm, *L3 = L2 + nl;
+    auto Lst = [&](int c) { return g->p2rows + p2_list_start(c, nm, nl); };
     if (nm + nl) {
-        RS_CUDA_TRY(cudaMemsetAsync(g->p2cnt, 0, 8 * sizeof(int32_t), s));
+        RS_CUDA_TRY(cudaMemsetAsync(g->p2cnt, 0, kP2Lists * sizeof(int32_t), s));
         p2_split_kernel<<<grid_for(nm + nl, 256, 8), 256, 0, s>>>(g->rows_mid, nm, g->rows_large, nl, g->rec,
                                                                   g->tune.p2_cta_dx, g->p2rows, g->p2cnt);
         RS_LAUNCHED(g, s, "p2_split");
@@ -1632,26 +1645,35 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->xcol, g->xS, g->xout, g->xin, SX);
         RS_LAUNCHED(g, g->aux[0], "p2_small");
     }
+    const size_t smem256 = (size_t)kMidWarps * 256 * kMidSlotBytes, smem512 = (size_t)kMidWarps * 512 * kMidSlotBytes;
     if (g->n_mid) {
         p2_warp_kernel<<<grid_for(g->n_mid * 32, NT, cps), NT, 0, g->aux[1]>>>(
-            g->off, L0, g->p2cnt + 0, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff, g->xcol,
+            g->off, Lst(0), g->p2cnt + 0, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff, g->xcol,
             g->xS, g->xout, g->xin, SX);
         RS_LAUNCHED(g, g->aux[1], "p2_warp");
-        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, p2_mid_smem, g->aux[5]>>>(
-            g->off, L1, g->p2cnt + 1, B, 1 << 30, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
-            g->xcol, g->xS, g->xout, g->xin, err, SX);
+        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 4), NT, smem256, g->aux[5]>>>(
+            g->off, Lst(1), g->p2cnt + 1, B, 1 << 30, 256, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
+            g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX);
         RS_LAUNCHED(g, g->aux[5], "p2_mid");
+        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, smem512, g->aux[1]>>>(
+            g->off, Lst(5), g->p2cnt + 5, B, 1 << 30, 512, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
+            g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX);
+        RS_LAUNCHED(g, g->aux[1], "p2_mid_wide");
     }
     if (g->n_large) {
         // large rows whose cross list fits a per-warp table go warp-per-row too
         p2_warp_kernel<<<grid_for(g->n_large * 32, NT, cps), NT, 0, g->aux[2]>>>(
-            g->off, L2, g->p2cnt + 2, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
+            g->off, Lst(2), g->p2cnt + 2, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin, SX);
         RS_LAUNCHED(g, g->aux[2], "p2_warp");
-        p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, p2_mid_smem, g->aux[2]>>>(
-            g->off, L3, g->p2cnt + 3, B, g->tune.p2_cta_dx, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab,
-            g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX);
+        p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 4), NT, smem256, g->aux[2]>>>(
+            g->off, Lst(3), g->p2cnt + 3, B, g->tune.p2_cta_dx, 256, g->LG, g->rec, g->rsum, g->cl_col,
+            g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX);
         RS_LAUNCHED(g, g->aux[2], "p2_large_warp");
+        p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, smem512, g->aux[3]>>>(
+            g->off, Lst(6), g->p2cnt + 6, B, g->tune.p2_cta_dx, 512, g->LG, g->rec, g->rsum, g->cl_col,
+            g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX);
+        RS_LAUNCHED(g, g->aux[3], "p2_large_warp_wide");
         switch (g->tune.p2_cta_threads) {
         case 256: launch_p2_large<256>(g, B, err, p2_smem); break;
         case 512: launch_p2_large<512>(g, B, err, p2_smem); break;
