@@ -574,7 +574,8 @@ static int alloc_workspace(rs_graph *g) {
     RS_CUDA_TRY(dmalloc(&g->xin, n));
     RS_CUDA_TRY(dmalloc(&g->xR, nnz));
     RS_CUDA_TRY(dmalloc(&g->p2rows, 4 * (size_t)n));
-    RS_CUDA_TRY(dmalloc(&g->p2cnt, 8));
+    RS_CUDA_TRY(dmalloc(&g->p2cnt, 16));
+    RS_CUDA_TRY(dmalloc(&g->wq, 16));
     if (g->strict) RS_CUDA_TRY(dmalloc(&g->sx, 2 * (size_t)nnz));
     RS_CUDA_TRY(dmalloc(&g->scan_tmp, scan_tmp_words(std::max<int64_t>(n + 1, 1)) + 64));
     RS_CUDA_TRY(dmalloc(&g->rows_small, n));
@@ -591,7 +592,7 @@ static void free_graph(rs_graph *g) {
                     g->rows_small, g->rows_mid, g->rows_large, g->rows_small_deg, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
                     g->Lall, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->scan_tmp, g->tk_hist,
                     g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->xR, g->rsum, g->cl_col, g->cl_lab,
-                    g->winv, g->gid, g->gk, g->gnode, g->p2rows, g->p2cnt, g->sx};
+                    g->winv, g->gid, g->gk, g->gnode, g->p2rows, g->p2cnt, g->sx, g->wq};
     for (void *p : ptrs) cudaFree(p);
     free_hub_tables(g);
     for (cudaEvent_t e : g->prof_ev) cudaEventDestroy(e);

@@ -148,6 +148,7 @@ struct rs_graph {
     rs::df *xR = nullptr;                     // at out-slot (w -> u): the reverse value S(u -> w)
     int32_t *p2rows = nullptr;                // P2 row lists by cross degree (4 n), counted in p2cnt
     int32_t *p2cnt = nullptr;
+    unsigned long long *wq = nullptr;         // per-pass row counters of the dynamically scheduled kernels
     int64_t *scan_tmp = nullptr;              // block sums for scans
     // top-k workspace
     uint32_t *tk_hist = nullptr;

@@ -111,6 +111,21 @@ __device__ __forceinline__ void publish_max(const Batch &B, int32_t gi, df m, fl
 // P1
 // ======================================================================================
 
+// Row kernels take their next row from a per-launch counter (zeroed at the start of
+// every scoring pass), so warps or CTAs that drew short rows take more and no long
+// tail is left on a few of them.
+__device__ __forceinline__ int64_t warp_next(unsigned long long *ctr) {
+    unsigned long long t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(ctr, 1ull);
+    return (int64_t)__shfl_sync(FULL, t, 0);
+}
+__device__ __forceinline__ int64_t cta_next(unsigned long long *ctr, long long *sh) {
+    __syncthreads();
+    if (threadIdx.x == 0) *sh = (long long)atomicAdd(ctr, 1ull);
+    __syncthreads();
+    return *sh;
+}
+
 constexpr int kSlots = kSmallMax;
 
 __device__ __forceinline__ void store_rowsum(RowSum *rsum, int32_t v, const RowAgg &a) {
@@ -263,16 +278,15 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
     const int32_t *__restrict__ rows, int64_t nrows, Batch B, const uint64_t *__restrict__ LG,
     NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, int *err,
-    RowSum *__restrict__ rsum, int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab) {
+    RowSum *__restrict__ rsum, int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab,
+    unsigned long long *wq) {
     __shared__ int32_t skey[kMidWarps][kWarpCap];
     __shared__ uint32_t scnt[kMidWarps][kWarpCap];
     __shared__ int16_t sused[kMidWarps][kWarpCap];    // slots taken by the current row
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (uint32_t j = lane; j < kWarpCap; j += 32) { skey[wid][j] = kEmpty; scnt[wid][j] = 0; }
     __syncwarp();
-    for (int64_t i = warp; i < nrows; i += nwarps) {
+    for (int64_t i = warp_next(wq); i < nrows; i = warp_next(wq)) {
         int32_t v = rows[i];
         int64_t b = off[v];
         int d = (int)(off[v + 1] - b);
@@ -360,14 +374,16 @@ __global__ void __launch_bounds__(NT) p1_large_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
     const int32_t *__restrict__ rows, int64_t nrows, Batch B, const uint64_t *__restrict__ LG,
     NodeRec *__restrict__ rec, int32_t *__restrict__ Lall, int *err,
-    RowSum *__restrict__ rsum, int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab) {
+    RowSum *__restrict__ rsum, int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab,
+    unsigned long long *wq) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t sh_u32[NT / 32];
     __shared__ u128 sh_u128[NT / 32];
     __shared__ df sh_df[NT / 32];
     __shared__ int32_t sh_cnt[NT / 32];
     int tid = threadIdx.x, lane = tid & 31;
-    for (int64_t i = blockIdx.x; i < nrows; i += gridDim.x) {
+    __shared__ long long sh_next;
+    for (int64_t i = cta_next(wq, &sh_next); i < nrows; i = cta_next(wq, &sh_next)) {
         int32_t v = rows[i];
         int64_t b = off[v];
         int d = (int)(off[v + 1] - b);
@@ -732,16 +748,14 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
-    int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err, Strict SX) {
+    int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err, Strict SX, unsigned long long *wq) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t stage[kThreads];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t *st = stage + (threadIdx.x & ~31);
     unsigned char *base_w = smem + (size_t)wid * wslots * kMidSlotBytes;   // wslots >= every row's table
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nrows = *nrows_dev;               // rows of this kernel, counted by p2_split
-    for (int64_t i = warp; i < nrows; i += nwarps) {
+    for (int64_t i = warp_next(wq); i < nrows; i = warp_next(wq)) {
         int32_t w = rows[i];
         int64_t b = off[w];
         int d = (int)(off[w + 1] - b);
@@ -859,14 +873,15 @@ __global__ void __launch_bounds__(NT) p2_large_kernel(
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
-    int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err, Strict SX) {
+    int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err, Strict SX, unsigned long long *wq) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int32_t sh_cnt[2 * NT / 32];
     __shared__ uint64_t stage[NT];
     int tid = threadIdx.x, lane = tid & 31;
     uint64_t *st = stage + (tid & ~31);
     const int64_t nrows = *nrows_dev;               // rows of this kernel, counted by p2_split
-    for (int64_t i = blockIdx.x; i < nrows; i += gridDim.x) {
+    __shared__ long long sh_next;
+    for (int64_t i = cta_next(wq, &sh_next); i < nrows; i = cta_next(wq, &sh_next)) {
         int32_t w = rows[i];
         int64_t b = off[w];
         int d = (int)(off[w + 1] - b);
@@ -1271,16 +1286,20 @@ __device__ void p3_node_global(int32_t a, int32_t dA, const int64_t *xoff, const
     }
 }
 
+// groups of 32 nodes are handed out by an atomic counter (next_group, zeroed before
+// the launch), so warps that drew light groups take more and no tail is left waiting
 __global__ void __launch_bounds__(kThreads) p3_list_kernel(
     int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
     const df *__restrict__ xR, const int32_t *__restrict__ xout, const NodeRec *__restrict__ rec,
-    unsigned long long *acc) {
+    unsigned long long *acc, unsigned long long *next_group) {
     __shared__ P3Stage stage[kP3Warps];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     P3Stage &S = stage[wid];
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+    while (true) {
+        unsigned long long ticket = 0;
+        if (lane == 0) ticket = atomicAdd(next_group, 1ull);
+        int64_t base = (int64_t)__shfl_sync(FULL, ticket, 0) * 32;
+        if (base >= n) break;
         int64_t av = base + lane;
         int32_t da = av < n ? xout[av] : 0;
         bool grp = da >= 2 && da <= kWinCap;
@@ -1552,14 +1571,14 @@ template <int NT>
 static void launch_p1_large(rs_graph *g, const Batch &B, int *err, size_t smem) {
     p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, smem, g->aux[1]>>>(
         g->off, g->col, g->lab, g->rows_large, g->n_large, B, g->LG, g->rec, g->Lall, err,
-        g->rsum, g->cl_col, g->cl_lab);
+        g->rsum, g->cl_col, g->cl_lab, g->wq + 1);
 }
 template <int NT>
 static void launch_p2_large(rs_graph *g, const Batch &B, int *err, size_t smem) {
     int32_t *L4 = g->p2rows + p2_list_start(4, g->n_mid, g->n_large);
     p2_large_kernel<NT><<<grid_for(g->n_large, 1, 2), NT, smem, g->aux[4]>>>(
         g->off, L4, g->p2cnt + 4, B, g->tune.p2_cta_dx + 1, g->LG, g->rec, g->rsum, g->cl_col,
-        g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, Strict{g->col, g->sx});
+        g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, Strict{g->col, g->sx}, g->wq + 6);
 }
 
 int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
@@ -1575,6 +1594,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     Batch B{g->gid, g->gk, g->k, g->wmax_bits};
     RS_CUDA_TRY(cudaMemsetAsync(g->acc, 0, 2 * n * sizeof(unsigned long long), s));
     RS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    RS_CUDA_TRY(cudaMemsetAsync(g->wq, 0, 16 * sizeof(unsigned long long), s));   // row counters
     if (g->n_hubs) {
         RS_CUDA_TRY(cudaMemsetAsync(g->hkey, 0xFF, g->hub_slots * sizeof(int32_t), s));
         RS_CUDA_TRY(cudaMemsetAsync(g->hcnt, 0, g->hub_slots * sizeof(uint32_t), s));
@@ -1606,7 +1626,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     if (g->n_mid) {
         p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, cps), NT, 0, g->aux[2]>>>(
             g->off, g->col, g->lab, g->rows_mid, g->n_mid, B, g->LG, g->rec, g->Lall, err,
-            g->rsum, g->cl_col, g->cl_lab);
+            g->rsum, g->cl_col, g->cl_lab, g->wq + 0);
         RS_LAUNCHED(g, g->aux[2], "p1_mid");
     }
     if (g->n_small) {
@@ -1653,11 +1673,11 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_LAUNCHED(g, g->aux[1], "p2_warp");
         p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 4), NT, smem256, g->aux[5]>>>(
             g->off, Lst(1), g->p2cnt + 1, B, 1 << 30, 256, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
-            g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX);
+            g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 2);
         RS_LAUNCHED(g, g->aux[5], "p2_mid");
         p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, smem512, g->aux[1]>>>(
             g->off, Lst(5), g->p2cnt + 5, B, 1 << 30, 512, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
-            g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX);
+            g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 3);
         RS_LAUNCHED(g, g->aux[1], "p2_mid_wide");
     }
     if (g->n_large) {
@@ -1668,11 +1688,11 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_LAUNCHED(g, g->aux[2], "p2_warp");
         p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 4), NT, smem256, g->aux[2]>>>(
             g->off, Lst(3), g->p2cnt + 3, B, g->tune.p2_cta_dx, 256, g->LG, g->rec, g->rsum, g->cl_col,
-            g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX);
+            g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 4);
         RS_LAUNCHED(g, g->aux[2], "p2_large_warp");
         p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, smem512, g->aux[3]>>>(
             g->off, Lst(6), g->p2cnt + 6, B, g->tune.p2_cta_dx, 512, g->LG, g->rec, g->rsum, g->cl_col,
-            g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX);
+            g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 5);
         RS_LAUNCHED(g, g->aux[3], "p2_large_warp_wide");
         switch (g->tune.p2_cta_threads) {
         case 256: launch_p2_large<256>(g, B, err, p2_smem); break;
@@ -1702,7 +1722,9 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     gx_mirror_kernel<<<grid_for(g->nnz, kMirTile, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xout, g->xin,
                                                                    g->xR, err);
     RS_LAUNCHED(g, s, "gx_mirror");
-    p3_list_kernel<<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xR, g->xout, g->rec, g->acc);
+    unsigned long long *next_group = g->wq + 7;
+    p3_list_kernel<<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xR, g->xout, g->rec, g->acc,
+                                                        next_group);
     RS_LAUNCHED(g, s, "p3_list");
     // ---- finalize
     graph_scale_kernel<<<(g->n_graphs + 255) / 256, 256, 0, s>>>(g->wmax_bits, g->n_graphs, g->winv);
