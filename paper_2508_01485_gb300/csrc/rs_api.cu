@@ -394,6 +394,28 @@ __global__ void degree_scatter_kernel(const int64_t *off, const int32_t *rows, i
     if (i < m) out[atomicAdd(&cursor[off[rows[i] + 1] - off[rows[i]]], 1)] = rows[i];
 }
 // per hub: row bounds and the communities of its graph
+// mid and large rows, largest first: the row kernels hand rows out dynamically,
+// so taking the longest ones first leaves short rows for the end (bucket of a
+// degree: 4 per octave, descending)
+constexpr int kDegBuckets = 4 * 32;
+__device__ __forceinline__ int desc_bucket(int64_t d) {
+    int e = 63 - __clzll((long long)(d | 1));
+    int q = e >= 2 ? (int)((d >> (e - 2)) & 3) : 0;
+    return kDegBuckets - 1 - (4 * e + q);
+}
+__global__ void bucket_hist_kernel(const int64_t *off, const int32_t *rows, int64_t m, int *hist) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) atomicAdd(&hist[desc_bucket(off[rows[i] + 1] - off[rows[i]])], 1);
+}
+__global__ void bucket_prefix_kernel(int *hist) {
+    int acc = 0;
+    for (int b = 0; b < kDegBuckets; ++b) { int c = hist[b]; hist[b] = acc; acc += c; }
+}
+__global__ void bucket_scatter_kernel(const int64_t *off, const int32_t *rows, int64_t m, int *cursor, int32_t *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[atomicAdd(&cursor[desc_bucket(off[rows[i] + 1] - off[rows[i]])], 1)] = rows[i];
+}
+
 __global__ void hub_bounds_kernel(const int64_t *off, const int32_t *hubs, int64_t nh, int32_t k, const int32_t *gid,
                                   const int32_t *gk, int64_t *bounds) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -468,6 +490,23 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
         RS_CUDA_TRY(cudaGetLastError());
     } else if (g->n_small == 1) {
         RS_CUDA_TRY(cudaMemcpyAsync(g->rows_small_deg, g->rows_small, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    }
+    // mid and large rows by degree, largest first (through the small-row scratch list)
+    for (int cls = 1; cls < 3; ++cls) {
+        int32_t *rows = cls == 1 ? g->rows_mid : g->rows_large;
+        int64_t m = cls == 1 ? g->n_mid : g->n_large;
+        if (m < 2) continue;
+        int *hist = nullptr;
+        RS_CUDA_TRY(cudaMalloc(&hist, kDegBuckets * sizeof(int)));
+        unsigned mb = (unsigned)((m + 255) / 256);
+        cudaError_t e = cudaMemsetAsync(hist, 0, kDegBuckets * sizeof(int), s);
+        if (!e) { bucket_hist_kernel<<<mb, 256, 0, s>>>(g->off, rows, m, hist); e = cudaGetLastError(); }
+        if (!e) { bucket_prefix_kernel<<<1, 1, 0, s>>>(hist); e = cudaGetLastError(); }
+        if (!e) { bucket_scatter_kernel<<<mb, 256, 0, s>>>(g->off, rows, m, hist, g->rows_small_deg + g->n_small); e = cudaGetLastError(); }
+        if (!e) e = cudaMemcpyAsync(rows, g->rows_small_deg + g->n_small, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        cudaFree(hist);
+        if (e) return cuda_fail(e, "sort rows by degree");
     }
     // hubs: host-side work list (hubs are few)
     int nh = hdr[2];

@@ -31,6 +31,14 @@ constexpr size_t kTkSmem = (size_t)kSortMax * (8 + 4);
 
 enum { C_CAND = 0, C_NEED = 1, C_SURE = 2, C_SEL = 3, C_DONE = 4, C_NEXT = 5, C_SRC = 6 };
 
+// keys left when the selection stops and sorts: a bitonic sort costs log^2 of its
+// size in barriers, so another radix level is cheaper than sorting much more than K
+__host__ __device__ __forceinline__ int sort_target(int k) {
+    int p = 2048;
+    while (p < 2 * k && p < kSortMax) p <<= 1;
+    return p;
+}
+
 // digit `level` (0 = most significant) of the 96-bit key (key64 : ~id)
 __device__ __forceinline__ uint32_t digit_of(unsigned long long key, uint32_t nid, int level) {
     int hi = 95 - kBits * level;                 // top bit of the digit
@@ -177,7 +185,7 @@ __global__ void __launch_bounds__(kTkThreads) tk_select_kernel(TkArgs A) {
         if (gtid == 0) {
             ctrl[C_CAND] = ctrl[C_NEXT];
             ctrl[C_SRC] = dst;
-            if (ctrl[C_CAND] <= ctrl[C_NEED] || ctrl[C_SURE] + ctrl[C_CAND] <= kSortMax) ctrl[C_DONE] = 1;
+            if (ctrl[C_CAND] <= ctrl[C_NEED] || ctrl[C_SURE] + ctrl[C_CAND] <= sort_target(A.k)) ctrl[C_DONE] = 1;
         }
         grid.sync();
     }
