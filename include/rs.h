@@ -234,6 +234,11 @@ rs_status rs_launch_count(const rs_graph *g, int64_t *launches);
  *   p1_cta_threads  threads per CTA row in the first pass                 {128, 256, 512}
  *   p2_cta_threads  threads per CTA row in the second pass                {256, 512, 1024}
  *   ctas_per_sm  grid size of the grid-stride kernels, in CTAs per SM     [1, 32]
+ *   p3_mirror    1: a pass pairs every G_x edge's two directed values     {0, 1}
+ *                before the triangle listing (an extra array of nnz
+ *                float pairs); 0: the listing looks the reverse values of
+ *                each triangle up in in-lists (fewer searches when G_x has
+ *                few triangles per edge)
  * Powers of two are required where a set is given.
  */
 typedef struct {
@@ -245,6 +250,7 @@ typedef struct {
     int32_t p1_cta_threads;
     int32_t p2_cta_threads;
     int32_t ctas_per_sm;
+    int32_t p3_mirror;
 } rs_tuning;
 
 /* rs_default_tuning -- the parameters a new graph starts with. */

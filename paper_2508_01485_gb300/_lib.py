@@ -22,7 +22,7 @@ RS_TRIAD_STRICT = 4
 _lib = None
 
 TUNING_FIELDS = ("small_max", "warp_cap", "cta_cap", "hub_chunk", "p2_cta_dx", "p1_cta_threads",
-                 "p2_cta_threads", "ctas_per_sm")
+                 "p2_cta_threads", "ctas_per_sm", "p3_mirror")
 
 
 class Tuning(ctypes.Structure):

@@ -591,6 +591,20 @@ static int build_tables(rs_graph *g, cudaStream_t s) {
     return 0;
 }
 
+// xR (one reverse value per G_x slot) exists while the mirror pass is selected
+int rs::set_mirror_buffer(rs_graph *g) {
+    if (g->tune.p3_mirror && !g->xR) {
+        RS_CUDA_TRY(dmalloc(&g->xR, std::max<int64_t>(g->nnz, 1)));
+        RS_CUDA_TRY(dmalloc(&g->xtile, g->nnz / kMirTile + 2));
+    } else if (!g->tune.p3_mirror && g->xR) {
+        RS_CUDA_TRY(cudaFree(g->xR));
+        RS_CUDA_TRY(cudaFree(g->xtile));
+        g->xR = nullptr;
+        g->xtile = nullptr;
+    }
+    return 0;
+}
+
 static int alloc_workspace(rs_graph *g) {
     int64_t n = g->n, nnz = g->nnz;
     for (int i = 0; i < rs_graph::kAux; ++i) {
@@ -611,7 +625,7 @@ static int alloc_workspace(rs_graph *g) {
     RS_CUDA_TRY(dmalloc(&g->xS, nnz));
     RS_CUDA_TRY(dmalloc(&g->xout, n));
     RS_CUDA_TRY(dmalloc(&g->xin, n));
-    RS_CUDA_TRY(dmalloc(&g->xR, nnz));
+    if (int rc = rs::set_mirror_buffer(g)) return rc;
     RS_CUDA_TRY(dmalloc(&g->p2rows, 4 * (size_t)n));
     RS_CUDA_TRY(dmalloc(&g->p2cnt, 16));
     RS_CUDA_TRY(dmalloc(&g->wq, 16));
@@ -630,7 +644,7 @@ static void free_graph(rs_graph *g) {
     void *ptrs[] = {g->off, g->off_alt, g->col, g->col_alt, g->lab, g->removed, g->dead,
                     g->rows_small, g->rows_mid, g->rows_large, g->rows_small_deg, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
                     g->Lall, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->scan_tmp, g->tk_hist,
-                    g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->xR, g->rsum, g->cl_col, g->cl_lab,
+                    g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->xR, g->xtile, g->rsum, g->cl_col, g->cl_lab,
                     g->winv, g->gid, g->gk, g->gnode, g->p2rows, g->p2cnt, g->sx, g->wq};
     for (void *p : ptrs) cudaFree(p);
     free_hub_tables(g);

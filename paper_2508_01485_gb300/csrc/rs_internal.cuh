@@ -96,6 +96,7 @@ inline rs_tuning default_tuning_value() {
     t.p1_cta_threads = 256;
     t.p2_cta_threads = 1024;
     t.ctas_per_sm = 8;
+    t.p3_mirror = 1;
     return t;
 }
 }  // namespace rs
@@ -145,7 +146,6 @@ struct rs_graph {
     int32_t *xcol = nullptr;                  // G_x neighbours (capacity nnz)
     rs::df *xS = nullptr;                     // S(w -> u) = w_w(C(u))^(1/3)
     int32_t *xout = nullptr, *xin = nullptr;  // out / in counts per node
-    rs::df *xR = nullptr;                     // at out-slot (w -> u): the reverse value S(u -> w)
     int32_t *p2rows = nullptr;                // P2 row lists by cross degree (4 n), counted in p2cnt
     int32_t *p2cnt = nullptr;
     unsigned long long *wq = nullptr;         // per-pass row counters of the dynamically scheduled kernels
@@ -173,6 +173,8 @@ struct rs_graph {
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kAux] = {};
     // launch parameters and a counter bumped whenever buffers or row classes change
+    rs::df *xR = nullptr;                     // p3_mirror: at out-slot (w -> u) the reverse value S(u -> w)
+    int32_t *xtile = nullptr;                 // p3_mirror: node holding the first slot of each mirror tile
     rs_tuning tune = rs::default_tuning_value();
     uint64_t version = 0;
     bool alg2 = false;                        // RS_ALG2_COMPAT: |L| = L_all - 1 for every column
@@ -184,6 +186,7 @@ struct rs_graph {
 namespace rs {
 
 constexpr int kThreads = 256;
+constexpr int kMirTile = 2048;               // G_x slots per tile of the mirror pass
 
 // error reporting (rs_api.cu): returns the status after recording the message
 int fail(int status, const std::string &msg);
@@ -201,6 +204,7 @@ int inclusive_scan_i64(int64_t *a, int64_t m, int64_t *tmp, cudaStream_t s, int6
 
 // launch accounting: count a kernel launch (or record a non-kernel operation)
 // and, when profiling is on, record an event after it on the stream
+int set_mirror_buffer(rs_graph *g);
 void prof_begin(rs_graph *g, cudaStream_t s);
 void prof_mark(rs_graph *g, cudaStream_t s, const char *name, bool is_kernel);
 // make the auxiliary streams wait for s / make s wait for the first `used` auxiliary streams

@@ -1084,18 +1084,72 @@ __global__ void __launch_bounds__(NT) hub_p2_emit_kernel(
 // ======================================================================================
 // P3: Type-I triads from G_x triangles
 // ======================================================================================
-// P3m (mirror): every G_x out-slot (w -> u) receives the reverse value
+// The reverse value of a G_x edge.  Row x writes its in-neighbours (the G_x
+// neighbours of lower rank) from the back of its G_x row in increasing id
+// order, so its in-list read backwards from the row's last slot is sorted and
+// S(x -> y) for an in-neighbour y is found by binary search there.  P3 needs
+// the reverse values only of the edges of triangles.  It either looks them up
+// per triangle (three searches in in-lists), or reads them from xR, which the
+// mirror pass below fills for every G_x edge beforehand (one search per edge,
+// in a short out-list).  The first wins when triangles are few per G_x edge
+// (0.11 on the 1M-node DC-SBM graph), the second when they are many; the
+// choice is a launch parameter (p3_mirror).
+__device__ __forceinline__ df in_value(int32_t x, int32_t y, const int64_t *xoff, const int32_t *xcol,
+                                       const df *xS, const int32_t *xin, int *err) {
+    const int64_t last = xoff[x + 1] - 1;
+    const int32_t len = xin[x];
+    int32_t l = 0, h = len;
+    while (l < h) {
+        int32_t mid = (l + h) >> 1;
+        if (xcol[last - mid] < y) l = mid + 1; else h = mid;
+    }
+    if (l < len && xcol[last - l] == y) return xS[last - l];
+    atomicOr(err, 16);
+    return df{0.0f, 0.0f};
+}
+
+// where P3 takes a reverse value: xR at the out-slot (mirror pass), or the
+// in-list of the higher-ranked end
+struct Rev {
+    const df *xR;                   // null: look the values up
+    const int64_t *xoff;
+    const int32_t *xcol;
+    const df *xS;
+    const int32_t *xin;
+    int *err;
+    // S(hi -> lo) for the G_x edge whose out-slot (lo -> hi) is `slot`
+    __device__ __forceinline__ df get(int64_t slot, int32_t hi, int32_t lo) const {
+        return xR ? xR[slot] : in_value(hi, lo, xoff, xcol, xS, xin, err);
+    }
+};
+
+// P3m (mirror, when p3_mirror is set): every G_x out-slot (w -> u) receives the reverse value
 // S(u -> w), which row u wrote at its in-slot for w.  Node u's slots are
 // [xoff[u], xoff[u] + dx(u)), its in-slots the last xin(u) of them.  The slot
 // space [0, xoff[n]) is cut into tiles of kMirTile consecutive slots, one
 // tile per CTA trip, so the work per CTA does not depend on the in-degrees.
-// A tile stages the offsets of the nodes it spans in shared memory, counts
+// The nodes a tile spans run from the node holding its first slot to the one
+// holding the next tile's first slot (a table filled during P2, so no tile
+// searches the offsets).  A tile stages their offsets in shared memory, counts
 // their in-slots inside the tile and spreads only those over the threads; a
 // slot's out-slot twin is found by binary search in w's out-list, which is
 // short (w has the lower rank).  A tile spanning more than kMirNodes nodes
 // (long runs of nodes outside G_x) searches the offsets in global memory.
-constexpr int kMirTile = 2048;
 constexpr int kMirNodes = 1024;
+
+// cover[t] = the node whose G_x row holds slot t kMirTile (t < tiles), and
+// cover[tiles] = the node holding the last slot; every slot lies in exactly
+// one non-empty row, so each entry is written once
+__global__ void mirror_tiles_kernel(int64_t n, const int64_t *__restrict__ xoff, int32_t *__restrict__ cover) {
+    const int64_t S = xoff[n];
+    const int64_t tiles = (S + kMirTile - 1) / kMirTile;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = xoff[u], hi = xoff[u + 1];
+        if (hi <= lo) continue;
+        for (int64_t t = (lo + kMirTile - 1) / kMirTile; t * kMirTile < hi; ++t) cover[t] = (int32_t)u;
+        if (hi == S) cover[tiles] = (int32_t)u;
+    }
+}
 
 __device__ __forceinline__ int64_t last_leq(const int64_t *xoff, int64_t lo, int64_t hi, int64_t key) {
     // last index i in [lo, hi) with xoff[i] <= key (xoff[lo] <= key)
@@ -1122,8 +1176,8 @@ __device__ __forceinline__ void mirror_one(int64_t sl, int32_t u, const int64_t 
 
 __global__ void __launch_bounds__(kThreads) gx_mirror_kernel(
     int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
-    const int32_t *__restrict__ xout, const int32_t *__restrict__ xin, df *__restrict__ xR, int *err) {
-    __shared__ int64_t range[2];
+    const int32_t *__restrict__ xout, const int32_t *__restrict__ xin, const int32_t *__restrict__ cover,
+    df *__restrict__ xR, int *err) {
     __shared__ int64_t s_lo[kMirNodes];          // first in-slot of each staged node inside the tile
     __shared__ int32_t s_pre[kMirNodes + 1];     // prefix sums of the staged nodes' in-slots in the tile
     __shared__ int32_t s_wsum[kThreads / 32];
@@ -1132,14 +1186,9 @@ __global__ void __launch_bounds__(kThreads) gx_mirror_kernel(
     const int64_t tiles = (S + kMirTile - 1) / kMirTile;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         int64_t s0 = t * kMirTile, s1 = min(S, s0 + kMirTile);
-        __syncthreads();
-        if (tid == 0) {
-            int64_t u0 = last_leq(xoff, 0, n + 1, s0);
-            range[0] = u0;
-            range[1] = last_leq(xoff, u0, n + 1, s1 - 1) + 1;
-        }
-        __syncthreads();
-        int64_t ulo = range[0], uhi = range[1];
+        // nodes [ulo, uhi): from the one holding s0 to the one holding s1 (or the last slot)
+        int64_t ulo = cover[t], uhi = (int64_t)cover[t + 1] + 1;
+        __syncthreads();                             // the previous tile's stage is free
         int32_t nn = (int32_t)(uhi - ulo);
         if (nn > kMirNodes) {
             for (int64_t sl = s0 + tid; sl < s1; sl += blockDim.x) {
@@ -1216,10 +1265,12 @@ __device__ __forceinline__ void triangle_terms(int32_t a, int32_t b, int32_t c, 
 // index space that the lanes share evenly (four per lane per trip): entry e
 // owns the pairs (e, f > e) of its node.  The closing edge is looked up by
 // binary search in the lower-ranked node's out-list in global memory (short:
-// the out-degree of a low-ranked node).  Each of the three slots of a
-// triangle holds both directed values (xS forward, xR reverse), so the
-// triangle's terms are added where it is found.  Nodes with more than kWinCap
-// out-neighbours take a lane-strided path over global memory.
+// the out-degree of a low-ranked node).  Found triangles are queued in shared
+// memory and finished a warp at a time, one per lane: the three forward values
+// sit at the out-slots, the three reverse ones are looked up in the in-lists
+// of the two higher-ranked nodes, and the terms of the three apexes are added.
+// Nodes with more than kWinCap out-neighbours take a lane-strided path over
+// global memory.
 constexpr int kWinCap = 128;
 constexpr int kP3Warps = kThreads / 32;
 
@@ -1238,15 +1289,17 @@ struct P3Stage {
     uint8_t qow[64], qlo[64], qhi[64];
 };
 
-// finish the first m (<= 32) queued triangles of the window, one per lane
-__device__ __forceinline__ void p3_flush(const P3Stage &S, int m, int64_t base, const df *xS, const df *xR,
+// finish the first m (<= 32) queued triangles of the window, one per lane: the
+// forward values are at the three out-slots
+__device__ __forceinline__ void p3_flush(const P3Stage &S, int m, int64_t base, const df *xS, const Rev &R,
                                          unsigned long long *acc, int lane) {
     if (lane < m) {
         int ow = S.qow[lane], el = S.qlo[lane], eh = S.qhi[lane];
         int64_t ao = S.aoff[ow] - S.seg[ow];
         int64_t il = ao + el, ih = ao + eh, pc = S.qpos[lane];
-        triangle_terms((int32_t)(base + ow), S.nb[el], S.nb[eh], xS[il], xR[il], xS[ih], xR[ih], xS[pc], xR[pc],
-                       acc);
+        int32_t a = (int32_t)(base + ow), b = S.nb[el], c = S.nb[eh];
+        df Sba = R.get(il, b, a), Sca = R.get(ih, c, a), Scb = R.get(pc, c, b);
+        triangle_terms(a, b, c, xS[il], Sba, xS[ih], Sca, xS[pc], Scb, acc);
     }
 }
 
@@ -1266,7 +1319,7 @@ __device__ __forceinline__ int64_t find_in_list(const int32_t *xcol, int64_t lo,
 
 // a node with more than kWinCap out-neighbours: lanes stride over its first entries
 __device__ void p3_node_global(int32_t a, int32_t dA, const int64_t *xoff, const int32_t *xcol, const df *xS,
-                               const df *xR, const int32_t *xout, const NodeRec *rec, unsigned long long *acc,
+                               const Rev &R, const int32_t *xout, const NodeRec *rec, unsigned long long *acc,
                                int lane) {
     int64_t bA = xoff[a];
     for (int32_t i = lane; i < dA; i += 32) {
@@ -1281,7 +1334,9 @@ __device__ void p3_node_global(int32_t a, int32_t dA, const int64_t *xoff, const
             int64_t pos = b_low ? find_in_list(xcol, ob, db, c) : find_in_list(xcol, xoff[c], xout[c], b);
             if (pos < 0) continue;
             int64_t il = bA + (b_low ? i : j), ih = bA + (b_low ? j : i);
-            triangle_terms(a, b_low ? b : c, b_low ? c : b, xS[il], xR[il], xS[ih], xR[ih], xS[pos], xR[pos], acc);
+            int32_t lo = b_low ? b : c, hi = b_low ? c : b;
+            df Sla = R.get(il, lo, a), Sha = R.get(ih, hi, a), Shl = R.get(pos, hi, lo);
+            triangle_terms(a, lo, hi, xS[il], Sla, xS[ih], Sha, xS[pos], Shl, acc);
         }
     }
 }
@@ -1290,8 +1345,8 @@ __device__ void p3_node_global(int32_t a, int32_t dA, const int64_t *xoff, const
 // the launch), so warps that drew light groups take more and no tail is left waiting
 __global__ void __launch_bounds__(kThreads) p3_list_kernel(
     int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
-    const df *__restrict__ xR, const int32_t *__restrict__ xout, const NodeRec *__restrict__ rec,
-    unsigned long long *acc, unsigned long long *next_group) {
+    Rev R, const int32_t *__restrict__ xout, const NodeRec *__restrict__ rec, unsigned long long *acc,
+    unsigned long long *next_group) {
     __shared__ P3Stage stage[kP3Warps];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     P3Stage &S = stage[wid];
@@ -1396,7 +1451,7 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
                         qn += __popc(hm);
                         if (qn >= 32) {                        // a full warp of triangles
                             __syncwarp();
-                            p3_flush(S, 32, base, xS, xR, acc, lane);
+                            p3_flush(S, 32, base, xS, R, acc, lane);
                             __syncwarp();
                             if (lane < qn - 32) {
                                 S.qpos[lane] = S.qpos[32 + lane];
@@ -1410,7 +1465,7 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
                     }
                 }
                 __syncwarp();
-                p3_flush(S, qn, base, xS, xR, acc, lane);   // the window's stage is reused next
+                p3_flush(S, qn, base, xS, R, acc, lane);   // the window's stage is reused next
                 qn = 0;
                 __syncwarp();
             }
@@ -1421,7 +1476,7 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
             int l = __ffs(big) - 1;
             big &= big - 1;
             int32_t dA = __shfl_sync(FULL, da, l);
-            p3_node_global((int32_t)(base + l), dA, xoff, xcol, xS, xR, xout, rec, acc, lane);
+            p3_node_global((int32_t)(base + l), dA, xoff, xcol, xS, R, xout, rec, acc, lane);
         }
     }
 }
@@ -1665,6 +1720,11 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->xcol, g->xS, g->xout, g->xin, SX);
         RS_LAUNCHED(g, g->aux[0], "p2_small");
     }
+    if (g->tune.p3_mirror) {                         // the mirror's tile table, beside P2
+        if (!g->xR || !g->xtile) return fail(RS_EINVAL, "rs_score: p3_mirror is set but its buffers are missing");
+        mirror_tiles_kernel<<<grid_for(n, NT, cps), NT, 0, g->aux[0]>>>(n, g->xoff, g->xtile);
+        RS_LAUNCHED(g, g->aux[0], "mirror_tiles");
+    }
     const size_t smem256 = (size_t)kMidWarps * 256 * kMidSlotBytes, smem512 = (size_t)kMidWarps * 512 * kMidSlotBytes;
     if (g->n_mid) {
         p2_warp_kernel<<<grid_for(g->n_mid * 32, NT, cps), NT, 0, g->aux[1]>>>(
@@ -1718,12 +1778,15 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_LAUNCHED(g, g->aux[3], "hub_p2_emit");
     }
     if (int rc = join_aux(g, s, rs_graph::kAux)) return rc;
-    // ---- P3: reverse values, then triangles
-    gx_mirror_kernel<<<grid_for(g->nnz, kMirTile, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xout, g->xin,
-                                                                   g->xR, err);
-    RS_LAUNCHED(g, s, "gx_mirror");
+    // ---- P3: reverse values (mirror mode), then triangles
+    if (g->tune.p3_mirror) {
+        gx_mirror_kernel<<<grid_for(g->nnz, kMirTile, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xout,
+                                                                       g->xin, g->xtile, g->xR, err);
+        RS_LAUNCHED(g, s, "gx_mirror");
+    }
+    const Rev R{g->tune.p3_mirror ? g->xR : nullptr, g->xoff, g->xcol, g->xS, g->xin, err};
     unsigned long long *next_group = g->wq + 7;
-    p3_list_kernel<<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xR, g->xout, g->rec, g->acc,
+    p3_list_kernel<<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, R, g->xout, g->rec, g->acc,
                                                         next_group);
     RS_LAUNCHED(g, s, "p3_list");
     // ---- finalize

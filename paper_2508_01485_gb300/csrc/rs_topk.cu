@@ -6,12 +6,13 @@
 // higher among equal scores.  One cooperative launch (one 1024-thread CTA per
 // SM, grid-wide barriers from cooperative groups) runs a most-significant-digit
 // radix select with 12-bit digits:
-//   per level: privatised shared-memory histograms of the digit over the
-//   current candidates, merged into a global histogram; CTA 0 finds the bucket
-//   that holds the K-th key; keys of higher buckets are final ("sure"), keys
-//   of that bucket stay candidates.
-// As soon as the sure keys and the candidates fit one shared-memory sort
-// (kSortMax keys), CTA 0 sorts them (bitonic) and writes the first K.
+//   per level (three grid-wide barriers): privatised shared-memory histograms
+//   of the digit over the current candidates, merged into a global histogram;
+//   CTA 0 finds the bucket that holds the K-th key; keys of higher buckets are
+//   final ("sure"), keys of that bucket stay candidates, both appended with one
+//   atomic per warp, while the global histogram is cleared for the next level.
+// As soon as the sure keys and the candidates fit a small shared-memory sort
+// (about 2K keys), CTA 0 sorts them (bitonic) and writes the first K.
 #include <cooperative_groups.h>
 
 #include "rs.h"
@@ -29,7 +30,7 @@ constexpr int kLevels = 96 / kBits;
 constexpr int kSortMax = 16384;   // largest K, and the size of the final sort
 constexpr size_t kTkSmem = (size_t)kSortMax * (8 + 4);
 
-enum { C_CAND = 0, C_NEED = 1, C_SURE = 2, C_SEL = 3, C_DONE = 4, C_NEXT = 5, C_SRC = 6 };
+enum { C_NEED = 0, C_SURE = 1, C_SEL = 2, C_NEXT = 3 /* and 4: candidate counters of even / odd levels */ };
 
 // keys left when the selection stops and sorts: a bitonic sort costs log^2 of its
 // size in barriers, so another radix level is cheaper than sorting much more than K
@@ -75,60 +76,85 @@ __device__ __forceinline__ void load_item(const TkArgs &A, int level, int src, i
     }
 }
 
-// descending bitonic sort of (key, nid) pairs in shared memory, P a power of two
+// descending bitonic sort of (key, nid) pairs in shared memory, P a power of two;
+// the pair of each compare-exchange comes from shifts and masks (st is a power of two)
 __device__ void block_sort_desc(unsigned long long *key, uint32_t *nid, int P) {
     for (int size = 2; size <= P; size <<= 1)
         for (int st = size >> 1; st; st >>= 1) {
+            const int lst = __ffs(st) - 1;
+            const bool flip = st == (size >> 1);
             for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
-                int lo, hi;
-                if (st == (size >> 1)) {
-                    int blk = i / st, o = i % st;
-                    lo = blk * size + o;
-                    hi = blk * size + size - 1 - o;
-                } else {
-                    lo = (i / st) * 2 * st + (i % st);
-                    hi = lo + st;
-                }
-                bool less = key[lo] < key[hi] || (key[lo] == key[hi] && nid[lo] < nid[hi]);
-                if (less) {
-                    unsigned long long tk = key[lo]; key[lo] = key[hi]; key[hi] = tk;
-                    uint32_t ti = nid[lo]; nid[lo] = nid[hi]; nid[hi] = ti;
+                int base = (i >> lst) << (lst + 1), o = i & (st - 1);
+                int lo = base + o;
+                int hi = flip ? base + 2 * st - 1 - o : lo + st;
+                unsigned long long kl = key[lo], kh = key[hi];
+                uint32_t nl = nid[lo], nh = nid[hi];
+                if (kl < kh || (kl == kh && nl < nh)) {
+                    key[lo] = kh; key[hi] = kl;
+                    nid[lo] = nh; nid[hi] = nl;
                 }
             }
             __syncthreads();
         }
 }
 
+// append the flagged items of a warp to buf at a position drawn with one atomic
+// per warp (every lane of the warp calls; order inside the buffer is free)
+__device__ __forceinline__ void warp_append(bool flag, unsigned long long key, uint32_t nid, int *counter,
+                                            unsigned long long *kbuf, uint32_t *ibuf) {
+    unsigned m = __ballot_sync(0xFFFFFFFFu, flag);
+    if (!m) return;
+    int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (flag) {
+        int p = base + __popc(m & ((1u << lane) - 1u));
+        kbuf[p] = key; ibuf[p] = nid;
+    }
+}
+
 __global__ void __launch_bounds__(kTkThreads) tk_select_kernel(TkArgs A) {
     cg::grid_group grid = cg::this_grid();
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *sh_hist = (uint32_t *)smem;                      // kBins (levels)
-    __shared__ uint32_t part[kTkThreads];
+    __shared__ uint32_t part[32];
     __shared__ int sh_sel;
     __shared__ int64_t sh_above;
     int tid = threadIdx.x;
     int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid;
     int64_t gsize = (int64_t)gridDim.x * blockDim.x;
+    // every warp walks the same trip count, so warp-wide ballots see whole warps
+    int64_t wbase = gtid & ~31ll;
     int *ctrl = A.ctrl;
     if (gtid == 0) {
-        ctrl[C_CAND] = (int)A.n; ctrl[C_NEED] = A.k; ctrl[C_SURE] = 0; ctrl[C_SEL] = 0;
-        ctrl[C_NEXT] = 0; ctrl[C_SRC] = 0;
-        ctrl[C_DONE] = A.n <= kSortMax ? 1 : 0;                 // everything fits the final sort
+        ctrl[C_SURE] = 0; ctrl[C_NEXT] = 0; ctrl[C_NEXT + 1] = 0;
     }
+    for (int64_t b = gtid; b < kBins; b += gsize) A.hist[b] = 0;
+    // the state every thread derives alike: candidates m in buffer src, rank need among them
+    int src = 0;
+    int64_t m = A.n;
+    int64_t need = A.k;
+    bool done = A.n <= sort_target(A.k);                        // everything fits the final sort
     grid.sync();
     int level = 0;
-    for (; level < kLevels; ++level) {
-        if (*(volatile int *)&ctrl[C_DONE]) break;
-        int src = ctrl[C_SRC];
-        int64_t m = ctrl[C_CAND];
-        // histogram of this level's digit
+    for (; level < kLevels && !done; ++level) {
+        // histogram of this level's digit (the global one was cleared before)
         for (int b = tid; b < kBins; b += blockDim.x) sh_hist[b] = 0;
-        for (int64_t b = gtid; b < kBins; b += gsize) A.hist[b] = 0;
-        grid.sync();
-        for (int64_t i = gtid; i < m; i += gsize) {
-            unsigned long long key; uint32_t nid;
-            load_item(A, level, src, i, key, nid);
-            atomicAdd(&sh_hist[digit_of(key, nid, level)], 1u);
+        __syncthreads();
+        // lanes with the same digit add once (the top digits of real scores crowd a
+        // few bins, where per-lane shared atomics would serialise)
+        for (int64_t i0 = wbase; i0 < m; i0 += gsize) {
+            int64_t i = i0 + (tid & 31);
+            bool in = i < m;
+            uint32_t dg = kBins;                                // no bin: lanes past the end
+            if (in) {
+                unsigned long long key; uint32_t nid;
+                load_item(A, level, src, i, key, nid);
+                dg = digit_of(key, nid, level);
+            }
+            unsigned same = __match_any_sync(0xFFFFFFFFu, dg);
+            if (in && (tid & 31) == __ffs(same) - 1) atomicAdd(&sh_hist[dg], (uint32_t)__popc(same));
         }
         __syncthreads();
         for (int b = tid; b < kBins; b += blockDim.x)
@@ -138,19 +164,29 @@ __global__ void __launch_bounds__(kTkThreads) tk_select_kernel(TkArgs A) {
         if (blockIdx.x == 0) {
             constexpr int per = kBins / kTkThreads;             // 4 bins per thread, from the top
             int top = kBins - per * tid;
-            uint32_t s = 0;
-            for (int j = 1; j <= per; ++j) s += A.hist[top - j];
-            part[tid] = s;
-            __syncthreads();
-            for (int o = 1; o < kTkThreads; o <<= 1) {
-                uint32_t v = tid >= o ? part[tid - o] : 0;
-                __syncthreads();
-                part[tid] += v;
-                __syncthreads();
+            uint32_t sacc = 0;
+            for (int j = 1; j <= per; ++j) sacc += A.hist[top - j];
+            // inclusive scan over the threads: within warps by shuffles, then over the warp sums
+            const int lane = tid & 31, wid = tid >> 5;
+            uint32_t incl = sacc;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += v;
             }
-            int64_t need = ctrl[C_NEED];
-            int64_t before = tid ? part[tid - 1] : 0;
-            if (before < need && need <= (int64_t)part[tid]) {
+            if (lane == 31) part[wid] = incl;
+            __syncthreads();
+            if (wid == 0) {
+                uint32_t w = lane < kTkThreads / 32 ? part[lane] : 0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t v = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                    if (lane >= o) w += v;
+                }
+                part[lane] = w;                                 // inclusive sums of the warp sums
+            }
+            __syncthreads();
+            const uint32_t mine = incl + (wid ? part[wid - 1] : 0u);
+            int64_t before = (int64_t)mine - sacc;
+            if (before < need && need <= (int64_t)mine) {
                 int64_t acc = before;
                 for (int j = 1; j <= per; ++j) {
                     int b = top - j;
@@ -162,41 +198,41 @@ __global__ void __launch_bounds__(kTkThreads) tk_select_kernel(TkArgs A) {
             if (tid == 0) {
                 ctrl[C_SEL] = sh_sel;
                 ctrl[C_NEED] = (int)(need - sh_above);
-                ctrl[C_NEXT] = 0;
             }
         }
         grid.sync();
-        // compact: higher buckets are sure, the selected bucket stays
-        uint32_t sel = (uint32_t)ctrl[C_SEL];
-        int dst = src ^ 1;
-        for (int64_t i = gtid; i < m; i += gsize) {
-            unsigned long long key; uint32_t nid;
-            load_item(A, level, src, i, key, nid);
-            uint32_t dg = digit_of(key, nid, level);
-            if (dg > sel) {
-                int p = atomicAdd(&ctrl[C_SURE], 1);
-                A.skey[p] = key; A.snid[p] = nid;
-            } else if (dg == sel) {
-                int p = atomicAdd(&ctrl[C_NEXT], 1);
-                A.key[dst][p] = key; A.nid[dst][p] = nid;
+        // compact: higher buckets are sure, the selected bucket stays; the global
+        // histogram is cleared for the next level, and the candidate counter of
+        // the next level (last read before this level's first barrier) reset
+        const uint32_t sel = (uint32_t)ctrl[C_SEL];
+        need = ctrl[C_NEED];
+        const int dst = src ^ 1;
+        int *next = &ctrl[C_NEXT + (level & 1)];
+        for (int64_t b = gtid; b < kBins; b += gsize) A.hist[b] = 0;
+        if (gtid == 0) ctrl[C_NEXT + ((level + 1) & 1)] = 0;
+        for (int64_t i0 = wbase; i0 < m; i0 += gsize) {
+            int64_t i = i0 + (tid & 31);
+            unsigned long long key = 0; uint32_t nid = 0, dg = 0;
+            bool in = i < m;
+            if (in) {
+                load_item(A, level, src, i, key, nid);
+                dg = digit_of(key, nid, level);
             }
+            warp_append(in && dg > sel, key, nid, &ctrl[C_SURE], A.skey, A.snid);
+            warp_append(in && dg == sel, key, nid, next, A.key[dst], A.nid[dst]);
         }
         grid.sync();
-        if (gtid == 0) {
-            ctrl[C_CAND] = ctrl[C_NEXT];
-            ctrl[C_SRC] = dst;
-            if (ctrl[C_CAND] <= ctrl[C_NEED] || ctrl[C_SURE] + ctrl[C_CAND] <= sort_target(A.k)) ctrl[C_DONE] = 1;
-        }
-        grid.sync();
+        m = *(volatile int *)next;
+        src = dst;
+        done = m <= need || *(volatile int *)&ctrl[C_SURE] + m <= sort_target(A.k);
     }
     // CTA 0: sort the sure keys and the candidates left, write the first K
     if (blockIdx.x != 0) return;
     unsigned long long *key = (unsigned long long *)smem;
     uint32_t *nid = (uint32_t *)(key + kSortMax);
-    bool from_scores = level == 0;                              // nothing was compacted: n <= kSortMax
+    bool from_scores = level == 0;                              // nothing was compacted: n fits the sort
     int ns = ctrl[C_SURE];
-    int nc = ctrl[C_CAND];
-    int src = ctrl[C_SRC];
+    int nc = (int)m;
     int total = ns + nc;
     int P = 1;
     while (P < total) P <<= 1;

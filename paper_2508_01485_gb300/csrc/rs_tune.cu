@@ -36,6 +36,8 @@ static int check_tuning(const rs_tuning &t) {
         return fail(RS_EINVAL, "rs_tuning: p2_cta_threads must be 256, 512 or 1024");
     if (t.ctas_per_sm < 1 || t.ctas_per_sm > 32)
         return fail(RS_EINVAL, "rs_tuning: ctas_per_sm must be in [1, 32]");
+    if (t.p3_mirror != 0 && t.p3_mirror != 1)
+        return fail(RS_EINVAL, "rs_tuning: p3_mirror must be 0 or 1");
     return 0;
 }
 
@@ -48,6 +50,7 @@ static bool same_split(const rs_tuning &a, const rs_tuning &b) {
 static int apply_tuning(rs_graph *g, const rs_tuning &t, cudaStream_t s) {
     bool resplit = !same_split(g->tune, t);
     g->tune = t;
+    if (int rc = set_mirror_buffer(g)) return rc;
     if (resplit) return reclassify(g, s);
     g->version++;                    // launch shapes changed: captured steps are stale
     return 0;
@@ -141,6 +144,7 @@ extern "C" rs_status rs_autotune(rs_graph *g, double *scores, int32_t topk_k, in
         {&rs_tuning::p1_cta_threads, {128, 256, 512}},
         {&rs_tuning::p2_cta_threads, {256, 512, 1024}},
         {&rs_tuning::hub_chunk, {1024, 4096, 16384}},
+        {&rs_tuning::p3_mirror, {0, 1}},
     };
     for (size_t a = 0; !rc && a < axes.size(); ++a) {
         for (int32_t v : axes[a].values) {

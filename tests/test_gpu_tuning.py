@@ -25,13 +25,13 @@ def rs():
 EXTREMES = [
     # every row above degree 1 is a hub of the global-table path, in tiny chunks
     dict(small_max=1, warp_cap=64, cta_cap=64, hub_chunk=512, p2_cta_dx=32, p1_cta_threads=128,
-         p2_cta_threads=256, ctas_per_sm=1),
+         p2_cta_threads=256, ctas_per_sm=1, p3_mirror=1),
     dict(small_max=16, warp_cap=128, cta_cap=512, hub_chunk=1024, p2_cta_dx=64, p1_cta_threads=512,
-         p2_cta_threads=512, ctas_per_sm=16),
+         p2_cta_threads=512, ctas_per_sm=16, p3_mirror=0),
     dict(small_max=32, warp_cap=512, cta_cap=512, hub_chunk=65536, p2_cta_dx=256, p1_cta_threads=256,
-         p2_cta_threads=1024, ctas_per_sm=32),
+         p2_cta_threads=1024, ctas_per_sm=32, p3_mirror=1),
     dict(small_max=24, warp_cap=256, cta_cap=2048, hub_chunk=2048, p2_cta_dx=100, p1_cta_threads=128,
-         p2_cta_threads=256, ctas_per_sm=3),
+         p2_cta_threads=256, ctas_per_sm=3, p3_mirror=0),
 ]
 
 
@@ -62,23 +62,50 @@ def test_any_tuning_gives_the_same_bits(rs, which):
     G.close()
 
 
-def test_extreme_tuning_matches_oracle(rs):
+@pytest.mark.parametrize("which", [0, 1])
+def test_extreme_tuning_matches_oracle(rs, which):
     g = graphgen.sbm_2000()
     o = oracle.Oracle.from_graph(g)
     G = rs.Graph.from_generated(g)
-    G.set_tuning(**EXTREMES[0])
+    G.set_tuning(**EXTREMES[which])
     got = G.score().cpu().numpy()
+    assert G.device_errors() == 0
     ref = o.scores()
     assert ((ref == 0) == (got == 0)).all()
     nz = ref != 0
     assert (np.abs(got[nz] - ref[nz]) / ref[nz]).max() <= 1e-12
 
 
+@pytest.mark.parametrize("which", ["hubs", "dcsbm", "batch"])
+def test_reverse_values_by_lookup_or_mirror_give_the_same_bits(rs, which):
+    """P3 takes the reverse value of a triangle edge from the in-list of its
+    higher-ranked end, or from the array the mirror pass fills: the six values
+    of every triangle, hence every bit of the scores, must agree."""
+    if which == "hubs":
+        g = graphgen.dcsbm(60000, 5000, 5.0, 2.1, 4, 8000, 0.5, seed=44)
+        G = rs.Graph.from_generated(g)
+    elif which == "dcsbm":
+        G = rs.Graph.from_generated(graphgen.dcsbm_small(50000, seed=8, dmax=3000))
+    else:
+        b = graphgen.dcsbm_batch(12, 500, 20000, seed=5, dmax=2000)
+        G = rs.Graph.build_batch(b.graph_node_offsets, b.graph_k, b.offsets, b.cols, b.labels)
+    assert G.tuning()["p3_mirror"] == 1
+    mir = _bits(G.score())
+    assert G.device_errors() == 0
+    G.set_tuning(p3_mirror=0)
+    look = _bits(G.score())
+    assert G.device_errors() == 0
+    np.testing.assert_array_equal(look, mir)
+    G.set_tuning(p3_mirror=1)
+    np.testing.assert_array_equal(_bits(G.score()), mir)
+    G.close()
+
+
 @pytest.mark.parametrize("bad", [
     dict(small_max=0), dict(small_max=33), dict(warp_cap=100), dict(warp_cap=32), dict(warp_cap=1024),
     dict(warp_cap=512, cta_cap=256), dict(cta_cap=4096), dict(hub_chunk=256), dict(hub_chunk=3000),
     dict(p2_cta_dx=31), dict(p2_cta_dx=257), dict(p1_cta_threads=64), dict(p2_cta_threads=128),
-    dict(ctas_per_sm=0), dict(ctas_per_sm=33),
+    dict(ctas_per_sm=0), dict(ctas_per_sm=33), dict(p3_mirror=2), dict(p3_mirror=-1),
 ])
 def test_invalid_tuning_is_rejected(rs, bad):
     G = rs.Graph.from_generated(graphgen.sbm_2000())
