@@ -231,7 +231,7 @@ def graph_stats(g, k_class=None):
 
 
 # kernels launched on the forked streams of P1 and P2 (they overlap one another)
-CONCURRENT = {"p1_small", "p1_mid", "p1_large", "hub_p1_insert", "hub_p1_finish", "p2_small", "p2_warp",
+CONCURRENT = {"p1_small", "p1_mid", "p1_large", "hub_p1_insert", "hub_p1_finish", "p2_small", "p2_narrow",
               "p2_mid", "p2_mid_wide", "p2_large_warp", "p2_large_warp_wide", "p2_large",
               "hub_p2_insert", "hub_p2_sigma", "hub_p2_emit", "mirror_tiles"}
 
@@ -251,7 +251,7 @@ def kernel_bytes(name, st):
         return (4 + 8 + 16 + 24 + 8 + 8) * R + 8 * Xc + 16 * n * Xc / X + 12 * Gc
     table = {
         "p1_small": lambda: p1("small"), "p1_mid": lambda: p1("mid"), "p1_large": lambda: p1("large"),
-        "p2_small": lambda: p2("small"), "p2_warp": lambda: p2("mid_w") + p2("large_w"),
+        "p2_small": lambda: p2("small"), "p2_narrow": lambda: p2("mid_w") + p2("large_w"),
         "p2_mid": lambda: p2("mid_t"), "p2_mid_wide": lambda: p2("mid_tw"),
         "p2_large_warp": lambda: p2("large_t"), "p2_large_warp_wide": lambda: p2("large_tw"),
         "p2_large": lambda: p2("large_c"),

@@ -538,11 +538,13 @@ __global__ void gx_capacity_kernel(const NodeRec *__restrict__ rec, int64_t n, i
 // another community, in id order) and the row aggregates; own-community
 // neighbours are never touched again.
 
-// Small rows, tiles of 32 consecutive rows (id order) per warp.  The union of
-// the tile's cross lists is processed one entry per lane; lane l prepares and
-// closes row l.  A community's count f and Type-II sum come from warp matching
-// on (row, community); the rare row whose cross list straddles two chunks
-// rescans its own list instead.
+// Rows with at most 32 cross neighbours, tiles of 32 consecutive rows of a list
+// per warp (the small rows, and the mid and large rows with dx <= 32).  The
+// union of the tile's cross lists is processed in chunks of whole rows, one
+// entry per lane (a chunk ends before the first row that would not fit its 32
+// lanes); lane l prepares and closes row l.  As no row spans two chunks, a
+// community's count f and Type-II sum come from one warp match on
+// (row, community).
 struct P2Tile {
     int32_t pre[33];            // prefix sums of dx over the tile
     int64_t rb[32], xb[32];     // cross list start (= CSR start), G_x row start
@@ -555,8 +557,8 @@ struct P2Tile {
 };
 
 __global__ void __launch_bounds__(kThreads) p2_small_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows,
-    const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
+    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows_host,
+    const int32_t *__restrict__ nrows_dev, const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
     const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
     int32_t *__restrict__ xout, int32_t *__restrict__ xin, Strict SX) {
@@ -565,6 +567,7 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
     P2Tile &T = tiles[wid];
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nrows = nrows_dev ? *nrows_dev : nrows_host;   // a list counted by p2_split, or the small rows
     for (int64_t t0 = warp * 32; t0 < nrows; t0 += nwarps * 32) {
         int64_t i = t0 + lane;
         bool have = i < nrows;
@@ -597,9 +600,13 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
         T.pre[lane + 1] = incl;
         if (lane == 0) T.pre[0] = 0;
         __syncwarp();
-        for (int32_t e0 = 0; e0 < DX; e0 += 32) {
+        for (int32_t e0 = 0; e0 < DX;) {
+            // rows [.., rb) end within e0 + 32: the chunk is [e0, pre[rb])
+            unsigned fit = __ballot_sync(FULL, incl <= e0 + 32);
+            int32_t rb = 32 - __clz(fit);
+            int32_t E = __shfl_sync(FULL, incl, rb - 1);
             int32_t e = e0 + lane;
-            bool act = e < DX;
+            bool act = e < E;
             int32_t r = 0, u = -1, c = -1, j = 0;
             NodeRec ru{0, -1, 0};
             if (act) {
@@ -622,24 +629,11 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
             if (act) gc = __match_any_sync(am, key);
             df sig{0.0f, 0.0f};
             if (act) {
-                int32_t rdx = T.dx[r];
-                bool whole = T.pre[r] >= e0 && T.pre[r] + rdx <= e0 + 32;   // row inside this chunk
-                uint32_t f;
+                uint32_t f = __popc(gc);
                 u128 rest = 0;
-                if (whole) {
-                    f = __popc(gc);
-                    if (f > 1) {
-                        unsigned m = gc & ~(1u << lane);
-                        while (m) { rest += T.st[__ffs(m) - 1]; m &= m - 1; }
-                    }
-                } else {
-                    f = 0;
-                    int64_t rb = T.rb[r];
-                    for (int32_t j2 = 0; j2 < rdx; ++j2) {
-                        if (cl_lab[rb + j2] != c) continue;
-                        ++f;
-                        if (j2 != j) rest += rec[cl_col[rb + j2]].s_fix;
-                    }
+                if (f > 1) {
+                    unsigned m = gc & ~(1u << lane);
+                    while (m) { rest += T.st[__ffs(m) - 1]; m &= m - 1; }
                 }
                 if (f == 1) sig = T.sig1[r];
                 else {
@@ -669,73 +663,10 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
                 if (lane == __ffs(gi) - 1) T.ni[r] = bi + __popc(gi);
             }
             __syncwarp();
+            e0 = E;
         }
         if (have) { xout[w] = T.no[lane]; xin[w] = T.ni[lane]; }
         __syncwarp();
-    }
-}
-
-// Rows with at most 32 cross neighbours, one warp per row: one chunk holds
-// the whole cross list, so warp matching gives each community's count and
-// Type-II sum directly; no table, no shared memory beyond a staging word per lane.
-__global__ void __launch_bounds__(kThreads) p2_warp_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_dev,
-    const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
-    const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
-    const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
-    int32_t *__restrict__ xout, int32_t *__restrict__ xin, Strict SX) {
-    __shared__ uint64_t stage[kThreads];
-    int lane = threadIdx.x & 31;
-    uint64_t *st = stage + (threadIdx.x & ~31);
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nrows = *nrows_dev;               // rows of this kernel, counted by p2_split
-    for (int64_t i = warp; i < nrows; i += nwarps) {
-        int32_t w = rows[i];
-        NodeRec rw = rec[w];
-        int dx = rw.dx;
-        if (dx > 32) continue;                     // left to the table kernel
-        int32_t bo = 0, bi = 0;
-        if (dx > 0) {
-            int64_t b = off[w];
-            int d = (int)(off[w + 1] - b);
-            RowSum rs = rsum[w];
-            RowAgg a{(uint32_t)d, rs.L, ((u128)rs.xhi << 64) | rs.xlo};
-            bool act = lane < dx;
-            int32_t u = act ? cl_col[b + lane] : -1;
-            int32_t c = act ? cl_lab[b + lane] : -1;
-            NodeRec ru{0, -1, 0};
-            if (act) ru = rec[u];
-            df sig1 = df_cbrt(column_weight(a, 1, LG));
-            st[lane] = ru.s_fix;
-            __syncwarp();
-            unsigned am = __ballot_sync(FULL, act);
-            unsigned grp = 0;
-            if (act) grp = __match_any_sync(am, c);
-            uint32_t f = __popc(grp);
-            df sig{0.0f, 0.0f};
-            if (act) {
-                sig = f == 1 ? sig1 : df_cbrt(column_weight(a, f, LG));
-                if (f > 1) {
-                    u128 rest = 0;
-                    unsigned m = grp & ~(1u << lane);
-                    while (m) { rest += st[__ffs(m) - 1]; m &= m - 1; }
-                    push_type2(acc, u, sig, strict_rest(SX, off, w, u, rest));
-                }
-            }
-            __syncwarp();
-            if (dx >= 2) {
-                int64_t xb = xoff[w];
-                bool inx = act && ru.dx >= 2;
-                bool o = inx && rank_after(ru.dx, u, dx, w);
-                bool in = inx && !o;
-                unsigned mo = __ballot_sync(FULL, o), mi = __ballot_sync(FULL, in);
-                if (o) { int64_t p = xb + __popc(mo & lanemask_lt()); xcol[p] = u; xS[p] = sig; }
-                if (in) { int64_t p = xb + dx - 1 - __popc(mi & lanemask_lt()); xcol[p] = u; xS[p] = sig; }
-                bo = __popc(mo); bi = __popc(mi);
-            }
-        }
-        if (lane == 0) { xout[w] = bo; xin[w] = bi; }
     }
 }
 
@@ -761,7 +692,7 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
         int d = (int)(off[w + 1] - b);
         NodeRec rw = rec[w];
         int dx = rw.dx;
-        if (dx > dx_max || dx <= 32) continue;     // the CTA-per-row kernel / p2_warp_kernel
+        if (dx > dx_max || dx <= 32) continue;     // the CTA-per-row kernel / the tile kernel
         int32_t bo = 0, bi = 0;
         {
             uint32_t cap = dev_pow2_at_least(2u * (uint32_t)min(dx, k_of(B, graph_of(B, w))));
@@ -1530,8 +1461,8 @@ __global__ void __launch_bounds__(kThreads) strict_pairs_kernel(int64_t n, const
 
 // ======================================================================================
 // P2 row lists by cross degree (known after P1): each P2 kernel then walks only its rows
-//   0 mid rows, dx <= 32 (p2_warp)           1 mid rows, 32 < dx <= 128 (p2_mid, 256 slots)
-//   2 large rows, dx <= 32 (p2_warp)         3 large rows, 32 < dx <= min(128, dx_cta) (p2_mid, 256)
+//   0 mid and large rows, dx <= 32 (tiles)   1 mid rows, 32 < dx <= 128 (p2_mid, 256 slots)
+//   2 unused                                 3 large rows, 32 < dx <= min(128, dx_cta) (p2_mid, 256)
 //   4 large rows, dx > dx_cta (p2_large)     5 mid rows, dx > 128 (p2_mid, 512 slots)
 //   6 large rows, 128 < dx <= dx_cta (p2_mid, 512 slots)
 // ======================================================================================
@@ -1547,10 +1478,10 @@ __device__ __forceinline__ void append_row(int32_t *list, int32_t *cnt, bool tak
     if (take) list[base + __popc(m & lanemask_lt())] = v;
 }
 
-// list c starts at p2_list_start(c) * (its class size): mid lists have n_mid entries, large ones n_large
+// list 0 has room for n_mid + n_large rows, the other mid lists for n_mid, the large ones for n_large
 __host__ __device__ __forceinline__ int64_t p2_list_start(int c, int64_t n_mid, int64_t n_large) {
     const int mids_before[kP2Lists] = {0, 1, 2, 2, 2, 2, 3};
-    const int larges_before[kP2Lists] = {0, 0, 0, 1, 2, 3, 3};
+    const int larges_before[kP2Lists] = {0, 1, 1, 1, 2, 3, 3};
     return mids_before[c] * n_mid + larges_before[c] * n_large;
 }
 
@@ -1566,8 +1497,9 @@ __global__ void p2_split_kernel(const int32_t *__restrict__ rows_mid, int64_t n_
         int32_t dx = act ? rec[v].dx : 0;
         int cls = -1;
         if (act) {
-            if (mid) cls = dx <= 32 ? 0 : dx <= kSmallTableDx ? 1 : 5;
-            else cls = dx <= 32 ? 2 : dx > dx_cta ? 4 : dx <= kSmallTableDx ? 3 : 6;
+            if (dx <= 32) cls = 0;                              // the tile kernel, either class
+            else if (mid) cls = dx <= kSmallTableDx ? 1 : 5;
+            else cls = dx > dx_cta ? 4 : dx <= kSmallTableDx ? 3 : 6;
         }
         for (int c = 0; c < kP2Lists; ++c)
             append_row(lists + p2_list_start(c, n_mid, n_large), cnt + c, cls == c, v);
@@ -1716,8 +1648,8 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     if (int rc = fork_aux(g, s)) return rc;
     if (g->n_small) {
         p2_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[0]>>>(
-            g->off, g->rows_small, g->n_small, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
-            g->xcol, g->xS, g->xout, g->xin, SX);
+            g->off, g->rows_small, g->n_small, nullptr, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
+            g->xoff, g->xcol, g->xS, g->xout, g->xin, SX);
         RS_LAUNCHED(g, g->aux[0], "p2_small");
     }
     if (g->tune.p3_mirror) {                         // the mirror's tile table, beside P2
@@ -1726,11 +1658,14 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_LAUNCHED(g, g->aux[0], "mirror_tiles");
     }
     const size_t smem256 = (size_t)kMidWarps * 256 * kMidSlotBytes, smem512 = (size_t)kMidWarps * 512 * kMidSlotBytes;
+    if (nm + nl) {
+        // the mid and large rows with at most 32 cross neighbours, in the tile kernel
+        p2_small_kernel<<<grid_for(nm + nl, NT, cps), NT, 0, g->aux[1]>>>(
+            g->off, Lst(0), 0, g->p2cnt + 0, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
+            g->xcol, g->xS, g->xout, g->xin, SX);
+        RS_LAUNCHED(g, g->aux[1], "p2_narrow");
+    }
     if (g->n_mid) {
-        p2_warp_kernel<<<grid_for(g->n_mid * 32, NT, cps), NT, 0, g->aux[1]>>>(
-            g->off, Lst(0), g->p2cnt + 0, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff, g->xcol,
-            g->xS, g->xout, g->xin, SX);
-        RS_LAUNCHED(g, g->aux[1], "p2_warp");
         p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 4), NT, smem256, g->aux[5]>>>(
             g->off, Lst(1), g->p2cnt + 1, B, 1 << 30, 256, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
             g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 2);
@@ -1742,10 +1677,6 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     }
     if (g->n_large) {
         // large rows whose cross list fits a per-warp table go warp-per-row too
-        p2_warp_kernel<<<grid_for(g->n_large * 32, NT, cps), NT, 0, g->aux[2]>>>(
-            g->off, Lst(2), g->p2cnt + 2, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
-            g->xcol, g->xS, g->xout, g->xin, SX);
-        RS_LAUNCHED(g, g->aux[2], "p2_warp");
         p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 4), NT, smem256, g->aux[2]>>>(
             g->off, Lst(3), g->p2cnt + 3, B, g->tune.p2_cta_dx, 256, g->LG, g->rec, g->rsum, g->cl_col,
             g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 4);
