@@ -184,20 +184,28 @@ __global__ void __launch_bounds__(kThreads) p1_small_kernel(
         T.nf[lane] = 0;
         T.nx[lane] = 0;
         __syncwarp();
-        for (int32_t e0 = 0; e0 < D; e0 += 32) {
-            int32_t e = e0 + lane;
-            bool act = e < D;
-            int32_t r = 0, x = -1, c = -1;
-            if (act) {
-                int32_t lo = 0, hi = 32;               // last r with pre[r] <= e
-                while (hi - lo > 1) {
-                    int32_t mid = (lo + hi) >> 1;
-                    if (T.pre[mid] <= e) lo = mid; else hi = mid;
-                }
-                r = lo;
-                x = col[T.rb[r] + (e - T.pre[r])];
-                c = lab[x];
+        // entry e of the tile: its row (last r with pre[r] <= e) and its CSR column
+        auto locate = [&](int32_t e, int32_t &r, int32_t &x) {
+            int32_t lo = 0, hi = 32;
+            while (hi - lo > 1) {
+                int32_t mid = (lo + hi) >> 1;
+                if (T.pre[mid] <= e) lo = mid; else hi = mid;
             }
+            r = lo;
+            x = col[T.rb[r] + (e - T.pre[r])];
+        };
+        // software pipeline: the label of the next chunk and the column of the one
+        // after it are loaded while the current chunk is matched
+        int32_t rA = 0, xA = -1, cA = -1, rB = 0, xB = -1;
+        if (lane < D) { locate(lane, rA, xA); cA = lab[xA]; }
+        if (32 + lane < D) locate(32 + lane, rB, xB);
+        for (int32_t e0 = 0; e0 < D; e0 += 32) {
+            const int32_t r = rA, x = xA, c = cA;
+            const bool act = e0 + lane < D;
+            int32_t cB = -1, rC = 0, xC = -1;
+            if (e0 + 32 + lane < D) cB = lab[xB];
+            if (e0 + 64 + lane < D) locate(e0 + 64 + lane, rC, xC);
+            rA = rB; xA = xB; cA = cB; rB = rC; xB = xC;
             bool own = act && c == T.cv[r];
             bool foreign = act && !own;
             unsigned om = __ballot_sync(FULL, own), fm = __ballot_sync(FULL, foreign);
@@ -297,11 +305,18 @@ __global__ void __launch_bounds__(kThreads) p1_mid_kernel(
         uint32_t own = 0, nused = 0;
         int32_t nx = 0;
         u128 X = 0;                       // foreign part, from count deltas at insert time
+        // software pipeline: the next chunk's labels and the columns of the one after
+        // it are loaded while the current chunk is inserted
+        int32_t xA = lane < d ? col[b + lane] : -1;
+        int32_t cA = lane < d ? lab[xA] : -1;
+        int32_t xB = 32 + lane < d ? col[b + 32 + lane] : -1;
         for (int base = 0; base < d; base += 32) {
             int e = base + lane;
             bool act = e < d;
-            int32_t x = act ? col[b + e] : -1;
-            int32_t c = act ? lab[x] : -1;
+            const int32_t x = xA, c = cA;
+            const int32_t cB = e + 32 < d ? lab[xB] : -1;
+            const int32_t xC = e + 64 < d ? col[b + e + 64] : -1;
+            xA = xB; cA = cB; xB = xC;
             own += (act && c == cv);
             bool foreign = act && c != cv;
             unsigned fm = __ballot_sync(FULL, foreign);
