@@ -410,11 +410,16 @@ __global__ void __launch_bounds__(NT) p1_large_kernel(
         __syncthreads();
         uint32_t own = 0;
         int32_t nx = 0;
+        int32_t xA = tid < d ? col[b + tid] : -1;
+        int32_t cA = tid < d ? lab[xA] : -1;
+        int32_t xB = NT + tid < d ? col[b + NT + tid] : -1;
         for (int base = 0; base < d; base += NT) {
             int e = base + tid;
             bool act = e < d;
-            int32_t x = act ? col[b + e] : -1;
-            int32_t c = act ? lab[x] : -1;
+            const int32_t x = xA, c = cA;
+            const int32_t cB = e + NT < d ? lab[xB] : -1;
+            const int32_t xC = e + 2 * NT < d ? col[b + e + 2 * NT] : -1;
+            xA = xB; cA = cB; xB = xC;
             own += (act && c == cv);
             bool foreign = act && c != cv;
             unsigned fm = __ballot_sync(FULL, foreign);
@@ -1685,10 +1690,11 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->off, Lst(1), g->p2cnt + 1, B, 1 << 30, 256, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
             g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 2);
         RS_LAUNCHED(g, g->aux[5], "p2_mid");
-        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, smem512, g->aux[1]>>>(
+        // few rows, each a long single-warp chain: on the lightly loaded stream
+        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, smem512, g->aux[2]>>>(
             g->off, Lst(5), g->p2cnt + 5, B, 1 << 30, 512, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
             g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 3);
-        RS_LAUNCHED(g, g->aux[1], "p2_mid_wide");
+        RS_LAUNCHED(g, g->aux[2], "p2_mid_wide");
     }
     if (g->n_large) {
         // large rows whose cross list fits a per-warp table go warp-per-row too
