@@ -607,8 +607,12 @@ int rs::set_mirror_buffer(rs_graph *g) {
 
 static int alloc_workspace(rs_graph *g) {
     int64_t n = g->n, nnz = g->nnz;
+    // streams 0 and 1 carry the many-short-rows kernels at the lowest priority; the
+    // others carry rows with long dependent chains, whose blocks go first
+    int lowest = 0, highest = 0;
+    RS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lowest, &highest));
     for (int i = 0; i < rs_graph::kAux; ++i) {
-        RS_CUDA_TRY(cudaStreamCreateWithFlags(&g->aux[i], cudaStreamNonBlocking));
+        RS_CUDA_TRY(cudaStreamCreateWithPriority(&g->aux[i], cudaStreamNonBlocking, i < 2 ? lowest : highest));
         RS_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_join[i], cudaEventDisableTiming));
     }
     RS_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));

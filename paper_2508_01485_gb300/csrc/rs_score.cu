@@ -1576,7 +1576,7 @@ int rs::prepare_score_kernels() {
 // the CTA-per-row kernels at the tuned CTA size
 template <int NT>
 static void launch_p1_large(rs_graph *g, const Batch &B, int *err, size_t smem) {
-    p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, smem, g->aux[1]>>>(
+    p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, smem, g->aux[2]>>>(
         g->off, g->col, g->lab, g->rows_large, g->n_large, B, g->LG, g->rec, g->Lall, err,
         g->rsum, g->cl_col, g->cl_lab, g->wq + 1);
 }
@@ -1611,16 +1611,17 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     prof_mark(g, s, "memset", false);
     size_t p1_smem = 8 * (size_t)g->large_cap, p2_smem = 32 * (size_t)g->large_cap;
     // ---- P1: every row class on its own stream; the larger classes are launched
-    //      first, so their maxima seed w_max early and most small rows skip theirs
+    //      first, on high-priority streams, so their maxima seed w_max early and most
+    //      small rows skip theirs (the small rows fill in at the lowest priority)
     if (int rc = fork_aux(g, s)) return rc;
     if (g->n_hubs) {
-        hub_p1_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[0]>>>(
+        hub_p1_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
             g->off, g->col, g->lab, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items,
             g->tune.hub_chunk, g->hkey, g->hcnt, g->hagg, err);
-        RS_LAUNCHED(g, g->aux[0], "hub_p1_insert");
-        hub_p1_finish_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, g->aux[0]>>>(
+        RS_LAUNCHED(g, g->aux[3], "hub_p1_insert");
+        hub_p1_finish_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, g->aux[3]>>>(
             g->off, g->lab, g->hubs, g->n_hubs, B, g->LG, g->hkey, g->hcnt, g->hagg, g->rec, g->Lall);
-        RS_LAUNCHED(g, g->aux[0], "hub_p1_finish");
+        RS_LAUNCHED(g, g->aux[3], "hub_p1_finish");
     }
     if (g->n_large) {
         switch (g->tune.p1_cta_threads) {
@@ -1628,21 +1629,21 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         case 512: launch_p1_large<512>(g, B, err, p1_smem); break;
         default: launch_p1_large<256>(g, B, err, p1_smem); break;
         }
-        RS_LAUNCHED(g, g->aux[1], "p1_large");
+        RS_LAUNCHED(g, g->aux[2], "p1_large");
     }
     if (g->n_mid) {
-        p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, cps), NT, 0, g->aux[2]>>>(
+        p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, cps), NT, 0, g->aux[4]>>>(
             g->off, g->col, g->lab, g->rows_mid, g->n_mid, B, g->LG, g->rec, g->Lall, err,
             g->rsum, g->cl_col, g->cl_lab, g->wq + 0);
-        RS_LAUNCHED(g, g->aux[2], "p1_mid");
+        RS_LAUNCHED(g, g->aux[4], "p1_mid");
     }
     if (g->n_small) {
-        p1_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[3]>>>(
+        p1_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[0]>>>(
             g->off, g->col, g->lab, g->rows_small, g->n_small, B, g->LG, g->rec, g->Lall,
             g->rsum, g->cl_col, g->cl_lab);
-        RS_LAUNCHED(g, g->aux[3], "p1_small");
+        RS_LAUNCHED(g, g->aux[0], "p1_small");
     }
-    if (int rc = join_aux(g, s, 4)) return rc;
+    if (int rc = join_aux(g, s, rs_graph::kAux)) return rc;
     // ---- G_x offsets
     gx_capacity_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->rec, n, g->xoff);
     RS_LAUNCHED(g, s, "gx_capacity");
@@ -1664,7 +1665,8 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
                                                                   g->tune.p2_cta_dx, g->p2rows, g->p2cnt);
         RS_LAUNCHED(g, s, "p2_split");
     }
-    // ---- P2: every row class on its own stream
+    // ---- P2: every row class on its own stream; the many-short-rows kernels on the
+    //      low-priority streams 0 and 1, the rows with long chains on the others
     if (int rc = fork_aux(g, s)) return rc;
     if (g->n_small) {
         p2_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[0]>>>(
