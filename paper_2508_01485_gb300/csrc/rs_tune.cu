@@ -83,20 +83,23 @@ extern "C" rs_status rs_set_tuning(rs_graph *g, const rs_tuning *t, void *stream
 // autotuner
 // ---------------------------------------------------------------------------
 
-// median device time of `reps` steps after one untimed step
+// median device time of `reps` replays of the step captured for the current
+// parameters (as rs_step_capture records it), after one untimed replay
 static int time_step(rs_graph *g, double *scores, int32_t topk_k, int32_t *ids, double *vals, int32_t reps,
                      cudaStream_t s, std::vector<cudaEvent_t> &ev, float *ms_out) {
-    if (int rc = score_graph(g, scores, s)) return rc;
-    if (topk_k > 0)
-        if (int rc = topk_scores(g, scores, g->n, topk_k, ids, vals, s)) return rc;
-    for (int32_t r = 0; r < reps; ++r) {
-        RS_CUDA_TRY(cudaEventRecord(ev[2 * r], s));
-        if (int rc = score_graph(g, scores, s)) return rc;
-        if (topk_k > 0)
-            if (int rc = topk_scores(g, scores, g->n, topk_k, ids, vals, s)) return rc;
-        RS_CUDA_TRY(cudaEventRecord(ev[2 * r + 1], s));
+    rs_step *st = nullptr;
+    if (rs_status rc = rs_step_capture(g, scores, topk_k, ids, vals, &st)) return rc;
+    int rc = rs_step_launch(st, s);
+    for (int32_t r = 0; !rc && r < reps; ++r) {
+        if (cudaError_t e = cudaEventRecord(ev[2 * r], s)) rc = cuda_fail(e, "rs_autotune: event");
+        if (!rc) rc = rs_step_launch(st, s);
+        if (!rc)
+            if (cudaError_t e = cudaEventRecord(ev[2 * r + 1], s)) rc = cuda_fail(e, "rs_autotune: event");
     }
-    RS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!rc)
+        if (cudaError_t e = cudaStreamSynchronize(s)) rc = cuda_fail(e, "rs_autotune: synchronize");
+    rs_step_free(st);
+    if (rc) return rc;
     std::vector<float> t(reps);
     for (int32_t r = 0; r < reps; ++r) RS_CUDA_TRY(cudaEventElapsedTime(&t[r], ev[2 * r], ev[2 * r + 1]));
     std::sort(t.begin(), t.end());
