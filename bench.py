@@ -233,7 +233,7 @@ def graph_stats(g, k_class=None):
 # kernels launched on the forked streams of P1 and P2 (they overlap one another)
 CONCURRENT = {"p1_small", "p1_mid", "p1_large", "hub_p1_insert", "hub_p1_finish", "p2_small", "p2_narrow",
               "p2_mid", "p2_mid_wide", "p2_large_warp", "p2_large_warp_wide", "p2_large",
-              "hub_p2_insert", "hub_p2_sigma", "hub_p2_emit", "mirror_tiles"}
+              "hub_p2_insert", "hub_p2_sigma", "hub_p2_emit", "mirror_tiles", "p2_split"}
 
 
 def kernel_bytes(name, st):
@@ -263,7 +263,8 @@ def kernel_bytes(name, st):
         "gx_mirror": lambda: (4 + 8 + 8) * st["out_slots"] + (4 + 8 + 4) * n,
         "finalize": lambda: (8 + 16 + 8) * n,
         "tk_select": lambda: 8 * n,
-        "gx_capacity": lambda: 16 * n + 8 * n,
+        # every node record (its dx) read, every G_x row offset written
+        "gx_offsets": lambda: 16 * n + 8 * n,
     }
     f = table.get(name)
     return f() if f else None

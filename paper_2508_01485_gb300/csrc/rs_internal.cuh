@@ -187,6 +187,11 @@ namespace rs {
 
 constexpr int kThreads = 256;
 constexpr int kMirTile = 2048;               // G_x slots per tile of the mirror pass
+constexpr int kGxTile = 4096;                // nodes per tile of the G_x offset scan
+// words of rs_graph::wq, zeroed before every scoring pass: 0..7 the row and group
+// counters of the row kernels, 8 the ticket of the G_x offset scan, 16.. its tile words
+constexpr int kWqGxTicket = 8, kWqGxStatus = 16;
+inline int64_t wq_words(int64_t n) { return kWqGxStatus + (n + kGxTile - 1) / kGxTile + 1; }
 
 // error reporting (rs_api.cu): returns the status after recording the message
 int fail(int status, const std::string &msg);

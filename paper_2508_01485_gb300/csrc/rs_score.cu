@@ -540,14 +540,98 @@ __global__ void __launch_bounds__(NT) hub_p1_finish_kernel(
 }
 
 // ======================================================================================
-// G_x row capacity: nodes with dx >= 2 keep dx slots
+// G_x row offsets: nodes with dx >= 2 keep dx slots; xoff is the exclusive scan of
+// those capacities, in one pass (decoupled look-back).  Tiles of kGxTile nodes are
+// taken in ticket order; a tile publishes its own total at once and its inclusive
+// prefix as soon as the tiles before it have, and its first warp sums the published
+// words of its predecessors back to the nearest inclusive one, 32 tiles per step.  A predecessor has
+// always started (its ticket is smaller), so every wait ends; the wait is bounded
+// all the same, and flags err if the bound is ever reached.
 // ======================================================================================
-__global__ void gx_capacity_kernel(const NodeRec *__restrict__ rec, int64_t n, int64_t *xoff) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v == 0) xoff[0] = 0;
-    if (v < n) {
-        int32_t dx = rec[v].dx;
-        xoff[v + 1] = dx >= 2 ? dx : 0;
+constexpr int kGxThreads = 256;
+constexpr int kGxPer = kGxTile / kGxThreads;
+constexpr unsigned long long kGxAgg = 1ull << 62, kGxIncl = 2ull << 62, kGxMask = (1ull << 62) - 1;
+constexpr long kGxSpin = 1l << 24;
+
+// status: one word per tile (flag in the top two bits), zeroed before the launch;
+// ticket: zeroed before the launch.  Warp w of a tile scans its kGxPer runs of 32
+// consecutive nodes (coalesced loads and stores), carrying its running total.
+__global__ void __launch_bounds__(kGxThreads) gx_offsets_kernel(
+    const NodeRec *__restrict__ rec, int64_t n, int64_t *__restrict__ xoff, unsigned long long *status,
+    unsigned long long *ticket, int *err) {
+    __shared__ int64_t warp_tot[kGxThreads / 32];
+    __shared__ unsigned long long sh_tile;
+    __shared__ int64_t sh_prefix;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) sh_tile = atomicAdd(ticket, 1ull);
+    __syncthreads();
+    const int64_t t = (int64_t)sh_tile;
+    const int64_t base = t * kGxTile + (int64_t)wid * (32 * kGxPer);
+    int32_t cap[kGxPer];
+#pragma unroll
+    for (int k = 0; k < kGxPer; ++k) {
+        int64_t v = base + k * 32 + lane;
+        int32_t dx = v < n ? rec[v].dx : 0;
+        cap[k] = dx >= 2 ? dx : 0;
+    }
+    int64_t val[kGxPer];
+    int64_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < kGxPer; ++k) {
+        int64_t x = cap[k];
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        val[k] = carry + x;                           // inclusive within the warp's nodes
+        carry += __shfl_sync(FULL, x, 31);
+    }
+    if (lane == 0) warp_tot[wid] = carry;
+    __syncthreads();
+    if (wid == 0) {
+        // exclusive prefixes of the warps inside the tile, and the tile's total
+        int64_t c = lane < kGxThreads / 32 ? warp_tot[lane] : 0, x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        const int64_t total = __shfl_sync(FULL, x, 31);
+        if (lane < kGxThreads / 32) warp_tot[lane] = x - c;
+        int64_t excl = 0;
+        if (t == 0) {
+            if (lane == 0) *(volatile unsigned long long *)&status[0] = kGxIncl | (unsigned long long)total;
+        } else {
+            if (lane == 0) *(volatile unsigned long long *)&status[t] = kGxAgg | (unsigned long long)total;
+            // look back 32 tiles at a time: lane l reads tile hi - l; the nearest
+            // inclusive word ends the walk, the aggregates after it are added
+            for (int64_t hi = t - 1;; hi -= 32) {
+                const int64_t j = hi - lane;
+                unsigned long long w = kGxIncl;          // before tile 0: an inclusive zero
+                if (j >= 0) {
+                    long spins = 0;
+                    do {
+                        w = *(volatile unsigned long long *)&status[j];
+                    } while (!(w >> 62) && ++spins < kGxSpin);
+                    if (!(w >> 62)) { atomicOr(err, 32); w = kGxIncl; }
+                }
+                const unsigned inc = __ballot_sync(FULL, (w >> 62) == 2);
+                const int stop = inc ? __ffs(inc) - 1 : 31;
+                int64_t add = lane <= stop ? (int64_t)(w & kGxMask) : 0;
+                for (int o = 16; o; o >>= 1) add += __shfl_xor_sync(FULL, add, o);
+                excl += add;
+                if (inc) break;
+            }
+            if (lane == 0) *(volatile unsigned long long *)&status[t] = kGxIncl | (unsigned long long)(excl + total);
+        }
+        if (lane == 0) sh_prefix = excl;
+    }
+    __syncthreads();
+    const int64_t before = sh_prefix + warp_tot[wid];
+    if (t == 0 && threadIdx.x == 0) xoff[0] = 0;
+#pragma unroll
+    for (int k = 0; k < kGxPer; ++k) {
+        int64_t v = base + k * 32 + lane;
+        if (v < n) xoff[v + 1] = before + val[k];
     }
 }
 
@@ -1536,15 +1620,25 @@ __global__ void graph_scale_kernel(const unsigned long long *__restrict__ wmax_b
     winv[gi] = wm > 0.0 ? 1.0 / wm : 0.0;
 }
 
+// one graph (gid null): every CTA takes 1 / w_max itself; a batch reads the
+// per-graph reciprocals graph_scale_kernel wrote
 __global__ void __launch_bounds__(kThreads) finalize_kernel(
     int64_t n, const int64_t *__restrict__ off, const unsigned long long *__restrict__ acc,
-    const int32_t *__restrict__ gid, const double *__restrict__ winv, const double *__restrict__ RD,
-    double *scores) {
+    const int32_t *__restrict__ gid, const double *__restrict__ winv, const unsigned long long *__restrict__ wmax_bits,
+    const double *__restrict__ RD, double *scores) {
+    __shared__ double sh_w;
+    if (!gid) {
+        if (threadIdx.x == 0) {
+            double wm = __longlong_as_double((long long)wmax_bits[0]);
+            sh_w = wm > 0.0 ? 1.0 / wm : 0.0;
+        }
+        __syncthreads();
+    }
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
         int64_t d = off[u + 1] - off[u];
         double r = 0.0;
         if (d >= 2) {
-            double W = winv[gid ? gid[u] : 0];
+            double W = gid ? winv[gid[u]] : sh_w;
             u128 s = ((u128)acc[2 * u + 1] << 64) | acc[2 * u];
             if (s && W > 0.0) r = u128_to_double(s, -kAccFrac) * W * RD[d];
         }
@@ -1601,7 +1695,8 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     Batch B{g->gid, g->gk, g->k, g->wmax_bits};
     RS_CUDA_TRY(cudaMemsetAsync(g->acc, 0, 2 * n * sizeof(unsigned long long), s));
     RS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-    RS_CUDA_TRY(cudaMemsetAsync(g->wq, 0, 16 * sizeof(unsigned long long), s));   // row counters
+    // row counters and the G_x scan's ticket and tile words
+    RS_CUDA_TRY(cudaMemsetAsync(g->wq, 0, wq_words(n) * sizeof(unsigned long long), s));
     if (g->n_hubs) {
         RS_CUDA_TRY(cudaMemsetAsync(g->hkey, 0xFF, g->hub_slots * sizeof(int32_t), s));
         RS_CUDA_TRY(cudaMemsetAsync(g->hcnt, 0, g->hub_slots * sizeof(uint32_t), s));
@@ -1644,26 +1739,24 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_LAUNCHED(g, g->aux[0], "p1_small");
     }
     if (int rc = join_aux(g, s, rs_graph::kAux)) return rc;
-    // ---- G_x offsets
-    gx_capacity_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->rec, n, g->xoff);
-    RS_LAUNCHED(g, s, "gx_capacity");
-    int64_t scan_launches = 0;
-    if (int rc = inclusive_scan_i64(g->xoff + 1, n, g->scan_tmp, s, &scan_launches)) return rc;
-    g->launches += scan_launches - 1;
-    prof_mark(g, s, "gx_scan", true);
-    const Strict SX{g->col, g->strict ? g->sx : nullptr};
-    if (g->strict) {
-        RS_CUDA_TRY(cudaMemsetAsync(g->sx, 0, 2 * g->nnz * sizeof(unsigned long long), s));
-        strict_pairs_kernel<<<grid_for(n * 32, NT, cps), NT, 0, s>>>(n, g->off, g->col, g->lab, g->rec, g->sx);
-        RS_LAUNCHED(g, s, "strict_pairs");
-    }
+    // ---- P2 row lists (on stream 5) beside the G_x offsets (on the step's stream)
     const int64_t nm = g->n_mid, nl = g->n_large;
     auto Lst = [&](int c) { return g->p2rows + p2_list_start(c, nm, nl); };
     if (nm + nl) {
         RS_CUDA_TRY(cudaMemsetAsync(g->p2cnt, 0, kP2Lists * sizeof(int32_t), s));
         p2_split_kernel<<<grid_for(nm + nl, 256, 8), 256, 0, s>>>(g->rows_mid, nm, g->rows_large, nl, g->rec,
-                                                                  g->tune.p2_cta_dx, g->p2rows, g->p2cnt);
+                                                                   g->tune.p2_cta_dx, g->p2rows, g->p2cnt);
         RS_LAUNCHED(g, s, "p2_split");
+    }
+    const int64_t gx_tiles = (n + kGxTile - 1) / kGxTile;
+    gx_offsets_kernel<<<(unsigned)gx_tiles, kGxThreads, 0, s>>>(g->rec, n, g->xoff, g->wq + kWqGxStatus,
+                                                              g->wq + kWqGxTicket, err);
+    RS_LAUNCHED(g, s, "gx_offsets");
+    const Strict SX{g->col, g->strict ? g->sx : nullptr};
+    if (g->strict) {
+        RS_CUDA_TRY(cudaMemsetAsync(g->sx, 0, 2 * g->nnz * sizeof(unsigned long long), s));
+        strict_pairs_kernel<<<grid_for(n * 32, NT, cps), NT, 0, s>>>(n, g->off, g->col, g->lab, g->rec, g->sx);
+        RS_LAUNCHED(g, s, "strict_pairs");
     }
     // ---- P2: every row class on its own stream; the many-short-rows kernels on the
     //      low-priority streams 0 and 1, the rows with long chains on the others
@@ -1744,9 +1837,12 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
                                                         next_group);
     RS_LAUNCHED(g, s, "p3_list");
     // ---- finalize
-    graph_scale_kernel<<<(g->n_graphs + 255) / 256, 256, 0, s>>>(g->wmax_bits, g->n_graphs, g->winv);
-    RS_LAUNCHED(g, s, "graph_scale");
-    finalize_kernel<<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->off, g->acc, g->gid, g->winv, g->RD, scores);
+    if (g->gid) {
+        graph_scale_kernel<<<(g->n_graphs + 255) / 256, 256, 0, s>>>(g->wmax_bits, g->n_graphs, g->winv);
+        RS_LAUNCHED(g, s, "graph_scale");
+    }
+    finalize_kernel<<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->off, g->acc, g->gid, g->winv, g->wmax_bits, g->RD,
+                                                         scores);
     RS_LAUNCHED(g, s, "finalize");
     return 0;
 }
