@@ -260,7 +260,7 @@ __global__ void init_tables_kernel(uint64_t *LG, double *RD, int32_t dmax, int a
 // ---------------------------------------------------------------------------
 // validation
 // ---------------------------------------------------------------------------
-enum : int { V_OFF = 1, V_COLRANGE = 2, V_SELF = 4, V_ORDER = 8, V_LABEL = 16, V_ASYM = 32 };
+enum : int { V_OFF = 1, V_COLRANGE = 2, V_SELF = 4, V_ORDER = 8, V_LABEL = 16 };
 
 __global__ void validate_offsets_kernel(const int64_t *off, int64_t n, int64_t nnz, int *flag) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -300,13 +300,44 @@ __device__ __forceinline__ int64_t find_in_row(const int64_t *off, const int32_t
     return (lo < off[row + 1] && col[lo] == key) ? lo : -1;
 }
 
-__global__ void validate_symmetry_kernel(const int64_t *off, const int32_t *col, int64_t n, int *flag) {
+// Symmetry: with every row strictly ascending (checked first) the directed edges
+// form a set E, and E is symmetric iff it equals its transpose.  Two keyed 64-bit
+// hashes of each entry are summed as h(u, v) - h(v, u) modulo 2^64 over all
+// entries; for a symmetric E every term cancels with its reverse's, so both sums
+// are 0.  An asymmetric E passes only if both sums vanish by chance (about 2^-128
+// for inputs not built against these keys).  One streaming pass over the CSR.
+// The mixer is the SplitMix64 finaliser (Steele, Lea and Flood, OOPSLA 2014).
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebull;
+    x ^= x >> 31;
+    return x;
+}
+constexpr uint64_t kSymKey0 = 0x243f6a8885a308d3ull, kSymKey1 = 0x13198a2e03707344ull;
+
+__global__ void validate_symmetry_kernel(const int64_t *off, const int32_t *col, int64_t n,
+                                         unsigned long long *sums) {
     int lane = threadIdx.x & 31;
     int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint64_t s0 = 0, s1 = 0;
     for (int64_t v = w; v < n; v += nw)
-        for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32)
-            if (find_in_row(off, col, col[e], (int32_t)v) < 0) atomicOr(flag, V_ASYM);
+        for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) {
+            uint64_t fwd = ((uint64_t)(uint32_t)v << 32) | (uint32_t)col[e];
+            uint64_t bwd = ((uint64_t)(uint32_t)col[e] << 32) | (uint32_t)v;
+            s0 += mix64(fwd ^ kSymKey0) - mix64(bwd ^ kSymKey0);
+            s1 += mix64(fwd ^ kSymKey1) - mix64(bwd ^ kSymKey1);
+        }
+    for (int o = 16; o; o >>= 1) {
+        s0 += __shfl_xor_sync(0xFFFFFFFFu, s0, o);
+        s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+    }
+    if (lane == 0 && (s0 | s1)) {
+        atomicAdd(&sums[0], (unsigned long long)s0);
+        atomicAdd(&sums[1], (unsigned long long)s1);
+    }
 }
 
 static int read_flag(rs_graph *g, cudaStream_t s, int *out) {
@@ -330,10 +361,14 @@ static int validate_graph(rs_graph *g, cudaStream_t s) {
     if (flag & V_SELF) return fail(RS_EINVAL, "invalid graph: self-loop");
     if (flag & V_ORDER) return fail(RS_EINVAL, "invalid graph: a row is not strictly ascending (unsorted or duplicate neighbour)");
     if (flag & V_LABEL) return fail(RS_EINVAL, "invalid graph: label outside [0, k)");
-    validate_symmetry_kernel<<<grid, kThreads, 0, s>>>(g->off, g->col, g->n, g->d_flag);
+    unsigned long long *sums = (unsigned long long *)(g->d_flag + 8);     // ints 8..11 of the 16
+    RS_CUDA_TRY(cudaMemsetAsync(sums, 0, 2 * sizeof(unsigned long long), s));
+    validate_symmetry_kernel<<<grid, kThreads, 0, s>>>(g->off, g->col, g->n, sums);
     RS_CUDA_TRY(cudaGetLastError());
-    if (int rc = read_flag(g, s, &flag)) return rc;
-    if (flag & V_ASYM) return fail(RS_EINVAL, "invalid graph: an edge is missing its reverse direction");
+    unsigned long long h[2] = {0, 0};
+    RS_CUDA_TRY(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+    RS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h[0] | h[1]) return fail(RS_EINVAL, "invalid graph: an edge is missing its reverse direction");
     return 0;
 }
 
@@ -726,7 +761,7 @@ static rs_status rs_build_graph_impl(int64_t n, int64_t nnz, const void *row_off
             return bail(cuda_fail(e, "copy labels"));
     if (cudaError_t e = cudaMemsetAsync(g->removed, 0, 4 * std::max<int64_t>(n, 1), s))
         return bail(cuda_fail(e, "clear flags"));
-    if (cudaError_t e = dmalloc(&g->d_flag, 8)) return bail(cuda_fail(e, "alloc flag"));
+    if (cudaError_t e = dmalloc(&g->d_flag, 16)) return bail(cuda_fail(e, "alloc flag"));   // flags + 2 hash sums
     if (flags & RS_VALIDATE) {
         if (int rc = validate_graph(g, s)) return bail(rc);
     }

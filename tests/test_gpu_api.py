@@ -103,6 +103,36 @@ def test_validation_rejects(rs, case):
     assert e.value.status == 1
 
 
+def test_validation_finds_one_sided_edges_in_a_large_graph(rs):
+    """The symmetry check must catch a single one-sided entry among millions: an edge
+    dropped in one direction, and one entry re-pointed (every degree unchanged)."""
+    g = graphgen.dcsbm_small(50000, seed=8, dmax=3000)
+    rs.Graph.build(g.offsets, g.cols, g.labels, g.k, validate=True).close()
+    rng = np.random.default_rng(3)
+    deg = np.diff(g.offsets)
+    for case in ("dropped", "repointed"):
+        u = int(rng.choice(np.nonzero(deg >= 3)[0]))
+        row = g.cols[g.offsets[u]:g.offsets[u + 1]]
+        if case == "dropped":
+            cols = np.delete(g.cols, g.offsets[u] + 1)
+            off = g.offsets.copy()
+            off[u + 1:] -= 1
+        else:
+            # replace one neighbour v of u by a non-neighbour w, keeping the row sorted
+            v = int(row[1])
+            w = next(x for x in range(row[0] + 1, row[2]) if x != u and x not in row) if row[2] - row[0] > 2 \
+                else None
+            if w is None:
+                continue
+            cols = g.cols.copy()
+            new_row = np.sort(np.where(row == v, w, row))
+            cols[g.offsets[u]:g.offsets[u + 1]] = new_row
+            off = g.offsets
+        with pytest.raises(rs.RSError) as e:
+            rs.Graph.build(off, cols, g.labels, g.k, validate=True)
+        assert e.value.status == 1 and "reverse" in str(e.value)
+
+
 def test_deterministic_and_clone(rs):
     g = graphgen.dcsbm_small(50000, seed=8, dmax=3000)
     G = rs.Graph.from_generated(g)
