@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "rs.h"
@@ -272,22 +273,44 @@ __global__ void validate_offsets_kernel(const int64_t *off, int64_t n, int64_t n
     if (bad) atomicOr(flag, V_OFF);
 }
 
+// tiles of 32 consecutive rows per warp: the tile's entries are streamed one per
+// lane (coalesced), and an entry's row is the last lane whose row starts at or
+// before it (binary lifting over the lanes' row starts by shuffles)
 __global__ void validate_rows_kernel(const int64_t *off, const int32_t *col, const int32_t *lab,
                                      int64_t n, int32_t k, int *flag) {
-    int lane = threadIdx.x & 31;
-    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = w; v < n; v += nw) {
-        int bad = 0;
-        if (lane == 0 && (lab[v] < 0 || lab[v] >= k)) bad |= V_LABEL;
-        for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) {
-            int32_t x = col[e];
-            if (x < 0 || x >= n) bad |= V_COLRANGE;
-            if (x == v) bad |= V_SELF;
-            if (e > off[v] && col[e - 1] >= x) bad |= V_ORDER;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int bad = 0;
+    for (int64_t r0 = w * 32; r0 < n; r0 += nw * 32) {
+        const int64_t v = r0 + lane;
+        const bool have = v < n;
+        const int64_t start = off[have ? v : n];
+        const int64_t tile_end = off[min(r0 + 32, n)];
+        if (have && (lab[v] < 0 || lab[v] >= k)) bad |= V_LABEL;
+        const int64_t e0 = __shfl_sync(0xFFFFFFFFu, start, 0);
+        for (int64_t base = e0; base < tile_end; base += 32) {
+            const int64_t e = base + lane;
+            int r = 0;
+            for (int step = 16; step; step >>= 1) {
+                int64_t sb = __shfl_sync(0xFFFFFFFFu, start, r + step);
+                if (sb <= e) r += step;
+            }
+            const int64_t rs = __shfl_sync(0xFFFFFFFFu, start, r);
+            if (e < tile_end) {
+                int32_t x = col[e];
+                if (x < 0 || x >= n) bad |= V_COLRANGE;
+                if (x == r0 + r) bad |= V_SELF;
+                if (e > rs && col[e - 1] >= x) bad |= V_ORDER;
+            }
         }
-        if (bad) atomicOr(flag, bad);
     }
+    bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, 16);
+    bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, 8);
+    bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, 4);
+    bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, 2);
+    bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, 1);
+    if (lane == 0 && bad) atomicOr(flag, bad);
 }
 
 __device__ __forceinline__ int64_t find_in_row(const int64_t *off, const int32_t *col, int32_t row,
@@ -353,22 +376,26 @@ static int validate_graph(rs_graph *g, cudaStream_t s) {
     RS_CUDA_TRY(cudaGetLastError());
     if (int rc = read_flag(g, s, &flag)) return rc;
     if (flag) return fail(RS_EINVAL, "invalid graph: row_offsets must start at 0, end at nnz and not decrease");
+    // with the offsets valid, the row checks and the symmetry sums (which read only
+    // offsets and columns) run back to back and are read together
     int grid = grid_for(g->n * 32, kThreads, 16);
-    validate_rows_kernel<<<grid, kThreads, 0, s>>>(g->off, g->col, g->lab, g->n, g->k, g->d_flag);
+    unsigned long long *sums = (unsigned long long *)(g->d_flag + 8);     // ints 8..11 of the 16
+    RS_CUDA_TRY(cudaMemsetAsync(sums, 0, 2 * sizeof(unsigned long long), s));
+    validate_rows_kernel<<<grid_for(g->n, kThreads, 16), kThreads, 0, s>>>(g->off, g->col, g->lab, g->n, g->k,
+                                                                         g->d_flag);
     RS_CUDA_TRY(cudaGetLastError());
-    if (int rc = read_flag(g, s, &flag)) return rc;
+    validate_symmetry_kernel<<<grid, kThreads, 0, s>>>(g->off, g->col, g->n, sums);
+    RS_CUDA_TRY(cudaGetLastError());
+    unsigned long long h[3] = {0, 0, 0};                                  // the flag word, then the sums
+    RS_CUDA_TRY(cudaMemcpyAsync(h, g->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RS_CUDA_TRY(cudaMemcpyAsync(h + 1, sums, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    RS_CUDA_TRY(cudaStreamSynchronize(s));
+    flag = (int)h[0];
     if (flag & V_COLRANGE) return fail(RS_EINVAL, "invalid graph: column id outside [0, n)");
     if (flag & V_SELF) return fail(RS_EINVAL, "invalid graph: self-loop");
     if (flag & V_ORDER) return fail(RS_EINVAL, "invalid graph: a row is not strictly ascending (unsorted or duplicate neighbour)");
     if (flag & V_LABEL) return fail(RS_EINVAL, "invalid graph: label outside [0, k)");
-    unsigned long long *sums = (unsigned long long *)(g->d_flag + 8);     // ints 8..11 of the 16
-    RS_CUDA_TRY(cudaMemsetAsync(sums, 0, 2 * sizeof(unsigned long long), s));
-    validate_symmetry_kernel<<<grid, kThreads, 0, s>>>(g->off, g->col, g->n, sums);
-    RS_CUDA_TRY(cudaGetLastError());
-    unsigned long long h[2] = {0, 0};
-    RS_CUDA_TRY(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
-    RS_CUDA_TRY(cudaStreamSynchronize(s));
-    if (h[0] | h[1]) return fail(RS_EINVAL, "invalid graph: an edge is missing its reverse direction");
+    if (h[1] | h[2]) return fail(RS_EINVAL, "invalid graph: an edge is missing its reverse direction");
     return 0;
 }
 
@@ -408,26 +435,6 @@ __global__ void classify_kernel(const int64_t *off, int64_t n, int32_t k, const 
     }
 }
 
-// small rows grouped by degree (so the threads of a warp run loops of equal length)
-__global__ void degree_hist_kernel(const int64_t *off, const int32_t *rows, int64_t m, int *hist) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool act = i < m;
-    int d = act ? (int)(off[rows[i] + 1] - off[rows[i]]) : 0;
-    unsigned am = __ballot_sync(0xFFFFFFFFu, act);
-    if (act) {
-        unsigned grp = __match_any_sync(am, d);
-        if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&hist[d], __popc(grp));
-    }
-}
-__global__ void degree_prefix_kernel(int *hist) {
-    int acc = 0;
-    for (int d = 0; d <= kSmallMax; ++d) { int c = hist[d]; hist[d] = acc; acc += c; }
-}
-__global__ void degree_scatter_kernel(const int64_t *off, const int32_t *rows, int64_t m, int *cursor,
-                                      int32_t *out) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) out[atomicAdd(&cursor[off[rows[i] + 1] - off[rows[i]]], 1)] = rows[i];
-}
 // per hub: row bounds and the communities of its graph
 // mid and large rows, largest first: the row kernels hand rows out dynamically,
 // so taking the longest ones first leaves short rows for the end (bucket of a
@@ -438,9 +445,12 @@ __device__ __forceinline__ int desc_bucket(int64_t d) {
     int q = e >= 2 ? (int)((d >> (e - 2)) & 3) : 0;
     return kDegBuckets - 1 - (4 * e + q);
 }
+// lanes with the same bucket count (and later take positions) with one atomic
 __global__ void bucket_hist_kernel(const int64_t *off, const int32_t *rows, int64_t m, int *hist) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) atomicAdd(&hist[desc_bucket(off[rows[i] + 1] - off[rows[i]])], 1);
+    int b = i < m ? desc_bucket(off[rows[i] + 1] - off[rows[i]]) : kDegBuckets;
+    unsigned same = __match_any_sync(0xFFFFFFFFu, b);
+    if (i < m && (threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[b], __popc(same));
 }
 __global__ void bucket_prefix_kernel(int *hist) {
     int acc = 0;
@@ -448,7 +458,13 @@ __global__ void bucket_prefix_kernel(int *hist) {
 }
 __global__ void bucket_scatter_kernel(const int64_t *off, const int32_t *rows, int64_t m, int *cursor, int32_t *out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) out[atomicAdd(&cursor[desc_bucket(off[rows[i] + 1] - off[rows[i]])], 1)] = rows[i];
+    int b = i < m ? desc_bucket(off[rows[i] + 1] - off[rows[i]]) : kDegBuckets;
+    unsigned same = __match_any_sync(0xFFFFFFFFu, b);
+    int lane = threadIdx.x & 31, leader = __ffs(same) - 1;
+    int base = 0;
+    if (i < m && lane == leader) base = atomicAdd(&cursor[b], __popc(same));
+    base = __shfl_sync(same, base, leader);
+    if (i < m) out[base + __popc(same & ((1u << lane) - 1u))] = rows[i];
 }
 
 __global__ void hub_bounds_kernel(const int64_t *off, const int32_t *hubs, int64_t nh, int32_t k, const int32_t *gid,
@@ -470,18 +486,78 @@ __global__ void scatter_class_kernel(const int64_t *a, int64_t n, int32_t *rows)
 }
 
 static void free_hub_tables(rs_graph *g) {
-    cudaFree(g->hubs); cudaFree(g->hub_items); cudaFree(g->hub_item_chunk);
-    cudaFree(g->hkey); cudaFree(g->hcnt); cudaFree(g->hq); cudaFree(g->hsig); cudaFree(g->hagg);
-    cudaFree(g->hitem_out); cudaFree(g->hitem_in);
+    void *ptrs[] = {g->hubs, g->hub_items, g->hub_item_chunk, g->hkey, g->hcnt, g->hq, g->hsig, g->hagg,
+                    g->hitem_out, g->hitem_in};
+    pool_free_many(ptrs, sizeof(ptrs) / sizeof(ptrs[0]));
     g->hubs = nullptr; g->hub_items = g->hub_item_chunk = nullptr; g->hkey = nullptr;
     g->hcnt = nullptr; g->hq = nullptr; g->hsig = nullptr; g->hagg = nullptr;
     g->hitem_out = g->hitem_in = nullptr;
     g->n_hubs = g->n_hub_items = g->hub_slots = 0;
 }
 
+// ---------------------------------------------------------------------------
+// device memory: one stream-ordered pool per device (created on first use)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr uint64_t kPoolKeep = 16ull << 30;      // freed bytes the pool keeps for reuse
+constexpr int kMaxDevices = 64;
+std::mutex pool_mutex;
+cudaMemPool_t pools[kMaxDevices];
+cudaStream_t pool_streams[kMaxDevices];
+
+cudaError_t pool_of_device(cudaMemPool_t *pool, cudaStream_t *st) {
+    int dev = 0;
+    if (cudaError_t e = cudaGetDevice(&dev)) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(pool_mutex);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pl = nullptr;
+        if (cudaError_t e = cudaMemPoolCreate(&pl, &props)) return e;
+        uint64_t keep = kPoolKeep;
+        if (cudaError_t e = cudaMemPoolSetAttribute(pl, cudaMemPoolAttrReleaseThreshold, &keep)) return e;
+        cudaStream_t s = nullptr;
+        if (cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) return e;
+        pools[dev] = pl;
+        pool_streams[dev] = s;
+    }
+    *pool = pools[dev];
+    *st = pool_streams[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t rs::pool_malloc(void **p, size_t bytes) {
+    cudaMemPool_t pl;
+    cudaStream_t st;
+    if (cudaError_t e = pool_of_device(&pl, &st)) return e;
+    if (cudaError_t e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 1), pl, st)) return e;
+    return cudaStreamSynchronize(st);            // usable on every stream from here on
+}
+
+cudaError_t rs::pool_free_many(void *const *p, size_t n) {
+    bool any = false;
+    for (size_t i = 0; i < n; ++i) any = any || p[i];
+    if (!any) return cudaSuccess;
+    cudaMemPool_t pl;
+    cudaStream_t st;
+    if (cudaError_t e = pool_of_device(&pl, &st)) return e;
+    if (cudaError_t e = cudaDeviceSynchronize()) return e;   // no kernel still uses the blocks
+    for (size_t i = 0; i < n; ++i)
+        if (p[i])
+            if (cudaError_t e = cudaFreeAsync(p[i], st)) return e;
+    return cudaSuccess;
+}
+
+cudaError_t rs::pool_free(void *p) { return pool_free_many(&p, 1); }
+
 template <class T>
 static cudaError_t dmalloc(T **p, size_t count) {
-    return cudaMalloc((void **)p, std::max<size_t>(count, 1) * sizeof(T));
+    return pool_malloc((void **)p, std::max<size_t>(count, 1) * sizeof(T));
 }
 
 // builds rows_small / rows_mid / rows_large / hub tables from the current offsets; syncs
@@ -513,35 +589,22 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
     g->n_small = counts[0]; g->n_mid = counts[1]; g->n_large = counts[2];
     g->dmax = hdr[0];
     g->large_cap = std::max(hdr[1], 64);
-    if (g->n_small > 1) {
-        int *hist = g->d_flag + 8;   // kSmallMax + 1 counters
-        unsigned sb = (unsigned)((g->n_small + 255) / 256);
-        RS_CUDA_TRY(cudaMemsetAsync(hist, 0, (kSmallMax + 1) * sizeof(int), s));
-        degree_hist_kernel<<<sb, 256, 0, s>>>(g->off, g->rows_small, g->n_small, hist);
-        RS_CUDA_TRY(cudaGetLastError());
-        degree_prefix_kernel<<<1, 1, 0, s>>>(hist);
-        RS_CUDA_TRY(cudaGetLastError());
-        degree_scatter_kernel<<<sb, 256, 0, s>>>(g->off, g->rows_small, g->n_small, hist, g->rows_small_deg);
-        RS_CUDA_TRY(cudaGetLastError());
-    } else if (g->n_small == 1) {
-        RS_CUDA_TRY(cudaMemcpyAsync(g->rows_small_deg, g->rows_small, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    }
-    // mid and large rows by degree, largest first (through the small-row scratch list)
+    // mid and large rows by degree, largest first (a counting sort by degree bucket through
+    // the scratch list; the counters live in the scan scratch, free at this point)
     for (int cls = 1; cls < 3; ++cls) {
         int32_t *rows = cls == 1 ? g->rows_mid : g->rows_large;
         int64_t m = cls == 1 ? g->n_mid : g->n_large;
         if (m < 2) continue;
-        int *hist = nullptr;
-        RS_CUDA_TRY(cudaMalloc(&hist, kDegBuckets * sizeof(int)));
+        int *hist = (int *)g->scan_tmp;
         unsigned mb = (unsigned)((m + 255) / 256);
-        cudaError_t e = cudaMemsetAsync(hist, 0, kDegBuckets * sizeof(int), s);
-        if (!e) { bucket_hist_kernel<<<mb, 256, 0, s>>>(g->off, rows, m, hist); e = cudaGetLastError(); }
-        if (!e) { bucket_prefix_kernel<<<1, 1, 0, s>>>(hist); e = cudaGetLastError(); }
-        if (!e) { bucket_scatter_kernel<<<mb, 256, 0, s>>>(g->off, rows, m, hist, g->rows_small_deg + g->n_small); e = cudaGetLastError(); }
-        if (!e) e = cudaMemcpyAsync(rows, g->rows_small_deg + g->n_small, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
-        if (!e) e = cudaStreamSynchronize(s);
-        cudaFree(hist);
-        if (e) return cuda_fail(e, "sort rows by degree");
+        RS_CUDA_TRY(cudaMemsetAsync(hist, 0, kDegBuckets * sizeof(int), s));
+        bucket_hist_kernel<<<mb, 256, 0, s>>>(g->off, rows, m, hist);
+        RS_CUDA_TRY(cudaGetLastError());
+        bucket_prefix_kernel<<<1, 1, 0, s>>>(hist);
+        RS_CUDA_TRY(cudaGetLastError());
+        bucket_scatter_kernel<<<mb, 256, 0, s>>>(g->off, rows, m, hist, g->rows_sort);
+        RS_CUDA_TRY(cudaGetLastError());
+        RS_CUDA_TRY(cudaMemcpyAsync(rows, g->rows_sort, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     }
     // hubs: host-side work list (hubs are few)
     int nh = hdr[2];
@@ -557,7 +620,7 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
         if (!e) e = cudaMemcpyAsync(hl.data(), hub_list, nh * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (!e) e = cudaMemcpyAsync(offs.data(), d_bounds, 3 * nh * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
         if (!e) e = cudaStreamSynchronize(s);
-        cudaFree(d_bounds);
+        pool_free(d_bounds);
         if (e) return cuda_fail(e, "hub bounds");
         // sort the hubs by row id, keeping their bounds
         std::vector<int> order(nh);
@@ -616,7 +679,7 @@ int rs::reclassify(rs_graph *g, cudaStream_t s) {
 }
 
 static int build_tables(rs_graph *g, cudaStream_t s) {
-    cudaFree(g->LG); cudaFree(g->RD);
+    pool_free(g->LG); pool_free(g->RD);
     g->LG = nullptr; g->RD = nullptr;
     int64_t m = (int64_t)g->dmax + 1;
     RS_CUDA_TRY(dmalloc(&g->LG, m));
@@ -632,8 +695,8 @@ int rs::set_mirror_buffer(rs_graph *g) {
         RS_CUDA_TRY(dmalloc(&g->xR, std::max<int64_t>(g->nnz, 1)));
         RS_CUDA_TRY(dmalloc(&g->xtile, g->nnz / kMirTile + 2));
     } else if (!g->tune.p3_mirror && g->xR) {
-        RS_CUDA_TRY(cudaFree(g->xR));
-        RS_CUDA_TRY(cudaFree(g->xtile));
+        RS_CUDA_TRY(pool_free(g->xR));
+        RS_CUDA_TRY(pool_free(g->xtile));
         g->xR = nullptr;
         g->xtile = nullptr;
     }
@@ -673,7 +736,7 @@ static int alloc_workspace(rs_graph *g) {
     RS_CUDA_TRY(dmalloc(&g->rows_small, n));
     RS_CUDA_TRY(dmalloc(&g->rows_mid, n));
     RS_CUDA_TRY(dmalloc(&g->rows_large, n));
-    RS_CUDA_TRY(dmalloc(&g->rows_small_deg, n));
+    RS_CUDA_TRY(dmalloc(&g->rows_sort, n));
     RS_CUDA_TRY(dmalloc(&g->d_flag, 64));
     return 0;
 }
@@ -681,11 +744,11 @@ static int alloc_workspace(rs_graph *g) {
 static void free_graph(rs_graph *g) {
     if (!g) return;
     void *ptrs[] = {g->off, g->off_alt, g->col, g->col_alt, g->lab, g->removed, g->dead,
-                    g->rows_small, g->rows_mid, g->rows_large, g->rows_small_deg, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
+                    g->rows_small, g->rows_mid, g->rows_large, g->rows_sort, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
                     g->Lall, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->scan_tmp, g->tk_hist,
                     g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->xR, g->xtile, g->rsum, g->cl_col, g->cl_lab,
                     g->winv, g->gid, g->gk, g->gnode, g->p2rows, g->p2cnt, g->sx, g->wq};
-    for (void *p : ptrs) cudaFree(p);
+    pool_free_many(ptrs, sizeof(ptrs) / sizeof(ptrs[0]));
     free_hub_tables(g);
     for (cudaEvent_t e : g->prof_ev) cudaEventDestroy(e);
     for (int i = 0; i < rs_graph::kAux; ++i) {
@@ -750,7 +813,7 @@ static rs_status rs_build_graph_impl(int64_t n, int64_t nnz, const void *row_off
             e = cudaGetLastError();
         }
         if (!e) e = cudaStreamSynchronize(s);
-        cudaFree(tmp);
+        pool_free(tmp);
         if (e) return bail(cuda_fail(e, "copy offsets"));
     }
     if (nnz > 0)
@@ -769,7 +832,7 @@ static rs_status rs_build_graph_impl(int64_t n, int64_t nnz, const void *row_off
         *out = g;
         return RS_OK;
     }
-    cudaFree(g->d_flag);
+    pool_free(g->d_flag);
     g->d_flag = nullptr;
     if (int rc = finish_graph(g, s)) return bail(rc);
     *out = g;
@@ -862,7 +925,7 @@ extern "C" rs_status rs_build_batch(int32_t n_graphs, const int64_t *graph_node_
         e = cudaGetLastError();
     }
     if (!e) e = cudaStreamSynchronize(s);
-    if (e) { cudaFree(d_koff); return bail(cuda_fail(e, "batch set-up")); }
+    if (e) { pool_free(d_koff); return bail(cuda_fail(e, "batch set-up")); }
     if (flags & RS_VALIDATE) {
         g->k = (int32_t)std::min<int64_t>(kmax, INT32_MAX);
         int rc = validate_graph(g, s);
@@ -878,17 +941,17 @@ extern "C" rs_status rs_build_batch(int32_t n_graphs, const int64_t *graph_node_
         }
         if (!rc && (flag & 2)) rc = fail(RS_EINVAL, "invalid batch: an edge leaves its graph");
         if (!rc && (flag & 1)) rc = fail(RS_EINVAL, "invalid batch: a label outside [0, k of its graph)");
-        if (rc) { cudaFree(d_koff); return bail(rc); }
+        if (rc) { pool_free(d_koff); return bail(rc); }
     }
     if (n > 0) {
         batch_labels_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->lab, g->gid, d_koff, n);
         e = cudaGetLastError();
         if (!e) e = cudaStreamSynchronize(s);
     }
-    cudaFree(d_koff);
+    pool_free(d_koff);
     if (e) return bail(cuda_fail(e, "batch labels"));
     g->k = (int32_t)ksum;
-    cudaFree(g->d_flag);
+    pool_free(g->d_flag);
     g->d_flag = nullptr;
     if (int rc = finish_graph(g, s)) return bail(rc);
     *out = g;
@@ -1050,7 +1113,7 @@ extern "C" rs_status rs_apply_removals(rs_graph *g, const int32_t *nodes, int64_
     int32_t *buf = nullptr;
     unsigned long long *d_applied = nullptr;
     int64_t words = n_nodes + 2 * n_edges;
-    auto done = [&](int rc) { cudaFree(buf); cudaFree(d_applied); return (rs_status)rc; };
+    auto done = [&](int rc) { pool_free(buf); pool_free(d_applied); return (rs_status)rc; };
     if (cudaError_t e = dmalloc(&buf, words)) return done(cuda_fail(e, "alloc removal lists"));
     if (cudaError_t e = dmalloc(&d_applied, 1)) return done(cuda_fail(e, "alloc counter"));
     cudaError_t e = cudaMemsetAsync(d_applied, 0, sizeof(unsigned long long), s);
@@ -1139,7 +1202,7 @@ extern "C" rs_status rs_target_subset(const rs_graph *g, const int32_t *targets,
             e = cudaGetLastError();
         }
         if (!e) {
-            if (int rc = inclusive_scan_i64(c->off_alt + 1, n, c->scan_tmp, s)) { cudaFree(d_map); return bail(rc); }
+            if (int rc = inclusive_scan_i64(c->off_alt + 1, n, c->scan_tmp, s)) { pool_free(d_map); return bail(rc); }
             compact_rows_kernel<<<grid, kThreads, 0, s>>>(c->off, c->col, (uint32_t *)c->dead, n, c->off_alt, c->col_alt);
             e = cudaGetLastError();
         }
@@ -1151,7 +1214,7 @@ extern "C" rs_status rs_target_subset(const rs_graph *g, const int32_t *targets,
         }
     }
     if (!e) e = cudaStreamSynchronize(s);
-    cudaFree(d_map);
+    pool_free(d_map);
     if (e) return bail(cuda_fail(e, "rs_target_subset"));
     c->k = n_targets;
     if (int rc = classify_rows(c, s)) return bail(rc);
@@ -1351,7 +1414,7 @@ extern "C" rs_status rs_awcc(rs_graph *g, const int32_t *nodes, int64_t m, const
     }
     if (!e) e = cudaMemcpyAsync(h.data(), d_buf + m, 2 * m * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
-    cudaFree(d_buf);
+    pool_free(d_buf);
     if (e) return (rs_status)cuda_fail(e, "rs_awcc");
     double sum = 0.0;
     for (int64_t i = 0; i < m; ++i) {

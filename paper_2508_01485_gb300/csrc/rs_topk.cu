@@ -256,13 +256,14 @@ __global__ void __launch_bounds__(kTkThreads) tk_select_kernel(TkArgs A) {
 
 static int ensure_topk_workspace(rs_graph *g, int64_t n) {
     if (g->tk_cap >= n && g->tk_hist) return 0;
-    cudaFree(g->tk_hist); cudaFree(g->tk_ctrl); cudaFree(g->tk_keys); cudaFree(g->tk_ids);
+    void *old[] = {g->tk_hist, g->tk_ctrl, g->tk_keys, g->tk_ids};
+    RS_CUDA_TRY(pool_free_many(old, 4));
     g->tk_hist = nullptr; g->tk_ctrl = nullptr; g->tk_keys = nullptr; g->tk_ids = nullptr;
     int64_t cap = n > 1 ? n : 1;
-    RS_CUDA_TRY(cudaMalloc(&g->tk_hist, kBins * sizeof(uint32_t)));
-    RS_CUDA_TRY(cudaMalloc(&g->tk_ctrl, 8 * sizeof(int)));
-    RS_CUDA_TRY(cudaMalloc(&g->tk_keys, (2 * cap + kSortMax) * sizeof(unsigned long long)));
-    RS_CUDA_TRY(cudaMalloc(&g->tk_ids, (2 * cap + kSortMax) * sizeof(uint32_t)));
+    RS_CUDA_TRY(pool_malloc((void **)&g->tk_hist, kBins * sizeof(uint32_t)));
+    RS_CUDA_TRY(pool_malloc((void **)&g->tk_ctrl, 8 * sizeof(int)));
+    RS_CUDA_TRY(pool_malloc((void **)&g->tk_keys, (2 * cap + kSortMax) * sizeof(unsigned long long)));
+    RS_CUDA_TRY(pool_malloc((void **)&g->tk_ids, (2 * cap + kSortMax) * sizeof(uint32_t)));
     g->tk_cap = cap;
     g->version++;                     // captured steps hold the old buffers
     return 0;
