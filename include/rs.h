@@ -80,10 +80,10 @@ typedef enum {
  *                   every row strictly ascending (sorted, no duplicates), no
  *                   self-loops, every edge present in both directions -- and
  *                   that labels lie in [0, k).  Returns RS_EINVAL otherwise.
- *                   Symmetry is checked by two keyed 64-bit hash sums of the
- *                   directed edges against their reverses, which cancel
+ *                   Symmetry is checked by a keyed 64-bit hash sum of the
+ *                   directed edges against their reverses, which cancels
  *                   exactly for a symmetric graph; an asymmetric one passes
- *                   only by a 2^-128-scale coincidence.
+ *                   only by a 2^-64-scale coincidence.
  *                   Without the flag the input must already satisfy this.
  *   out             receives the new graph (free with rs_free_graph).
  * Synchronises `stream` (the degree profile is read back to size workspaces).

@@ -273,15 +273,32 @@ __global__ void validate_offsets_kernel(const int64_t *off, int64_t n, int64_t n
     if (bad) atomicOr(flag, V_OFF);
 }
 
+// Symmetry: with every row strictly ascending (checked in the same pass) the directed
+// edges form a set E, and E is symmetric iff it equals its transpose.  A keyed 64-bit
+// hash of each entry is summed as h(u, v) - h(v, u) modulo 2^64 over all entries; for a
+// symmetric E every term cancels with its reverse's, so the sum is 0.  An asymmetric E
+// passes only if the sum vanishes by chance (about 2^-64 for inputs not built against
+// the key).  The mixer is the SplitMix64 finaliser (Steele, Lea and Flood, OOPSLA 2014).
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebull;
+    x ^= x >> 31;
+    return x;
+}
+constexpr uint64_t kSymKey = 0x243f6a8885a308d3ull;
+
 // tiles of 32 consecutive rows per warp: the tile's entries are streamed one per
 // lane (coalesced), and an entry's row is the last lane whose row starts at or
 // before it (binary lifting over the lanes' row starts by shuffles)
 __global__ void validate_rows_kernel(const int64_t *off, const int32_t *col, const int32_t *lab,
-                                     int64_t n, int32_t k, int *flag) {
+                                     int64_t n, int32_t k, int *flag, unsigned long long *sym) {
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int bad = 0;
+    uint64_t hs = 0;
     for (int64_t r0 = w * 32; r0 < n; r0 += nw * 32) {
         const int64_t v = r0 + lane;
         const bool have = v < n;
@@ -299,9 +316,12 @@ __global__ void validate_rows_kernel(const int64_t *off, const int32_t *col, con
             const int64_t rs = __shfl_sync(0xFFFFFFFFu, start, r);
             if (e < tile_end) {
                 int32_t x = col[e];
+                const uint32_t u = (uint32_t)(r0 + r);
                 if (x < 0 || x >= n) bad |= V_COLRANGE;
-                if (x == r0 + r) bad |= V_SELF;
+                if (x == (int32_t)u) bad |= V_SELF;
                 if (e > rs && col[e - 1] >= x) bad |= V_ORDER;
+                hs += mix64((((uint64_t)u << 32) | (uint32_t)x) ^ kSymKey) -
+                      mix64((((uint64_t)(uint32_t)x << 32) | u) ^ kSymKey);
             }
         }
     }
@@ -311,6 +331,8 @@ __global__ void validate_rows_kernel(const int64_t *off, const int32_t *col, con
     bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, 2);
     bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, 1);
     if (lane == 0 && bad) atomicOr(flag, bad);
+    for (int o = 16; o; o >>= 1) hs += __shfl_xor_sync(0xFFFFFFFFu, hs, o);
+    if (lane == 0 && hs) atomicAdd(sym, (unsigned long long)hs);
 }
 
 __device__ __forceinline__ int64_t find_in_row(const int64_t *off, const int32_t *col, int32_t row,
@@ -321,46 +343,6 @@ __device__ __forceinline__ int64_t find_in_row(const int64_t *off, const int32_t
         if (col[mid] < key) lo = mid + 1; else hi = mid;
     }
     return (lo < off[row + 1] && col[lo] == key) ? lo : -1;
-}
-
-// Symmetry: with every row strictly ascending (checked first) the directed edges
-// form a set E, and E is symmetric iff it equals its transpose.  Two keyed 64-bit
-// hashes of each entry are summed as h(u, v) - h(v, u) modulo 2^64 over all
-// entries; for a symmetric E every term cancels with its reverse's, so both sums
-// are 0.  An asymmetric E passes only if both sums vanish by chance (about 2^-128
-// for inputs not built against these keys).  One streaming pass over the CSR.
-// The mixer is the SplitMix64 finaliser (Steele, Lea and Flood, OOPSLA 2014).
-__device__ __forceinline__ uint64_t mix64(uint64_t x) {
-    x ^= x >> 30;
-    x *= 0xbf58476d1ce4e5b9ull;
-    x ^= x >> 27;
-    x *= 0x94d049bb133111ebull;
-    x ^= x >> 31;
-    return x;
-}
-constexpr uint64_t kSymKey0 = 0x243f6a8885a308d3ull, kSymKey1 = 0x13198a2e03707344ull;
-
-__global__ void validate_symmetry_kernel(const int64_t *off, const int32_t *col, int64_t n,
-                                         unsigned long long *sums) {
-    int lane = threadIdx.x & 31;
-    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    uint64_t s0 = 0, s1 = 0;
-    for (int64_t v = w; v < n; v += nw)
-        for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) {
-            uint64_t fwd = ((uint64_t)(uint32_t)v << 32) | (uint32_t)col[e];
-            uint64_t bwd = ((uint64_t)(uint32_t)col[e] << 32) | (uint32_t)v;
-            s0 += mix64(fwd ^ kSymKey0) - mix64(bwd ^ kSymKey0);
-            s1 += mix64(fwd ^ kSymKey1) - mix64(bwd ^ kSymKey1);
-        }
-    for (int o = 16; o; o >>= 1) {
-        s0 += __shfl_xor_sync(0xFFFFFFFFu, s0, o);
-        s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
-    }
-    if (lane == 0 && (s0 | s1)) {
-        atomicAdd(&sums[0], (unsigned long long)s0);
-        atomicAdd(&sums[1], (unsigned long long)s1);
-    }
 }
 
 static int read_flag(rs_graph *g, cudaStream_t s, int *out) {
@@ -376,26 +358,22 @@ static int validate_graph(rs_graph *g, cudaStream_t s) {
     RS_CUDA_TRY(cudaGetLastError());
     if (int rc = read_flag(g, s, &flag)) return rc;
     if (flag) return fail(RS_EINVAL, "invalid graph: row_offsets must start at 0, end at nnz and not decrease");
-    // with the offsets valid, the row checks and the symmetry sums (which read only
-    // offsets and columns) run back to back and are read together
-    int grid = grid_for(g->n * 32, kThreads, 16);
-    unsigned long long *sums = (unsigned long long *)(g->d_flag + 8);     // ints 8..11 of the 16
-    RS_CUDA_TRY(cudaMemsetAsync(sums, 0, 2 * sizeof(unsigned long long), s));
+    // with the offsets valid, one pass checks the rows and sums the symmetry hash
+    unsigned long long *sym = (unsigned long long *)(g->d_flag + 8);      // ints 8..9 of the 16
+    RS_CUDA_TRY(cudaMemsetAsync(sym, 0, sizeof(unsigned long long), s));
     validate_rows_kernel<<<grid_for(g->n, kThreads, 16), kThreads, 0, s>>>(g->off, g->col, g->lab, g->n, g->k,
-                                                                         g->d_flag);
+                                                                         g->d_flag, sym);
     RS_CUDA_TRY(cudaGetLastError());
-    validate_symmetry_kernel<<<grid, kThreads, 0, s>>>(g->off, g->col, g->n, sums);
-    RS_CUDA_TRY(cudaGetLastError());
-    unsigned long long h[3] = {0, 0, 0};                                  // the flag word, then the sums
+    unsigned long long h[2] = {0, 0};                                     // the flag word, then the sum
     RS_CUDA_TRY(cudaMemcpyAsync(h, g->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    RS_CUDA_TRY(cudaMemcpyAsync(h + 1, sums, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    RS_CUDA_TRY(cudaMemcpyAsync(h + 1, sym, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     RS_CUDA_TRY(cudaStreamSynchronize(s));
     flag = (int)h[0];
     if (flag & V_COLRANGE) return fail(RS_EINVAL, "invalid graph: column id outside [0, n)");
     if (flag & V_SELF) return fail(RS_EINVAL, "invalid graph: self-loop");
     if (flag & V_ORDER) return fail(RS_EINVAL, "invalid graph: a row is not strictly ascending (unsorted or duplicate neighbour)");
     if (flag & V_LABEL) return fail(RS_EINVAL, "invalid graph: label outside [0, k)");
-    if (h[1] | h[2]) return fail(RS_EINVAL, "invalid graph: an edge is missing its reverse direction");
+    if (h[1]) return fail(RS_EINVAL, "invalid graph: an edge is missing its reverse direction");
     return 0;
 }
 
