@@ -57,6 +57,11 @@ typedef enum {
                                communities left (Eq. weight); differs only for communities
                                absent from N(v): w_max and s of nodes without own-community
                                neighbours */
+#define RS_REORDER 8u      /* renumber the nodes internally by community, then degree (largest
+                               first), for locality; every id the caller sees or passes -- scores,
+                               top-K ids, interaction rows, removals, AWCC nodes -- stays the
+                               caller's own.  Not for rs_build_batch; graphs built with it are not
+                               served by rs_server */
 #define RS_TRIAD_STRICT 4u  /* the strict reading of the triad types (Sec. III-A): a closed
                                triangle (u, w, v) with C(v) = C(u) != C(w) is not a triad for
                                u (by default it counts once, as an augmented-edge triad).

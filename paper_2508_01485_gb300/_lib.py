@@ -18,6 +18,7 @@ RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ETIMEOUT, RS_EBUDGET = range(6)
 RS_VALIDATE = 1
 RS_ALG2_COMPAT = 2
 RS_TRIAD_STRICT = 4
+RS_REORDER = 8
 
 _lib = None
 
@@ -149,12 +150,13 @@ class Graph:
         self.k = int(k)
 
     @classmethod
-    def build(cls, offsets, cols, labels, k, validate=True, stream=None, alg2=False, strict=False):
+    def build(cls, offsets, cols, labels, k, validate=True, stream=None, alg2=False, strict=False, reorder=False):
         """rs_build_graph from numpy arrays (host) or torch CUDA tensors (device).
 
         offsets: int64 or int32 [n+1]; cols: int32 [nnz]; labels: int32 [n].
         alg2: RS_ALG2_COMPAT (weights with |L| = L_all - 1 for every column).
         strict: RS_TRIAD_STRICT (no closed triad with C(v) = C(u) != C(w)).
+        reorder: RS_REORDER (internal ids by community, then degree; ids stay the caller's).
         """
         import torch
         on_dev = isinstance(offsets, torch.Tensor) and offsets.is_cuda
@@ -179,7 +181,7 @@ class Graph:
                                     ctypes.c_void_p(p_col if nnz else None), ctypes.c_void_p(p_lab if n else None),
                                     int(k), 1 if on_dev else 0,
                                     (RS_VALIDATE if validate else 0) | (RS_ALG2_COMPAT if alg2 else 0)
-                                    | (RS_TRIAD_STRICT if strict else 0), s,
+                                    | (RS_TRIAD_STRICT if strict else 0) | (RS_REORDER if reorder else 0), s,
                                     ctypes.byref(h)))
         return cls(h, n, k)
 
@@ -208,9 +210,9 @@ class Graph:
         return out
 
     @classmethod
-    def from_generated(cls, g, validate=True, stream=None, alg2=False, strict=False):
+    def from_generated(cls, g, validate=True, stream=None, alg2=False, strict=False, reorder=False):
         return cls.build(g.offsets, g.cols, g.labels, g.k, validate=validate, stream=stream, alg2=alg2,
-                         strict=strict)
+                         strict=strict, reorder=reorder)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

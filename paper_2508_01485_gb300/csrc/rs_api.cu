@@ -725,7 +725,7 @@ static void free_graph(rs_graph *g) {
                     g->rows_small, g->rows_mid, g->rows_large, g->rows_sort, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
                     g->Lall, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->scan_tmp, g->tk_hist,
                     g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->xR, g->xtile, g->rsum, g->cl_col, g->cl_lab,
-                    g->winv, g->gid, g->gk, g->gnode, g->p2rows, g->p2cnt, g->sx, g->wq};
+                    g->winv, g->gid, g->gk, g->gnode, g->p2rows, g->p2cnt, g->sx, g->wq, g->perm};
     pool_free_many(ptrs, sizeof(ptrs) / sizeof(ptrs[0]));
     free_hub_tables(g);
     for (cudaEvent_t e : g->prof_ev) cudaEventDestroy(e);
@@ -743,8 +743,12 @@ __global__ void widen_offsets_kernel(const int32_t *in, int64_t *out, int64_t m)
 }
 
 // allocations and tables for a graph whose CSR/labels/removed are already on the device
-static int finish_graph(rs_graph *g, cudaStream_t s) {
+static int reorder_graph(rs_graph *g, cudaStream_t s);
+
+static int finish_graph(rs_graph *g, cudaStream_t s, bool reorder = false) {
     if (int rc = alloc_workspace(g)) return rc;
+    if (reorder)
+        if (int rc = reorder_graph(g, s)) return rc;
     if (int rc = classify_rows(g, s)) return rc;
     if (g->dmax >= (1 << 24)) return fail(RS_EINVAL, "max degree must be < 2^24");
     if (int rc = build_tables(g, s)) return rc;
@@ -806,13 +810,14 @@ static rs_status rs_build_graph_impl(int64_t n, int64_t nnz, const void *row_off
     if (flags & RS_VALIDATE) {
         if (int rc = validate_graph(g, s)) return bail(rc);
     }
+    if ((flags & RS_REORDER) && !finish) return bail(fail(RS_EINVAL, "rs_build_batch: RS_REORDER is for single graphs"));
     if (!finish) {                 // the caller completes the graph (batches)
         *out = g;
         return RS_OK;
     }
     pool_free(g->d_flag);
     g->d_flag = nullptr;
-    if (int rc = finish_graph(g, s)) return bail(rc);
+    if (int rc = finish_graph(g, s, (flags & RS_REORDER) != 0)) return bail(rc);
     *out = g;
     return RS_OK;
 }
@@ -983,6 +988,11 @@ extern "C" rs_status rs_clone_graph(const rs_graph *src, rs_graph **out, void *s
     if (!e && cur_nnz) e = cudaMemcpyAsync(g->col, src->col, cur_nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
     if (!e && n) e = cudaMemcpyAsync(g->lab, src->lab, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
     if (!e && n) e = cudaMemcpyAsync(g->removed, src->removed, 4 * n, cudaMemcpyDeviceToDevice, s);
+    if (!e && src->perm) {
+        g->iperm = src->iperm;
+        e = dmalloc(&g->perm, n);
+        if (!e) e = cudaMemcpyAsync(g->perm, src->perm, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    }
     if (e) return bail(cuda_fail(e, "copy graph"));
     g->n_graphs = src->n_graphs;
     if (src->gid) {
@@ -1088,6 +1098,19 @@ extern "C" rs_status rs_apply_removals(rs_graph *g, const int32_t *nodes, int64_
     for (int64_t i = 0; i < n_edges; ++i)
         if (edge_src[i] < 0 || edge_src[i] >= g->n || edge_dst[i] < 0 || edge_dst[i] >= g->n)
             return (rs_status)fail(RS_EINVAL, "rs_apply_removals: edge endpoint out of range");
+    // a reordered graph takes the caller's ids: map them to internal ones
+    std::vector<int32_t> mapped;
+    if (g->perm) {
+        mapped.resize(n_nodes + 2 * n_edges);
+        for (int64_t i = 0; i < n_nodes; ++i) mapped[i] = g->iperm[nodes[i]];
+        for (int64_t i = 0; i < n_edges; ++i) {
+            mapped[n_nodes + i] = g->iperm[edge_src[i]];
+            mapped[n_nodes + n_edges + i] = g->iperm[edge_dst[i]];
+        }
+        nodes = mapped.data();
+        edge_src = mapped.data() + n_nodes;
+        edge_dst = mapped.data() + n_nodes + n_edges;
+    }
     int32_t *buf = nullptr;
     unsigned long long *d_applied = nullptr;
     int64_t words = n_nodes + 2 * n_edges;
@@ -1274,13 +1297,14 @@ __global__ void count_runs_kernel(const int64_t *off, const int32_t *a, int64_t 
     }
 }
 
+// rows in the caller's order: internal row v lands at rp[perm[v]] (perm null: no reorder)
 __global__ void emit_runs_kernel(const int64_t *off, const int32_t *a, int64_t n, const int64_t *rp,
-                                 int32_t *comm, int32_t *count) {
+                                 const int32_t *perm, int32_t *comm, int32_t *count) {
     int lane = threadIdx.x & 31;
     int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t v = w; v < n; v += nw) {
-        int64_t out = rp[v];
+        int64_t out = rp[perm ? perm[v] : v];
         int64_t end = off[v + 1];
         for (int64_t base = off[v]; base < end; base += 32) {
             int64_t e = base + lane;
@@ -1296,6 +1320,98 @@ __global__ void emit_runs_kernel(const int64_t *off, const int32_t *a, int64_t n
             out += __popc(m);
         }
     }
+}
+
+__global__ void permute_counts_kernel(const int64_t *cnt_internal, const int32_t *perm, int64_t n, int64_t *cnt) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v == 0) cnt[0] = 0;
+    if (v < n) cnt[(int64_t)perm[v] + 1] = cnt_internal[v + 1];
+}
+
+// ---------------------------------------------------------------------------
+// RS_REORDER: internal ids by (community, degree descending, the caller's id).  The
+// permutation is a host counting sort (two stable passes); the CSR is rebuilt on the
+// device: degrees and rows gathered through the permutation, columns renamed, rows
+// sorted again, labels gathered.
+// ---------------------------------------------------------------------------
+__global__ void reorder_degrees_kernel(const int64_t *off, const int32_t *perm, int64_t n, int64_t *deg1) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) deg1[-1] = 0;
+    if (i < n) deg1[i] = off[(int64_t)perm[i] + 1] - off[perm[i]];
+}
+__global__ void reorder_rows_kernel(const int64_t *off, const int32_t *col, const int32_t *perm, const int32_t *iperm,
+                                    int64_t n, const int64_t *noff, int32_t *ncol) {
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w; i < n; i += nw) {
+        int64_t src = off[perm[i]], d = off[(int64_t)perm[i] + 1] - src, dst = noff[i];
+        for (int64_t j = lane; j < d; j += 32) ncol[dst + j] = iperm[col[src + j]];
+    }
+}
+__global__ void reorder_labels_kernel(const int32_t *lab, const int32_t *perm, int64_t n, int32_t *nlab) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) nlab[i] = lab[perm[i]];
+}
+
+static int reorder_graph(rs_graph *g, cudaStream_t s) {
+    const int64_t n = g->n;
+    if (n == 0) return 0;
+    std::vector<int64_t> off(n + 1);
+    std::vector<int32_t> lab(n);
+    RS_CUDA_TRY(cudaMemcpyAsync(off.data(), g->off, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RS_CUDA_TRY(cudaMemcpyAsync(lab.data(), g->lab, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RS_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t dmax = 0;
+    for (int64_t v = 0; v < n; ++v) dmax = std::max(dmax, off[v + 1] - off[v]);
+    // pass 1: stable by degree, largest first; pass 2: stable by community
+    std::vector<int64_t> cnt(std::max<int64_t>(dmax, g->k) + 2, 0);
+    std::vector<int32_t> by_deg(n), order(n);
+    for (int64_t v = 0; v < n; ++v) cnt[dmax - (off[v + 1] - off[v]) + 1]++;
+    for (int64_t b = 1; b <= dmax + 1; ++b) cnt[b] += cnt[b - 1];
+    for (int64_t v = 0; v < n; ++v) by_deg[cnt[dmax - (off[v + 1] - off[v])]++] = (int32_t)v;
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int64_t v = 0; v < n; ++v) cnt[(int64_t)lab[v] + 1]++;
+    for (int64_t c = 1; c <= g->k; ++c) cnt[c] += cnt[c - 1];
+    for (int64_t i = 0; i < n; ++i) order[cnt[lab[by_deg[i]]]++] = by_deg[i];
+    g->iperm.assign(n, 0);
+    for (int64_t i = 0; i < n; ++i) g->iperm[order[i]] = (int32_t)i;
+    int32_t *d_iperm = nullptr;
+    RS_CUDA_TRY(dmalloc(&g->perm, n));
+    RS_CUDA_TRY(dmalloc(&d_iperm, n));
+    cudaError_t e = cudaMemcpyAsync(g->perm, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d_iperm, g->iperm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    // new offsets in off_alt, new rows in col_alt, new labels through the removed flags' storage
+    if (!e) {
+        reorder_degrees_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->off, g->perm, n, g->off_alt + 1);
+        e = cudaGetLastError();
+    }
+    if (!e) {
+        if (int rc = inclusive_scan_i64(g->off_alt + 1, n, g->scan_tmp, s)) { pool_free(d_iperm); return rc; }
+        int grid = grid_for(n * 32, kThreads, 16);
+        reorder_rows_kernel<<<grid, kThreads, 0, s>>>(g->off, g->col, g->perm, d_iperm, n, g->off_alt, g->col_alt);
+        e = cudaGetLastError();
+        if (!e) {
+            sort_small_rows_kernel<<<grid, kThreads, 0, s>>>(g->off_alt, n, g->col_alt);
+            e = cudaGetLastError();
+        }
+        if (!e) {
+            sort_large_rows_kernel<<<grid_for(n, 1, 8), 512, 0, s>>>(g->off_alt, n, g->col_alt);
+            e = cudaGetLastError();
+        }
+        if (!e) {
+            reorder_labels_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->lab, g->perm, n, (int32_t *)g->removed);
+            e = cudaGetLastError();
+        }
+        if (!e) e = cudaMemcpyAsync(g->lab, g->removed, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        if (!e) e = cudaMemsetAsync(g->removed, 0, 4 * n, s);
+        if (!e) e = cudaStreamSynchronize(s);
+    }
+    pool_free(d_iperm);
+    if (e) return cuda_fail(e, "RS_REORDER");
+    std::swap(g->off, g->off_alt);
+    std::swap(g->col, g->col_alt);
+    return 0;
 }
 
 int rs::interaction_table(rs_graph *g, int64_t *t_out, int64_t *row_ptr, int32_t *comm, int32_t *count,
@@ -1315,7 +1431,14 @@ int rs::interaction_table(rs_graph *g, int64_t *t_out, int64_t *row_ptr, int32_t
         RS_CUDA_TRY(cudaGetLastError());
         sort_large_rows_kernel<<<grid_for(n, 1, 8), 512, 0, s>>>(g->off, n, a);
         RS_CUDA_TRY(cudaGetLastError());
-        count_runs_kernel<<<grid, kThreads, 0, s>>>(g->off, a, n, rp);
+        if (g->perm) {
+            // counts per internal row, then moved to the caller's row order before the scan
+            count_runs_kernel<<<grid, kThreads, 0, s>>>(g->off, a, n, g->xoff);
+            RS_CUDA_TRY(cudaGetLastError());
+            permute_counts_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->xoff, g->perm, n, rp);
+        } else {
+            count_runs_kernel<<<grid, kThreads, 0, s>>>(g->off, a, n, rp);
+        }
         RS_CUDA_TRY(cudaGetLastError());
         if (int rc = inclusive_scan_i64(rp + 1, n, g->scan_tmp, s)) return rc;
     } else {
@@ -1326,7 +1449,8 @@ int rs::interaction_table(rs_graph *g, int64_t *t_out, int64_t *row_ptr, int32_t
     RS_CUDA_TRY(cudaStreamSynchronize(s));
     if (row_ptr) RS_CUDA_TRY(cudaMemcpyAsync(row_ptr, rp, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     if (comm && count && n > 0) {
-        emit_runs_kernel<<<grid_for(n * 32, kThreads, 16), kThreads, 0, s>>>(g->off, a, n, rp, comm, count);
+        emit_runs_kernel<<<grid_for(n * 32, kThreads, 16), kThreads, 0, s>>>(g->off, a, n, rp, g->perm, comm,
+                                                                              count);
         RS_CUDA_TRY(cudaGetLastError());
     }
     RS_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1382,6 +1506,12 @@ extern "C" rs_status rs_awcc(rs_graph *g, const int32_t *nodes, int64_t m, const
     for (int64_t i = 0; i < m; ++i)
         if (nodes[i] < 0 || nodes[i] >= g->n) return (rs_status)fail(RS_EINVAL, "rs_awcc: node id out of range");
     if (m == 0) { *awcc_out = 0.0; return RS_OK; }
+    std::vector<int32_t> mapped;
+    if (g->perm) {                               // the caller's ids -> internal ones
+        mapped.resize(m);
+        for (int64_t i = 0; i < m; ++i) mapped[i] = g->iperm[nodes[i]];
+        nodes = mapped.data();
+    }
     int32_t *d_buf = nullptr;
     std::vector<int32_t> h(2 * (size_t)m);
     cudaError_t e = dmalloc(&d_buf, 3 * (size_t)m);

@@ -175,6 +175,8 @@ struct rs_graph {
     // launch parameters and a counter bumped whenever buffers or row classes change
     rs::df *xR = nullptr;                     // p3_mirror: at out-slot (w -> u) the reverse value S(u -> w)
     int32_t *xtile = nullptr;                 // p3_mirror: node holding the first slot of each mirror tile
+    int32_t *perm = nullptr;                  // RS_REORDER: internal id -> the caller's id (device)
+    std::vector<int32_t> iperm;               // RS_REORDER: the caller's id -> internal id (host)
     rs_tuning tune = rs::default_tuning_value();
     uint64_t version = 0;
     bool alg2 = false;                        // RS_ALG2_COMPAT: |L| = L_all - 1 for every column

@@ -1318,6 +1318,7 @@ struct P3Stage {
     uint8_t owner[kWinCap];         // lane (node) of the entry
     int32_t seg[33];                // first entry of each lane's node in the window
     int64_t aoff[32];               // xoff[a]
+    int32_t anode[32];              // a, the node of each lane
     // triangles found and not yet finished: the closing slot, the owner lane
     // and the window entries of the lower- and higher-ranked neighbours
     int64_t qpos[64];
@@ -1326,13 +1327,13 @@ struct P3Stage {
 
 // finish the first m (<= 32) queued triangles of the window, one per lane: the
 // forward values are at the three out-slots
-__device__ __forceinline__ void p3_flush(const P3Stage &S, int m, int64_t base, const df *xS, const Rev &R,
+__device__ __forceinline__ void p3_flush(const P3Stage &S, int m, const df *xS, const Rev &R,
                                          unsigned long long *acc, int lane) {
     if (lane < m) {
         int ow = S.qow[lane], el = S.qlo[lane], eh = S.qhi[lane];
         int64_t ao = S.aoff[ow] - S.seg[ow];
         int64_t il = ao + el, ih = ao + eh, pc = S.qpos[lane];
-        int32_t a = (int32_t)(base + ow), b = S.nb[el], c = S.nb[eh];
+        int32_t a = S.anode[ow], b = S.nb[el], c = S.nb[eh];
         df Sba = R.get(il, b, a), Sca = R.get(ih, c, a), Scb = R.get(pc, c, b);
         triangle_terms(a, b, c, xS[il], Sba, xS[ih], Sca, xS[pc], Scb, acc);
     }
@@ -1377,20 +1378,24 @@ __device__ void p3_node_global(int32_t a, int32_t dA, const int64_t *xoff, const
 }
 
 // groups of 32 nodes are handed out by an atomic counter (next_group, zeroed before
-// the launch), so warps that drew light groups take more and no tail is left waiting
+// the launch), so warps that drew light groups take more and no tail is left waiting.
+// Lane j of group g takes node (32 g + j) * stride mod n (stride coprime to n): on a
+// graph numbered by community and degree, consecutive ids hold a community's
+// heaviest nodes together, and one group of them would be a long tail for its warp.
 __global__ void __launch_bounds__(kThreads) p3_list_kernel(
     int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
     Rev R, const int32_t *__restrict__ xout, const NodeRec *__restrict__ rec, unsigned long long *acc,
-    unsigned long long *next_group) {
+    unsigned long long *next_group, int64_t stride) {
     __shared__ P3Stage stage[kP3Warps];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     P3Stage &S = stage[wid];
     while (true) {
         unsigned long long ticket = 0;
         if (lane == 0) ticket = atomicAdd(next_group, 1ull);
-        int64_t base = (int64_t)__shfl_sync(FULL, ticket, 0) * 32;
+        const int64_t base = (int64_t)__shfl_sync(FULL, ticket, 0) * 32;
         if (base >= n) break;
         int64_t av = base + lane;
+        if (stride != 1 && av < n) av = (int64_t)(((unsigned __int128)av * (uint64_t)stride) % (uint64_t)n);
         int32_t da = av < n ? xout[av] : 0;
         bool grp = da >= 2 && da <= kWinCap;
         int32_t mine = grp ? da : 0;
@@ -1416,6 +1421,7 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
                 S.seg[lane] = lane < start ? 0 : (inwin ? e0 : Ew);
                 if (lane == 0) S.seg[32] = Ew;
                 S.aoff[lane] = ba;
+                S.anode[lane] = (int32_t)av;
                 __syncwarp();
                 // entries, their data and the pair prefix sums, lanes over entries
                 uint32_t carry = 0;
@@ -1486,7 +1492,7 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
                         qn += __popc(hm);
                         if (qn >= 32) {                        // a full warp of triangles
                             __syncwarp();
-                            p3_flush(S, 32, base, xS, R, acc, lane);
+                            p3_flush(S, 32, xS, R, acc, lane);
                             __syncwarp();
                             if (lane < qn - 32) {
                                 S.qpos[lane] = S.qpos[32 + lane];
@@ -1500,7 +1506,7 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
                     }
                 }
                 __syncwarp();
-                p3_flush(S, qn, base, xS, R, acc, lane);   // the window's stage is reused next
+                p3_flush(S, qn, xS, R, acc, lane);   // the window's stage is reused next
                 qn = 0;
                 __syncwarp();
             }
@@ -1511,7 +1517,8 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
             int l = __ffs(big) - 1;
             big &= big - 1;
             int32_t dA = __shfl_sync(FULL, da, l);
-            p3_node_global((int32_t)(base + l), dA, xoff, xcol, xS, R, xout, rec, acc, lane);
+            int32_t aL = (int32_t)__shfl_sync(FULL, av, l);
+            p3_node_global(aL, dA, xoff, xcol, xS, R, xout, rec, acc, lane);
         }
     }
 }
@@ -1621,11 +1628,12 @@ __global__ void graph_scale_kernel(const unsigned long long *__restrict__ wmax_b
 }
 
 // one graph (gid null): every CTA takes 1 / w_max itself; a batch reads the
-// per-graph reciprocals graph_scale_kernel wrote
+// per-graph reciprocals graph_scale_kernel wrote.  A reordered graph (perm) writes
+// each score at the caller's id of its node.
 __global__ void __launch_bounds__(kThreads) finalize_kernel(
     int64_t n, const int64_t *__restrict__ off, const unsigned long long *__restrict__ acc,
     const int32_t *__restrict__ gid, const double *__restrict__ winv, const unsigned long long *__restrict__ wmax_bits,
-    const double *__restrict__ RD, double *scores) {
+    const double *__restrict__ RD, const int32_t *__restrict__ perm, double *scores) {
     __shared__ double sh_w;
     if (!gid) {
         if (threadIdx.x == 0) {
@@ -1642,7 +1650,7 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(
             u128 s = ((u128)acc[2 * u + 1] << 64) | acc[2 * u];
             if (s && W > 0.0) r = u128_to_double(s, -kAccFrac) * W * RD[d];
         }
-        scores[u] = r;
+        scores[perm ? (int64_t)perm[u] : u] = r;
     }
 }
 
@@ -1680,6 +1688,15 @@ static void launch_p2_large(rs_graph *g, const Batch &B, int *err, size_t smem) 
     p2_large_kernel<NT><<<grid_for(g->n_large, 1, 2), NT, smem, g->aux[4]>>>(
         g->off, L4, g->p2cnt + 4, B, g->tune.p2_cta_dx + 1, g->LG, g->rec, g->rsum, g->cl_col,
         g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, Strict{g->col, g->sx}, g->wq + 6);
+}
+
+// a stride near n / golden ratio, coprime to n (a bijection of [0, n) by multiplication)
+static int64_t p3_stride(int64_t n) {
+    if (n < 3) return 1;
+    auto gcd = [](int64_t a, int64_t b) { while (b) { int64_t t = a % b; a = b; b = t; } return a; };
+    int64_t st = (int64_t)((double)n * 0.6180339887) | 1;
+    while (st < n && gcd(st, n) != 1) st += 2;
+    return st < n ? st : 1;
 }
 
 int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
@@ -1834,7 +1851,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     const Rev R{g->tune.p3_mirror ? g->xR : nullptr, g->xoff, g->xcol, g->xS, g->xin, err};
     unsigned long long *next_group = g->wq + 7;
     p3_list_kernel<<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, R, g->xout, g->rec, g->acc,
-                                                        next_group);
+                                                        next_group, g->perm ? p3_stride(n) : 1);
     RS_LAUNCHED(g, s, "p3_list");
     // ---- finalize
     if (g->gid) {
@@ -1842,7 +1859,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_LAUNCHED(g, s, "graph_scale");
     }
     finalize_kernel<<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->off, g->acc, g->gid, g->winv, g->wmax_bits, g->RD,
-                                                         scores);
+                                                         g->perm, scores);
     RS_LAUNCHED(g, s, "finalize");
     return 0;
 }

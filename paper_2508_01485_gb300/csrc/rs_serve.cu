@@ -826,6 +826,7 @@ namespace {
 int prepare_base(Base &b) {
     rs_graph *g = b.g;
     if (g->n_graphs != 1) return fail(RS_EINVAL, "rs_server_create: batches are not served (build single graphs)");
+    if (g->perm) return fail(RS_EINVAL, "rs_server_create: graphs built with RS_REORDER are not served");
     b.n = g->n; b.nnz = g->nnz; b.k = g->k; b.dmax = g->dmax;
     int64_t unused = 0;
     RS_CUDA_TRY(dalloc(&b.acc, 2 * (size_t)b.n, unused));
