@@ -1318,7 +1318,6 @@ struct P3Stage {
     uint8_t owner[kWinCap];         // lane (node) of the entry
     int32_t seg[33];                // first entry of each lane's node in the window
     int64_t aoff[32];               // xoff[a]
-    int32_t anode[32];              // a, the node of each lane
     // triangles found and not yet finished: the closing slot, the owner lane
     // and the window entries of the lower- and higher-ranked neighbours
     int64_t qpos[64];
@@ -1327,13 +1326,16 @@ struct P3Stage {
 
 // finish the first m (<= 32) queued triangles of the window, one per lane: the
 // forward values are at the three out-slots
-__device__ __forceinline__ void p3_flush(const P3Stage &S, int m, const df *xS, const Rev &R,
+// the node of owner lane ow: base + ow, or (scrambled groups) the staged id anode[ow]
+template <bool kScr>
+__device__ __forceinline__ void p3_flush(const P3Stage &S, const int32_t *anode, int m, int64_t base, const df *xS,
+                                         const Rev &R,
                                          unsigned long long *acc, int lane) {
     if (lane < m) {
         int ow = S.qow[lane], el = S.qlo[lane], eh = S.qhi[lane];
         int64_t ao = S.aoff[ow] - S.seg[ow];
         int64_t il = ao + el, ih = ao + eh, pc = S.qpos[lane];
-        int32_t a = S.anode[ow], b = S.nb[el], c = S.nb[eh];
+        int32_t a = kScr ? anode[ow] : (int32_t)(base + ow), b = S.nb[el], c = S.nb[eh];
         df Sba = R.get(il, b, a), Sca = R.get(ih, c, a), Scb = R.get(pc, c, b);
         triangle_terms(a, b, c, xS[il], Sba, xS[ih], Sca, xS[pc], Scb, acc);
     }
@@ -1382,20 +1384,23 @@ __device__ void p3_node_global(int32_t a, int32_t dA, const int64_t *xoff, const
 // Lane j of group g takes node (32 g + j) * stride mod n (stride coprime to n): on a
 // graph numbered by community and degree, consecutive ids hold a community's
 // heaviest nodes together, and one group of them would be a long tail for its warp.
+template <bool kScr>
 __global__ void __launch_bounds__(kThreads) p3_list_kernel(
     int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
     Rev R, const int32_t *__restrict__ xout, const NodeRec *__restrict__ rec, unsigned long long *acc,
     unsigned long long *next_group, int64_t stride) {
     __shared__ P3Stage stage[kP3Warps];
+    __shared__ int32_t s_anode[kScr ? kP3Warps * 32 : 1];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     P3Stage &S = stage[wid];
+    int32_t *anode = s_anode + (kScr ? wid * 32 : 0);
     while (true) {
         unsigned long long ticket = 0;
         if (lane == 0) ticket = atomicAdd(next_group, 1ull);
         const int64_t base = (int64_t)__shfl_sync(FULL, ticket, 0) * 32;
         if (base >= n) break;
         int64_t av = base + lane;
-        if (stride != 1 && av < n) av = (int64_t)(((unsigned __int128)av * (uint64_t)stride) % (uint64_t)n);
+        if (kScr && av < n) av = (int64_t)(((unsigned __int128)av * (uint64_t)stride) % (uint64_t)n);
         int32_t da = av < n ? xout[av] : 0;
         bool grp = da >= 2 && da <= kWinCap;
         int32_t mine = grp ? da : 0;
@@ -1421,7 +1426,7 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
                 S.seg[lane] = lane < start ? 0 : (inwin ? e0 : Ew);
                 if (lane == 0) S.seg[32] = Ew;
                 S.aoff[lane] = ba;
-                S.anode[lane] = (int32_t)av;
+                if (kScr) anode[lane] = (int32_t)av;
                 __syncwarp();
                 // entries, their data and the pair prefix sums, lanes over entries
                 uint32_t carry = 0;
@@ -1492,7 +1497,7 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
                         qn += __popc(hm);
                         if (qn >= 32) {                        // a full warp of triangles
                             __syncwarp();
-                            p3_flush(S, 32, xS, R, acc, lane);
+                            p3_flush<kScr>(S, anode, 32, base, xS, R, acc, lane);
                             __syncwarp();
                             if (lane < qn - 32) {
                                 S.qpos[lane] = S.qpos[32 + lane];
@@ -1506,7 +1511,7 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
                     }
                 }
                 __syncwarp();
-                p3_flush(S, qn, xS, R, acc, lane);   // the window's stage is reused next
+                p3_flush<kScr>(S, anode, qn, base, xS, R, acc, lane);   // the window's stage is reused next
                 qn = 0;
                 __syncwarp();
             }
@@ -1517,7 +1522,7 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
             int l = __ffs(big) - 1;
             big &= big - 1;
             int32_t dA = __shfl_sync(FULL, da, l);
-            int32_t aL = (int32_t)__shfl_sync(FULL, av, l);
+            int32_t aL = kScr ? (int32_t)__shfl_sync(FULL, av, l) : (int32_t)(base + l);
             p3_node_global(aL, dA, xoff, xcol, xS, R, xout, rec, acc, lane);
         }
     }
@@ -1850,8 +1855,12 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     }
     const Rev R{g->tune.p3_mirror ? g->xR : nullptr, g->xoff, g->xcol, g->xS, g->xin, err};
     unsigned long long *next_group = g->wq + 7;
-    p3_list_kernel<<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, R, g->xout, g->rec, g->acc,
-                                                        next_group, g->perm ? p3_stride(n) : 1);
+    if (g->perm)                                     // a graph numbered by community: scrambled groups
+        p3_list_kernel<true><<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, R, g->xout, g->rec,
+                                                                  g->acc, next_group, p3_stride(n));
+    else
+        p3_list_kernel<false><<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, R, g->xout, g->rec,
+                                                                   g->acc, next_group, 1);
     RS_LAUNCHED(g, s, "p3_list");
     // ---- finalize
     if (g->gid) {
