@@ -642,8 +642,11 @@ __global__ void __launch_bounds__(kGxThreads) gx_offsets_kernel(
 // another community, in id order) and the row aggregates; own-community
 // neighbours are never touched again.
 
-// Rows with at most 32 cross neighbours, tiles of 32 consecutive rows of a list
-// per warp (the small rows, and the mid and large rows with dx <= 32).  The
+constexpr int kNarrowRows = 8;                 // rows per tile of the narrow mid and large rows
+
+// Rows with at most 32 cross neighbours, tiles of R <= 32 consecutive rows of a list
+// per warp (the small rows, R = 32, and the mid and large rows with dx <= 32, whose
+// longer cross lists take smaller tiles so that more warps share them).  The
 // union of the tile's cross lists is processed in chunks of whole rows, one
 // entry per lane (a chunk ends before the first row that would not fit its 32
 // lanes); lane l prepares and closes row l.  As no row spans two chunks, a
@@ -660,6 +663,7 @@ struct P2Tile {
     uint64_t st[32];
 };
 
+template <int R>
 __global__ void __launch_bounds__(kThreads) p2_small_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows_host,
     const int32_t *__restrict__ nrows_dev, const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
@@ -672,9 +676,9 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nrows = nrows_dev ? *nrows_dev : nrows_host;   // a list counted by p2_split, or the small rows
-    for (int64_t t0 = warp * 32; t0 < nrows; t0 += nwarps * 32) {
+    for (int64_t t0 = warp * R; t0 < nrows; t0 += nwarps * R) {
         int64_t i = t0 + lane;
-        bool have = i < nrows;
+        bool have = lane < R && i < nrows;
         int32_t w = have ? rows[i] : 0;
         int32_t dx = 0;
         if (have) {
@@ -1784,7 +1788,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     //      low-priority streams 0 and 1, the rows with long chains on the others
     if (int rc = fork_aux(g, s)) return rc;
     if (g->n_small) {
-        p2_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[0]>>>(
+        p2_small_kernel<32><<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[0]>>>(
             g->off, g->rows_small, g->n_small, nullptr, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
             g->xoff, g->xcol, g->xS, g->xout, g->xin, SX);
         RS_LAUNCHED(g, g->aux[0], "p2_small");
@@ -1797,7 +1801,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     const size_t smem256 = (size_t)kMidWarps * 256 * kMidSlotBytes, smem512 = (size_t)kMidWarps * 512 * kMidSlotBytes;
     if (nm + nl) {
         // the mid and large rows with at most 32 cross neighbours, in the tile kernel
-        p2_small_kernel<<<grid_for(nm + nl, NT, cps), NT, 0, g->aux[1]>>>(
+        p2_small_kernel<kNarrowRows><<<grid_for((nm + nl) * (32 / kNarrowRows), NT, cps), NT, 0, g->aux[1]>>>(
             g->off, Lst(0), 0, g->p2cnt + 0, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin, SX);
         RS_LAUNCHED(g, g->aux[1], "p2_narrow");

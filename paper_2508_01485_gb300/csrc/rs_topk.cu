@@ -13,6 +13,7 @@
 //   atomic per warp, while the global histogram is cleared for the next level.
 // As soon as the sure keys and the candidates fit a small shared-memory sort
 // (about 2K keys), CTA 0 sorts them (bitonic) and writes the first K.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "rs.h"
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(kTkThreads) tk_select_kernel(TkArgs A) {
     // CTA 0: sort the sure keys and the candidates left, write the first K
     if (blockIdx.x != 0) return;
     unsigned long long *key = (unsigned long long *)smem;
-    uint32_t *nid = (uint32_t *)(key + kSortMax);
+    uint32_t *nid = (uint32_t *)(key + sort_target(A.k));      // the launch sized the sort for k
     bool from_scores = level == 0;                              // nothing was compacted: n fits the sort
     int ns = ctrl[C_SURE];
     int nc = (int)m;
@@ -302,7 +303,10 @@ int rs::topk_scores(rs_graph *g, const double *scores, int64_t n, int32_t k, int
     A.nid[0] = ib; A.nid[1] = ib + cap; A.snid = ib + 2 * cap;
     prof_begin(g, s);
     void *args[] = {&A};
-    RS_CUDA_TRY(cudaLaunchCooperativeKernel((void *)tk_select_kernel, dim3(grid), dim3(kTkThreads), args, kTkSmem, s));
+    // dynamic shared memory: the level histograms, or the final sort of up to sort_target(k)
+    // keys, whichever is larger (24 KB for k <= 1024; the attribute allows kTkSmem)
+    const size_t smem = std::max((size_t)kBins * sizeof(uint32_t), (size_t)sort_target(k) * (8 + 4));
+    RS_CUDA_TRY(cudaLaunchCooperativeKernel((void *)tk_select_kernel, dim3(grid), dim3(kTkThreads), args, smem, s));
     RS_LAUNCHED(g, s, "tk_select");
     return 0;
 }
