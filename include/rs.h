@@ -276,7 +276,9 @@ rs_status rs_set_tuning(rs_graph *g, const rs_tuning *t, void *stream);
  *   topk_k > 0) under a coordinate sweep of the parameters above, starting
  *   from the current ones, and leave g on the fastest.  Each candidate's step
  *   is captured as rs_step_capture does and timed as the median of `reps`
- *   replays (>= 1) with CUDA events on `stream`, after one untimed replay.  `scores` (device, n doubles), `ids_out` and
+ *   replays (>= 1) with CUDA events on `stream`, after one untimed replay.
+ *   When the sweep ends away from the starting parameters, both are timed
+ *   again with 3 reps replays and the faster is kept.  `scores` (device, n doubles), `ids_out` and
  *   `vals_out` (device, topk_k each; may be NULL when topk_k == 0) are
  *   scratch.  best_out / best_ms_out (host, nullable) receive the choice and
  *   its median step time; n_tried_out (nullable) the candidates timed.
