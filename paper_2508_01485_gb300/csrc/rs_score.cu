@@ -1385,9 +1385,10 @@ __device__ void p3_node_global(int32_t a, int32_t dA, const int64_t *xoff, const
 
 // groups of 32 nodes are handed out by an atomic counter (next_group, zeroed before
 // the launch), so warps that drew light groups take more and no tail is left waiting.
-// Lane j of group g takes node (32 g + j) * stride mod n (stride coprime to n): on a
-// graph numbered by community and degree, consecutive ids hold a community's
-// heaviest nodes together, and one group of them would be a long tail for its warp.
+// kScr (graphs built with RS_REORDER): lane j of group g takes node
+// (32 g + j) * stride mod n (stride coprime to n), because consecutive ids then hold a
+// community's heaviest nodes together and one group of them would be a long tail for
+// its warp; otherwise lane j takes node 32 g + j and stride is unused.
 template <bool kScr>
 __global__ void __launch_bounds__(kThreads) p3_list_kernel(
     int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
