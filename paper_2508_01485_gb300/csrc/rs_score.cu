@@ -1306,10 +1306,10 @@ __device__ __forceinline__ void triangle_terms(int32_t a, int32_t b, int32_t c, 
 // binary search in the lower-ranked node's out-list in global memory (short:
 // the out-degree of a low-ranked node).  Found triangles are queued in shared
 // memory and finished a warp at a time, one per lane: the three forward values
-// sit at the out-slots, the three reverse ones are looked up in the in-lists
-// of the two higher-ranked nodes, and the terms of the three apexes are added.
-// Nodes with more than kWinCap out-neighbours take a lane-strided path over
-// global memory.
+// sit at the out-slots, the three reverse ones in xR (the mirror pass) or, with
+// p3_mirror = 0, in the in-lists of the two higher-ranked nodes, and the terms
+// of the three apexes are added.  Nodes with more than kWinCap out-neighbours
+// enumerate their pairs in staged tiles of out-list blocks (p3_node_tiled).
 constexpr int kWinCap = 128;
 constexpr int kP3Warps = kThreads / 32;
 
@@ -1359,28 +1359,60 @@ __device__ __forceinline__ int64_t find_in_list(const int32_t *xcol, int64_t lo,
     return (l < len && xcol[lo + l] == key) ? lo + l : -1;
 }
 
-// a node with more than kWinCap out-neighbours: lanes stride over its first entries
-__device__ void p3_node_global(int32_t a, int32_t dA, const int64_t *xoff, const int32_t *xcol, const df *xS,
-                               const Rev &R, const int32_t *xout, const NodeRec *rec, unsigned long long *acc,
-                               int lane) {
-    int64_t bA = xoff[a];
-    for (int32_t i = lane; i < dA; i += 32) {
-        int32_t b = xcol[bA + i];
-        int32_t dxb = rec[b].dx;
-        int64_t ob = xoff[b];
-        int32_t db = xout[b];
-        for (int32_t j = i + 1; j < dA; ++j) {
-            int32_t c = xcol[bA + j];
-            int32_t dxc = rec[c].dx;
-            bool b_low = rank_less(dxb, b, dxc, c);
-            int64_t pos = b_low ? find_in_list(xcol, ob, db, c) : find_in_list(xcol, xoff[c], xout[c], b);
-            if (pos < 0) continue;
-            int64_t il = bA + (b_low ? i : j), ih = bA + (b_low ? j : i);
-            int32_t lo = b_low ? b : c, hi = b_low ? c : b;
-            df Sla = R.get(il, lo, a), Sha = R.get(ih, hi, a), Shl = R.get(pos, hi, lo);
-            triangle_terms(a, lo, hi, xS[il], Sla, xS[ih], Sha, xS[pos], Shl, acc);
+// A node with more than kWinCap out-neighbours: its pairs in tiles.  The out-list is
+// cut into blocks of kHTile entries; for every pair of blocks (bi <= bj) the two blocks
+// are staged in the warp's P3Stage (ids, G_x offsets, out-degrees, ranks: slots
+// [0, kHTile) and [kHTile, 2 kHTile)), and the block pair's entry pairs are spread over
+// the lanes (the diagonal block keeps j > i).  A pair then costs the closing-edge
+// search alone, instead of the gathers of both ends' data besides.
+constexpr int kHTile = kWinCap / 2;
+
+__device__ __forceinline__ void p3_stage_block(P3Stage &S, int slot0, const int32_t *xcol, int64_t e0, int cnt,
+                                               const int64_t *xoff, const int32_t *xout, const NodeRec *rec,
+                                               int lane) {
+    for (int k = lane; k < cnt; k += 32) {
+        int32_t b = xcol[e0 + k];
+        S.nb[slot0 + k] = b;
+        S.boff[slot0 + k] = xoff[b];
+        S.bdeg[slot0 + k] = xout[b];
+        S.bdx[slot0 + k] = rec[b].dx;
+    }
+}
+
+__device__ __noinline__ void p3_node_tiled(P3Stage &S, int32_t a, int32_t dA, const int64_t *xoff, const int32_t *xcol,
+                              const df *xS, const Rev &R, const int32_t *xout, const NodeRec *rec,
+                              unsigned long long *acc, int lane) {
+    const int64_t bA = xoff[a];
+    const int nblk = (dA + kHTile - 1) / kHTile;
+    for (int bi = 0; bi < nblk; ++bi) {
+        const int ni = min(kHTile, dA - bi * kHTile);
+        __syncwarp();
+        p3_stage_block(S, 0, xcol, bA + (int64_t)bi * kHTile, ni, xoff, xout, rec, lane);
+        for (int bj = bi; bj < nblk; ++bj) {
+            const bool diag = bj == bi;
+            const int nj = diag ? ni : min(kHTile, dA - bj * kHTile);
+            const int sj = diag ? 0 : kHTile;          // slot of block bj's first entry
+            __syncwarp();
+            if (!diag) p3_stage_block(S, kHTile, xcol, bA + (int64_t)bj * kHTile, nj, xoff, xout, rec, lane);
+            __syncwarp();
+            for (int q = lane; q < ni * nj; q += 32) {
+                const int i = q / nj, jj = q - i * nj;
+                if (diag && jj <= i) continue;
+                const int si = i, sjj = sj + jj;
+                const bool i_low = rank_less(S.bdx[si], S.nb[si], S.bdx[sjj], S.nb[sjj]);
+                const int slo = i_low ? si : sjj, shi = i_low ? sjj : si;
+                const int64_t pos = find_in_list(xcol, S.boff[slo], S.bdeg[slo], S.nb[shi]);
+                if (pos < 0) continue;
+                // entry indices in a's out-list
+                const int64_t ei = (int64_t)bi * kHTile + i, ej = (int64_t)bj * kHTile + jj;
+                const int64_t il = bA + (i_low ? ei : ej), ih = bA + (i_low ? ej : ei);
+                const int32_t lo = S.nb[slo], hi = S.nb[shi];
+                df Sla = R.get(il, lo, a), Sha = R.get(ih, hi, a), Shl = R.get(pos, hi, lo);
+                triangle_terms(a, lo, hi, xS[il], Sla, xS[ih], Sha, xS[pos], Shl, acc);
+            }
         }
     }
+    __syncwarp();
 }
 
 // groups of 32 nodes are handed out by an atomic counter (next_group, zeroed before
@@ -1528,7 +1560,7 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
             big &= big - 1;
             int32_t dA = __shfl_sync(FULL, da, l);
             int32_t aL = kScr ? (int32_t)__shfl_sync(FULL, av, l) : (int32_t)(base + l);
-            p3_node_global(aL, dA, xoff, xcol, xS, R, xout, rec, acc, lane);
+            p3_node_tiled(S, aL, dA, xoff, xcol, xS, R, xout, rec, acc, lane);
         }
     }
 }
