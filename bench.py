@@ -9,7 +9,9 @@ degree-corrected SBM (1,000 power-law communities, degree power law 2.5 on
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  `value` = undirected edges scored per second
-over all ranks (weak scaling: each rank scores its own replica); `e2e` is the
+over all ranks (weak scaling: each rank scores its own replica of the graph, or,
+with --workload batch-G, its own G graphs of the batch: members [rG, (r+1)G));
+`e2e` is the
 same metric through the C ABI from pinned host buffers with the host<->device
 copies inside the timed region; `roofline` is the dominant kernel's
 algorithmic bytes over its CUDA-event time against the measured HBM peak;
@@ -113,11 +115,14 @@ class Packed:
     """Many graphs packed into one CSR: the step is rs_score over all of them at once."""
     tune_reps = 3
 
-    def __init__(self, n_graphs, workers):
+    def __init__(self, n_graphs, workers, shard=0):
         import graphgen
-        sizes = graphgen._batch_sizes(n_graphs, BATCH_N_MIN, BATCH_N_MAX, BATCH_SEED)
+        # rank r scores batch members [r * n_graphs, (r + 1) * n_graphs): its own graphs, the
+        # same count on every rank (weak scaling), and rank 0 alone has the 1-GPU batch
+        self.first = first = shard * n_graphs
+        sizes = graphgen._batch_sizes(n_graphs, BATCH_N_MIN, BATCH_N_MAX, BATCH_SEED, first)
         K = sum(max(2, n // 100) for n in sizes)
-        jobs = [((n, BATCH_SEED, i, BATCH_DMAX), K) for i, n in enumerate(sizes)]
+        jobs = [((n, BATCH_SEED, first + i, BATCH_DMAX), K) for i, n in enumerate(sizes)]
         workers = workers or min(32, os.cpu_count() or 1)
         if workers > 1 and n_graphs > 1:
             import concurrent.futures as cf
@@ -164,16 +169,17 @@ class Packed:
                           "extrapolated time" % (len(self.sample), ", ".join(parts))}
 
     def config(self):
-        return {"workload": self.name, "graphs": self.n_graphs, "n": self.n, "m": self.m, "k": self.k,
+        return {"workload": self.name, "graphs": self.n_graphs, "members": [self.first, self.first + self.n_graphs],
+                "n": self.n, "m": self.m, "k": self.k,
                 "max_degree": self.st["dmax"],
                 "sizes": "log-uniform n on [%d, %d], k = n/100, degrees 2.5 on [8, %d], mixing 0.2"
                          % (BATCH_N_MIN, BATCH_N_MAX, BATCH_DMAX),
                 "step": "rs_score over the packed batch (per-graph w_max)"}
 
 
-def make_workload(args):
+def make_workload(args, rank=0):
     if args.workload.startswith("batch-"):
-        return Packed(int(args.workload.split("-")[1]), args.gen_workers)
+        return Packed(int(args.workload.split("-")[1]), args.gen_workers, rank)
     return Single(workload(args.workload))
 
 
@@ -280,16 +286,19 @@ def step_bytes(st):
 
 # ---- aggregation over ranks -----------------------------------------------------------
 
-def aggregate(local_ms, units_per_rank, world, device=None):
-    """Whole-job throughput over ranks: every rank processed units_per_rank units in
-    local_ms; the job took the slowest rank's time.  Returns (value per second, max ms)."""
+def aggregate(local_ms, local_units, world, device=None):
+    """Whole-job throughput over ranks: this rank processed local_units units in local_ms;
+    the job processed every rank's units and took the slowest rank's time.  Returns
+    (value per second, max ms)."""
     import torch
     import torch.distributed as dist
     t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
     ms = float(t.item())
-    return world * units_per_rank / (ms / 1e3), ms
+    return float(u.item()) / (ms / 1e3), ms
 
 
 # ---- clocks --------------------------------------------------------------------------
@@ -380,7 +389,7 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    W = make_workload(args)              # host-side generation before the first CUDA call
+    W = make_workload(args, rank)        # host-side generation before the first CUDA call
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -538,7 +547,8 @@ def run_ours(args):
     config.update({"l2": "flushed between timed steps (512 MB write outside the events)",
                    "launch": "the step captured once as a CUDA graph (rs_step_capture) and replayed "
                              "(rs_step_launch); per-kernel times from the same steps launched directly",
-                   "parallelism": "replicas" if world > 1 else "single",
+                   "parallelism": "single" if world == 1 else
+                                  ("graph shards" if isinstance(W, Packed) else "replicas"),
                    "tuning": tuning, "autotune": autotune})
     out = {
         "metric": "RS-scored edges/s", "value": value, "unit": "edges/s", "n_gpus": world,

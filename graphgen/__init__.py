@@ -192,11 +192,12 @@ def pack(graphs, name="batch") -> Batch:
                  offsets=offsets, cols=cols, labels=labels, name=name)
 
 
-def _batch_sizes(n_graphs: int, n_min: int, n_max: int, seed: int):
-    """Graph i's node count, log-uniform on [n_min, n_max] from a hash of (seed, i)."""
+def _batch_sizes(n_graphs: int, n_min: int, n_max: int, seed: int, first: int = 0):
+    """Node counts of graphs first .. first + n_graphs - 1: graph i's is log-uniform on
+    [n_min, n_max] from a hash of (seed, i), so any range of members can be drawn alone."""
     import math
     out = []
-    for i in range(n_graphs):
+    for i in range(first, first + n_graphs):
         u = ((i * 0x9E3779B97F4A7C15 + seed * 0xBF58476D1CE4E5B9) % (1 << 64)) / float(1 << 64)
         out.append(int(round(math.exp(math.log(n_min) + u * (math.log(n_max) - math.log(n_min))))))
     return out
