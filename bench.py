@@ -215,6 +215,14 @@ def graph_stats(g, k_class=None):
     cls = np.where(deg <= 32, 0, np.where(cap <= 512, 1, np.where(cap <= 2048, 2, 3)))
     st = {"n": n, "E": E, "m": E // 2, "k": g.k, "dmax": int(deg.max()) if n else 0,
           "gx_slots": int(keep.sum()), "out_slots": int(out.sum()), "cross": int(cross.sum())}
+    # P3's heavy nodes (more than 128 G_x out-neighbours): their out-slots and the
+    # wedges a -> b -> c that their walk streams
+    xo = np.bincount(a[out], minlength=n)
+    hv = xo > 128
+    ha = hv[a[out]]
+    st["heavy_nodes"] = int(hv.sum())
+    st["heavy_slots"] = int(xo[hv].sum())
+    st["heavy_wedges"] = int(xo[b[out][ha]].sum())
     def put(name, sel):
         st["R_" + name] = int(sel.sum())
         st["E_" + name] = int(deg[sel].sum())
@@ -265,6 +273,9 @@ def kernel_bytes(name, st):
         # out-lists (ids, forward and reverse values are read only for triangles), out counts,
         # offsets and ranks of every node
         "p3_list": lambda: 4 * st["out_slots"] + (4 + 8 + 4) * n,
+        # heavy nodes: their out-lists (ids), their out-neighbours' offsets and out counts,
+        # and every wedge's closing id, once each
+        "p3_heavy": lambda: (4 + 8 + 4) * st["heavy_slots"] + 4 * st["heavy_wedges"],
         # every in-slot (id, value) read once, its out-slot's reverse value written once;
         # in counts, offsets and ranks of every node
         "gx_mirror": lambda: (4 + 8 + 8) * st["out_slots"] + (4 + 8 + 4) * n,

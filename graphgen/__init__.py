@@ -139,6 +139,39 @@ def dcsbm_small(n: int, seed: int, dmax: int = 1000, mu: float = 0.2, gamma: flo
 
 # ---- batches of independent graphs -----------------------------------------
 
+def dense_core(n_core: int = 600, n_fan: int = 2500, fan_min: int = 40, fan_max: int = 420, n_full: int = 6,
+               core_edges: int = 400, fan_edges: int = 400, k: int = 40, seed: int = 11) -> Graph:
+    """A dense bipartite core, so that many nodes have long G_x out-lists (G_x oriented by
+    cross degree, then id).  Each of n_fan fan nodes is joined to a uniform random subset of
+    the n_core core nodes (subset size uniform on [fan_min, fan_max]); n_full nodes are joined
+    to every core node; core_edges random pairs of core nodes and fan_edges random pairs of
+    fan nodes are joined as well (duplicates and loops dropped); labels uniform on [0, k).
+    Core nodes end up with the largest cross degrees, so the fan nodes' out-lists (up to
+    ~fan_max) and the full nodes' (~n_core) hold core nodes."""
+    rng = np.random.default_rng(seed)
+    n = n_core + n_fan + n_full
+    parts = []
+    for f in range(n_fan):
+        s = int(rng.integers(fan_min, fan_max + 1))
+        parts.append(np.stack([np.full(s, n_core + f), rng.choice(n_core, s, replace=False)], 1))
+    for x in range(n_full):
+        parts.append(np.stack([np.full(n_core, n_core + n_fan + x), np.arange(n_core)], 1))
+    parts.append(rng.integers(0, n_core, (core_edges, 2)))
+    parts.append(n_core + rng.integers(0, n_fan, (fan_edges, 2)))
+    e = np.concatenate(parts).astype(np.int64)
+    e = e[e[:, 0] != e[:, 1]]
+    key = np.unique(np.minimum(e[:, 0], e[:, 1]) * n + np.maximum(e[:, 0], e[:, 1]))
+    u, v = key // n, key % n
+    src, dst = np.concatenate([u, v]), np.concatenate([v, u])
+    order = np.lexsort((dst, src))
+    src, dst = src[order], dst[order]
+    offsets = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(src, minlength=n), out=offsets[1:])
+    labels = rng.integers(0, k, n).astype(np.int32)
+    return Graph(n=n, k=k, offsets=offsets, cols=dst.astype(np.int32), labels=labels,
+                 name="dense-core-%d-%d" % (n_core, n_fan))
+
+
 @dataclass
 class Batch:
     """Independent graphs packed into one CSR (node ids global, labels local)."""

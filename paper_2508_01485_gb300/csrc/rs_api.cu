@@ -708,7 +708,7 @@ static int alloc_workspace(rs_graph *g) {
     if (int rc = rs::set_mirror_buffer(g)) return rc;
     RS_CUDA_TRY(dmalloc(&g->p2rows, 4 * (size_t)n));
     RS_CUDA_TRY(dmalloc(&g->p2cnt, 16));
-    RS_CUDA_TRY(dmalloc(&g->wq, wq_words(n)));
+    RS_CUDA_TRY(dmalloc(&g->wq, wq_words(n, nnz)));
     if (g->strict) RS_CUDA_TRY(dmalloc(&g->sx, 2 * (size_t)nnz));
     RS_CUDA_TRY(dmalloc(&g->scan_tmp, scan_tmp_words(std::max<int64_t>(n + 1, 1)) + 64));
     RS_CUDA_TRY(dmalloc(&g->rows_small, n));

@@ -190,10 +190,21 @@ namespace rs {
 constexpr int kThreads = 256;
 constexpr int kMirTile = 2048;               // G_x slots per tile of the mirror pass
 constexpr int kGxTile = 4096;                // nodes per tile of the G_x offset scan
-// words of rs_graph::wq, zeroed before every scoring pass: 0..7 the row and group
-// counters of the row kernels, 8 the ticket of the G_x offset scan, 16.. its tile words
-constexpr int kWqGxTicket = 8, kWqGxStatus = 16;
-inline int64_t wq_words(int64_t n) { return kWqGxStatus + (n + kGxTile - 1) / kGxTile + 1; }
+// P3: a node with more than kWinCap G_x out-neighbours is heavy, and its walk is cut into
+// tasks of kHvBlock out-neighbours.  Every G_x edge has one tail, so the heavy nodes
+// number at most m_x / (kWinCap + 1), and their tasks at most
+// sum (d+ + kHvBlock - 1) / kHvBlock <= m_x (1 + 31 / 129) / 32 < nnz / 51 (m_x <= nnz / 2).
+constexpr int kWinCap = 128, kHvBlock = 32;
+static_assert(kWinCap == 128 && kHvBlock == 32, "hv_cap's bound is worked out for these values");
+inline int64_t hv_cap(int64_t nnz) { return nnz / 51 + 1; }
+// words of rs_graph::wq: 0..7 the row and group counters of the row kernels, 8 the
+// ticket of the G_x offset scan, 9 and 10 the append and claim counters of P3's
+// heavy-node task list, 16.. the scan's tile words (all these zeroed before every
+// scoring pass: wq_hv_word words); then the task list, hv_cap words (node << 32 | block),
+// each written before it is read
+constexpr int kWqGxTicket = 8, kWqHvCount = 9, kWqHvNext = 10, kWqGxStatus = 16;
+inline int64_t wq_hv_word(int64_t n) { return kWqGxStatus + (n + kGxTile - 1) / kGxTile + 1; }
+inline int64_t wq_words(int64_t n, int64_t nnz) { return wq_hv_word(n) + hv_cap(nnz); }
 
 // error reporting (rs_api.cu): returns the status after recording the message
 int fail(int status, const std::string &msg);

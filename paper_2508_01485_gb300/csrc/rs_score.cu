@@ -1309,8 +1309,7 @@ __device__ __forceinline__ void triangle_terms(int32_t a, int32_t b, int32_t c, 
 // sit at the out-slots, the three reverse ones in xR (the mirror pass) or, with
 // p3_mirror = 0, in the in-lists of the two higher-ranked nodes, and the terms
 // of the three apexes are added.  Nodes with more than kWinCap out-neighbours
-// enumerate their pairs in staged tiles of out-list blocks (p3_node_tiled).
-constexpr int kWinCap = 128;
+// (heavy nodes) are walked by wedges instead (p3_node_wedges).
 constexpr int kP3Warps = kThreads / 32;
 
 struct P3Stage {
@@ -1359,59 +1358,137 @@ __device__ __forceinline__ int64_t find_in_list(const int32_t *xcol, int64_t lo,
     return (l < len && xcol[lo + l] == key) ? lo + l : -1;
 }
 
-// A node with more than kWinCap out-neighbours: its pairs in tiles.  The out-list is
-// cut into blocks of kHTile entries; for every pair of blocks (bi <= bj) the two blocks
-// are staged in the warp's P3Stage (ids, G_x offsets, out-degrees, ranks: slots
-// [0, kHTile) and [kHTile, 2 kHTile)), and the block pair's entry pairs are spread over
-// the lanes (the diagonal block keeps j > i).  A pair then costs the closing-edge
-// search alone, instead of the gathers of both ends' data besides.
-constexpr int kHTile = kWinCap / 2;
+// Heavy nodes: a wedge walk.  Node a's out-list A (sorted by id) is staged in shared
+// memory, kHvIds ids at a time.  For every b in A the warp streams b's out-list (the
+// nodes c ranked above b), and c closes the triangle {a, b, c} iff c is in A: a binary
+// search in the staged ids.  Every triangle whose lowest-ranked node is heavy is met
+// once, at its middle-ranked node b.  When A takes several chunks, b's out-list is first
+// cut to the chunk's id range.  There are several times more wedges than pairs on such
+// nodes, but a wedge costs a coalesced load and a shared-memory search where a pair
+// costs a binary search in global memory.
+//
+// The warp whose group holds a heavy node does not walk it: it appends the node's tasks,
+// one per block of kHvBlock out-neighbours b, to the task list (slots taken with an
+// atomic counter), and p3_heavy_kernel, launched next on the same stream, runs the
+// tasks, a warp per task, so that the heaviest node is spread over many warps.  The walk
+// has its own kernel so that its registers do not lower the occupancy of the group
+// kernel.
+constexpr int kHvIds = 512;
+constexpr int kHvQ = 64;
 
-__device__ __forceinline__ void p3_stage_block(P3Stage &S, int slot0, const int32_t *xcol, int64_t e0, int cnt,
-                                               const int64_t *xoff, const int32_t *xout, const NodeRec *rec,
-                                               int lane) {
-    for (int k = lane; k < cnt; k += 32) {
-        int32_t b = xcol[e0 + k];
-        S.nb[slot0 + k] = b;
-        S.boff[slot0 + k] = xoff[b];
-        S.bdeg[slot0 + k] = xout[b];
-        S.bdx[slot0 + k] = rec[b].dx;
+struct P3Heavy {
+    int32_t ids[kHvIds];            // a chunk of a's out-list
+    // triangles found and not yet finished: the closing slot (c in b's out-list), the
+    // entries of b and c in a's out-list, b and c
+    int64_t qpc[kHvQ];
+    int32_t qeb[kHvQ], qec[kHvQ], qb[kHvQ], qc[kHvQ];
+};
+
+// first position of the sorted p[0, cnt) (cnt >= 1) holding an id >= key, or cnt;
+// the trip count depends on cnt alone
+__device__ __forceinline__ int32_t lower_pos(const int32_t *p, int32_t cnt, int32_t key) {
+    int32_t base = 0, len = cnt;
+    while (len > 1) {
+        const int32_t half = len >> 1;
+        base = p[base + half] < key ? base + half : base;
+        len -= half;
+    }
+    return base + (p[base] < key ? 1 : 0);
+}
+
+// finish the first m (<= 32) queued triangles of heavy node a, one per lane
+__device__ __forceinline__ void hv_flush(const P3Heavy &H, int m, int32_t a, int64_t bA, const df *xS,
+                                         const Rev &R, unsigned long long *acc, int lane) {
+    if (lane < m) {
+        const int64_t il = bA + H.qeb[lane], ih = bA + H.qec[lane], pc = H.qpc[lane];
+        const int32_t b = H.qb[lane], c = H.qc[lane];
+        df Sba = R.get(il, b, a), Sca = R.get(ih, c, a), Scb = R.get(pc, c, b);
+        triangle_terms(a, b, c, xS[il], Sba, xS[ih], Sca, xS[pc], Scb, acc);
     }
 }
 
-__device__ __noinline__ void p3_node_tiled(P3Stage &S, int32_t a, int32_t dA, const int64_t *xoff, const int32_t *xcol,
-                              const df *xS, const Rev &R, const int32_t *xout, const NodeRec *rec,
-                              unsigned long long *acc, int lane) {
+// one task: heavy node a, its out-neighbours b at entries [eb0, eb0 + kHvBlock) of A
+__device__ __forceinline__ void p3_node_wedges(P3Heavy &H, int32_t a, int32_t eb0, const int64_t *xoff,
+                                            const int32_t *xcol, const df *xS, const Rev &R,
+                                            const int32_t *xout, unsigned long long *acc, int lane) {
+    static_assert(kHvBlock == 32, "a task's out-neighbours are one per lane");
     const int64_t bA = xoff[a];
-    const int nblk = (dA + kHTile - 1) / kHTile;
-    for (int bi = 0; bi < nblk; ++bi) {
-        const int ni = min(kHTile, dA - bi * kHTile);
+    const int32_t dA = xout[a];
+    const bool whole = dA <= kHvIds;                   // A in one chunk: no range cuts
+    // lane j holds out-neighbour b = A[eb0 + j], the start and length of b's out-list
+    int32_t bj = 0, dbj = 0;
+    int64_t obj = 0;
+    if (eb0 + lane < dA) {
+        bj = xcol[bA + eb0 + lane];
+        obj = xoff[bj];
+        dbj = xout[bj];
+    }
+    const int32_t nb = min(kHvBlock, dA - eb0);
+    int qn = 0;                                        // queued triangles (warp-uniform)
+    for (int32_t k0 = 0; k0 < dA; k0 += kHvIds) {
+        const int32_t cnt = min(kHvIds, dA - k0);
         __syncwarp();
-        p3_stage_block(S, 0, xcol, bA + (int64_t)bi * kHTile, ni, xoff, xout, rec, lane);
-        for (int bj = bi; bj < nblk; ++bj) {
-            const bool diag = bj == bi;
-            const int nj = diag ? ni : min(kHTile, dA - bj * kHTile);
-            const int sj = diag ? 0 : kHTile;          // slot of block bj's first entry
-            __syncwarp();
-            if (!diag) p3_stage_block(S, kHTile, xcol, bA + (int64_t)bj * kHTile, nj, xoff, xout, rec, lane);
-            __syncwarp();
-            for (int q = lane; q < ni * nj; q += 32) {
-                const int i = q / nj, jj = q - i * nj;
-                if (diag && jj <= i) continue;
-                const int si = i, sjj = sj + jj;
-                const bool i_low = rank_less(S.bdx[si], S.nb[si], S.bdx[sjj], S.nb[sjj]);
-                const int slo = i_low ? si : sjj, shi = i_low ? sjj : si;
-                const int64_t pos = find_in_list(xcol, S.boff[slo], S.bdeg[slo], S.nb[shi]);
-                if (pos < 0) continue;
-                // entry indices in a's out-list
-                const int64_t ei = (int64_t)bi * kHTile + i, ej = (int64_t)bj * kHTile + jj;
-                const int64_t il = bA + (i_low ? ei : ej), ih = bA + (i_low ? ej : ei);
-                const int32_t lo = S.nb[slo], hi = S.nb[shi];
-                df Sla = R.get(il, lo, a), Sha = R.get(ih, hi, a), Shl = R.get(pos, hi, lo);
-                triangle_terms(a, lo, hi, xS[il], Sla, xS[ih], Sha, xS[pos], Shl, acc);
+        for (int32_t k = lane; k < cnt; k += 32) H.ids[k] = xcol[bA + k0 + k];
+        __syncwarp();
+        // the part of b's out-list within the chunk's id range
+        int32_t sj = 0, ej = dbj;
+        if (!whole && dbj > 0) {
+            sj = lower_pos(xcol + obj, dbj, H.ids[0]);
+            ej = lower_pos(xcol + obj, dbj, H.ids[cnt - 1] + 1);
+        }
+        for (int32_t j = 0; j < nb; ++j) {
+            const int32_t s = __shfl_sync(FULL, sj, j), e = __shfl_sync(FULL, ej, j);
+            if (s >= e) continue;
+            const int32_t b = __shfl_sync(FULL, bj, j);
+            const int64_t ob = __shfl_sync(FULL, obj, j);
+            for (int32_t j0 = s; j0 < e; j0 += 64) {
+                int32_t c[2], pos[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int32_t k = j0 + u * 32 + lane;
+                    c[u] = k < e ? xcol[ob + k] : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    pos[u] = -1;
+                    if (c[u] >= 0) {
+                        const int32_t p = lower_pos(H.ids, cnt, c[u]);
+                        if (p < cnt && H.ids[p] == c[u]) pos[u] = p;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const bool hit = pos[u] >= 0;
+                    const unsigned hm = __ballot_sync(FULL, hit);
+                    if (hit) {
+                        const int slot = qn + __popc(hm & lanemask_lt());
+                        H.qpc[slot] = ob + j0 + u * 32 + lane;
+                        H.qeb[slot] = eb0 + j;
+                        H.qec[slot] = k0 + pos[u];
+                        H.qb[slot] = b;
+                        H.qc[slot] = c[u];
+                    }
+                    qn += __popc(hm);
+                    if (qn >= 32) {                        // a full warp of triangles
+                        __syncwarp();
+                        hv_flush(H, 32, a, bA, xS, R, acc, lane);
+                        __syncwarp();
+                        if (lane < qn - 32) {
+                            H.qpc[lane] = H.qpc[32 + lane];
+                            H.qeb[lane] = H.qeb[32 + lane];
+                            H.qec[lane] = H.qec[32 + lane];
+                            H.qb[lane] = H.qb[32 + lane];
+                            H.qc[lane] = H.qc[32 + lane];
+                        }
+                        qn -= 32;
+                        __syncwarp();
+                    }
+                }
             }
         }
     }
+    __syncwarp();
+    hv_flush(H, qn, a, bA, xS, R, acc, lane);
     __syncwarp();
 }
 
@@ -1422,10 +1499,11 @@ __device__ __noinline__ void p3_node_tiled(P3Stage &S, int32_t a, int32_t dA, co
 // community's heaviest nodes together and one group of them would be a long tail for
 // its warp; otherwise lane j takes node 32 g + j and stride is unused.
 template <bool kScr>
-__global__ void __launch_bounds__(kThreads) p3_list_kernel(
+__global__ void __launch_bounds__(kThreads, 5) p3_list_kernel(
     int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
     Rev R, const int32_t *__restrict__ xout, const NodeRec *__restrict__ rec, unsigned long long *acc,
-    unsigned long long *next_group, int64_t stride) {
+    unsigned long long *next_group, int64_t stride, unsigned long long *hvl, int64_t hvcap,
+    unsigned long long *hv_count) {
     __shared__ P3Stage stage[kP3Warps];
     __shared__ int32_t s_anode[kScr ? kP3Warps * 32 : 1];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1554,14 +1632,44 @@ __global__ void __launch_bounds__(kThreads) p3_list_kernel(
             }
             start = end;
         }
-        unsigned big = __ballot_sync(FULL, da > kWinCap);
-        while (big) {
-            int l = __ffs(big) - 1;
-            big &= big - 1;
-            int32_t dA = __shfl_sync(FULL, da, l);
-            int32_t aL = kScr ? (int32_t)__shfl_sync(FULL, av, l) : (int32_t)(base + l);
-            p3_node_tiled(S, aL, dA, xoff, xcol, xS, R, xout, rec, acc, lane);
+        // heavy nodes' tasks go to the list (its capacity bounds their number, so the
+        // error branch is not taken)
+        if (da > kWinCap) {
+            const int32_t nt = (da + kHvBlock - 1) / kHvBlock;
+            const unsigned long long h = atomicAdd(hv_count, (unsigned long long)nt);
+            if (h + nt <= (unsigned long long)hvcap) {
+                for (int32_t i = 0; i < nt; ++i) hvl[h + i] = (unsigned long long)av << 32 | (unsigned)i;
+            } else {
+                atomicOr(R.err, 64);
+            }
         }
+    }
+}
+
+// the heavy-node tasks listed by p3_list_kernel, a warp per task, claimed with an atomic
+// counter
+__global__ void __launch_bounds__(kThreads) p3_heavy_kernel(
+    int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
+    Rev R, const int32_t *__restrict__ xout, unsigned long long *acc, const unsigned long long *__restrict__ hvl,
+    int64_t hvcap, const unsigned long long *hv_count, unsigned long long *hv_next) {
+    __shared__ P3Heavy heavy[kP3Warps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    P3Heavy &H = heavy[wid];
+    unsigned long long lim = *hv_count;
+    if (lim > (unsigned long long)hvcap) lim = (unsigned long long)hvcap;
+    if (lim == 0) return;
+    while (true) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(hv_next, 1ull);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= lim) break;
+        const unsigned long long w = hvl[t];
+        const int64_t a = (int64_t)(w >> 32), blk = (int64_t)(w & 0xffffffffull);
+        if (a >= n || xout[a] <= kWinCap || blk * kHvBlock >= xout[a]) {
+            if (lane == 0) atomicOr(R.err, 64);
+            continue;
+        }
+        p3_node_wedges(H, (int32_t)a, (int32_t)(blk * kHvBlock), xoff, xcol, xS, R, xout, acc, lane);
     }
 }
 
@@ -1755,7 +1863,7 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     RS_CUDA_TRY(cudaMemsetAsync(g->acc, 0, 2 * n * sizeof(unsigned long long), s));
     RS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
     // row counters and the G_x scan's ticket and tile words
-    RS_CUDA_TRY(cudaMemsetAsync(g->wq, 0, wq_words(n) * sizeof(unsigned long long), s));
+    RS_CUDA_TRY(cudaMemsetAsync(g->wq, 0, wq_hv_word(n) * sizeof(unsigned long long), s));
     if (g->n_hubs) {
         RS_CUDA_TRY(cudaMemsetAsync(g->hkey, 0xFF, g->hub_slots * sizeof(int32_t), s));
         RS_CUDA_TRY(cudaMemsetAsync(g->hcnt, 0, g->hub_slots * sizeof(uint32_t), s));
@@ -1892,13 +2000,20 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     }
     const Rev R{g->tune.p3_mirror ? g->xR : nullptr, g->xoff, g->xcol, g->xS, g->xin, err};
     unsigned long long *next_group = g->wq + 7;
+    unsigned long long *hvl = g->wq + wq_hv_word(n);
+    const int64_t hvcap = hv_cap(g->nnz);
     if (g->perm)                                     // a graph numbered by community: scrambled groups
         p3_list_kernel<true><<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, R, g->xout, g->rec,
-                                                                  g->acc, next_group, p3_stride(n));
+                                                                  g->acc, next_group, p3_stride(n), hvl, hvcap,
+                                                                  g->wq + kWqHvCount);
     else
         p3_list_kernel<false><<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, R, g->xout, g->rec,
-                                                                   g->acc, next_group, 1);
+                                                                   g->acc, next_group, 1, hvl, hvcap,
+                                                                   g->wq + kWqHvCount);
     RS_LAUNCHED(g, s, "p3_list");
+    p3_heavy_kernel<<<grid_for(hvcap * 32, NT, 4), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, R, g->xout, g->acc, hvl,
+                                                                hvcap, g->wq + kWqHvCount, g->wq + kWqHvNext);
+    RS_LAUNCHED(g, s, "p3_heavy");
     // ---- finalize
     if (g->gid) {
         graph_scale_kernel<<<(g->n_graphs + 255) / 256, 256, 0, s>>>(g->wmax_bits, g->n_graphs, g->winv);
