@@ -1396,15 +1396,42 @@ __device__ __forceinline__ int32_t lower_pos(const int32_t *p, int32_t cnt, int3
     return base + (p[base] < key ? 1 : 0);
 }
 
-// finish the first m (<= 32) queued triangles of heavy node a, one per lane
+__device__ __forceinline__ u128 shfl_up_u128(u128 v, int d) {
+    uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
+    lo = __shfl_up_sync(FULL, lo, d);
+    hi = __shfl_up_sync(FULL, hi, d);
+    return ((u128)hi << 64) | lo;
+}
+
+// finish the first m (<= 32) queued triangles of heavy node a, one per lane (all lanes
+// call).  The heavy triangles are many (a third of the wedges close on the 8M-node
+// graph), so the accumulator atomics are cut down: a's terms stay in the lane's acc_a
+// until the task ends, and b's terms are summed over the runs of equal b (the queue
+// holds the hits in walk order), one add per run; c's terms are added one by one.
 __device__ __forceinline__ void hv_flush(const P3Heavy &H, int m, int32_t a, int64_t bA, const df *xS,
-                                         const Rev &R, unsigned long long *acc, int lane) {
+                                         const Rev &R, unsigned long long *acc, int lane, u128 &acc_a) {
+    int32_t b = -1;
+    u128 tb = 0;
     if (lane < m) {
         const int64_t il = bA + H.qeb[lane], ih = bA + H.qec[lane], pc = H.qpc[lane];
-        const int32_t b = H.qb[lane], c = H.qc[lane];
+        b = H.qb[lane];
+        const int32_t c = H.qc[lane];
         df Sba = R.get(il, b, a), Sca = R.get(ih, c, a), Scb = R.get(pc, c, b);
-        triangle_terms(a, b, c, xS[il], Sba, xS[ih], Sca, xS[pc], Scb, acc);
+        const TriTerms t = triangle_term_values(xS[il], Sba, xS[ih], Sca, xS[pc], Scb);
+        acc_a += t.a;
+        tb = t.b;
+        atomic_add_u128(acc + 2 * (int64_t)c, t.c);
     }
+    // segmented inclusive sum of tb over the runs of equal b
+    const int32_t prev = __shfl_up_sync(FULL, b, 1);
+    const unsigned heads = __ballot_sync(FULL, lane == 0 || b != prev);
+    const int start = 31 - __clz(heads & (0xFFFFFFFFu >> (31 - lane)));
+    for (int d = 1; d < 32; d <<= 1) {
+        const u128 y = shfl_up_u128(tb, d);
+        if (lane - d >= start) tb += y;
+    }
+    const bool run_end = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (run_end && lane < m) atomic_add_u128(acc + 2 * (int64_t)b, tb);
 }
 
 // one task: heavy node a, its out-neighbours b at entries [eb0, eb0 + kHvBlock) of A
@@ -1425,6 +1452,7 @@ __device__ __forceinline__ void p3_node_wedges(P3Heavy &H, int32_t a, int32_t eb
     }
     const int32_t nb = min(kHvBlock, dA - eb0);
     int qn = 0;                                        // queued triangles (warp-uniform)
+    u128 acc_a = 0;                                    // a's terms of this lane's triangles
     for (int32_t k0 = 0; k0 < dA; k0 += kHvIds) {
         const int32_t cnt = min(kHvIds, dA - k0);
         __syncwarp();
@@ -1471,7 +1499,7 @@ __device__ __forceinline__ void p3_node_wedges(P3Heavy &H, int32_t a, int32_t eb
                     qn += __popc(hm);
                     if (qn >= 32) {                        // a full warp of triangles
                         __syncwarp();
-                        hv_flush(H, 32, a, bA, xS, R, acc, lane);
+                        hv_flush(H, 32, a, bA, xS, R, acc, lane, acc_a);
                         __syncwarp();
                         if (lane < qn - 32) {
                             H.qpc[lane] = H.qpc[32 + lane];
@@ -1488,8 +1516,10 @@ __device__ __forceinline__ void p3_node_wedges(P3Heavy &H, int32_t a, int32_t eb
         }
     }
     __syncwarp();
-    hv_flush(H, qn, a, bA, xS, R, acc, lane);
+    hv_flush(H, qn, a, bA, xS, R, acc, lane, acc_a);
     __syncwarp();
+    acc_a = warp_sum_u128(acc_a);
+    if (lane == 0 && acc_a) atomic_add_u128(acc + 2 * (int64_t)a, acc_a);
 }
 
 // groups of 32 nodes are handed out by an atomic counter (next_group, zeroed before
