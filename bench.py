@@ -192,7 +192,7 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# ---- algorithmic bytes (model stated in the design doc) ---------------------------------
+# ---- algorithmic bytes (the byte model of each kernel) -----------------------------
 
 def graph_stats(g, k_class=None):
     """Per row class (the library's default classes: small d <= 32, mid/large by

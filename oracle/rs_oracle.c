@@ -14,7 +14,7 @@
  *             (w_v(u) w_w(v) w_w(u))^(1/3)  with weights / w_max     (Eq. RSI)
  *   1(u,w,v)= [(u,w,v) is a triad] [C(v) != C(w)] [C(u) != C(w)]    (indicator)
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - log base 2 (the worked example of Sec. V-B gives H = 1 for counts {1,1}
  *     and w_max = 4.754 = 3 log2 3);
  *   - a triad (u,w,v) needs the real edges u-w and w-v and v != u; it is valid

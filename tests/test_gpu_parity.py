@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle.
 
-Scores within 1e-12 relative (the bound the BASELINE states for the fp64
-score); counts, removals and top-K ids bit-exact.
+Scores within 1e-12 relative (the bound set for the fp64 score); counts,
+removals and top-K ids bit-exact.
 """
 import numpy as np
 import pytest
