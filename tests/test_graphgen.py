@@ -94,3 +94,22 @@ def test_dcsbm_shape():
 def test_bad_arguments():
     with pytest.raises(ValueError):
         graphgen.dcsbm(10, 20, 1.0, 2.5, 2, 5, 0.2, seed=1)   # k > n
+
+
+def test_dense_core_structure():
+    """The dense core: a simple symmetric CSR, seeded; fan nodes joined only to core nodes
+    (and other fans), full nodes to every core node, subset sizes within their range."""
+    g = graphgen.dense_core()
+    check_simple_symmetric(g)
+    assert csr_digest(g) == csr_digest(graphgen.dense_core())
+    assert csr_digest(g) != csr_digest(graphgen.dense_core(seed=12))
+    n_core, n_fan = 600, 2500
+    assert g.n == n_core + n_fan + 6
+    deg = np.diff(g.offsets)
+    rows = np.repeat(np.arange(g.n), deg)
+    to_core = np.bincount(rows[g.cols < n_core], minlength=g.n)
+    fan = slice(n_core, n_core + n_fan)
+    assert to_core[fan].min() >= 40 and to_core[fan].max() <= 420
+    assert (to_core[n_core + n_fan:] == n_core).all()
+    # the full nodes touch nothing but the core
+    assert (deg[n_core + n_fan:] == n_core).all()
