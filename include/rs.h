@@ -394,9 +394,12 @@ void rs_server_free(rs_server *srv);
 /*
  * rs_device_errors -- synchronise `stream` and return in *flags_out the
  *   internal consistency checks that failed in g's kernels during the last
- *   rs_score (bit flags; 0 when none).  A non-zero value means a library bug
- *   (a hash table found full, a G_x slot not found), not bad input: inputs are
- *   checked before any kernel runs.
+ *   rs_score (bit flags; 0 when none).  A non-zero value means a library bug,
+ *   not bad input: inputs are checked before any kernel runs.  The bits:
+ *   1 a community hash table found full; 2, 4, 8 a community missing from a
+ *   row's table in P2; 16 the reverse value of a G_x edge not found (P3);
+ *   32 the G_x offset scan gave up waiting for a tile; 64 P3's heavy-node task
+ *   list over its capacity or holding an invalid entry.
  */
 rs_status rs_device_errors(rs_graph *g, int32_t *flags_out, void *stream);
 
