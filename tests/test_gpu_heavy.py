@@ -61,3 +61,16 @@ def test_heavy_nodes_in_a_batch(rs, core):
     a, z = int(b.graph_node_offsets[1]), int(b.graph_node_offsets[2])
     _close(s[a:z], ref)
     G.close()
+
+
+@pytest.mark.parametrize("strict,alg2", [(True, False), (False, True)])
+def test_heavy_nodes_under_the_other_readings(rs, strict, alg2):
+    """The strict triad reading and the Alg. 2 weights change P1 and P2; P3's heavy walk
+    takes the weights they give, and the result is still the definition's."""
+    g = graphgen.dense_core()
+    G = rs.Graph.from_generated(g, strict=strict, alg2=alg2)
+    got = G.score().cpu().numpy()
+    assert G.device_errors() == 0
+    ref = oracle.Oracle.from_graph(g, alg2=alg2).scores(strict=strict)
+    _close(got, ref)
+    G.close()
