@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_LIB_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -59,10 +59,17 @@ def _load():
         lib.rso_topk.argtypes = [P, I64, I64, P]
         lib.rso_triad_term.restype = D; lib.rso_triad_term.argtypes = [D, D, D]
         lib.rso_finish.restype = D; lib.rso_finish.argtypes = [D, I64, D]
+        lib.rso_set_threads.restype = ctypes.c_int; lib.rso_set_threads.argtypes = [ctypes.c_int]
         lib.rso_remove.restype = I64
         lib.rso_remove.argtypes = [I64, P, P, P, P, I64, P, P, I64, P, P]
         _lib = lib
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Host threads for the loops over nodes (0: all cores).  Results are bit-identical
+    for any count: every node is computed by one thread in a fixed order."""
+    return int(_load().rso_set_threads(int(n)))
 
 
 def _c(a, dtype):

@@ -33,12 +33,20 @@
  * Numerics: every entropy term is positive and evaluated as
  * (f/Y) log2(Y/f), with log1p((Y-f)/f)/ln 2 when 2f > Y (no cancellation);
  * sums use Neumaier compensation.  Relative error is a few ulps.
+ *
+ * Threads (OpenMP, rso_set_threads): nodes are shared out over threads, and
+ * each node's table, weights and score sum are computed by one thread in the
+ * same order as with one thread, so results are bit-identical for any thread
+ * count; w_max is a max, which does not depend on the order either.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
     int64_t n;
@@ -136,6 +144,14 @@ static int cmp_i32(const void *a, const void *b) {
     return (x > y) - (x < y);
 }
 
+/* the counts of row v's neighbour labels, sorted: buf[0, d) */
+static int64_t sorted_labels(const rso_graph *g, int64_t v, int32_t *buf) {
+    int64_t d = g->off[v + 1] - g->off[v];
+    for (int64_t i = 0; i < d; ++i) buf[i] = g->lab[g->col[g->off[v] + i]];
+    qsort(buf, (size_t)d, sizeof(int32_t), cmp_i32);
+    return d;
+}
+
 static int build_tables(rso_graph *g) {
     int64_t n = g->n;
     int64_t dmax = 0;
@@ -143,60 +159,73 @@ static int build_tables(rso_graph *g) {
         int64_t d = g->off[v + 1] - g->off[v];
         if (d > dmax) dmax = d;
     }
-    int32_t *buf = (int32_t *)malloc((size_t)(dmax + 1) * sizeof(int32_t));
-    int32_t *cs = (int32_t *)malloc((size_t)(dmax + 1) * sizeof(int32_t));
-    int32_t *dist = (int32_t *)malloc((size_t)(dmax + 1) * sizeof(int32_t));
-    double *dw = (double *)malloc((size_t)(dmax + 1) * sizeof(double));
     g->tptr = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
     g->wabs = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
-    if (!buf || !cs || !dist || !dw || !g->tptr || !g->wabs) return -1;
-    /* pass 1: table sizes */
+    if (!g->tptr || !g->wabs) return -1;
+    int fail = 0;
+    /* pass 1: table sizes (row v's distinct labels into tptr[v + 1]) */
     g->tptr[0] = 0;
-    for (int64_t v = 0; v < n; ++v) {
-        int64_t d = g->off[v + 1] - g->off[v];
-        for (int64_t i = 0; i < d; ++i) buf[i] = g->lab[g->col[g->off[v] + i]];
-        qsort(buf, (size_t)d, sizeof(int32_t), cmp_i32);
-        int64_t t = 0;
-        for (int64_t i = 0; i < d; ++i) if (i == 0 || buf[i] != buf[i - 1]) t++;
-        g->tptr[v + 1] = g->tptr[v] + t;
+#pragma omp parallel reduction(|:fail)
+    {
+        int32_t *buf = (int32_t *)malloc((size_t)(dmax + 1) * sizeof(int32_t));
+        if (!buf) fail = 1;
+#pragma omp for schedule(dynamic, 1024)
+        for (int64_t v = 0; v < n; ++v) {
+            if (!buf) continue;
+            int64_t d = sorted_labels(g, v, buf), t = 0;
+            for (int64_t i = 0; i < d; ++i) if (i == 0 || buf[i] != buf[i - 1]) t++;
+            g->tptr[v + 1] = t;
+        }
+        free(buf);
     }
+    if (fail) return -1;
+    for (int64_t v = 0; v < n; ++v) g->tptr[v + 1] += g->tptr[v];
     int64_t T = g->tptr[n];
     g->tcomm = (int32_t *)malloc((size_t)(T > 0 ? T : 1) * sizeof(int32_t));
     g->tcnt = (int32_t *)malloc((size_t)(T > 0 ? T : 1) * sizeof(int32_t));
     g->tw = (double *)malloc((size_t)(T > 0 ? T : 1) * sizeof(double));
     if (!g->tcomm || !g->tcnt || !g->tw) return -1;
     /* pass 2: counts f_v(c), then weights */
-    g->wmax = 0.0;
-    for (int64_t v = 0; v < n; ++v) {
-        int64_t d = g->off[v + 1] - g->off[v];
-        for (int64_t i = 0; i < d; ++i) buf[i] = g->lab[g->col[g->off[v] + i]];
-        qsort(buf, (size_t)d, sizeof(int32_t), cmp_i32);
-        int64_t p = g->tptr[v];
-        for (int64_t i = 0; i < d; ++i) {
-            if (i == 0 || buf[i] != buf[i - 1]) { g->tcomm[p] = buf[i]; g->tcnt[p] = 0; p++; }
-            g->tcnt[p - 1]++;
+    double wmax = 0.0;
+#pragma omp parallel reduction(|:fail) reduction(max:wmax)
+    {
+        int32_t *buf = (int32_t *)malloc((size_t)(dmax + 1) * sizeof(int32_t));
+        int32_t *cs = (int32_t *)malloc((size_t)(dmax + 1) * sizeof(int32_t));
+        int32_t *dist = (int32_t *)malloc((size_t)(dmax + 1) * sizeof(int32_t));
+        double *dw = (double *)malloc((size_t)(dmax + 1) * sizeof(double));
+        if (!buf || !cs || !dist || !dw) fail = 1;
+#pragma omp for schedule(dynamic, 1024)
+        for (int64_t v = 0; v < n; ++v) {
+            if (!buf || !cs || !dist || !dw) continue;
+            int64_t d = sorted_labels(g, v, buf);
+            int64_t p = g->tptr[v];
+            for (int64_t i = 0; i < d; ++i) {
+                if (i == 0 || buf[i] != buf[i - 1]) { g->tcomm[p] = buf[i]; g->tcnt[p] = 0; p++; }
+                g->tcnt[p - 1]++;
+            }
+            int m = (int)(g->tptr[v + 1] - g->tptr[v]);
+            for (int i = 0; i < m; ++i) cs[i] = g->tcnt[g->tptr[v] + i];
+            qsort(cs, (size_t)m, sizeof(int32_t), cmp_i32);
+            /* w_v(c) depends on c only through f_v(c): the multiset left after
+               removing one copy of f_v(c) is the same for equal counts */
+            int nd = 0;
+            for (int i = 0; i < m; ++i)
+                if (i == 0 || cs[i] != cs[i - 1]) { dist[nd] = cs[i]; dw[nd] = weight_of_counts(cs, m, cs[i], g->alg2); nd++; }
+            for (int i = 0; i < m; ++i) {
+                int32_t f = g->tcnt[g->tptr[v] + i];
+                int lo = 0, hi = nd - 1;
+                while (lo < hi) { int mid = (lo + hi) / 2; if (dist[mid] < f) lo = mid + 1; else hi = mid; }
+                double w = dw[lo];
+                g->tw[g->tptr[v] + i] = w;
+                if (w > wmax) wmax = w;
+            }
+            g->wabs[v] = weight_of_counts(cs, m, -1, g->alg2);
+            if (m < g->k && g->wabs[v] > wmax) wmax = g->wabs[v];
         }
-        int m = (int)(g->tptr[v + 1] - g->tptr[v]);
-        for (int i = 0; i < m; ++i) cs[i] = g->tcnt[g->tptr[v] + i];
-        qsort(cs, (size_t)m, sizeof(int32_t), cmp_i32);
-        /* w_v(c) depends on c only through f_v(c): the multiset left after
-           removing one copy of f_v(c) is the same for equal counts */
-        int nd = 0;
-        for (int i = 0; i < m; ++i)
-            if (i == 0 || cs[i] != cs[i - 1]) { dist[nd] = cs[i]; dw[nd] = weight_of_counts(cs, m, cs[i], g->alg2); nd++; }
-        for (int i = 0; i < m; ++i) {
-            int32_t f = g->tcnt[g->tptr[v] + i];
-            int lo = 0, hi = nd - 1;
-            while (lo < hi) { int mid = (lo + hi) / 2; if (dist[mid] < f) lo = mid + 1; else hi = mid; }
-            double w = dw[lo];
-            g->tw[g->tptr[v] + i] = w;
-            if (w > g->wmax) g->wmax = w;
-        }
-        g->wabs[v] = weight_of_counts(cs, m, -1, g->alg2);
-        if (m < g->k && g->wabs[v] > g->wmax) g->wmax = g->wabs[v];
+        free(buf); free(cs); free(dist); free(dw);
     }
-    free(buf); free(cs); free(dist); free(dw);
-    return 0;
+    g->wmax = wmax;
+    return fail ? -1 : 0;
 }
 
 /* w_v(c) for any community c */
@@ -292,6 +321,7 @@ double rso_omega(const rso_graph *g, int32_t v, int32_t c) { return omega(g, v, 
 
 /* R(u) for the listed nodes; strict != 0 drops closed triangles with C(v) = C(u) */
 void rso_scores(const rso_graph *g, const int32_t *ids, int64_t m, int strict, double *out) {
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < m; ++i) {
         int32_t u = ids[i];
         int64_t d = g->off[u + 1] - g->off[u];
@@ -301,10 +331,23 @@ void rso_scores(const rso_graph *g, const int32_t *ids, int64_t m, int strict, d
 }
 
 void rso_scores_all(const rso_graph *g, int strict, double *out) {
+#pragma omp parallel for schedule(dynamic, 64)
     for (int64_t u = 0; u < g->n; ++u) {
-        int32_t id = (int32_t)u;
-        rso_scores(g, &id, 1, strict, out + u);
+        int64_t d = g->off[u + 1] - g->off[u];
+        out[u] = (d < 2 || g->wmax <= 0.0) ? 0.0 : rso_finish(score_sum(g, (int32_t)u, strict), d, g->wmax);
     }
+}
+
+/* threads used by the loops over nodes (n < 1: all the host's cores); returns the count set */
+int rso_set_threads(int n) {
+#ifdef _OPENMP
+    if (n < 1) n = omp_get_num_procs();
+    omp_set_num_threads(n);
+    return n;
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* ---- top-K: order by (score descending, node id ascending) --------------- */
