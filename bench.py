@@ -66,6 +66,8 @@ def workload(name):
         return graphgen.dcsbm_8m()
     if name == "sbm-2k":
         return graphgen.sbm_2000()
+    if name.startswith("dcsbm-hub-"):
+        return graphgen.dcsbm_hub(int(name.split("-")[-1]))
     if name.startswith("dcsbm-small-"):
         return graphgen.dcsbm_small(int(name.split("-")[-1]), seed=7)
     raise SystemExit("unknown workload " + name)

@@ -129,6 +129,14 @@ def dcsbm_8m(seed: int = 3) -> Graph:
     return dcsbm(8_000_000, 50_000, 1.0, 2.1, 5, 100_000, 0.1, seed, name="dcsbm-8m-k50000")
 
 
+def dcsbm_hub(n: int, seed: int = 13) -> Graph:
+    """The 8M workload's shape scaled to n nodes: k = n / 160 communities (sizes ~1/r),
+    degrees power law 2.1 on [5, 100000], mu 0.1.  At n = 2M it has ~23.6M edges and
+    ~8,700 nodes with more than 128 G_x out-neighbours: the heavy-node triangle walk at
+    about a tenth of the 8M graph's."""
+    return dcsbm(n, max(2, n // 160), 1.0, 2.1, 5, 100_000, 0.1, seed, name="dcsbm-hub-%d" % n)
+
+
 def dcsbm_small(n: int, seed: int, dmax: int = 1000, mu: float = 0.2, gamma: float = 2.5,
                 dmin: int = 7) -> Graph:
     """Scaled DC-SBM with the 1M workload's shape: k = n / 100 communities (min size 50)."""
