@@ -1,14 +1,25 @@
-"""Parity on the large hub-skewed workload (8M nodes, ~1e8 edges, 50,000
-communities, degrees up to 1e5): the hub path with its multi-CTA merge,
-w_max, the whole interaction table, sampled scores and top-K properties."""
+"""Parity on the large hub-skewed workload (8M nodes, 100.8M edges, 50,000
+communities, degrees up to 54,097), in the launch configuration bench.py times:
+w_max and the whole interaction table bit for bit; the scores of the 20 largest
+hubs (the multi-CTA hub path), of 100,000 seeded random nodes and of the GPU's
+2,000 best nodes against the oracle; the top-1000 list against the oracle's
+ranking of those 2,000 candidates.
+
+The literal oracle needs ~3.4e11 inner steps for all 8M nodes, too many for a
+test, so the top-K check ranks candidates: the GPU's 2,000 best nodes.  That
+no node outside them belongs in the oracle's top 1000 is checked on the
+100,000-node sample and the hubs (each scores below the oracle's 1000th)."""
 import numpy as np
 import pytest
 
 import graphgen
 import oracle
+from tests.parity import RTOL, assert_scores, assert_topk, rank_order
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+K, CAND, SAMPLE, HUBS = 1000, 2000, 100_000, 20
 
 
 @pytest.fixture(scope="module")
@@ -19,9 +30,13 @@ def setup():
     g = graphgen.dcsbm_8m()
     G = rsgpu.Graph.from_generated(g, validate=False)
     s, wmax = G.score(want_omega_max=True)
-    ids, vals = G.topk(s, 1000)
+    ids, vals = G.topk(s, CAND)
+    ids_k, _ = G.topk(s, K)                          # the list length bench.py asks for
+    assert (ids_k.cpu().numpy() == ids[:K].cpu().numpy()).all()
+    oracle.set_threads(0)
     o = oracle.Oracle.from_graph(g, validate=False)
-    return g, G, s.cpu().numpy(), wmax, ids.cpu().numpy(), vals.cpu().numpy(), o
+    yield g, G, s.cpu().numpy(), wmax, ids.cpu().numpy(), vals.cpu().numpy(), o
+    G.close()
 
 
 def test_wmax_8m(setup):
@@ -38,22 +53,32 @@ def test_interaction_table_8m(setup):
     np.testing.assert_array_equal(cnt.cpu().numpy(), ocnt)
 
 
+def test_largest_hubs_8m(setup):
+    g, G, s, wmax, ids, vals, o = setup
+    deg = np.diff(g.offsets)
+    hubs = np.argsort(-deg, kind="stable")[:HUBS].astype(np.int32)
+    assert deg[hubs].min() > 40_000                  # the hub path: tables far above one CTA's
+    assert_scores(s[hubs], o.scores(hubs), RTOL)
+
+
 def test_sampled_scores_8m(setup):
     g, G, s, wmax, ids, vals, o = setup
-    rng = np.random.default_rng(88)
-    deg = np.diff(g.offsets)
-    order = np.argsort(-deg)
-    hubs = order[(deg[order] > 2048) & (deg[order] < 6000)][:3]     # hub path, bounded oracle cost
-    sample = np.concatenate([rng.integers(0, g.n, size=200), ids[:10], hubs,
-                             np.flatnonzero((deg > 256) & (deg <= 2048))[:10]]).astype(np.int32)
+    sample = np.unique(np.random.default_rng(88).integers(0, g.n, size=SAMPLE)).astype(np.int32)
     ref = o.scores(sample)
-    got = s[sample]
-    assert ((ref == 0) == (got == 0)).all()
-    nz = ref != 0
-    assert (np.abs(got[nz] - ref[nz]) / ref[nz]).max() <= 1e-12
+    assert_scores(s[sample], ref, RTOL)
+    # no sampled node outside the GPU's top K belongs above the oracle's K-th score
+    top = o.scores(ids[:K].astype(np.int32))
+    kth = rank_order(ids[:K], top)[-1]
+    kth_score = top[list(ids[:K]).index(kth)]
+    outside = ~np.isin(sample, ids[:K])
+    assert (ref[outside] <= kth_score * (1 + RTOL)).all()
 
 
-def test_topk_properties_8m(setup):
+def test_topk_against_oracle_8m(setup):
     g, G, s, wmax, ids, vals, o = setup
     np.testing.assert_array_equal(vals, s[ids])
-    np.testing.assert_array_equal(ids, oracle.topk(s, 1000))
+    cand = ids.astype(np.int32)
+    ref = o.scores(cand)
+    assert_scores(s[cand], ref, RTOL)
+    groups, differ = assert_topk(ids[:K], cand, ref, K, RTOL)
+    print("top-%d: %d near-tie groups, %d positions differ inside them" % (K, groups, differ))

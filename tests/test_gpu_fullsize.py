@@ -1,37 +1,44 @@
-"""Parity at the full benchmark size (1M nodes, 10.3M edges, k = 1000), in the
-launch configuration bench.py times: w_max, the whole interaction table,
-sampled scores against the oracle computed node by node, and top-K
-properties that hold at any size."""
+"""Parity at the full size of the 1M-node workload (10.3M edges, k = 1000), in
+the launch configuration bench.py times, element by element: w_max, the whole
+interaction table, all 1,000,000 scores against the oracle's (all host cores),
+and the top-1000 list against the oracle's ranking.  The same checks run on the
+literal degree law of that workload (minimum degree 2, 2.3M edges)."""
 import numpy as np
 import pytest
 
 import graphgen
 import oracle
+from tests.parity import RTOL, assert_scores, assert_topk
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+K = 1000
 
-@pytest.fixture(scope="module")
-def setup():
+
+@pytest.fixture(scope="module", params=["dcsbm_1m", "dcsbm_1m_dmin2"])
+def setup(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_2508_01485_gb300 as rsgpu
-    g = graphgen.dcsbm_1m()
+    g = getattr(graphgen, request.param)()
     G = rsgpu.Graph.from_generated(g)
     s, wmax = G.score(want_omega_max=True)
-    ids, vals = G.topk(s, 1000)
+    ids, vals = G.topk(s, K)
+    oracle.set_threads(0)
     o = oracle.Oracle.from_graph(g, validate=False)
-    return g, G, s.cpu().numpy(), wmax, ids.cpu().numpy(), vals.cpu().numpy(), o
+    ref = o.scores()
+    yield g, G, s.cpu().numpy(), wmax, ids.cpu().numpy(), vals.cpu().numpy(), o, ref
+    G.close()
 
 
 def test_wmax_full(setup):
-    g, G, s, wmax, ids, vals, o = setup
+    g, G, s, wmax, ids, vals, o, ref = setup
     assert abs(wmax - o.wmax) <= 1e-13 * o.wmax
 
 
 def test_interaction_table_full(setup):
-    g, G, s, wmax, ids, vals, o = setup
+    g, G, s, wmax, ids, vals, o, ref = setup
     rp, comm, cnt = G.interaction()
     ptr, ocomm, ocnt = o.table()
     np.testing.assert_array_equal(rp.cpu().numpy(), ptr)
@@ -39,34 +46,15 @@ def test_interaction_table_full(setup):
     np.testing.assert_array_equal(cnt.cpu().numpy(), ocnt)
 
 
-def test_sampled_scores_full(setup):
-    g, G, s, wmax, ids, vals, o = setup
-    rng = np.random.default_rng(2024)
-    deg = np.diff(g.offsets)
-    sample = np.concatenate([
-        rng.integers(0, g.n, size=300),                 # random nodes
-        ids[:20],                                       # the top of the ranking
-        np.argsort(-deg)[:5],                           # the largest hubs
-        np.flatnonzero((deg > 32) & (deg <= 256))[:20], # mid rows
-    ]).astype(np.int32)
-    ref = o.scores(sample)
-    got = s[sample]
-    assert ((ref == 0) == (got == 0)).all()
-    nz = ref != 0
-    assert (np.abs(got[nz] - ref[nz]) / ref[nz]).max() <= 1e-12
+def test_all_scores_full(setup):
+    g, G, s, wmax, ids, vals, o, ref = setup
+    assert (ref > 0).sum() > g.n // 20         # a sizeable share of non-zero scores
+    assert_scores(s, ref, RTOL)
 
 
-def test_topk_properties_full(setup):
-    g, G, s, wmax, ids, vals, o = setup
-    # the returned scores are the scores of the returned ids, in (score desc, id asc) order
+def test_topk_against_oracle_full(setup):
+    g, G, s, wmax, ids, vals, o, ref = setup
+    # the returned scores are the scores of the returned ids
     np.testing.assert_array_equal(vals, s[ids])
-    key = list(zip(-vals, ids))
-    assert key == sorted(key)
-    # nothing outside the list beats the K-th entry
-    rest = np.ones(g.n, bool); rest[ids] = False
-    kth = (vals[-1], ids[-1])
-    out = np.flatnonzero(rest)
-    better = (s[out] > kth[0]) | ((s[out] == kth[0]) & (out < kth[1]))
-    assert not better.any()
-    # the same list as ranking the GPU scores on the host
-    np.testing.assert_array_equal(ids, oracle.topk(s, 1000))
+    groups, differ = assert_topk(ids, np.arange(g.n), ref, K, RTOL)
+    print("top-%d: %d near-tie groups, %d positions differ inside them" % (K, groups, differ))
