@@ -124,11 +124,17 @@ __device__ __forceinline__ u128 strict_rest(const Strict &SX, const int64_t *off
 // S(x -> y) = w_x(C(y))^(1/3): at apex a the ordered pairs (w, v) = (b, c) and
 // (c, b) give S(c->a) S(b->c) S(b->a) + S(b->a) S(c->b) S(c->a)
 struct TriTerms { u128 a, b, c; };
-__device__ __forceinline__ TriTerms triangle_term_values(df Sab, df Sba, df Sac, df Sca, df Sbc, df Scb) {
+// the same with the pair sums Pac = S(a->c) + S(c->a) and Pab = S(a->b) + S(b->a)
+// given (df_add(Sac, Sca) and df_add(Sab, Sba)): the same operations, so the same bits
+__device__ __forceinline__ TriTerms triangle_term_values_p(df Sab, df Sba, df Sac, df Sca, df Sbc, df Scb, df Pac,
+                                                           df Pab) {
     df ta = df_mul(df_mul(Sba, Sca), df_add(Sbc, Scb));
-    df tb = df_mul(df_mul(Sab, Scb), df_add(Sac, Sca));
-    df tc = df_mul(df_mul(Sac, Sbc), df_add(Sab, Sba));
+    df tb = df_mul(df_mul(Sab, Scb), Pac);
+    df tc = df_mul(df_mul(Sac, Sbc), Pab);
     return TriTerms{df_to_fixed(ta, kAccFrac), df_to_fixed(tb, kAccFrac), df_to_fixed(tc, kAccFrac)};
+}
+__device__ __forceinline__ TriTerms triangle_term_values(df Sab, df Sba, df Sac, df Sca, df Sbc, df Scb) {
+    return triangle_term_values_p(Sab, Sba, Sac, Sca, Sbc, Scb, df_add(Sac, Sca), df_add(Sab, Sba));
 }
 __device__ __forceinline__ void add_triangle(unsigned long long *acc, int32_t a, int32_t b, int32_t c,
                                              const TriTerms &t, bool neg = false) {

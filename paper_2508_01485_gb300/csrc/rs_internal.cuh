@@ -183,6 +183,10 @@ struct rs_graph {
     bool strict = false;                      // RS_TRIAD_STRICT: no closed triad with C(v) = C(u)
     unsigned long long *sx = nullptr;         // strict: X(w, u) per CSR entry (2 words), else null
     uint64_t scored_version = ~0ull;          // version of the last rs_score (Lall and the scores are current)
+    // bounded waits of the G_x offset scan: reads of a tile's word before giving up, and
+    // a tile kept from publishing (-1: none; set only by rs_test_gx_stall)
+    long gx_spin = 1l << 24;
+    int64_t gx_withhold = -1;
 };
 
 namespace rs {
@@ -191,12 +195,12 @@ constexpr int kThreads = 256;
 constexpr int kMirTile = 2048;               // G_x slots per tile of the mirror pass
 constexpr int kGxTile = 4096;                // nodes per tile of the G_x offset scan
 // P3: a node with more than kWinCap G_x out-neighbours is heavy, and its walk is cut into
-// tasks of kHvBlock out-neighbours.  Every G_x edge has one tail, so the heavy nodes
-// number at most m_x / (kWinCap + 1), and their tasks at most
-// sum (d+ + kHvBlock - 1) / kHvBlock <= m_x (1 + 31 / 129) / 32 < nnz / 51 (m_x <= nnz / 2).
-constexpr int kWinCap = 128, kHvBlock = 32;
-static_assert(kWinCap == 128 && kHvBlock == 32, "hv_cap's bound is worked out for these values");
-inline int64_t hv_cap(int64_t nnz) { return nnz / 51 + 1; }
+// tasks of kHvBlock out-neighbours.  Every G_x edge has one tail, and a heavy node has
+// d+ >= 129 out-neighbours, so its (d+ + 127) / 128 tasks are at most d+ 256 / (128 129),
+// and all tasks together at most 2 m_x / 129 <= nnz / 129 (m_x <= nnz / 2).
+constexpr int kWinCap = 128, kHvBlock = 128;
+static_assert(kWinCap == 128 && kHvBlock == 128, "hv_cap's bound is worked out for these values");
+inline int64_t hv_cap(int64_t nnz) { return nnz / 129 + 1; }
 // words of rs_graph::wq: 0..7 the row and group counters of the row kernels, 8 the
 // ticket of the G_x offset scan, 9 and 10 the append and claim counters of P3's
 // heavy-node task list, 16.. the scan's tile words (all these zeroed before every

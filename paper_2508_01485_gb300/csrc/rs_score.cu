@@ -546,19 +546,22 @@ __global__ void __launch_bounds__(NT) hub_p1_finish_kernel(
 // prefix as soon as the tiles before it have, and its first warp sums the published
 // words of its predecessors back to the nearest inclusive one, 32 tiles per step.  A predecessor has
 // always started (its ticket is smaller), so every wait ends; the wait is bounded
-// all the same, and flags err if the bound is ever reached.
+// all the same (spin_limit reads of a word).  If the bound is ever reached, the tile
+// flags err (bit 32, reported by rs_score as RS_ETIMEOUT) and takes its prefix from a
+// direct sum of the capacities of every node before it instead, so the offsets stay
+// exact.  withhold_tile >= 0 (a test hook, -1 otherwise) keeps that tile from
+// publishing its words, so that the waits of the tiles after it run out.
 // ======================================================================================
 constexpr int kGxThreads = 256;
 constexpr int kGxPer = kGxTile / kGxThreads;
 constexpr unsigned long long kGxAgg = 1ull << 62, kGxIncl = 2ull << 62, kGxMask = (1ull << 62) - 1;
-constexpr long kGxSpin = 1l << 24;
 
 // status: one word per tile (flag in the top two bits), zeroed before the launch;
 // ticket: zeroed before the launch.  Warp w of a tile scans its kGxPer runs of 32
 // consecutive nodes (coalesced loads and stores), carrying its running total.
 __global__ void __launch_bounds__(kGxThreads) gx_offsets_kernel(
     const NodeRec *__restrict__ rec, int64_t n, int64_t *__restrict__ xoff, unsigned long long *status,
-    unsigned long long *ticket, int *err) {
+    unsigned long long *ticket, int *err, long spin_limit, int64_t withhold_tile) {
     __shared__ int64_t warp_tot[kGxThreads / 32];
     __shared__ unsigned long long sh_tile;
     __shared__ int64_t sh_prefix;
@@ -598,12 +601,14 @@ __global__ void __launch_bounds__(kGxThreads) gx_offsets_kernel(
         const int64_t total = __shfl_sync(FULL, x, 31);
         if (lane < kGxThreads / 32) warp_tot[lane] = x - c;
         int64_t excl = 0;
+        const bool publish = t != withhold_tile;
         if (t == 0) {
-            if (lane == 0) *(volatile unsigned long long *)&status[0] = kGxIncl | (unsigned long long)total;
+            if (lane == 0 && publish) *(volatile unsigned long long *)&status[0] = kGxIncl | (unsigned long long)total;
         } else {
-            if (lane == 0) *(volatile unsigned long long *)&status[t] = kGxAgg | (unsigned long long)total;
+            if (lane == 0 && publish) *(volatile unsigned long long *)&status[t] = kGxAgg | (unsigned long long)total;
             // look back 32 tiles at a time: lane l reads tile hi - l; the nearest
             // inclusive word ends the walk, the aggregates after it are added
+            bool gave_up = false;
             for (int64_t hi = t - 1;; hi -= 32) {
                 const int64_t j = hi - lane;
                 unsigned long long w = kGxIncl;          // before tile 0: an inclusive zero
@@ -611,8 +616,11 @@ __global__ void __launch_bounds__(kGxThreads) gx_offsets_kernel(
                     long spins = 0;
                     do {
                         w = *(volatile unsigned long long *)&status[j];
-                    } while (!(w >> 62) && ++spins < kGxSpin);
-                    if (!(w >> 62)) { atomicOr(err, 32); w = kGxIncl; }
+                    } while (!(w >> 62) && ++spins < spin_limit);
+                }
+                if (__any_sync(FULL, !(w >> 62))) {     // a wait ran out
+                    gave_up = true;
+                    break;
                 }
                 const unsigned inc = __ballot_sync(FULL, (w >> 62) == 2);
                 const int stop = inc ? __ffs(inc) - 1 : 31;
@@ -621,7 +629,19 @@ __global__ void __launch_bounds__(kGxThreads) gx_offsets_kernel(
                 excl += add;
                 if (inc) break;
             }
-            if (lane == 0) *(volatile unsigned long long *)&status[t] = kGxIncl | (unsigned long long)(excl + total);
+            if (gave_up) {
+                // the exact prefix from the node records themselves
+                if (lane == 0) atomicOr(err, 32);
+                int64_t sum = 0;
+                for (int64_t v = lane; v < t * kGxTile; v += 32) {
+                    const int32_t dx = rec[v].dx;
+                    sum += dx >= 2 ? dx : 0;
+                }
+                for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+                excl = sum;
+            }
+            if (lane == 0 && publish)
+                *(volatile unsigned long long *)&status[t] = kGxIncl | (unsigned long long)(excl + total);
         }
         if (lane == 0) sh_prefix = excl;
     }
@@ -1309,7 +1329,7 @@ __device__ __forceinline__ void triangle_terms(int32_t a, int32_t b, int32_t c, 
 // sit at the out-slots, the three reverse ones in xR (the mirror pass) or, with
 // p3_mirror = 0, in the in-lists of the two higher-ranked nodes, and the terms
 // of the three apexes are added.  Nodes with more than kWinCap out-neighbours
-// (heavy nodes) are walked by wedges instead (p3_node_wedges).
+// (heavy nodes) are walked by wedges instead (p3_heavy_kernel).
 constexpr int kP3Warps = kThreads / 32;
 
 struct P3Stage {
@@ -1358,30 +1378,46 @@ __device__ __forceinline__ int64_t find_in_list(const int32_t *xcol, int64_t lo,
     return (l < len && xcol[lo + l] == key) ? lo + l : -1;
 }
 
-// Heavy nodes: a wedge walk.  Node a's out-list A (sorted by id) is staged in shared
-// memory, kHvIds ids at a time.  For every b in A the warp streams b's out-list (the
-// nodes c ranked above b), and c closes the triangle {a, b, c} iff c is in A: a binary
-// search in the staged ids.  Every triangle whose lowest-ranked node is heavy is met
-// once, at its middle-ranked node b.  When A takes several chunks, b's out-list is first
-// cut to the chunk's id range.  There are several times more wedges than pairs on such
-// nodes, but a wedge costs a coalesced load and a shared-memory search where a pair
+// Heavy nodes: a wedge walk, one CTA per task.  A task is a heavy node a with a block
+// of kHvBlock of its out-neighbours b.  The CTA stages a's out-list A (sorted by id),
+// kHvIds ids at a time, as a shared-memory hash table (id -> position in the chunk, at
+// most half full) beside the values S(a->c), S(c->a) and their sum for every c of the
+// chunk.  Its warps then take the task's out-neighbours b one at a time: a warp
+// streams b's out-list (the nodes c ranked above b), coalesced, and looks every c up in
+// the table; a hit closes the triangle {a, b, c}, which is met once, at its
+// middle-ranked node b.  When A takes several chunks, b's out-list is first cut to the
+// chunk's id range.  There are several times more wedges than pairs on such nodes, but
+// a wedge costs a coalesced load and a probe or two in shared memory where a pair
 // costs a binary search in global memory.
 //
-// The warp whose group holds a heavy node does not walk it: it appends the node's tasks,
-// one per block of kHvBlock out-neighbours b, to the task list (slots taken with an
-// atomic counter), and p3_heavy_kernel, launched next on the same stream, runs the
-// tasks, a warp per task, so that the heaviest node is spread over many warps.  The walk
-// has its own kernel so that its registers do not lower the occupancy of the group
-// kernel.
-constexpr int kHvIds = 512;
-constexpr int kHvQ = 64;
+// A third of the heavy wedges close on the 8M-node graph, so finishing the triangles
+// dominates, and its atomics are cut down: hits are queued and finished a warp at a
+// time (one triangle per lane); a's terms are summed in registers over the task, b's
+// over the warp's walk of b (every queued triangle has the same b), and c's in a
+// 128-bit sum per staged position in shared memory, added to the accumulators once per
+// chunk.  The integer sums are exact, so the bits do not depend on how they are split.
+//
+// The warp whose group holds a heavy node does not walk it: it appends the node's
+// tasks to the task list (slots taken with an atomic counter), and p3_heavy_kernel,
+// launched next on the same stream, runs them, a CTA per task.
+constexpr int kHvIds = 1024;                  // ids of A staged per chunk
+constexpr int kHvSlots = 2 * kHvIds;          // hash slots: the table is at most half full
+constexpr int kHvQ = 64;                      // queued triangles per warp
+constexpr int kHvWarps = kThreads / 32;
 
+struct HvQueue {
+    int32_t k[kHvQ];                          // c's entry in b's out-list
+    int32_t c[kHvQ];
+    int32_t pos[kHvQ];                        // c's position in the chunk of A
+};
 struct P3Heavy {
-    int32_t ids[kHvIds];            // a chunk of a's out-list
-    // triangles found and not yet finished: the closing slot (c in b's out-list), the
-    // entries of b and c in a's out-list, b and c
-    int64_t qpc[kHvQ];
-    int32_t qeb[kHvQ], qec[kHvQ], qb[kHvQ], qc[kHvQ];
+    int32_t key[kHvSlots];                    // the chunk's ids (-1: empty slot)
+    uint16_t slot_pos[kHvSlots];              // their positions in the chunk
+    df sac[kHvIds], sca[kHvIds], pac[kHvIds]; // S(a->c), S(c->a), S(a->c) + S(c->a)
+    unsigned long long clo[kHvIds], chi[kHvIds];   // c's terms of the chunk: low, high words
+    HvQueue q[kHvWarps];
+    int64_t a, bA;
+    int32_t dA, eb0, nb, next_b, stop;
 };
 
 // first position of the sorted p[0, cnt) (cnt >= 1) holding an id >= key, or cnt;
@@ -1396,130 +1432,106 @@ __device__ __forceinline__ int32_t lower_pos(const int32_t *p, int32_t cnt, int3
     return base + (p[base] < key ? 1 : 0);
 }
 
-__device__ __forceinline__ u128 shfl_up_u128(u128 v, int d) {
-    uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
-    lo = __shfl_up_sync(FULL, lo, d);
-    hi = __shfl_up_sync(FULL, hi, d);
-    return ((u128)hi << 64) | lo;
+__device__ __forceinline__ uint32_t hv_hash(int32_t c, uint32_t mask) {
+    return (((uint32_t)c * 0x9E3779B1u) >> 16) & mask;
 }
 
-// finish the first m (<= 32) queued triangles of heavy node a, one per lane (all lanes
-// call).  The heavy triangles are many (a third of the wedges close on the 8M-node
-// graph), so the accumulator atomics are cut down: a's terms stay in the lane's acc_a
-// until the task ends, and b's terms are summed over the runs of equal b (the queue
-// holds the hits in walk order), one add per run; c's terms are added one by one.
-__device__ __forceinline__ void hv_flush(const P3Heavy &H, int m, int32_t a, int64_t bA, const df *xS,
-                                         const Rev &R, unsigned long long *acc, int lane, u128 &acc_a) {
-    int32_t b = -1;
-    u128 tb = 0;
+// position of id c in the staged chunk, or -1 (the table has empty slots, so the
+// probe ends at one long before it could visit every slot)
+__device__ __forceinline__ int32_t hv_find(const P3Heavy &H, int32_t c, uint32_t mask) {
+    uint32_t h = hv_hash(c, mask);
+    for (uint32_t it = 0; it <= mask; ++it) {
+        const int32_t k = H.key[h];
+        if (k == c) return H.slot_pos[h];
+        if (k < 0) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ void shared_add_u128(unsigned long long *lo_w, unsigned long long *hi_w, u128 v) {
+    unsigned long long lo = (unsigned long long)(uint64_t)v, hi = (unsigned long long)(uint64_t)(v >> 64);
+    if (lo) {
+        const unsigned long long old = atomicAdd(lo_w, lo);
+        if (old + lo < old) hi += 1ull;
+    }
+    if (hi) atomicAdd(hi_w, hi);
+}
+
+// finish the first m (<= 32) queued triangles {a, b, c} of the warp's current b, one
+// per lane (all lanes call)
+__device__ __forceinline__ void hv_finish(P3Heavy &H, const HvQueue &Q, int m, int32_t b, int64_t ob, df Sab,
+                                          df Sba, df Pab, const df *xS, const Rev &R, int lane, u128 &acc_a,
+                                          u128 &acc_b) {
     if (lane < m) {
-        const int64_t il = bA + H.qeb[lane], ih = bA + H.qec[lane], pc = H.qpc[lane];
-        b = H.qb[lane];
-        const int32_t c = H.qc[lane];
-        df Sba = R.get(il, b, a), Sca = R.get(ih, c, a), Scb = R.get(pc, c, b);
-        const TriTerms t = triangle_term_values(xS[il], Sba, xS[ih], Sca, xS[pc], Scb);
+        const int32_t c = Q.c[lane], p = Q.pos[lane];
+        const int64_t pc = ob + Q.k[lane];
+        const df Sbc = xS[pc], Scb = R.get(pc, c, b);
+        const TriTerms t = triangle_term_values_p(Sab, Sba, H.sac[p], H.sca[p], Sbc, Scb, H.pac[p], Pab);
         acc_a += t.a;
-        tb = t.b;
-        atomic_add_u128(acc + 2 * (int64_t)c, t.c);
+        acc_b += t.b;
+        shared_add_u128(&H.clo[p], &H.chi[p], t.c);
     }
-    // segmented inclusive sum of tb over the runs of equal b
-    const int32_t prev = __shfl_up_sync(FULL, b, 1);
-    const unsigned heads = __ballot_sync(FULL, lane == 0 || b != prev);
-    const int start = 31 - __clz(heads & (0xFFFFFFFFu >> (31 - lane)));
-    for (int d = 1; d < 32; d <<= 1) {
-        const u128 y = shfl_up_u128(tb, d);
-        if (lane - d >= start) tb += y;
-    }
-    const bool run_end = lane == 31 || ((heads >> (lane + 1)) & 1u);
-    if (run_end && lane < m) atomic_add_u128(acc + 2 * (int64_t)b, tb);
 }
 
-// one task: heavy node a, its out-neighbours b at entries [eb0, eb0 + kHvBlock) of A
-__device__ __forceinline__ void p3_node_wedges(P3Heavy &H, int32_t a, int32_t eb0, const int64_t *xoff,
-                                            const int32_t *xcol, const df *xS, const Rev &R,
-                                            const int32_t *xout, unsigned long long *acc, int lane) {
-    static_assert(kHvBlock == 32, "a task's out-neighbours are one per lane");
-    const int64_t bA = xoff[a];
-    const int32_t dA = xout[a];
-    const bool whole = dA <= kHvIds;                   // A in one chunk: no range cuts
-    // lane j holds out-neighbour b = A[eb0 + j], the start and length of b's out-list
-    int32_t bj = 0, dbj = 0;
-    int64_t obj = 0;
-    if (eb0 + lane < dA) {
-        bj = xcol[bA + eb0 + lane];
-        obj = xoff[bj];
-        dbj = xout[bj];
+// one warp's walk of out-neighbour b (entry eb of A) over the staged chunk, whose ids
+// lie in [lo_id, hi_id]
+__device__ __forceinline__ void hv_walk_b(P3Heavy &H, HvQueue &Q, int32_t a, int64_t eb, bool cut, int32_t lo_id,
+                                          int32_t hi_id, uint32_t mask, const int64_t *xoff, const int32_t *xcol,
+                                          const df *xS, const Rev &R, const int32_t *xout,
+                                          unsigned long long *acc, int lane, u128 &acc_a) {
+    const int32_t b = xcol[eb];
+    const int64_t ob = xoff[b];
+    const int32_t db = xout[b];
+    int32_t s = 0, e = db;
+    if (cut && db > 0) {
+        s = lower_pos(xcol + ob, db, lo_id);
+        e = lower_pos(xcol + ob, db, hi_id + 1);
     }
-    const int32_t nb = min(kHvBlock, dA - eb0);
+    if (s >= e) return;
+    const df Sab = xS[eb], Sba = R.get(eb, b, a), Pab = df_add(Sab, Sba);
     int qn = 0;                                        // queued triangles (warp-uniform)
-    u128 acc_a = 0;                                    // a's terms of this lane's triangles
-    for (int32_t k0 = 0; k0 < dA; k0 += kHvIds) {
-        const int32_t cnt = min(kHvIds, dA - k0);
-        __syncwarp();
-        for (int32_t k = lane; k < cnt; k += 32) H.ids[k] = xcol[bA + k0 + k];
-        __syncwarp();
-        // the part of b's out-list within the chunk's id range
-        int32_t sj = 0, ej = dbj;
-        if (!whole && dbj > 0) {
-            sj = lower_pos(xcol + obj, dbj, H.ids[0]);
-            ej = lower_pos(xcol + obj, dbj, H.ids[cnt - 1] + 1);
+    u128 acc_b = 0;
+    for (int32_t j0 = s; j0 < e; j0 += 64) {
+        int32_t c[2], pos[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int32_t k = j0 + u * 32 + lane;
+            c[u] = k < e ? xcol[ob + k] : -1;
         }
-        for (int32_t j = 0; j < nb; ++j) {
-            const int32_t s = __shfl_sync(FULL, sj, j), e = __shfl_sync(FULL, ej, j);
-            if (s >= e) continue;
-            const int32_t b = __shfl_sync(FULL, bj, j);
-            const int64_t ob = __shfl_sync(FULL, obj, j);
-            for (int32_t j0 = s; j0 < e; j0 += 64) {
-                int32_t c[2], pos[2];
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int32_t k = j0 + u * 32 + lane;
-                    c[u] = k < e ? xcol[ob + k] : -1;
-                }
+        for (int u = 0; u < 2; ++u)
+            pos[u] = (c[u] >= lo_id && c[u] <= hi_id) ? hv_find(H, c[u], mask) : -1;
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    pos[u] = -1;
-                    if (c[u] >= 0) {
-                        const int32_t p = lower_pos(H.ids, cnt, c[u]);
-                        if (p < cnt && H.ids[p] == c[u]) pos[u] = p;
-                    }
+        for (int u = 0; u < 2; ++u) {
+            const bool hit = pos[u] >= 0;
+            const unsigned hm = __ballot_sync(FULL, hit);
+            if (hit) {
+                const int slot = qn + __popc(hm & lanemask_lt());
+                Q.k[slot] = j0 + u * 32 + lane;
+                Q.c[slot] = c[u];
+                Q.pos[slot] = pos[u];
+            }
+            qn += __popc(hm);
+            if (qn >= 32) {                            // a full warp of triangles
+                __syncwarp();
+                hv_finish(H, Q, 32, b, ob, Sab, Sba, Pab, xS, R, lane, acc_a, acc_b);
+                __syncwarp();
+                if (lane < qn - 32) {
+                    Q.k[lane] = Q.k[32 + lane];
+                    Q.c[lane] = Q.c[32 + lane];
+                    Q.pos[lane] = Q.pos[32 + lane];
                 }
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const bool hit = pos[u] >= 0;
-                    const unsigned hm = __ballot_sync(FULL, hit);
-                    if (hit) {
-                        const int slot = qn + __popc(hm & lanemask_lt());
-                        H.qpc[slot] = ob + j0 + u * 32 + lane;
-                        H.qeb[slot] = eb0 + j;
-                        H.qec[slot] = k0 + pos[u];
-                        H.qb[slot] = b;
-                        H.qc[slot] = c[u];
-                    }
-                    qn += __popc(hm);
-                    if (qn >= 32) {                        // a full warp of triangles
-                        __syncwarp();
-                        hv_flush(H, 32, a, bA, xS, R, acc, lane, acc_a);
-                        __syncwarp();
-                        if (lane < qn - 32) {
-                            H.qpc[lane] = H.qpc[32 + lane];
-                            H.qeb[lane] = H.qeb[32 + lane];
-                            H.qec[lane] = H.qec[32 + lane];
-                            H.qb[lane] = H.qb[32 + lane];
-                            H.qc[lane] = H.qc[32 + lane];
-                        }
-                        qn -= 32;
-                        __syncwarp();
-                    }
-                }
+                qn -= 32;
+                __syncwarp();
             }
         }
     }
     __syncwarp();
-    hv_flush(H, qn, a, bA, xS, R, acc, lane, acc_a);
+    hv_finish(H, Q, qn, b, ob, Sab, Sba, Pab, xS, R, lane, acc_a, acc_b);
     __syncwarp();
-    acc_a = warp_sum_u128(acc_a);
-    if (lane == 0 && acc_a) atomic_add_u128(acc + 2 * (int64_t)a, acc_a);
+    acc_b = warp_sum_u128(acc_b);
+    if (lane == 0 && acc_b) atomic_add_u128(acc + 2 * (int64_t)b, acc_b);
 }
 
 // groups of 32 nodes are handed out by an atomic counter (next_group, zeroed before
@@ -1676,30 +1688,94 @@ __global__ void __launch_bounds__(kThreads, 5) p3_list_kernel(
     }
 }
 
-// the heavy-node tasks listed by p3_list_kernel, a warp per task, claimed with an atomic
-// counter
-__global__ void __launch_bounds__(kThreads) p3_heavy_kernel(
+// the heavy-node tasks listed by p3_list_kernel, a CTA per task, claimed with an atomic
+// counter; the CTA's warps claim the task's out-neighbours b from a counter in shared
+// memory (dynamic shared memory: sizeof(P3Heavy))
+__global__ void __launch_bounds__(kThreads, 3) p3_heavy_kernel(
     int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
     Rev R, const int32_t *__restrict__ xout, unsigned long long *acc, const unsigned long long *__restrict__ hvl,
     int64_t hvcap, const unsigned long long *hv_count, unsigned long long *hv_next) {
-    __shared__ P3Heavy heavy[kP3Warps];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    P3Heavy &H = heavy[wid];
+    extern __shared__ __align__(16) unsigned char hv_smem[];
+    P3Heavy &H = *reinterpret_cast<P3Heavy *>(hv_smem);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, tid = threadIdx.x;
+    HvQueue &Q = H.q[wid];
     unsigned long long lim = *hv_count;
     if (lim > (unsigned long long)hvcap) lim = (unsigned long long)hvcap;
     if (lim == 0) return;
+    for (int i = tid; i < kHvIds; i += kThreads) {
+        H.clo[i] = 0;
+        H.chi[i] = 0;
+    }
     while (true) {
-        unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(hv_next, 1ull);
-        t = __shfl_sync(FULL, t, 0);
-        if (t >= lim) break;
-        const unsigned long long w = hvl[t];
-        const int64_t a = (int64_t)(w >> 32), blk = (int64_t)(w & 0xffffffffull);
-        if (a >= n || xout[a] <= kWinCap || blk * kHvBlock >= xout[a]) {
-            if (lane == 0) atomicOr(R.err, 64);
-            continue;
+        __syncthreads();                               // the previous task is flushed
+        if (tid == 0) {
+            const unsigned long long t = atomicAdd(hv_next, 1ull);
+            H.stop = t >= lim;
+            H.a = -1;
+            if (!H.stop) {
+                const unsigned long long w = hvl[t];
+                const int64_t a = (int64_t)(w >> 32), blk = (int64_t)(w & 0xffffffffull);
+                if (a >= n || xout[a] <= kWinCap || blk * kHvBlock >= xout[a]) {
+                    atomicOr(R.err, 64);
+                } else {
+                    H.a = a;
+                    H.bA = xoff[a];
+                    H.dA = xout[a];
+                    H.eb0 = (int32_t)(blk * kHvBlock);
+                    H.nb = min(kHvBlock, H.dA - H.eb0);
+                }
+            }
         }
-        p3_node_wedges(H, (int32_t)a, (int32_t)(blk * kHvBlock), xoff, xcol, xS, R, xout, acc, lane);
+        __syncthreads();
+        if (H.stop) break;
+        if (H.a < 0) continue;
+        const int32_t a = (int32_t)H.a, dA = H.dA, eb0 = H.eb0, nb = H.nb;
+        const int64_t bA = H.bA;
+        u128 acc_a = 0;
+        for (int32_t k0 = 0; k0 < dA; k0 += kHvIds) {
+            const int32_t cnt = min(kHvIds, dA - k0);
+            const uint32_t slots = max(64u, dev_pow2_at_least(2u * (uint32_t)cnt)), mask = slots - 1;
+            for (uint32_t i = tid; i < slots; i += kThreads) H.key[i] = -1;
+            if (tid == 0) H.next_b = 0;
+            __syncthreads();
+            for (int32_t i = tid; i < cnt; i += kThreads) {
+                const int64_t sl = bA + k0 + i;
+                const int32_t c = xcol[sl];
+                uint32_t h = hv_hash(c, mask), it = 0;
+                // the ids are distinct and the table at most half full: a free slot is found
+                for (; it <= mask && atomicCAS(&H.key[h], -1, c) != -1; ++it) h = (h + 1) & mask;
+                if (it <= mask) H.slot_pos[h] = (uint16_t)i;
+                else atomicOr(R.err, 64);
+                const df sac = xS[sl], sca = R.get(sl, c, a);
+                H.sac[i] = sac;
+                H.sca[i] = sca;
+                H.pac[i] = df_add(sac, sca);
+            }
+            __syncthreads();
+            const int32_t lo_id = xcol[bA + k0], hi_id = xcol[bA + k0 + cnt - 1];
+            const bool cut = dA > kHvIds;
+            while (true) {
+                int32_t j = 0;
+                if (lane == 0) j = atomicAdd(&H.next_b, 1);
+                j = __shfl_sync(FULL, j, 0);
+                if (j >= nb) break;
+                hv_walk_b(H, Q, a, bA + eb0 + j, cut, lo_id, hi_id, mask, xoff, xcol, xS, R, xout, acc, lane,
+                          acc_a);
+            }
+            __syncthreads();
+            // c's sums of the chunk to the accumulators, zeroed for the next chunk
+            for (int32_t i = tid; i < cnt; i += kThreads) {
+                const unsigned long long lo = H.clo[i], hi = H.chi[i];
+                if (lo | hi) {
+                    atomic_add_u128(acc + 2 * (int64_t)xcol[bA + k0 + i], ((u128)hi << 64) | lo);
+                    H.clo[i] = 0;
+                    H.chi[i] = 0;
+                }
+            }
+            __syncthreads();
+        }
+        acc_a = warp_sum_u128(acc_a);
+        if (lane == 0 && acc_a) atomic_add_u128(acc + 2 * (int64_t)a, acc_a);
     }
 }
 
@@ -1851,6 +1927,8 @@ int rs::prepare_score_kernels() {
     RS_CUDA_TRY(cudaFuncSetAttribute(p2_large_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kMidCap));
     RS_CUDA_TRY(cudaFuncSetAttribute(p2_large_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kMidCap));
     RS_CUDA_TRY(cudaFuncSetAttribute(p2_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, p2_mid_smem));
+    RS_CUDA_TRY(cudaFuncSetAttribute(p3_heavy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(P3Heavy)));
     done = 1;
     return 0;
 }
@@ -1947,7 +2025,8 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     }
     const int64_t gx_tiles = (n + kGxTile - 1) / kGxTile;
     gx_offsets_kernel<<<(unsigned)gx_tiles, kGxThreads, 0, s>>>(g->rec, n, g->xoff, g->wq + kWqGxStatus,
-                                                              g->wq + kWqGxTicket, err);
+                                                              g->wq + kWqGxTicket, err, g->gx_spin,
+                                                              g->gx_withhold);
     RS_LAUNCHED(g, s, "gx_offsets");
     const Strict SX{g->col, g->strict ? g->sx : nullptr};
     if (g->strict) {
@@ -2041,8 +2120,9 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
                                                                    g->acc, next_group, 1, hvl, hvcap,
                                                                    g->wq + kWqHvCount);
     RS_LAUNCHED(g, s, "p3_list");
-    p3_heavy_kernel<<<grid_for(hvcap * 32, NT, 4), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, R, g->xout, g->acc, hvl,
-                                                                hvcap, g->wq + kWqHvCount, g->wq + kWqHvNext);
+    p3_heavy_kernel<<<grid_for(hvcap, 1, 3), NT, sizeof(P3Heavy), s>>>(n, g->xoff, g->xcol, g->xS, R, g->xout,
+                                                                       g->acc, hvl, hvcap, g->wq + kWqHvCount,
+                                                                       g->wq + kWqHvNext);
     RS_LAUNCHED(g, s, "p3_heavy");
     // ---- finalize
     if (g->gid) {

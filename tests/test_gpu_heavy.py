@@ -1,9 +1,11 @@
 """Triangles whose lowest-ranked node has a long G_x out-list (more than 128
 out-neighbours, the heavy-node walk of P3), against the oracle at 1e-12
 relative.  The dense bipartite core gives ~1,900 such nodes with 129-410
-out-neighbours (one staged chunk of ids) and 6 with ~590 (two chunks), beside
-ordinary nodes; both reverse-value modes, the reordered numbering and a packed
-batch take the same walk."""
+out-neighbours and 6 with ~590, beside ordinary nodes (one staged chunk of at most
+1,024 ids each); a larger core adds 6 nodes with ~1,070 out-neighbours, whose
+out-lists take two chunks (the out-lists of their out-neighbours cut to each
+chunk's id range).  Both reverse-value modes, the reordered numbering and a
+packed batch take the same walk."""
 import numpy as np
 import pytest
 
@@ -46,6 +48,26 @@ def test_heavy_nodes_match_the_oracle(rs, core, mirror, reorder):
     ids, _ = G.topk(torch.as_tensor(got, device="cuda"), 100)
     assert ids.cpu().numpy().tolist() == oracle.topk(got, 100).tolist()
     # a second pass (the task list is rebuilt from zeroed counters) gives the same bits
+    again = G.score().cpu().numpy()
+    np.testing.assert_array_equal(again.view(np.uint64), got.view(np.uint64))
+    G.close()
+
+
+@pytest.fixture(scope="module")
+def core2():
+    g = graphgen.dense_core(n_core=1100, n_fan=3500, fan_min=150, fan_max=650, n_full=6, k=40, seed=17)
+    oracle.set_threads(0)
+    return g, oracle.Oracle.from_graph(g).scores()
+
+
+@pytest.mark.parametrize("mirror", [1, 0])
+def test_heavy_nodes_over_two_chunks(rs, core2, mirror):
+    g, ref = core2
+    G = rs.Graph.from_generated(g)
+    G.set_tuning(p3_mirror=mirror)
+    got = G.score().cpu().numpy()
+    assert G.device_errors() == 0
+    _close(got, ref)
     again = G.score().cpu().numpy()
     np.testing.assert_array_equal(again.view(np.uint64), got.view(np.uint64))
     G.close()

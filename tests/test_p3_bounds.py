@@ -1,9 +1,9 @@
 """The capacity of P3's heavy-node task list (host logic, no GPU).
 
-A node with more than 128 G_x out-neighbours is walked in tasks of 32
+A node with more than 128 G_x out-neighbours is walked in tasks of 128
 out-neighbours, listed in a buffer sized from nnz alone before any kernel runs.
-Every G_x edge has one tail, so the tasks number at most
-m_x (1 + 31/129) / 32 <= nnz / 51.  These graphs check that bound on the
+Every G_x edge has one tail, and a heavy node's ceil(d+/128) tasks are at most
+d+ 256/(128 129), so the tasks number at most 2 m_x / 129 <= nnz / 129.  These graphs check that bound on the
 orientation the library uses (cross degree, then id), including cliques and a
 complete bipartite graph whose heavy nodes all sit at the 129-neighbour worst
 case."""
@@ -22,7 +22,7 @@ def _cap_divisor():
     src = open(HEADER).read()
     m = re.search(r"hv_cap\(int64_t nnz\) \{ return nnz / (\d+) \+ 1; \}", src)
     assert m, "hv_cap's formula not found"
-    assert re.search(r"constexpr int kWinCap = 128, kHvBlock = 32;", src)
+    assert re.search(r"constexpr int kWinCap = 128, kHvBlock = 128;", src)
     return int(m.group(1))
 
 
@@ -38,7 +38,7 @@ def _tasks(offsets, cols, labels):
     out = (dx[b] > dx[a]) | ((dx[b] == dx[a]) & (b > a))
     xo = np.bincount(a[out], minlength=n)
     heavy = xo[xo > 128]
-    return int(((heavy + 31) // 32).sum()), int(heavy.size)
+    return int(((heavy + 127) // 128).sum()), int(heavy.size)
 
 
 def _csr(n, u, v):
@@ -60,7 +60,7 @@ def _clique(k):
 def _worst_case(leaves):
     """Complete bipartite: `leaves` nodes each joined to the same 129 hubs (other
     communities).  The hubs' cross degree is the larger, so every G_x edge's tail is a
-    leaf with exactly 129 out-neighbours: 5 tasks per 129 edges, the bound's worst case."""
+    leaf with exactly 129 out-neighbours: 2 tasks per 129 edges, the bound's worst case."""
     n = leaves + 129
     u = np.repeat(np.arange(leaves), 129)
     v = leaves + np.tile(np.arange(129), leaves)
@@ -87,5 +87,5 @@ def test_worst_case_comes_close_to_the_capacity():
     div = _cap_divisor()
     off, cols, labels = _worst_case(300)
     tasks, heavy = _tasks(off, cols, labels)
-    assert heavy == 300 and tasks == 1500
+    assert heavy == 300 and tasks == 600
     assert 0.95 * (int(off[-1]) // div + 1) < tasks <= int(off[-1]) // div + 1
