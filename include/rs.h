@@ -137,6 +137,12 @@ rs_status rs_batch_omega_max(rs_graph *g, double *wmax_out, void *stream);
  * bit-identical from run to run (all sums are exact fixed-point).
  */
 rs_status rs_score(rs_graph *g, double *scores, double *omega_max_out, void *stream);
+/*
+ * Every wait inside rs_score's kernels is bounded.  When rs_score synchronises
+ * (omega_max_out given) and a wait of this call ran out, it returns RS_ETIMEOUT
+ * (the scores are still written: the wait's data is then recomputed directly);
+ * without omega_max_out, rs_device_errors reports it (bit 32).
+ */
 
 /*
  * rs_get_interaction -- the per-node community counts f_v(c) (Sec. V-A,
@@ -192,7 +198,7 @@ rs_status rs_graph_info(const rs_graph *g, int64_t *n, int64_t *nnz, int32_t *k,
  * memory is owned by another allocator (a framework's caching allocator, a
  * fixed memory budget), and latency-critical loops that cannot afford
  * cudaMalloc's implicit device synchronisation or its failure mid-request.
- * The paper has no counterpart; this is a deployment variant of Step 4.
+ * The paper has no counterpart; it ranks like rs_topk.
  *
  *   scores      device double[n], every value >= 0 (not NaN); 1 <= n < 2^31.
  *   k           1 <= k <= min(n, 16384); larger k returns RS_EINVAL.
@@ -402,6 +408,15 @@ void rs_server_free(rs_server *srv);
  *   list over its capacity or holding an invalid entry.
  */
 rs_status rs_device_errors(rs_graph *g, int32_t *flags_out, void *stream);
+
+/*
+ * rs_test_gx_stall -- test hook (no counterpart in the paper): from the next
+ * rs_score on, tile `tile` of the G_x offset scan does not publish its words and
+ * every wait of the scan gives up after spin_limit reads, so that the tiles after
+ * it run out of their bounded waits and take the fallback.  tile < 0 restores the
+ * normal scan.  Invalidates captured steps.
+ */
+rs_status rs_test_gx_stall(rs_graph *g, int64_t tile, int64_t spin_limit);
 
 /* rs_free_graph -- release a graph and its device memory (NULL is a no-op). */
 void rs_free_graph(rs_graph *g);

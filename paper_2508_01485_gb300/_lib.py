@@ -117,6 +117,8 @@ def lib():
         L.rs_server_free.argtypes = [P]
         L.rs_device_errors.restype = I
         L.rs_device_errors.argtypes = [P, ctypes.POINTER(I32), P]
+        L.rs_test_gx_stall.restype = I
+        L.rs_test_gx_stall.argtypes = [P, I64, I64]
         L.rs_free_graph.restype = None
         L.rs_free_graph.argtypes = [P]
         L.rs_last_error.restype = ctypes.c_char_p
@@ -301,6 +303,11 @@ class Graph:
         f = ctypes.c_int32(0)
         _check(lib().rs_device_errors(self._h, ctypes.byref(f), _stream(stream)))
         return f.value
+
+    def test_gx_stall(self, tile, spin_limit=1000):
+        """Test hook: tile `tile` of the G_x offset scan withholds its words and the scan's
+        waits give up after spin_limit reads (tile < 0: the normal scan)."""
+        _check(lib().rs_test_gx_stall(self._h, int(tile), int(spin_limit)))
 
     def launch_count(self):
         c = ctypes.c_int64(0)

@@ -1477,13 +1477,28 @@ extern "C" rs_status rs_score(rs_graph *g, double *scores, double *omega_max_out
     if (rc) return (rs_status)rc;
     if (omega_max_out) {
         unsigned long long bits = 0;
+        int32_t flags = 0;
         if (cudaError_t e = cudaMemcpyAsync(&bits, g->wmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, s))
             return (rs_status)cuda_fail(e, "read w_max");
+        if (g->n > 0)
+            if (cudaError_t e = cudaMemcpyAsync(&flags, g->d_flag + 4, sizeof(flags), cudaMemcpyDeviceToHost, s))
+                return (rs_status)cuda_fail(e, "read device flags");
         if (cudaError_t e = cudaStreamSynchronize(s)) return (rs_status)cuda_fail(e, "rs_score");
+        if (flags & 32)
+            return (rs_status)fail(RS_ETIMEOUT, "rs_score: a bounded wait of the G_x offset scan ran out "
+                                                "(the offsets were summed directly instead)");
         double w;
         memcpy(&w, &bits, sizeof(w));
         *omega_max_out = w;
     }
+    return RS_OK;
+}
+
+extern "C" rs_status rs_test_gx_stall(rs_graph *g, int64_t tile, int64_t spin_limit) {
+    if (!g || spin_limit < 1) return (rs_status)fail(RS_EINVAL, "rs_test_gx_stall: bad arguments");
+    g->gx_withhold = tile < 0 ? -1 : tile;
+    g->gx_spin = tile < 0 ? (1l << 24) : (long)spin_limit;
+    g->version++;                                  // captured steps hold the old launch arguments
     return RS_OK;
 }
 

@@ -68,6 +68,20 @@ def test_noalloc_ties_and_small_inputs(rs):
     check_against_rs_topk(rs, G, dup, g.n)        # all of them
 
 
+def test_noalloc_ties_above_the_scratch(rs):
+    """More scores than the 16,384-key scratch and heavy ties: the radix levels must
+    select down into the node-id digits (the last level's digit spans score and id)."""
+    g = graphgen.dcsbm_small(100_000, seed=5)
+    G = rs.Graph.from_generated(g)
+    rng = np.random.default_rng(9)
+    zeros = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    few = torch.as_tensor(rng.integers(0, 3, size=g.n).astype(np.float64), device="cuda")
+    for s in (zeros, few):
+        for k in (1, 5000, 16384):
+            check_against_rs_topk(rs, G, s, k)
+    G.close()
+
+
 def test_noalloc_rejects_k_beyond_the_scratch(rs):
     s = torch.zeros(20000, dtype=torch.float64, device="cuda")
     ids = torch.empty(16385, dtype=torch.int32, device="cuda")
