@@ -456,6 +456,37 @@ __global__ void hub_bounds_kernel(const int64_t *off, const int32_t *hubs, int64
     }
 }
 
+// distinct foreign communities of each hub row (neighbours outside the hub's own
+// community), counted by inserting their labels into a scratch table per hub sized by
+// the row's degree; the scoring tables are then sized by these counts
+__global__ void hub_distinct_kernel(const int64_t *off, const int32_t *col, const int32_t *lab, const HubInfo *hubs,
+                                    const int32_t *items, const int32_t *chunks, int64_t nitems, int32_t chunk_len,
+                                    int32_t *tkey, int32_t *lf, int *err) {
+    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const HubInfo h = hubs[items[it]];
+        const int64_t b = off[h.row], d = off[h.row + 1] - b;
+        const int64_t lo = (int64_t)chunks[it] * chunk_len, hi = min(d, lo + chunk_len);
+        const int32_t cv = lab[h.row];
+        const uint32_t mask = (uint32_t)h.cap - 1;
+        int32_t fresh = 0;
+        for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+            const int32_t c = lab[col[b + e]];
+            if (c == cv) continue;
+            uint32_t s = hash_label(c);
+            s = (s ^ (s >> 15)) & mask;
+            uint32_t t = 0;
+            for (; t <= mask; ++t) {
+                const int32_t prev = atomicCAS(&tkey[h.tab + s], kEmpty, c);
+                if (prev == kEmpty) { ++fresh; break; }
+                if (prev == c) break;
+                s = (s + 1) & mask;
+            }
+            if (t > mask) atomicOr(err, 1);
+        }
+        if (fresh) atomicAdd(&lf[items[it]], fresh);
+    }
+}
+
 __global__ void scatter_class_kernel(const int64_t *a, int64_t n, int32_t *rows) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
@@ -620,7 +651,7 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
         int64_t d = offs[3 * i + 1] - offs[3 * i];
         int64_t m = std::min<int64_t>(d, offs[3 * i + 2]);
         info[i].row = hl[i];
-        info[i].cap = (int32_t)pow2_at_least((uint64_t)(2 * m));
+        info[i].cap = (int32_t)pow2_at_least((uint64_t)(2 * m));   // by degree: the scratch count below
         info[i].tab = slots;
         info[i].first_item = (int32_t)items.size();
         int nc = (int)((d + g->tune.hub_chunk - 1) / g->tune.hub_chunk);
@@ -631,11 +662,44 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
     free_hub_tables(g);
     g->n_hubs = nh;
     g->n_hub_items = (int64_t)items.size();
-    g->hub_slots = slots;
     if (nh) {
         RS_CUDA_TRY(dmalloc(&g->hubs, nh));
         RS_CUDA_TRY(dmalloc(&g->hub_items, items.size()));
         RS_CUDA_TRY(dmalloc(&g->hub_item_chunk, items.size()));
+        RS_CUDA_TRY(cudaMemcpy(g->hubs, info.data(), nh * sizeof(HubInfo), cudaMemcpyHostToDevice));
+        RS_CUDA_TRY(cudaMemcpy(g->hub_items, items.data(), items.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        RS_CUDA_TRY(cudaMemcpy(g->hub_item_chunk, chunks.data(), chunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        // each hub's distinct foreign communities L_f, in scratch tables sized by degree;
+        // the scoring tables then take 2 L_f slots (rounded up to a power of two), which
+        // is far less on hub-skewed graphs (degree 54,097 with 4,671 communities)
+        int32_t *tkey = nullptr, *lf = nullptr;
+        cudaError_t e = dmalloc(&tkey, (size_t)slots);
+        if (!e) e = dmalloc(&lf, (size_t)nh);
+        if (!e) e = cudaMemsetAsync(tkey, 0xFF, (size_t)slots * sizeof(int32_t), s);
+        if (!e) e = cudaMemsetAsync(lf, 0, (size_t)nh * sizeof(int32_t), s);
+        if (!e) e = cudaMemsetAsync(d_hdr + 3, 0, sizeof(int), s);
+        if (!e) {
+            hub_distinct_kernel<<<grid_for((int64_t)items.size(), 1, 8), 256, 0, s>>>(
+                g->off, g->col, g->lab, g->hubs, g->hub_items, g->hub_item_chunk, (int64_t)items.size(),
+                g->tune.hub_chunk, tkey, lf, d_hdr + 3);
+            e = cudaGetLastError();
+        }
+        std::vector<int32_t> L(nh);
+        int overflow = 0;
+        if (!e) e = cudaMemcpyAsync(L.data(), lf, nh * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaMemcpyAsync(&overflow, d_hdr + 3, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        pool_free(tkey);
+        pool_free(lf);
+        if (e) return cuda_fail(e, "hub community counts");
+        if (overflow) return fail(RS_ECUDA, "hub community count: scratch table full (library bug)");
+        slots = 0;
+        for (int i = 0; i < nh; ++i) {
+            info[i].cap = (int32_t)std::max<uint64_t>(2, pow2_at_least((uint64_t)(2 * (int64_t)L[i])));
+            info[i].tab = slots;
+            slots += info[i].cap;
+        }
+        RS_CUDA_TRY(cudaMemcpy(g->hubs, info.data(), nh * sizeof(HubInfo), cudaMemcpyHostToDevice));
         RS_CUDA_TRY(dmalloc(&g->hkey, slots));
         RS_CUDA_TRY(dmalloc(&g->hcnt, slots));
         RS_CUDA_TRY(dmalloc(&g->hq, 2 * slots));
@@ -643,10 +707,8 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
         RS_CUDA_TRY(dmalloc(&g->hagg, nh));
         RS_CUDA_TRY(dmalloc(&g->hitem_out, items.size()));
         RS_CUDA_TRY(dmalloc(&g->hitem_in, items.size()));
-        RS_CUDA_TRY(cudaMemcpy(g->hubs, info.data(), nh * sizeof(HubInfo), cudaMemcpyHostToDevice));
-        RS_CUDA_TRY(cudaMemcpy(g->hub_items, items.data(), items.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-        RS_CUDA_TRY(cudaMemcpy(g->hub_item_chunk, chunks.data(), chunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     }
+    g->hub_slots = slots;
     return 0;
 }
 

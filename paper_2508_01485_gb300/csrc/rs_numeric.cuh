@@ -115,29 +115,43 @@ __device__ __forceinline__ df df_from_u128(u128 x, int e) {
 }
 __device__ __forceinline__ df df_from_u64(uint64_t x, int e) { return df_from_u128((u128)x, e); }
 
-// the exact value of a finite float as (mantissa, exponent): f = m * 2^q
-__device__ __forceinline__ void float_parts(float f, int32_t &m, int &q) {
-    uint32_t b = __float_as_uint(f);
-    int ex = (int)((b >> 23) & 0xFF);
-    int32_t mant = (int32_t)(b & 0x7FFFFF);
-    if (ex == 0) { q = -149; } else { mant |= 0x800000; q = ex - 150; }
-    m = (b >> 31) ? -mant : mant;
+// f * 2^frac truncated toward zero, as a two's complement 128-bit integer (hi:lo), for
+// a finite float f: its 24-bit significand shifted by the exponent, with 64-bit pieces
+// (every score term keeps the shift below 128)
+__device__ __forceinline__ void fixed_part(float f, int frac, uint64_t &lo, uint64_t &hi) {
+    const uint32_t b = __float_as_uint(f);
+    const int ex = (int)((b >> 23) & 0xFF);
+    const uint32_t mant = (b & 0x7FFFFFu) | (ex ? 0x800000u : 0u);
+    const int q = (ex ? ex - 150 : -149) + frac;
+    uint64_t l, h;
+    if (q >= 64) {
+        l = 0;
+        h = (uint64_t)mant << (q - 64);
+    } else if (q > 0) {
+        l = (uint64_t)mant << q;
+        h = (uint64_t)mant >> (64 - q);
+    } else {
+        const int s = -q;                          // bits below 1 are dropped
+        l = s < 32 ? (uint64_t)(mant >> s) : 0;
+        h = 0;
+    }
+    if (b >> 31) {                                 // negative: the magnitude's two's complement
+        l = ~l + 1;
+        h = ~h + (l == 0 ? 1 : 0);
+    }
+    lo = l;
+    hi = h;
 }
-// signed value m * 2^(q + frac) as a 128-bit integer (bits below 1 are dropped toward 0)
-__device__ __forceinline__ __int128 scaled_i128(int32_t m, int q) {
-    __int128 v = (__int128)m;
-    if (q >= 0) return v << q;
-    int s = -q;
-    if (s >= 63) return 0;
-    return m >= 0 ? (v >> s) : -((-v) >> s);
-}
-// round-toward-zero of a * 2^frac for a >= 0 as an unsigned 128-bit integer
+// round-toward-zero of each part of a * 2^frac, summed, for a >= 0 as an unsigned
+// 128-bit integer (0 when the sum is negative)
 __device__ __forceinline__ u128 df_to_fixed(df a, int frac) {
-    int32_t mh, ml; int qh, ql;
-    float_parts(a.hi, mh, qh);
-    float_parts(a.lo, ml, ql);
-    __int128 v = scaled_i128(mh, qh + frac) + scaled_i128(ml, ql + frac);
-    return v > 0 ? (u128)v : (u128)0;
+    uint64_t l1, h1, l2, h2;
+    fixed_part(a.hi, frac, l1, h1);
+    fixed_part(a.lo, frac, l2, h2);
+    const uint64_t lo = l1 + l2;
+    const uint64_t hi = h1 + h2 + (lo < l1 ? 1 : 0);
+    if ((int64_t)hi < 0) return 0;
+    return ((u128)hi << 64) | lo;
 }
 
 // correctly rounded (nearest, ties to even) double of x * 2^e, x < 2^128, |e| moderate

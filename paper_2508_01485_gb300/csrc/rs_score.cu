@@ -1381,8 +1381,8 @@ __device__ __forceinline__ int64_t find_in_list(const int32_t *xcol, int64_t lo,
 // Heavy nodes: a wedge walk, one CTA per task.  A task is a heavy node a with a block
 // of kHvBlock of its out-neighbours b.  The CTA stages a's out-list A (sorted by id),
 // kHvIds ids at a time, as a shared-memory hash table (id -> position in the chunk, at
-// most half full) beside the values S(a->c), S(c->a) and their sum for every c of the
-// chunk.  Its warps then take the task's out-neighbours b one at a time: a warp
+// most a quarter full) beside the value S(c->a) and the sum S(a->c) + S(c->a) for
+// every c of the chunk.  Its warps then take the task's out-neighbours b one at a time: a warp
 // streams b's out-list (the nodes c ranked above b), coalesced, and looks every c up in
 // the table; a hit closes the triangle {a, b, c}, which is met once, at its
 // middle-ranked node b.  When A takes several chunks, b's out-list is first cut to the
@@ -1401,8 +1401,9 @@ __device__ __forceinline__ int64_t find_in_list(const int32_t *xcol, int64_t lo,
 // tasks to the task list (slots taken with an atomic counter), and p3_heavy_kernel,
 // launched next on the same stream, runs them, a CTA per task.
 constexpr int kHvIds = 1024;                  // ids of A staged per chunk
-constexpr int kHvSlots = 2 * kHvIds;          // hash slots: the table is at most half full
-constexpr int kHvQ = 64;                      // queued triangles per warp
+constexpr int kHvSlots = 4 * kHvIds;          // hash slots: the table is at most a quarter full
+constexpr int kHvUnroll = 4;                  // 32-entry rows of b's out-list per trip
+constexpr int kHvQ = 32 * kHvUnroll + 32;     // queued triangles per warp: < 32 left + one trip
 constexpr int kHvWarps = kThreads / 32;
 
 struct HvQueue {
@@ -1413,7 +1414,7 @@ struct HvQueue {
 struct P3Heavy {
     int32_t key[kHvSlots];                    // the chunk's ids (-1: empty slot)
     uint16_t slot_pos[kHvSlots];              // their positions in the chunk
-    df sac[kHvIds], sca[kHvIds], pac[kHvIds]; // S(a->c), S(c->a), S(a->c) + S(c->a)
+    df sca[kHvIds], pac[kHvIds];              // S(c->a), S(a->c) + S(c->a)
     unsigned long long clo[kHvIds], chi[kHvIds];   // c's terms of the chunk: low, high words
     HvQueue q[kHvWarps];
     int64_t a, bA;
@@ -1436,8 +1437,8 @@ __device__ __forceinline__ uint32_t hv_hash(int32_t c, uint32_t mask) {
     return (((uint32_t)c * 0x9E3779B1u) >> 16) & mask;
 }
 
-// position of id c in the staged chunk, or -1 (the table has empty slots, so the
-// probe ends at one long before it could visit every slot)
+// position of id c in the staged chunk, or -1 (three quarters of the slots are empty,
+// so the probe ends at one long before it could visit every slot)
 __device__ __forceinline__ int32_t hv_find(const P3Heavy &H, int32_t c, uint32_t mask) {
     uint32_t h = hv_hash(c, mask);
     for (uint32_t it = 0; it <= mask; ++it) {
@@ -1458,52 +1459,71 @@ __device__ __forceinline__ void shared_add_u128(unsigned long long *lo_w, unsign
     if (hi) atomicAdd(hi_w, hi);
 }
 
-// finish the first m (<= 32) queued triangles {a, b, c} of the warp's current b, one
-// per lane (all lanes call)
-__device__ __forceinline__ void hv_finish(P3Heavy &H, const HvQueue &Q, int m, int32_t b, int64_t ob, df Sab,
-                                          df Sba, df Pab, const df *xS, const Rev &R, int lane, u128 &acc_a,
-                                          u128 &acc_b) {
+// finish the m (<= 32) queued triangles {a, b, c} at queue entries [f, f + m) of the
+// warp's current b, one per lane (all lanes call); the chunk of A starts at slot aslot0
+__device__ __forceinline__ void hv_finish(P3Heavy &H, const HvQueue &Q, int f, int m, int32_t b, int64_t ob,
+                                          int64_t aslot0, df Sab, df Sba, df Pab, const df *xS, const Rev &R,
+                                          int lane, u128 &acc_a, u128 &acc_b) {
     if (lane < m) {
-        const int32_t c = Q.c[lane], p = Q.pos[lane];
-        const int64_t pc = ob + Q.k[lane];
-        const df Sbc = xS[pc], Scb = R.get(pc, c, b);
-        const TriTerms t = triangle_term_values_p(Sab, Sba, H.sac[p], H.sca[p], Sbc, Scb, H.pac[p], Pab);
+        const int32_t c = Q.c[f + lane], p = Q.pos[f + lane];
+        const int64_t pc = ob + Q.k[f + lane];
+        const df Sbc = xS[pc], Scb = R.get(pc, c, b), Sac = xS[aslot0 + p];
+        const TriTerms t = triangle_term_values_p(Sab, Sba, Sac, H.sca[p], Sbc, Scb, H.pac[p], Pab);
         acc_a += t.a;
         acc_b += t.b;
         shared_add_u128(&H.clo[p], &H.chi[p], t.c);
     }
 }
 
-// one warp's walk of out-neighbour b (entry eb of A) over the staged chunk, whose ids
-// lie in [lo_id, hi_id]
-__device__ __forceinline__ void hv_walk_b(P3Heavy &H, HvQueue &Q, int32_t a, int64_t eb, bool cut, int32_t lo_id,
-                                          int32_t hi_id, uint32_t mask, const int64_t *xoff, const int32_t *xcol,
-                                          const df *xS, const Rev &R, const int32_t *xout,
-                                          unsigned long long *acc, int lane, u128 &acc_a) {
-    const int32_t b = xcol[eb];
-    const int64_t ob = xoff[b];
-    const int32_t db = xout[b];
-    int32_t s = 0, e = db;
+// an out-neighbour b of the task (entry eb of A): its out-list [ob + s, ob + e) cut to
+// the chunk's id range [lo_id, hi_id] when A takes several chunks, and the values of
+// the edge a -> b
+struct HvB {
+    int32_t b, s, e;
+    int64_t ob;
+    df Sab, Sba;
+};
+__device__ __forceinline__ HvB hv_load_b(int32_t a, int64_t eb, bool cut, int32_t lo_id, int32_t hi_id,
+                                         const int64_t *xoff, const int32_t *xcol, const df *xS, const Rev &R,
+                                         const int32_t *xout) {
+    HvB B;
+    B.b = xcol[eb];
+    B.ob = xoff[B.b];
+    const int32_t db = xout[B.b];
+    B.s = 0;
+    B.e = db;
     if (cut && db > 0) {
-        s = lower_pos(xcol + ob, db, lo_id);
-        e = lower_pos(xcol + ob, db, hi_id + 1);
+        B.s = lower_pos(xcol + B.ob, db, lo_id);
+        B.e = lower_pos(xcol + B.ob, db, hi_id + 1);
     }
-    if (s >= e) return;
-    const df Sab = xS[eb], Sba = R.get(eb, b, a), Pab = df_add(Sab, Sba);
+    B.Sab = xS[eb];
+    B.Sba = R.get(eb, B.b, a);
+    return B;
+}
+
+// one warp's walk of out-neighbour b over the staged chunk (starting at slot aslot0):
+// each trip loads and looks up kHvUnroll rows of 32 entries of b's out-list, queues the
+// hits, and finishes the queued triangles 32 at a time (at the end of the list, the
+// rest too); the finishing code is inlined once
+__device__ __forceinline__ void hv_walk_b(P3Heavy &H, HvQueue &Q, const HvB &B, int64_t aslot0, int32_t lo_id,
+                                          int32_t hi_id, uint32_t mask, const int32_t *xcol, const df *xS,
+                                          const Rev &R, unsigned long long *acc, int lane, u128 &acc_a) {
+    if (B.s >= B.e) return;
+    const df Pab = df_add(B.Sab, B.Sba);
     int qn = 0;                                        // queued triangles (warp-uniform)
     u128 acc_b = 0;
-    for (int32_t j0 = s; j0 < e; j0 += 64) {
-        int32_t c[2], pos[2];
+    for (int32_t j0 = B.s; j0 < B.e; j0 += 32 * kHvUnroll) {
+        int32_t c[kHvUnroll], pos[kHvUnroll];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kHvUnroll; ++u) {
             const int32_t k = j0 + u * 32 + lane;
-            c[u] = k < e ? xcol[ob + k] : -1;
+            c[u] = k < B.e ? xcol[B.ob + k] : -1;
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
+        for (int u = 0; u < kHvUnroll; ++u)
             pos[u] = (c[u] >= lo_id && c[u] <= hi_id) ? hv_find(H, c[u], mask) : -1;
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kHvUnroll; ++u) {
             const bool hit = pos[u] >= 0;
             const unsigned hm = __ballot_sync(FULL, hit);
             if (hit) {
@@ -1513,25 +1533,27 @@ __device__ __forceinline__ void hv_walk_b(P3Heavy &H, HvQueue &Q, int32_t a, int
                 Q.pos[slot] = pos[u];
             }
             qn += __popc(hm);
-            if (qn >= 32) {                            // a full warp of triangles
-                __syncwarp();
-                hv_finish(H, Q, 32, b, ob, Sab, Sba, Pab, xS, R, lane, acc_a, acc_b);
-                __syncwarp();
-                if (lane < qn - 32) {
-                    Q.k[lane] = Q.k[32 + lane];
-                    Q.c[lane] = Q.c[32 + lane];
-                    Q.pos[lane] = Q.pos[32 + lane];
-                }
-                qn -= 32;
-                __syncwarp();
-            }
         }
+        const bool last = j0 + 32 * kHvUnroll >= B.e;
+        int f = 0;
+        while (qn - f >= 32 || (last && qn > f)) {
+            const int m = min(32, qn - f);
+            __syncwarp();
+            hv_finish(H, Q, f, m, B.b, B.ob, aslot0, B.Sab, B.Sba, Pab, xS, R, lane, acc_a, acc_b);
+            f += m;
+        }
+        if (f > 0) {                                   // the rest (< 32) to the front
+            __syncwarp();
+            int32_t k = 0, cc = 0, pp = 0;
+            if (lane < qn - f) { k = Q.k[f + lane]; cc = Q.c[f + lane]; pp = Q.pos[f + lane]; }
+            __syncwarp();
+            if (lane < qn - f) { Q.k[lane] = k; Q.c[lane] = cc; Q.pos[lane] = pp; }
+            qn -= f;
+        }
+        __syncwarp();
     }
-    __syncwarp();
-    hv_finish(H, Q, qn, b, ob, Sab, Sba, Pab, xS, R, lane, acc_a, acc_b);
-    __syncwarp();
     acc_b = warp_sum_u128(acc_b);
-    if (lane == 0 && acc_b) atomic_add_u128(acc + 2 * (int64_t)b, acc_b);
+    if (lane == 0 && acc_b) atomic_add_u128(acc + 2 * (int64_t)B.b, acc_b);
 }
 
 // groups of 32 nodes are handed out by an atomic counter (next_group, zeroed before
@@ -1734,7 +1756,7 @@ __global__ void __launch_bounds__(kThreads, 3) p3_heavy_kernel(
         u128 acc_a = 0;
         for (int32_t k0 = 0; k0 < dA; k0 += kHvIds) {
             const int32_t cnt = min(kHvIds, dA - k0);
-            const uint32_t slots = max(64u, dev_pow2_at_least(2u * (uint32_t)cnt)), mask = slots - 1;
+            const uint32_t slots = max(128u, dev_pow2_at_least(4u * (uint32_t)cnt)), mask = slots - 1;
             for (uint32_t i = tid; i < slots; i += kThreads) H.key[i] = -1;
             if (tid == 0) H.next_b = 0;
             __syncthreads();
@@ -1742,25 +1764,34 @@ __global__ void __launch_bounds__(kThreads, 3) p3_heavy_kernel(
                 const int64_t sl = bA + k0 + i;
                 const int32_t c = xcol[sl];
                 uint32_t h = hv_hash(c, mask), it = 0;
-                // the ids are distinct and the table at most half full: a free slot is found
+                // the ids are distinct and the table at most a quarter full: a free slot is found
                 for (; it <= mask && atomicCAS(&H.key[h], -1, c) != -1; ++it) h = (h + 1) & mask;
                 if (it <= mask) H.slot_pos[h] = (uint16_t)i;
                 else atomicOr(R.err, 64);
                 const df sac = xS[sl], sca = R.get(sl, c, a);
-                H.sac[i] = sac;
                 H.sca[i] = sca;
                 H.pac[i] = df_add(sac, sca);
             }
             __syncthreads();
             const int32_t lo_id = xcol[bA + k0], hi_id = xcol[bA + k0 + cnt - 1];
             const bool cut = dA > kHvIds;
-            while (true) {
+            // the warp claims out-neighbours one at a time; the next one's data is loaded
+            // while the current one is walked
+            auto claim = [&]() {
                 int32_t j = 0;
                 if (lane == 0) j = atomicAdd(&H.next_b, 1);
-                j = __shfl_sync(FULL, j, 0);
-                if (j >= nb) break;
-                hv_walk_b(H, Q, a, bA + eb0 + j, cut, lo_id, hi_id, mask, xoff, xcol, xS, R, xout, acc, lane,
-                          acc_a);
+                return __shfl_sync(FULL, j, 0);
+            };
+            int32_t j = claim();
+            HvB cur{};
+            if (j < nb) cur = hv_load_b(a, bA + eb0 + j, cut, lo_id, hi_id, xoff, xcol, xS, R, xout);
+            while (j < nb) {
+                const int32_t jn = claim();
+                HvB nxt{};
+                if (jn < nb) nxt = hv_load_b(a, bA + eb0 + jn, cut, lo_id, hi_id, xoff, xcol, xS, R, xout);
+                hv_walk_b(H, Q, cur, bA + k0, lo_id, hi_id, mask, xcol, xS, R, acc, lane, acc_a);
+                j = jn;
+                cur = nxt;
             }
             __syncthreads();
             // c's sums of the chunk to the accumulators, zeroed for the next chunk
