@@ -321,7 +321,7 @@ double rso_omega(const rso_graph *g, int32_t v, int32_t c) { return omega(g, v, 
 
 /* R(u) for the listed nodes; strict != 0 drops closed triangles with C(v) = C(u) */
 void rso_scores(const rso_graph *g, const int32_t *ids, int64_t m, int strict, double *out) {
-#pragma omp parallel for schedule(dynamic, 16)
+#pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < m; ++i) {
         int32_t u = ids[i];
         int64_t d = g->off[u + 1] - g->off[u];
@@ -331,7 +331,7 @@ void rso_scores(const rso_graph *g, const int32_t *ids, int64_t m, int strict, d
 }
 
 void rso_scores_all(const rso_graph *g, int strict, double *out) {
-#pragma omp parallel for schedule(dynamic, 64)
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t u = 0; u < g->n; ++u) {
         int64_t d = g->off[u + 1] - g->off[u];
         out[u] = (d < 2 || g->wmax <= 0.0) ? 0.0 : rso_finish(score_sum(g, (int32_t)u, strict), d, g->wmax);
