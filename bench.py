@@ -56,10 +56,12 @@ def parse():
     ap.add_argument("--profile-json", default="")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch parameters")
     ap.add_argument("--gen-workers", type=int, default=0, help="processes generating a batch (0: all cores)")
-    ap.add_argument("--serve-requests", type=int, default=20000, help="serve: requests per incremental pass")
-    ap.add_argument("--serve-plain", type=int, default=1500, help="serve: requests per plain (full) pass")
+    ap.add_argument("--serve-requests", type=int, default=100000,
+                    help="serve: incremental requests over the whole rate sweep")
+    ap.add_argument("--serve-plain", type=int, default=2000, help="serve: plain (full) requests per rate point")
     ap.add_argument("--serve-slots", type=int, default=16)
-    ap.add_argument("--serve-load", type=float, default=0.5, help="serve: open-loop rate as a fraction of capacity")
+    ap.add_argument("--serve-points", type=int, default=8, help="serve: Poisson rates of the shared sweep")
+    ap.add_argument("--serve-slo-ms", type=float, default=10.0, help="serve: the p99 latency objective")
     return ap.parse_args()
 
 
@@ -724,29 +726,29 @@ def serve_pass(srv, reqs, rate):
     return time.perf_counter() - t0, np.array(lat), np.array(paths), np.array(stats)
 
 
-def serve_mode(rsgpu, gens, mode, reqs_cap, reqs_open, args):
+def _pcts(lat):
     import numpy as np
+    pct = lambda q: float(np.percentile(lat, q)) if len(lat) else None
+    return {"p50_ms": pct(50), "p99_ms": pct(99), "p999_ms": pct(99.9)}
+
+
+def serve_open(rsgpu, gens, mode, reqs_cap, args):
+    """A server of `mode`: warm-up, then its closed-loop capacity (all requests queued at once)."""
     srv = rsgpu.Server([rsgpu.Graph.from_generated(g, validate=False) for g in gens], max_slots=args.serve_slots,
                        budget_bytes=SERVE_BUDGET, max_top_k=SERVE_TOPK, mode=mode)
     serve_pass(srv, reqs_cap[:64], None)                  # warm-up: kernels, copies, slots
-    wall, lat_c, paths_c, st_c = serve_pass(srv, reqs_cap, None)
-    capacity = len(reqs_cap) / wall
-    rate = args.serve_load * capacity
-    wall_o, lat, paths, st = serve_pass(srv, reqs_open, rate)
-    info = srv.info()
-    srv.close()
-    pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
-    return {"mode": mode, "slots": info["slots"], "device_bytes": info["bytes"],
-            "closed_loop": {"requests": len(reqs_cap), "requests_per_s": capacity,
-                            "incremental_share": float(paths_c.mean()) if len(paths_c) else None,
-                            "errors": int((st_c != 0).sum())},
-            "open_loop": {"requests": len(reqs_open), "offered_rps": rate, "achieved_rps": len(reqs_open) / wall_o,
-                          "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "p999_ms": pct(lat, 99.9),
-                          "incremental_share": float(paths.mean()) if len(paths) else None,
-                          "errors": int((st != 0).sum())}}
+    wall, lat, paths, st = serve_pass(srv, reqs_cap, None)
+    closed = {"requests": len(reqs_cap), "requests_per_s": len(reqs_cap) / wall,
+              "incremental_share": float(paths.mean()) if len(paths) else None, "errors": int((st != 0).sum())}
+    return srv, closed
 
 
 def run_serve(args):
+    """Serving: the same Poisson rate grid offered to the incremental server and to plain
+    per-request full rescoring.  Each mode's closed-loop capacity is measured first; the grid
+    runs from a fifth of the plain capacity to 1.1x the incremental one.  Each rate point is
+    an open-loop pass (latency = completion - scheduled arrival); the throughput at the p99
+    objective is the highest achieved rate of a point whose p99 stays within it."""
     import numpy as np
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -759,17 +761,41 @@ def run_serve(args):
         G = rsgpu.Graph.from_generated(g, validate=False)
         base.append(G.score().cpu().numpy())
         G.close()
-    n_inc, n_plain = args.serve_requests, args.serve_plain
-    reqs_inc_c = serve_requests(gens, base, n_inc, 501)
-    reqs_inc_o = serve_requests(gens, base, n_inc, 502)
+    P = max(2, args.serve_points)
+    per_point = max(200, args.serve_requests // P)
+    reqs_cap = serve_requests(gens, base, 4000, 501)
+    reqs = serve_requests(gens, base, per_point * P, 502)
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
-    inc = serve_mode(rsgpu, gens, "incremental", reqs_inc_c, reqs_inc_o, args)
-    plain = serve_mode(rsgpu, gens, "full", reqs_inc_c[:n_plain], reqs_inc_o[:n_plain], args)
+    inc_srv, inc_closed = serve_open(rsgpu, gens, "incremental", reqs_cap, args)
+    plain_srv, plain_closed = serve_open(rsgpu, gens, "full", reqs_cap[:1500], args)
+    c_inc, c_plain = inc_closed["requests_per_s"], plain_closed["requests_per_s"]
+    rates = list(np.geomspace(0.2 * c_plain, 1.1 * max(c_inc, c_plain), P))
+    sweep = []
+    for i, r in enumerate(rates):
+        point = {"offered_rps": float(r)}
+        for name, srv, cnt in (("incremental", inc_srv, per_point), ("plain", plain_srv, min(per_point, args.serve_plain))):
+            part = reqs[i * per_point:i * per_point + cnt]
+            wall, lat, paths, st = serve_pass(srv, part, float(r))
+            d = {"requests": len(part), "achieved_rps": len(part) / wall, **_pcts(lat),
+                 "errors": int((st != 0).sum())}
+            if name == "incremental":
+                d["incremental_share"] = float(paths.mean()) if len(paths) else None
+            point[name] = d
+        sweep.append(point)
+    inc_info, plain_info = inc_srv.info(), plain_srv.info()
+    inc_srv.close()
+    plain_srv.close()
     clk = clocks.stop()
+
+    def at_slo(name):
+        ok = [p[name]["achieved_rps"] for p in sweep if p[name]["p99_ms"] is not None and p[name]["p99_ms"] <= args.serve_slo_ms]
+        return max(ok) if ok else 0.0
+
+    inc_slo, plain_slo = at_slo("incremental"), at_slo("plain")
     out = {
-        "metric": "served what-if requests/s (removals + rescoring + top-100), closed loop",
-        "value": inc["closed_loop"]["requests_per_s"], "unit": "requests/s", "n_gpus": 1,
-        "steps": n_inc, "warmup": 64, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": "served what-if requests/s at p99 <= %g ms (removals + rescoring + top-100)" % args.serve_slo_ms,
+        "value": inc_slo, "unit": "requests/s", "n_gpus": 1,
+        "steps": per_point * P, "warmup": 64, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": "serve-%d-graphs" % len(gens), "graphs": len(gens),
                    "n_total": int(sum(g.n for g in gens)), "m_total": int(sum(g.m for g in gens)),
@@ -777,9 +803,15 @@ def run_serve(args):
                             "degrees 2.5 on [8, 5000], mixing 0.2) + the 1M-node graph",
                    "requests": "k log-uniform on [1, 10000] (<= n/10), half nodes / half edges, 70% of targets "
                                "among the graph's top-1% scorers; top-100 each; what-if on the base graph",
-                   "budget_bytes": SERVE_BUDGET, "slots": args.serve_slots, "open_loop_load": args.serve_load},
-        "serving": {"incremental": inc, "plain_full_rescoring": plain},
-        "vs_plain_closed_loop": inc["closed_loop"]["requests_per_s"] / plain["closed_loop"]["requests_per_s"],
+                   "budget_bytes": SERVE_BUDGET, "slots": args.serve_slots, "slo_p99_ms": args.serve_slo_ms,
+                   "rate_points": P, "incremental_requests_per_point": per_point,
+                   "plain_requests_per_point": min(per_point, args.serve_plain)},
+        "serving": {"incremental": {"closed_loop": inc_closed, "slots": inc_info["slots"], "device_bytes": inc_info["bytes"],
+                                    "requests_per_s_at_slo": inc_slo},
+                    "plain_full_rescoring": {"closed_loop": plain_closed, "slots": plain_info["slots"],
+                                             "device_bytes": plain_info["bytes"], "requests_per_s_at_slo": plain_slo},
+                    "sweep": sweep},
+        "vs_plain_at_slo": inc_slo / plain_slo if plain_slo else None,
         "clocks": clk,
     }
     if rank == 0:

@@ -143,8 +143,25 @@ __device__ __forceinline__ void fixed_part(float f, int frac, uint64_t &lo, uint
     hi = h;
 }
 // round-toward-zero of each part of a * 2^frac, summed, for a >= 0 as an unsigned
-// 128-bit integer (0 when the sum is negative)
+// 128-bit integer (0 when the sum is negative).  The usual case (a.hi a positive normal
+// float whose scaled significand ends below bit 64, a.lo small enough for 63 bits) takes
+// a short path with the same result.
 __device__ __forceinline__ u128 df_to_fixed(df a, int frac) {
+    const uint32_t bh = __float_as_uint(a.hi), bl = __float_as_uint(a.lo);
+    const int eh = (int)(bh >> 23);                // with the sign bit: < 255 means a.hi >= 0, finite
+    const int el = (int)((bl >> 23) & 0xFF);
+    const int qh = eh - 150 + frac, ql = el - 150 + frac;
+    if (eh > 0 && eh < 255 && qh > 0 && qh < 64 && ql < 40) {
+        const uint64_t mh = (uint64_t)((bh & 0x7FFFFFu) | 0x800000u);
+        const uint64_t l = mh << qh, h = mh >> (64 - qh);
+        const uint64_t ml = (uint64_t)((bl & 0x7FFFFFu) | 0x800000u);
+        int64_t lp = el == 0 ? 0 : (ql >= 0 ? (int64_t)(ml << ql) : (ql > -32 ? (int64_t)(ml >> -ql) : 0));
+        if (bl >> 31) lp = -lp;
+        const uint64_t l2 = l + (uint64_t)lp;
+        const uint64_t h2 = h + (lp < 0 ? ~0ull : 0ull) + (l2 < l ? 1ull : 0ull);
+        if ((int64_t)h2 < 0) return 0;
+        return ((u128)h2 << 64) | l2;
+    }
     uint64_t l1, h1, l2, h2;
     fixed_part(a.hi, frac, l1, h1);
     fixed_part(a.lo, frac, l2, h2);

@@ -1380,8 +1380,8 @@ __device__ __forceinline__ int64_t find_in_list(const int32_t *xcol, int64_t lo,
 
 // Heavy nodes: a wedge walk, one CTA per task.  A task is a heavy node a with a block
 // of kHvBlock of its out-neighbours b.  The CTA stages a's out-list A (sorted by id),
-// kHvIds ids at a time, as a shared-memory hash table (id -> position in the chunk, at
-// most a quarter full) beside the value S(c->a) and the sum S(a->c) + S(c->a) for
+// kHvIds ids at a time, as a shared-memory hash table of 4-slot buckets (id -> position
+// in the chunk, at most a quarter of the slots used) beside the value S(c->a) and the sum S(a->c) + S(c->a) for
 // every c of the chunk.  Its warps then take the task's out-neighbours b one at a time: a warp
 // streams b's out-list (the nodes c ranked above b), coalesced, and looks every c up in
 // the table; a hit closes the triangle {a, b, c}, which is met once, at its
@@ -1412,7 +1412,7 @@ struct HvQueue {
     int32_t pos[kHvQ];                        // c's position in the chunk of A
 };
 struct P3Heavy {
-    int32_t key[kHvSlots];                    // the chunk's ids (-1: empty slot)
+    int4 key[kHvSlots / 4];                   // the chunk's ids, 4 slots per bucket (-1: empty slot)
     uint16_t slot_pos[kHvSlots];              // their positions in the chunk
     df sca[kHvIds], pac[kHvIds];              // S(c->a), S(a->c) + S(c->a)
     unsigned long long clo[kHvIds], chi[kHvIds];   // c's terms of the chunk: low, high words
@@ -1437,15 +1437,18 @@ __device__ __forceinline__ uint32_t hv_hash(int32_t c, uint32_t mask) {
     return (((uint32_t)c * 0x9E3779B1u) >> 16) & mask;
 }
 
-// position of id c in the staged chunk, or -1 (three quarters of the slots are empty,
-// so the probe ends at one long before it could visit every slot)
-__device__ __forceinline__ int32_t hv_find(const P3Heavy &H, int32_t c, uint32_t mask) {
-    uint32_t h = hv_hash(c, mask);
-    for (uint32_t it = 0; it <= mask; ++it) {
-        const int32_t k = H.key[h];
-        if (k == c) return H.slot_pos[h];
-        if (k < 0) return -1;
-        h = (h + 1) & mask;
+// position of id c in the staged chunk, or -1.  The table is buckets of 4 slots, filled
+// in slot order, at most a quarter of the slots used: one 16-byte load of the home bucket
+// settles nearly every lookup (a key is there, or the bucket has an empty slot); a full
+// home bucket (under 1% of them) sends the probe on to the next buckets.
+__device__ __forceinline__ int32_t hv_find(const P3Heavy &H, int32_t c, uint32_t bmask) {
+    uint32_t bk = hv_hash(c, bmask);
+    for (uint32_t it = 0; it <= bmask; ++it) {
+        const int4 q = H.key[bk];
+        const int j = q.x == c ? 0 : q.y == c ? 1 : q.z == c ? 2 : q.w == c ? 3 : -1;
+        if (j >= 0) return H.slot_pos[4 * bk + j];
+        if (q.w < 0) return -1;
+        bk = (bk + 1) & bmask;
     }
     return -1;
 }
@@ -1756,17 +1759,25 @@ __global__ void __launch_bounds__(kThreads, 3) p3_heavy_kernel(
         u128 acc_a = 0;
         for (int32_t k0 = 0; k0 < dA; k0 += kHvIds) {
             const int32_t cnt = min(kHvIds, dA - k0);
-            const uint32_t slots = max(128u, dev_pow2_at_least(4u * (uint32_t)cnt)), mask = slots - 1;
-            for (uint32_t i = tid; i < slots; i += kThreads) H.key[i] = -1;
+            const uint32_t buckets = max(32u, dev_pow2_at_least((uint32_t)cnt)), mask = buckets - 1;
+            for (uint32_t i = tid; i < buckets; i += kThreads) H.key[i] = make_int4(-1, -1, -1, -1);
             if (tid == 0) H.next_b = 0;
             __syncthreads();
             for (int32_t i = tid; i < cnt; i += kThreads) {
                 const int64_t sl = bA + k0 + i;
                 const int32_t c = xcol[sl];
-                uint32_t h = hv_hash(c, mask), it = 0;
-                // the ids are distinct and the table at most a quarter full: a free slot is found
-                for (; it <= mask && atomicCAS(&H.key[h], -1, c) != -1; ++it) h = (h + 1) & mask;
-                if (it <= mask) H.slot_pos[h] = (uint16_t)i;
+                // the first free slot of the first bucket with one, from the home bucket on
+                // (the ids are distinct and at most a quarter of the slots are used, so one
+                // is found); slots fill in order, so a bucket with an empty last slot has
+                // room and holds every key that hashes to it
+                int32_t *keys = reinterpret_cast<int32_t *>(H.key);
+                uint32_t bk = hv_hash(c, mask), slot = 4u * kHvSlots;
+                for (uint32_t it = 0; it <= mask && slot >= 4u * kHvSlots; ++it) {
+                    for (int j = 0; j < 4; ++j)
+                        if (atomicCAS(&keys[4 * bk + j], -1, c) == -1) { slot = 4 * bk + j; break; }
+                    bk = (bk + 1) & mask;
+                }
+                if (slot < 4u * kHvSlots) H.slot_pos[slot] = (uint16_t)i;
                 else atomicOr(R.err, 64);
                 const df sac = xS[sl], sca = R.get(sl, c, a);
                 H.sca[i] = sca;
