@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-json", default="")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch parameters")
+    ap.add_argument("--tuning", default="", help="launch parameters to start from, e.g. p1_stage=1,p3_mirror=0")
     ap.add_argument("--gen-workers", type=int, default=0, help="processes generating a batch (0: all cores)")
     ap.add_argument("--serve-requests", type=int, default=100000,
                     help="serve: incremental requests over the whole rate sweep")
@@ -450,6 +451,8 @@ def run_ours(args):
         if kk:
             G.topk_into(scores, kk, ids, vals)
 
+    if args.tuning:
+        G.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))})
     tuning, autotune = G.tuning(), None
     if not args.no_autotune:
         tuning, best_ms, tried = G.autotune(topk=kk, reps=W.tune_reps)

@@ -254,6 +254,10 @@ rs_status rs_launch_count(const rs_graph *g, int64_t *launches);
  *                float pairs); 0: the listing looks the reverse values of
  *                each triangle up in in-lists (fewer searches when G_x has
  *                few triangles per edge)
+ *   p1_stage     1: the small-row tiles of the first pass copy their          {0, 1}
+ *                columns, then the neighbours' labels, into shared memory
+ *                with asynchronous copies (cp.async) before matching; 0:
+ *                the loads are pipelined in registers two chunks ahead
  * Powers of two are required where a set is given.
  */
 typedef struct {
@@ -266,6 +270,7 @@ typedef struct {
     int32_t p2_cta_threads;
     int32_t ctas_per_sm;
     int32_t p3_mirror;
+    int32_t p1_stage;
 } rs_tuning;
 
 /* rs_default_tuning -- the parameters a new graph starts with. */

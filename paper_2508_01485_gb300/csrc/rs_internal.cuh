@@ -97,6 +97,7 @@ inline rs_tuning default_tuning_value() {
     t.p2_cta_threads = 1024;
     t.ctas_per_sm = 8;
     t.p3_mirror = 1;
+    t.p1_stage = 0;
     return t;
 }
 }  // namespace rs

@@ -153,6 +153,112 @@ struct SmallTile {
     int32_t nx[32];                 // cross list fill
 };
 
+// one chunk of up to 32 tile entries, entry e0 + lane in this lane (act): its row r, its
+// neighbour x and x's label c; the own-community counts, the cross lists and the
+// (row, community) groups are updated
+__device__ __forceinline__ void p1_small_chunk(SmallTile &T, bool act, int32_t r, int32_t x, int32_t c,
+                                               int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab, int lane) {
+    bool own = act && c == T.cv[r];
+    bool foreign = act && !own;
+    unsigned om = __ballot_sync(FULL, own), fm = __ballot_sync(FULL, foreign);
+    unsigned gown = 0, grow = 0;
+    if (own) gown = __match_any_sync(om, r);
+    if (foreign) grow = __match_any_sync(fm, r);
+    int32_t xbase = foreign ? T.nx[r] : 0;
+    __syncwarp();
+    if (own && lane == __ffs(gown) - 1) T.own[r] += __popc(gown);
+    if (foreign) {
+        int64_t p = T.rb[r] + xbase + __popc(grow & lanemask_lt());
+        cl_col[p] = x;
+        cl_lab[p] = c;
+        if (lane == __ffs(grow) - 1) T.nx[r] = xbase + __popc(grow);
+        unsigned long long key = ((unsigned long long)(uint32_t)r << 32) | (uint32_t)c;
+        unsigned gc = __match_any_sync(fm, key);
+        if (lane == __ffs(gc) - 1) {
+            uint32_t slot = atomicAdd(&T.nf[r], 1u);
+            T.flab[slot][r] = c;
+            T.fcnt[slot][r] = (uint8_t)__popc(gc);
+        }
+    }
+    __syncwarp();
+}
+
+// lane `lane` finishes row v (degree d, label cv) of the tile: aggregates, weights, s_v
+__device__ __forceinline__ void p1_small_finish(SmallTile &T, int32_t v, int32_t d, int32_t cv, const Batch &B,
+                                                const uint64_t *__restrict__ LG, NodeRec *__restrict__ rec,
+                                                int32_t *__restrict__ Lall, RowSum *__restrict__ rsum, int lane) {
+    int32_t gi = graph_of(B, v);
+    float wcur = current_wmax(&B.wmax[gi]);
+    uint32_t own = T.own[lane];
+    int nf = (int)T.nf[lane];
+    // merge a community listed from two chunks
+    for (int j = 1; j < nf; ++j)
+        for (int j2 = 0; j2 < j; ++j2)
+            if (T.fcnt[j2][lane] && T.flab[j2][lane] == T.flab[j][lane]) {
+                T.fcnt[j2][lane] += T.fcnt[j][lane];
+                T.fcnt[j][lane] = 0;
+                break;
+            }
+    u128 X = (u128)own * LG[own];
+    uint64_t seen = own ? (1ull << own) : 0ull;
+    uint32_t L = own > 0 ? 1u : 0u;
+    for (int j = 0; j < nf; ++j) {
+        uint32_t f = T.fcnt[j][lane];
+        if (!f) continue;
+        X += (u128)f * LG[f];
+        seen |= 1ull << f;
+        ++L;
+    }
+    RowAgg a{(uint32_t)d, L, X};
+    store_rowsum(rsum, v, a);
+    bool want_max = row_may_raise_max(a.L, wcur);
+    df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
+    if (want_max) {
+        while (seen) {
+            uint32_t f = (uint32_t)(__ffsll((long long)seen) - 1);
+            df w = column_weight(a, f, LG);
+            if (f == own) wown = w;
+            cm = df_max(cm, w);
+            seen &= seen - 1;
+        }
+    } else if (own > 0) {
+        wown = column_weight(a, own, LG);
+    }
+    NodeRec rr;
+    df m = p1_row_result(a, own, cm, k_of(B, gi), LG, rr, cv, wown, want_max);
+    publish_max(B, gi, m, wcur);
+    rec[v] = rr;
+    Lall[v] = (int32_t)a.L;
+}
+
+// the tile's rows: lane l takes row rows[t0 + l]; prefix sums of the degrees, row starts
+// and labels into T; returns the tile's entry count D
+__device__ __forceinline__ int32_t p1_small_setup(SmallTile &T, const int64_t *__restrict__ off,
+                                                  const int32_t *__restrict__ lab, const int32_t *__restrict__ rows,
+                                                  int64_t nrows, int64_t t0, int lane, bool &have, int32_t &v,
+                                                  int32_t &d, int32_t &cv) {
+    int64_t i = t0 + lane;
+    have = i < nrows;
+    v = have ? rows[i] : 0;
+    int64_t b = have ? off[v] : 0;
+    d = have ? (int32_t)(off[v + 1] - b) : 0;
+    cv = have ? lab[v] : -1;
+    int32_t incl = d;
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    T.pre[lane + 1] = incl;
+    if (lane == 0) T.pre[0] = 0;
+    T.rb[lane] = b;
+    T.cv[lane] = cv;
+    T.own[lane] = 0;
+    T.nf[lane] = 0;
+    T.nx[lane] = 0;
+    __syncwarp();
+    return __shfl_sync(FULL, incl, 31);
+}
+
 __global__ void __launch_bounds__(kThreads) p1_small_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
     const int32_t *__restrict__ rows, int64_t nrows, Batch B, const uint64_t *__restrict__ LG,
@@ -164,26 +270,9 @@ __global__ void __launch_bounds__(kThreads) p1_small_kernel(
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t t0 = warp * 32; t0 < nrows; t0 += nwarps * 32) {
-        int64_t i = t0 + lane;
-        bool have = i < nrows;
-        int32_t v = have ? rows[i] : 0;
-        int64_t b = have ? off[v] : 0;
-        int32_t d = have ? (int32_t)(off[v + 1] - b) : 0;
-        int32_t cv = have ? lab[v] : -1;
-        int32_t incl = d;
-        for (int o = 1; o < 32; o <<= 1) {
-            int32_t y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        int32_t D = __shfl_sync(FULL, incl, 31);
-        T.pre[lane + 1] = incl;
-        if (lane == 0) T.pre[0] = 0;
-        T.rb[lane] = b;
-        T.cv[lane] = cv;
-        T.own[lane] = 0;
-        T.nf[lane] = 0;
-        T.nx[lane] = 0;
-        __syncwarp();
+        bool have;
+        int32_t v, d, cv;
+        const int32_t D = p1_small_setup(T, off, lab, rows, nrows, t0, lane, have, v, d, cv);
         // entry e of the tile: its row (last r with pre[r] <= e) and its CSR column
         auto locate = [&](int32_t e, int32_t &r, int32_t &x) {
             int32_t lo = 0, hi = 32;
@@ -206,75 +295,71 @@ __global__ void __launch_bounds__(kThreads) p1_small_kernel(
             if (e0 + 32 + lane < D) cB = lab[xB];
             if (e0 + 64 + lane < D) locate(e0 + 64 + lane, rC, xC);
             rA = rB; xA = xB; cA = cB; rB = rC; xB = xC;
-            bool own = act && c == T.cv[r];
-            bool foreign = act && !own;
-            unsigned om = __ballot_sync(FULL, own), fm = __ballot_sync(FULL, foreign);
-            unsigned gown = 0, grow = 0;
-            if (own) gown = __match_any_sync(om, r);
-            if (foreign) grow = __match_any_sync(fm, r);
-            int32_t xbase = foreign ? T.nx[r] : 0;
-            __syncwarp();
-            if (own && lane == __ffs(gown) - 1) T.own[r] += __popc(gown);
-            if (foreign) {
-                int64_t p = T.rb[r] + xbase + __popc(grow & lanemask_lt());
-                cl_col[p] = x;
-                cl_lab[p] = c;
-                if (lane == __ffs(grow) - 1) T.nx[r] = xbase + __popc(grow);
-                unsigned long long key = ((unsigned long long)(uint32_t)r << 32) | (uint32_t)c;
-                unsigned gc = __match_any_sync(fm, key);
-                if (lane == __ffs(gc) - 1) {
-                    uint32_t slot = atomicAdd(&T.nf[r], 1u);
-                    T.flab[slot][r] = c;
-                    T.fcnt[slot][r] = (uint8_t)__popc(gc);
-                }
-            }
-            __syncwarp();
+            p1_small_chunk(T, act, r, x, c, cl_col, cl_lab, lane);
         }
         // lane `lane` finishes row `lane` of the tile
-        if (have) {
-            int32_t gi = graph_of(B, v);
-            float wcur = current_wmax(&B.wmax[gi]);
-            uint32_t own = T.own[lane];
-            int nf = (int)T.nf[lane];
-            // merge a community listed from two chunks
-            for (int j = 1; j < nf; ++j)
-                for (int j2 = 0; j2 < j; ++j2)
-                    if (T.fcnt[j2][lane] && T.flab[j2][lane] == T.flab[j][lane]) {
-                        T.fcnt[j2][lane] += T.fcnt[j][lane];
-                        T.fcnt[j][lane] = 0;
-                        break;
-                    }
-            u128 X = (u128)own * LG[own];
-            uint64_t seen = own ? (1ull << own) : 0ull;
-            uint32_t L = own > 0 ? 1u : 0u;
-            for (int j = 0; j < nf; ++j) {
-                uint32_t f = T.fcnt[j][lane];
-                if (!f) continue;
-                X += (u128)f * LG[f];
-                seen |= 1ull << f;
-                ++L;
+        if (have) p1_small_finish(T, v, d, cv, B, LG, rec, Lall, rsum, lane);
+        __syncwarp();
+    }
+}
+
+// The same tiles with the loads staged in shared memory by asynchronous copies
+// (p1_stage = 1): lane l copies its row's columns (cp.async, 4 bytes each) to the tile's
+// entry range [pre[l], pre[l+1]) and writes the entries' row number; after the wait the
+// lanes copy the labels of those neighbours in the same way (a gather by cp.async);
+// the chunks then read row, column and label from shared memory.  A warp keeps its
+// tile's entries (at most 32 x 32) and their labels in flight at once instead of two
+// chunks ahead.  Dynamic shared memory: kStageWarps x (SmallTile + SmallStage).
+constexpr int kStageWarps = 4;
+struct SmallStage {
+    int32_t col[kSmallMax * 32];
+    int32_t lab[kSmallMax * 32];
+    uint8_t row[kSmallMax * 32];
+};
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kStageWarps * 32) p1_small_staged_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ lab,
+    const int32_t *__restrict__ rows, int64_t nrows, Batch B, const uint64_t *__restrict__ LG,
+    NodeRec *__restrict__ rec, int32_t *__restrict__ Lall,
+    RowSum *__restrict__ rsum, int32_t *__restrict__ cl_col, int32_t *__restrict__ cl_lab) {
+    extern __shared__ __align__(16) unsigned char st_smem[];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    SmallTile &T = reinterpret_cast<SmallTile *>(st_smem)[wid];
+    SmallStage &S = reinterpret_cast<SmallStage *>(st_smem + kStageWarps * sizeof(SmallTile))[wid];
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t0 = warp * 32; t0 < nrows; t0 += nwarps * 32) {
+        bool have;
+        int32_t v, d, cv;
+        const int32_t D = p1_small_setup(T, off, lab, rows, nrows, t0, lane, have, v, d, cv);
+        {
+            const int32_t p0 = T.pre[lane];
+            const int32_t *src = col + T.rb[lane];
+            for (int32_t j = 0; j < d; ++j) {
+                cp_async4(&S.col[p0 + j], src + j);
+                S.row[p0 + j] = (uint8_t)lane;
             }
-            RowAgg a{(uint32_t)d, L, X};
-            store_rowsum(rsum, v, a);
-            bool want_max = row_may_raise_max(a.L, wcur);
-            df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
-            if (want_max) {
-                while (seen) {
-                    uint32_t f = (uint32_t)(__ffsll((long long)seen) - 1);
-                    df w = column_weight(a, f, LG);
-                    if (f == own) wown = w;
-                    cm = df_max(cm, w);
-                    seen &= seen - 1;
-                }
-            } else if (own > 0) {
-                wown = column_weight(a, own, LG);
-            }
-            NodeRec rr;
-            df m = p1_row_result(a, own, cm, k_of(B, gi), LG, rr, cv, wown, want_max);
-            publish_max(B, gi, m, wcur);
-            rec[v] = rr;
-            Lall[v] = (int32_t)a.L;
+            cp_async_wait_all();
+            __syncwarp();
+            for (int32_t e = lane; e < D; e += 32) cp_async4(&S.lab[e], lab + S.col[e]);
+            cp_async_wait_all();
+            __syncwarp();
         }
+        for (int32_t e0 = 0; e0 < D; e0 += 32) {
+            const int32_t e = e0 + lane;
+            const bool act = e < D;
+            const int32_t r = act ? S.row[e] : 0, x = act ? S.col[e] : -1, c = act ? S.lab[e] : -1;
+            p1_small_chunk(T, act, r, x, c, cl_col, cl_lab, lane);
+        }
+        if (have) p1_small_finish(T, v, d, cv, B, LG, rec, Lall, rsum, lane);
         __syncwarp();
     }
 }
@@ -1971,6 +2056,8 @@ int rs::prepare_score_kernels() {
     RS_CUDA_TRY(cudaFuncSetAttribute(p2_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, p2_mid_smem));
     RS_CUDA_TRY(cudaFuncSetAttribute(p3_heavy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sizeof(P3Heavy)));
+    RS_CUDA_TRY(cudaFuncSetAttribute(p1_small_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kStageWarps * (sizeof(SmallTile) + sizeof(SmallStage)))));
     done = 1;
     return 0;
 }
@@ -2050,9 +2137,15 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_LAUNCHED(g, g->aux[4], "p1_mid");
     }
     if (g->n_small) {
-        p1_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[0]>>>(
-            g->off, g->col, g->lab, g->rows_small, g->n_small, B, g->LG, g->rec, g->Lall,
-            g->rsum, g->cl_col, g->cl_lab);
+        if (g->tune.p1_stage)
+            p1_small_staged_kernel<<<grid_for(g->n_small, kStageWarps * 32, cps), kStageWarps * 32,
+                                     kStageWarps * (sizeof(SmallTile) + sizeof(SmallStage)), g->aux[0]>>>(
+                g->off, g->col, g->lab, g->rows_small, g->n_small, B, g->LG, g->rec, g->Lall,
+                g->rsum, g->cl_col, g->cl_lab);
+        else
+            p1_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[0]>>>(
+                g->off, g->col, g->lab, g->rows_small, g->n_small, B, g->LG, g->rec, g->Lall,
+                g->rsum, g->cl_col, g->cl_lab);
         RS_LAUNCHED(g, g->aux[0], "p1_small");
     }
     if (int rc = join_aux(g, s, rs_graph::kAux)) return rc;

@@ -39,6 +39,8 @@ static int check_tuning(const rs_tuning &t) {
         return fail(RS_EINVAL, "rs_tuning: ctas_per_sm must be in [1, 32]");
     if (t.p3_mirror != 0 && t.p3_mirror != 1)
         return fail(RS_EINVAL, "rs_tuning: p3_mirror must be 0 or 1");
+    if (t.p1_stage != 0 && t.p1_stage != 1)
+        return fail(RS_EINVAL, "rs_tuning: p1_stage must be 0 or 1");
     return 0;
 }
 
@@ -151,6 +153,7 @@ extern "C" rs_status rs_autotune(rs_graph *g, double *scores, int32_t topk_k, in
         {&rs_tuning::p2_cta_threads, {256, 512, 1024}},
         {&rs_tuning::hub_chunk, {1024, 4096, 16384}},
         {&rs_tuning::p3_mirror, {0, 1}},
+        {&rs_tuning::p1_stage, {0, 1}},
     };
     for (size_t a = 0; !rc && a < axes.size(); ++a) {
         for (int32_t v : axes[a].values) {
