@@ -72,6 +72,8 @@ def workload(name):
         return graphgen.dcsbm_1m()
     if name == "dcsbm-8m":
         return graphgen.dcsbm_8m()
+    if name == "dcsbm-1m-dmin2":
+        return graphgen.dcsbm_1m_dmin2()
     if name == "sbm-2k":
         return graphgen.sbm_2000()
     if name.startswith("dcsbm-hub-"):
