@@ -361,7 +361,7 @@ rs_status rs_awcc(rs_graph *g, const int32_t *nodes, int64_t m, const int64_t *d
  *                           change (bit-identical to a full rescoring); requests
  *                           whose touched rows exceed a slot's buffers, or whose
  *                           touched rows' degrees (bounded from the removed
- *                           nodes' 2-hop degree sums) exceed 1/48 of the CSR
+ *                           nodes' 2-hop degree sums) exceed 1/4 of the CSR
  *                           entries, are rescored in full instead;
  *     RS_SERVE_FULL         every request restores a full copy of its graph,
  *                           applies the removals and rescores it completely.

@@ -2170,8 +2170,26 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         RS_LAUNCHED(g, s, "strict_pairs");
     }
     // ---- P2: every row class on its own stream; the many-short-rows kernels on the
-    //      low-priority streams 0 and 1, the rows with long chains on the others
+    //      low-priority streams 0 and 1, the rows with long chains on the others.  The hub
+    //      chain (three dependent kernels, the longest of the phase on hub-skewed graphs)
+    //      is issued first, so that its blocks are dispatched ahead of the other classes'
     if (int rc = fork_aux(g, s)) return rc;
+    if (g->n_hubs) {
+        hub_p2_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
+            g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
+            g->hkey, g->hq,
+            g->hitem_out, g->hitem_in, err);
+        RS_LAUNCHED(g, g->aux[3], "hub_p2_insert");
+        hub_p2_sigma_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, g->aux[3]>>>(
+            g->hubs, g->n_hubs, g->LG, g->hagg, g->off, g->hkey, g->hcnt, g->hsig, g->hitem_out, g->hitem_in,
+            g->xout, g->xin);
+        RS_LAUNCHED(g, g->aux[3], "hub_p2_sigma");
+        hub_p2_emit_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
+            g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
+            g->hkey, g->hcnt,
+            g->hq, g->hsig, g->hitem_out, g->hitem_in, g->acc, g->xoff, g->xcol, g->xS, err, SX);
+        RS_LAUNCHED(g, g->aux[3], "hub_p2_emit");
+    }
     if (g->n_small) {
         p2_small_kernel<32><<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[0]>>>(
             g->off, g->rows_small, g->n_small, nullptr, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
@@ -2208,32 +2226,18 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->off, Lst(3), g->p2cnt + 3, B, g->tune.p2_cta_dx, 256, g->LG, g->rec, g->rsum, g->cl_col,
             g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 4);
         RS_LAUNCHED(g, g->aux[2], "p2_large_warp");
-        p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, smem512, g->aux[3]>>>(
+        // (with hubs, stream 3 carries the hub chain: these rows go beside p2_mid instead)
+        cudaStream_t sw = g->n_hubs ? g->aux[5] : g->aux[3];
+        p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, smem512, sw>>>(
             g->off, Lst(6), g->p2cnt + 6, B, g->tune.p2_cta_dx, 512, g->LG, g->rec, g->rsum, g->cl_col,
             g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 5);
-        RS_LAUNCHED(g, g->aux[3], "p2_large_warp_wide");
+        RS_LAUNCHED(g, sw, "p2_large_warp_wide");
         switch (g->tune.p2_cta_threads) {
         case 256: launch_p2_large<256>(g, B, err, p2_smem); break;
         case 512: launch_p2_large<512>(g, B, err, p2_smem); break;
         default: launch_p2_large<1024>(g, B, err, p2_smem); break;
         }
         RS_LAUNCHED(g, g->aux[4], "p2_large");
-    }
-    if (g->n_hubs) {
-        hub_p2_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
-            g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
-            g->hkey, g->hq,
-            g->hitem_out, g->hitem_in, err);
-        RS_LAUNCHED(g, g->aux[3], "hub_p2_insert");
-        hub_p2_sigma_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, g->aux[3]>>>(
-            g->hubs, g->n_hubs, g->LG, g->hagg, g->off, g->hkey, g->hcnt, g->hsig, g->hitem_out, g->hitem_in,
-            g->xout, g->xin);
-        RS_LAUNCHED(g, g->aux[3], "hub_p2_sigma");
-        hub_p2_emit_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
-            g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
-            g->hkey, g->hcnt,
-            g->hq, g->hsig, g->hitem_out, g->hitem_in, g->acc, g->xoff, g->xcol, g->xS, err, SX);
-        RS_LAUNCHED(g, g->aux[3], "hub_p2_emit");
     }
     if (int rc = join_aux(g, s, rs_graph::kAux)) return rc;
     // ---- P3: reverse values (mirror mode), then triangles
