@@ -1593,9 +1593,9 @@ __device__ __forceinline__ HvB hv_load_b(int32_t a, int64_t eb, bool cut, int32_
 // each trip loads and looks up kHvUnroll rows of 32 entries of b's out-list, queues the
 // hits, and finishes the queued triangles 32 at a time (at the end of the list, the
 // rest too); the finishing code is inlined once
-__device__ __forceinline__ void hv_walk_b(P3Heavy &H, HvQueue &Q, const HvB &B, int64_t aslot0, int32_t lo_id,
-                                          int32_t hi_id, uint32_t mask, const int32_t *xcol, const df *xS,
-                                          const Rev &R, unsigned long long *acc, int lane, u128 &acc_a) {
+__device__ __forceinline__ void hv_walk_b(P3Heavy &H, HvQueue &Q, const HvB &B, int64_t aslot0, uint32_t mask,
+                                          const int32_t *xcol, const df *xS, const Rev &R,
+                                          unsigned long long *acc, int lane, u128 &acc_a) {
     if (B.s >= B.e) return;
     const df Pab = df_add(B.Sab, B.Sba);
     int qn = 0;                                        // queued triangles (warp-uniform)
@@ -1607,9 +1607,24 @@ __device__ __forceinline__ void hv_walk_b(P3Heavy &H, HvQueue &Q, const HvB &B, 
             const int32_t k = j0 + u * 32 + lane;
             c[u] = k < B.e ? xcol[B.ob + k] : -1;
         }
+        // every row's home bucket is probed with no loop (b's out-list is already cut to
+        // the chunk's id range, so an id outside it simply misses); the rare lanes whose
+        // home bucket is full without their id probe on, in a branch the warp takes together
+        bool more = false;
 #pragma unroll
-        for (int u = 0; u < kHvUnroll; ++u)
-            pos[u] = (c[u] >= lo_id && c[u] <= hi_id) ? hv_find(H, c[u], mask) : -1;
+        for (int u = 0; u < kHvUnroll; ++u) {
+            const uint32_t bk = hv_hash(c[u], mask);
+            const int4 q = H.key[bk];
+            const int j = q.x == c[u] ? 0 : q.y == c[u] ? 1 : q.z == c[u] ? 2 : q.w == c[u] ? 3 : -1;
+            const bool valid = j0 + u * 32 + lane < B.e;
+            pos[u] = valid && j >= 0 ? (int32_t)H.slot_pos[4 * bk + j] : -1;
+            more |= valid && j < 0 && q.w >= 0;
+        }
+        if (__any_sync(FULL, more)) {
+#pragma unroll
+            for (int u = 0; u < kHvUnroll; ++u)
+                if (pos[u] < 0 && j0 + u * 32 + lane < B.e) pos[u] = hv_find(H, c[u], mask);
+        }
 #pragma unroll
         for (int u = 0; u < kHvUnroll; ++u) {
             const bool hit = pos[u] >= 0;
@@ -1885,7 +1900,7 @@ __global__ void __launch_bounds__(kThreads, 3) p3_heavy_kernel(
                 const int32_t jn = claim();
                 HvB nxt{};
                 if (jn < nb) nxt = hv_load_b(a, bA + eb0 + jn, cut, lo_id, hi_id, xoff, xcol, xS, R, xout);
-                hv_walk_b(H, Q, cur, bA + k0, lo_id, hi_id, mask, xcol, xS, R, acc, lane, acc_a);
+                hv_walk_b(H, Q, cur, bA + k0, mask, xcol, xS, R, acc, lane, acc_a);
                 j = jn;
                 cur = nxt;
             }
