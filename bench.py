@@ -465,13 +465,39 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
 
-    # timed region: the step captured once as a CUDA graph (rs_step_capture) and replayed
-    # with rs_step_launch, per-step CUDA events on the launching stream, L2 flushed between
-    # steps (outside the events)
+    # the launch mode: the step captured once as a CUDA graph (rs_step_capture) and replayed
+    # with rs_step_launch, or launched kernel by kernel through rs_score and rs_topk.  Both
+    # run the same kernels; the graph saves the host's launch overhead, which matters on
+    # small graphs, while direct launches let the block scheduler follow the streams'
+    # priorities (long row chains first), which the replayed graph does not, and that
+    # matters on the large ones.  The faster over a few untimed, L2-flushed steps is timed
+    # (the slowest rank's figures decide under torchrun, so every rank takes the same mode).
     cap = G.capture_step(scores, kk, ids if kk else None, vals if kk else None)
     for i in range(2):
         flush.fill_(i & 0xFF)
         cap.launch()
+
+    def probe(fn, reps=3):
+        ts = []
+        for i in range(reps):
+            flush.fill_((i + 11) & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return sorted(ts)[reps // 2]
+
+    probes = torch.tensor([probe(cap.launch), probe(step)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(probes, op=dist.ReduceOp.MAX)
+    t_cap, t_dir = probes.tolist()
+    mode = "captured" if t_cap <= t_dir else "direct"
+    run = cap.launch if mode == "captured" else step
+
+    # timed region: per-step CUDA events on the launching stream, L2 flushed between steps
+    # (outside the events)
     clocks = Clocks(local)
     launches0 = G.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -481,7 +507,7 @@ def run_ours(args):
     for i in range(args.steps):
         flush.fill_((i + 7) & 0xFF)
         ev[i][0].record()
-        cap.launch()
+        run()
         ev[i][1].record()
     torch.cuda.synchronize()
     if world > 1:
@@ -592,8 +618,12 @@ def run_ours(args):
 
     config = W.config()
     config.update({"l2": "flushed between timed steps (512 MB write outside the events)",
-                   "launch": "the step captured once as a CUDA graph (rs_step_capture) and replayed "
-                             "(rs_step_launch); per-kernel times from the same steps launched directly",
+                   "launch": ("the step captured once as a CUDA graph (rs_step_capture) and replayed "
+                              "(rs_step_launch)" if mode == "captured" else
+                              "the step launched kernel by kernel (rs_score + rs_topk), faster here than "
+                              "its captured graph") + "; per-kernel times from the same steps launched "
+                             "directly with profiling events",
+                   "launch_probe": {"captured_ms": t_cap, "direct_ms": t_dir, "steps": 3, "chosen": mode},
                    "parallelism": "single" if world == 1 else
                                   ("graph shards" if isinstance(W, Packed) else "replicas"),
                    "tuning": tuning, "autotune": autotune})
