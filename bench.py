@@ -266,7 +266,8 @@ def graph_stats(g, k_class=None):
 
 
 # kernels launched on the forked streams of P1 and P2 (they overlap one another)
-CONCURRENT = {"p1_small", "p1_mid", "p1_large", "hub_p1_insert", "hub_p1_finish", "p2_small", "p2_narrow",
+CONCURRENT = {"p1_small", "p1_mid", "p1_large", "hub_p1_insert", "hub_p1_sums", "hub_p1_finish", "hub_p1_colmax",
+              "p2_small", "p2_narrow",
               "p2_mid", "p2_mid_wide", "p2_large_warp", "p2_large_warp_wide", "p2_large",
               "hub_p2_insert", "hub_p2_sigma", "hub_p2_emit", "mirror_tiles", "p2_split"}
 

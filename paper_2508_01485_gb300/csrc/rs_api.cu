@@ -496,9 +496,11 @@ __global__ void scatter_class_kernel(const int64_t *a, int64_t n, int32_t *rows)
 
 static void free_hub_tables(rs_graph *g) {
     void *ptrs[] = {g->hubs, g->hub_items, g->hub_item_chunk, g->hkey, g->hcnt, g->hq, g->hsig, g->hagg,
-                    g->hitem_out, g->hitem_in};
+                    g->hitem_out, g->hitem_in, g->hub_sitem, g->hub_srange};
     pool_free_many(ptrs, sizeof(ptrs) / sizeof(ptrs[0]));
     g->hubs = nullptr; g->hub_items = g->hub_item_chunk = nullptr; g->hkey = nullptr;
+    g->hub_sitem = g->hub_srange = nullptr;
+    g->n_hub_sitems = 0;
     g->hcnt = nullptr; g->hq = nullptr; g->hsig = nullptr; g->hagg = nullptr;
     g->hitem_out = g->hitem_in = nullptr;
     g->n_hubs = g->n_hub_items = g->hub_slots = 0;
@@ -700,6 +702,17 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
             slots += info[i].cap;
         }
         RS_CUDA_TRY(cudaMemcpy(g->hubs, info.data(), nh * sizeof(HubInfo), cudaMemcpyHostToDevice));
+        std::vector<int32_t> sitem, srange;
+        for (int i = 0; i < nh; ++i)
+            for (int32_t r = 0; (int64_t)r * kHubSlotRange < info[i].cap; ++r) {
+                sitem.push_back(i);
+                srange.push_back(r);
+            }
+        g->n_hub_sitems = (int64_t)sitem.size();
+        RS_CUDA_TRY(dmalloc(&g->hub_sitem, sitem.size()));
+        RS_CUDA_TRY(dmalloc(&g->hub_srange, srange.size()));
+        RS_CUDA_TRY(cudaMemcpy(g->hub_sitem, sitem.data(), sitem.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        RS_CUDA_TRY(cudaMemcpy(g->hub_srange, srange.data(), srange.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
         RS_CUDA_TRY(dmalloc(&g->hkey, slots));
         RS_CUDA_TRY(dmalloc(&g->hcnt, slots));
         RS_CUDA_TRY(dmalloc(&g->hq, 2 * slots));

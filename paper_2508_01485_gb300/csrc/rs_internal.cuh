@@ -36,6 +36,10 @@ struct __align__(16) NodeRec {
 };
 
 // per-hub state (global hash table and row aggregates)
+// the per-slot passes over the hubs' tables (their sums, column maxima and sigma) take a
+// hub's table in ranges of this many slots, so that a large hub's table is spread over
+// CTAs instead of walked by one
+constexpr int32_t kHubSlotRange = 4096;
 struct HubInfo {
     int32_t row;
     int32_t cap;          // table slots (power of two)
@@ -126,6 +130,9 @@ struct rs_graph {
     int32_t *hub_items = nullptr;     // per chunk item: hub index
     int32_t *hub_item_chunk = nullptr;// per chunk item: chunk number within the hub
     int64_t n_hubs = 0, n_hub_items = 0, hub_slots = 0;
+    int32_t *hub_sitem = nullptr;     // per slot-range item: hub index (a hub's table in ranges of
+    int32_t *hub_srange = nullptr;    //   kHubSlotRange slots) and the range's number in the hub
+    int64_t n_hub_sitems = 0;
     int32_t *hkey = nullptr;          // hub hash tables
     uint32_t *hcnt = nullptr;
     unsigned long long *hq = nullptr; // 2 words per slot

@@ -578,49 +578,91 @@ __global__ void __launch_bounds__(NT) hub_p1_insert_kernel(
     }
 }
 
+// hub rows, P1 step 2: each slot range of a hub's table adds its foreign groups and
+// their sum f LG[f] to the hub's aggregates (exact integer sums, so any order gives the
+// same bits)
 template <int NT>
-__global__ void __launch_bounds__(NT) hub_p1_finish_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ lab, const HubInfo *__restrict__ hubs,
-    int64_t nhubs, Batch B, const uint64_t *__restrict__ LG, const int32_t *hkey, const uint32_t *hcnt,
-    HubAgg *hagg, NodeRec *__restrict__ rec, int32_t *__restrict__ Lall) {
+__global__ void __launch_bounds__(NT) hub_p1_sums_kernel(
+    const HubInfo *__restrict__ hubs, const int32_t *__restrict__ sitem, const int32_t *__restrict__ srange,
+    int64_t nsitems, const uint64_t *__restrict__ LG, const int32_t *hkey, const uint32_t *hcnt, HubAgg *hagg) {
     __shared__ uint32_t sh_u32[NT / 32];
     __shared__ u128 sh_u128[NT / 32];
-    __shared__ df sh_df[NT / 32];
-    int tid = threadIdx.x;
-    for (int64_t hi = blockIdx.x; hi < nhubs; hi += gridDim.x) {
-        HubInfo h = hubs[hi];
-        int32_t gi = graph_of(B, h.row);
-        int64_t d = off[h.row + 1] - off[h.row];
-        uint32_t own = hagg[hi].own;
+    for (int64_t it = blockIdx.x; it < nsitems; it += gridDim.x) {
+        const int32_t hi = sitem[it];
+        const HubInfo h = hubs[hi];
+        const int64_t j0 = (int64_t)srange[it] * kHubSlotRange, j1 = min((int64_t)h.cap, j0 + (int64_t)kHubSlotRange);
         uint32_t Lf = 0;
         u128 X = 0;
-        for (int64_t j = tid; j < h.cap; j += NT) {
-            int64_t s = h.tab + j;
-            if (hkey[s] != kEmpty) { Lf++; X += (u128)hcnt[s] * LG[hcnt[s]]; }
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += NT) {
+            const int64_t s = h.tab + j;
+            if (hkey[s] != kEmpty) {
+                const uint32_t c = hcnt[s];
+                Lf++;
+                X += (u128)c * LG[c];
+            }
         }
         Lf = block_sum_u32<NT>(Lf, sh_u32);
         X = block_sum_u128<NT>(X, sh_u128);
-        RowAgg a{(uint32_t)d, Lf + (own > 0 ? 1u : 0u), X + (u128)own * LG[own]};
-        df cm{0.0f, 0.0f}, wown{0.0f, 0.0f};
-        bool want_max = true;
-        for (int64_t j = tid; j < h.cap; j += NT) {
-            int64_t s = h.tab + j;
+        if (threadIdx.x == 0) {
+            if (Lf) atomicAdd(&hagg[hi].L, Lf);
+            if (X) atomic_add_u128(reinterpret_cast<unsigned long long *>(&hagg[hi].X), X);
+        }
+        __syncthreads();                               // the reductions' words are reused
+    }
+}
+
+// hub rows, P1 step 3, a thread per hub: the row aggregates with the own community, the
+// own and absent columns' weights (published to w_max), the node record
+template <int NT>
+__global__ void __launch_bounds__(NT) hub_p1_finish_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ lab, const HubInfo *__restrict__ hubs,
+    int64_t nhubs, Batch B, const uint64_t *__restrict__ LG, HubAgg *hagg, NodeRec *__restrict__ rec,
+    int32_t *__restrict__ Lall) {
+    for (int64_t hi = (int64_t)blockIdx.x * NT + threadIdx.x; hi < nhubs; hi += (int64_t)gridDim.x * NT) {
+        const HubInfo h = hubs[hi];
+        const int32_t gi = graph_of(B, h.row);
+        const int64_t d = off[h.row + 1] - off[h.row];
+        HubAgg g = hagg[hi];
+        const uint32_t own = g.own;
+        const RowAgg a{(uint32_t)d, g.L + (own > 0 ? 1u : 0u), g.X + (u128)own * LG[own]};
+        df wown{0.0f, 0.0f};
+        if (own > 0) wown = column_weight(a, own, LG);
+        NodeRec r;
+        const df m = p1_row_result(a, own, wown, k_of(B, gi), LG, r, lab[h.row], wown, true);
+        publish_max(B, gi, m, current_wmax(&B.wmax[gi]));
+        rec[h.row] = r;
+        Lall[h.row] = (int32_t)a.L;
+        g.X = a.X;
+        g.L = a.L;
+        hagg[hi] = g;
+    }
+}
+
+// hub rows, P1 step 4: the largest weight of the foreign columns of each slot range, to
+// w_max (a maximum, so the order of the ranges does not matter)
+template <int NT>
+__global__ void __launch_bounds__(NT) hub_p1_colmax_kernel(
+    const int64_t *__restrict__ off, const HubInfo *__restrict__ hubs, const int32_t *__restrict__ sitem,
+    const int32_t *__restrict__ srange, int64_t nsitems, Batch B, const uint64_t *__restrict__ LG,
+    const int32_t *hkey, const uint32_t *hcnt, const HubAgg *__restrict__ hagg) {
+    __shared__ df sh_df[NT / 32];
+    for (int64_t it = blockIdx.x; it < nsitems; it += gridDim.x) {
+        const int32_t hi = sitem[it];
+        const HubInfo h = hubs[hi];
+        const HubAgg g = hagg[hi];
+        const RowAgg a{(uint32_t)(off[h.row + 1] - off[h.row]), g.L, g.X};
+        const int64_t j0 = (int64_t)srange[it] * kHubSlotRange, j1 = min((int64_t)h.cap, j0 + (int64_t)kHubSlotRange);
+        df cm{0.0f, 0.0f};
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += NT) {
+            const int64_t s = h.tab + j;
             if (hkey[s] != kEmpty) cm = df_max(cm, column_weight(a, hcnt[s], LG));
         }
-        if (own > 0) { wown = column_weight(a, own, LG); cm = df_max(cm, wown); }
         cm = block_max_df<NT>(cm, sh_df);
-        if (tid == 0) {
-            HubAgg g = hagg[hi];
-            g.X = a.X;
-            g.L = a.L;
-            hagg[hi] = g;
-            NodeRec r;
-            df m = p1_row_result(a, own, cm, k_of(B, gi), LG, r, lab[h.row], wown, want_max);
-            publish_max(B, gi, m, current_wmax(&B.wmax[gi]));
-            rec[h.row] = r;
-            Lall[h.row] = (int32_t)a.L;
+        if (threadIdx.x == 0) {
+            const int32_t gi = graph_of(B, h.row);
+            publish_max(B, gi, cm, current_wmax(&B.wmax[gi]));
         }
-        __syncthreads();
+        __syncthreads();                               // the reduction's words are reused
     }
 }
 
@@ -1146,28 +1188,32 @@ __global__ void __launch_bounds__(NT) hub_p2_insert_kernel(
     }
 }
 
-// hub rows, P2 step 2: sigma per table slot, G_x counts of the row
+// hub rows, P2 step 2: sigma per table slot, over the tables' slot ranges; the first range
+// of each hub also sums the row's G_x counts
 template <int NT>
 __global__ void __launch_bounds__(NT) hub_p2_sigma_kernel(
-    const HubInfo *__restrict__ hubs, int64_t nhubs, const uint64_t *__restrict__ LG,
-    const HubAgg *__restrict__ hagg, const int64_t *__restrict__ off, const int32_t *hkey,
-    const uint32_t *hcnt, df *hsig, const int32_t *hitem_out, const int32_t *hitem_in,
-    int32_t *xout, int32_t *xin) {
-    for (int64_t hi = blockIdx.x; hi < nhubs; hi += gridDim.x) {
-        HubInfo h = hubs[hi];
-        HubAgg g = hagg[hi];
-        RowAgg a{(uint32_t)(off[h.row + 1] - off[h.row]), g.L, g.X};
-        for (int64_t j = threadIdx.x; j < h.cap; j += NT) {
-            int64_t s = h.tab + j;
+    const HubInfo *__restrict__ hubs, const int32_t *__restrict__ sitem, const int32_t *__restrict__ srange,
+    int64_t nsitems, const uint64_t *__restrict__ LG, const HubAgg *__restrict__ hagg,
+    const int64_t *__restrict__ off, const int32_t *hkey, const uint32_t *hcnt, df *hsig,
+    const int32_t *hitem_out, const int32_t *hitem_in, int32_t *xout, int32_t *xin) {
+    for (int64_t it = blockIdx.x; it < nsitems; it += gridDim.x) {
+        const int32_t hi = sitem[it];
+        const HubInfo h = hubs[hi];
+        const HubAgg g = hagg[hi];
+        const RowAgg a{(uint32_t)(off[h.row + 1] - off[h.row]), g.L, g.X};
+        const int64_t j0 = (int64_t)srange[it] * kHubSlotRange, j1 = min((int64_t)h.cap, j0 + (int64_t)kHubSlotRange);
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += NT) {
+            const int64_t s = h.tab + j;
             if (hkey[s] != kEmpty) hsig[s] = df_cbrt(column_weight(a, hcnt[s], LG));
         }
-        if (threadIdx.x == 0) {
+        if (j0 == 0 && threadIdx.x == 0) {
             int32_t so = 0, si = 0;
             for (int j = 0; j < h.n_items; ++j) {
                 so += hitem_out[h.first_item + j];
                 si += hitem_in[h.first_item + j];
             }
-            xout[h.row] = so; xin[h.row] = si;
+            xout[h.row] = so;
+            xin[h.row] = si;
         }
     }
 }
@@ -2133,9 +2179,15 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->off, g->col, g->lab, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items,
             g->tune.hub_chunk, g->hkey, g->hcnt, g->hagg, err);
         RS_LAUNCHED(g, g->aux[3], "hub_p1_insert");
-        hub_p1_finish_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, g->aux[3]>>>(
-            g->off, g->lab, g->hubs, g->n_hubs, B, g->LG, g->hkey, g->hcnt, g->hagg, g->rec, g->Lall);
+        hub_p1_sums_kernel<NT><<<grid_for(g->n_hub_sitems, 1, 8), NT, 0, g->aux[3]>>>(
+            g->hubs, g->hub_sitem, g->hub_srange, g->n_hub_sitems, g->LG, g->hkey, g->hcnt, g->hagg);
+        RS_LAUNCHED(g, g->aux[3], "hub_p1_sums");
+        hub_p1_finish_kernel<NT><<<(unsigned)((g->n_hubs + NT - 1) / NT), NT, 0, g->aux[3]>>>(
+            g->off, g->lab, g->hubs, g->n_hubs, B, g->LG, g->hagg, g->rec, g->Lall);
         RS_LAUNCHED(g, g->aux[3], "hub_p1_finish");
+        hub_p1_colmax_kernel<NT><<<grid_for(g->n_hub_sitems, 1, 8), NT, 0, g->aux[3]>>>(
+            g->off, g->hubs, g->hub_sitem, g->hub_srange, g->n_hub_sitems, B, g->LG, g->hkey, g->hcnt, g->hagg);
+        RS_LAUNCHED(g, g->aux[3], "hub_p1_colmax");
     }
     if (g->n_large) {
         switch (g->tune.p1_cta_threads) {
@@ -2195,9 +2247,9 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->hkey, g->hq,
             g->hitem_out, g->hitem_in, err);
         RS_LAUNCHED(g, g->aux[3], "hub_p2_insert");
-        hub_p2_sigma_kernel<NT><<<grid_for(g->n_hubs, 1, 8), NT, 0, g->aux[3]>>>(
-            g->hubs, g->n_hubs, g->LG, g->hagg, g->off, g->hkey, g->hcnt, g->hsig, g->hitem_out, g->hitem_in,
-            g->xout, g->xin);
+        hub_p2_sigma_kernel<NT><<<grid_for(g->n_hub_sitems, 1, 8), NT, 0, g->aux[3]>>>(
+            g->hubs, g->hub_sitem, g->hub_srange, g->n_hub_sitems, g->LG, g->hagg, g->off, g->hkey, g->hcnt,
+            g->hsig, g->hitem_out, g->hitem_in, g->xout, g->xin);
         RS_LAUNCHED(g, g->aux[3], "hub_p2_sigma");
         hub_p2_emit_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
             g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
