@@ -269,7 +269,7 @@ def graph_stats(g, k_class=None):
 CONCURRENT = {"p1_small", "p1_mid", "p1_large", "hub_p1_insert", "hub_p1_sums", "hub_p1_finish", "hub_p1_colmax",
               "p2_small", "p2_narrow",
               "p2_mid", "p2_mid_wide", "p2_large_warp", "p2_large_warp_wide", "p2_large",
-              "hub_p2_insert", "hub_p2_sigma", "hub_p2_emit", "mirror_tiles", "p2_split"}
+              "hub_p2_insert", "hub_p2_counts", "hub_p2_emit", "mirror_tiles", "p2_split"}
 
 
 def kernel_bytes(name, st):

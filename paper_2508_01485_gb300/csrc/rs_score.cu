@@ -638,13 +638,15 @@ __global__ void __launch_bounds__(NT) hub_p1_finish_kernel(
     }
 }
 
-// hub rows, P1 step 4: the largest weight of the foreign columns of each slot range, to
-// w_max (a maximum, so the order of the ranges does not matter)
+// hub rows, P1 step 4: the weight of every foreign column of each slot range, its cube root
+// sigma kept for P2 (a column's weight depends only on the row's aggregates and its count,
+// both final here), and the range's largest weight to w_max (a maximum, so the order of
+// the ranges does not matter)
 template <int NT>
 __global__ void __launch_bounds__(NT) hub_p1_colmax_kernel(
     const int64_t *__restrict__ off, const HubInfo *__restrict__ hubs, const int32_t *__restrict__ sitem,
     const int32_t *__restrict__ srange, int64_t nsitems, Batch B, const uint64_t *__restrict__ LG,
-    const int32_t *hkey, const uint32_t *hcnt, const HubAgg *__restrict__ hagg) {
+    const int32_t *hkey, const uint32_t *hcnt, const HubAgg *__restrict__ hagg, df *hsig) {
     __shared__ df sh_df[NT / 32];
     for (int64_t it = blockIdx.x; it < nsitems; it += gridDim.x) {
         const int32_t hi = sitem[it];
@@ -655,7 +657,11 @@ __global__ void __launch_bounds__(NT) hub_p1_colmax_kernel(
         df cm{0.0f, 0.0f};
         for (int64_t j = j0 + threadIdx.x; j < j1; j += NT) {
             const int64_t s = h.tab + j;
-            if (hkey[s] != kEmpty) cm = df_max(cm, column_weight(a, hcnt[s], LG));
+            if (hkey[s] != kEmpty) {
+                const df w = column_weight(a, hcnt[s], LG);
+                cm = df_max(cm, w);
+                hsig[s] = df_cbrt(w);
+            }
         }
         cm = block_max_df<NT>(cm, sh_df);
         if (threadIdx.x == 0) {
@@ -1188,33 +1194,20 @@ __global__ void __launch_bounds__(NT) hub_p2_insert_kernel(
     }
 }
 
-// hub rows, P2 step 2: sigma per table slot, over the tables' slot ranges; the first range
-// of each hub also sums the row's G_x counts
+// hub rows, P2 step 2, a thread per hub: the row's G_x out and in counts, summed over its chunks
 template <int NT>
-__global__ void __launch_bounds__(NT) hub_p2_sigma_kernel(
-    const HubInfo *__restrict__ hubs, const int32_t *__restrict__ sitem, const int32_t *__restrict__ srange,
-    int64_t nsitems, const uint64_t *__restrict__ LG, const HubAgg *__restrict__ hagg,
-    const int64_t *__restrict__ off, const int32_t *hkey, const uint32_t *hcnt, df *hsig,
-    const int32_t *hitem_out, const int32_t *hitem_in, int32_t *xout, int32_t *xin) {
-    for (int64_t it = blockIdx.x; it < nsitems; it += gridDim.x) {
-        const int32_t hi = sitem[it];
+__global__ void __launch_bounds__(NT) hub_p2_counts_kernel(
+    const HubInfo *__restrict__ hubs, int64_t nhubs, const int32_t *hitem_out, const int32_t *hitem_in,
+    int32_t *xout, int32_t *xin) {
+    for (int64_t hi = (int64_t)blockIdx.x * NT + threadIdx.x; hi < nhubs; hi += (int64_t)gridDim.x * NT) {
         const HubInfo h = hubs[hi];
-        const HubAgg g = hagg[hi];
-        const RowAgg a{(uint32_t)(off[h.row + 1] - off[h.row]), g.L, g.X};
-        const int64_t j0 = (int64_t)srange[it] * kHubSlotRange, j1 = min((int64_t)h.cap, j0 + (int64_t)kHubSlotRange);
-        for (int64_t j = j0 + threadIdx.x; j < j1; j += NT) {
-            const int64_t s = h.tab + j;
-            if (hkey[s] != kEmpty) hsig[s] = df_cbrt(column_weight(a, hcnt[s], LG));
+        int32_t so = 0, si = 0;
+        for (int j = 0; j < h.n_items; ++j) {
+            so += hitem_out[h.first_item + j];
+            si += hitem_in[h.first_item + j];
         }
-        if (j0 == 0 && threadIdx.x == 0) {
-            int32_t so = 0, si = 0;
-            for (int j = 0; j < h.n_items; ++j) {
-                so += hitem_out[h.first_item + j];
-                si += hitem_in[h.first_item + j];
-            }
-            xout[h.row] = so;
-            xin[h.row] = si;
-        }
+        xout[h.row] = so;
+        xin[h.row] = si;
     }
 }
 
@@ -2186,7 +2179,8 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->off, g->lab, g->hubs, g->n_hubs, B, g->LG, g->hagg, g->rec, g->Lall);
         RS_LAUNCHED(g, g->aux[3], "hub_p1_finish");
         hub_p1_colmax_kernel<NT><<<grid_for(g->n_hub_sitems, 1, 8), NT, 0, g->aux[3]>>>(
-            g->off, g->hubs, g->hub_sitem, g->hub_srange, g->n_hub_sitems, B, g->LG, g->hkey, g->hcnt, g->hagg);
+            g->off, g->hubs, g->hub_sitem, g->hub_srange, g->n_hub_sitems, B, g->LG, g->hkey, g->hcnt, g->hagg,
+            g->hsig);
         RS_LAUNCHED(g, g->aux[3], "hub_p1_colmax");
     }
     if (g->n_large) {
@@ -2247,10 +2241,9 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
             g->hkey, g->hq,
             g->hitem_out, g->hitem_in, err);
         RS_LAUNCHED(g, g->aux[3], "hub_p2_insert");
-        hub_p2_sigma_kernel<NT><<<grid_for(g->n_hub_sitems, 1, 8), NT, 0, g->aux[3]>>>(
-            g->hubs, g->hub_sitem, g->hub_srange, g->n_hub_sitems, g->LG, g->hagg, g->off, g->hkey, g->hcnt,
-            g->hsig, g->hitem_out, g->hitem_in, g->xout, g->xin);
-        RS_LAUNCHED(g, g->aux[3], "hub_p2_sigma");
+        hub_p2_counts_kernel<NT><<<(unsigned)((g->n_hubs + NT - 1) / NT), NT, 0, g->aux[3]>>>(
+            g->hubs, g->n_hubs, g->hitem_out, g->hitem_in, g->xout, g->xin);
+        RS_LAUNCHED(g, g->aux[3], "hub_p2_counts");
         hub_p2_emit_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
             g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
             g->hkey, g->hcnt,
