@@ -496,10 +496,10 @@ __global__ void scatter_class_kernel(const int64_t *a, int64_t n, int32_t *rows)
 
 static void free_hub_tables(rs_graph *g) {
     void *ptrs[] = {g->hubs, g->hub_items, g->hub_item_chunk, g->hkey, g->hcnt, g->hq, g->hsig, g->hagg,
-                    g->hitem_out, g->hitem_in, g->hub_sitem, g->hub_srange};
+                    g->hitem_out, g->hitem_in, g->hub_sitem, g->hub_srange, g->hslot};
     pool_free_many(ptrs, sizeof(ptrs) / sizeof(ptrs[0]));
     g->hubs = nullptr; g->hub_items = g->hub_item_chunk = nullptr; g->hkey = nullptr;
-    g->hub_sitem = g->hub_srange = nullptr;
+    g->hub_sitem = g->hub_srange = g->hslot = nullptr;
     g->n_hub_sitems = 0;
     g->hcnt = nullptr; g->hq = nullptr; g->hsig = nullptr; g->hagg = nullptr;
     g->hitem_out = g->hitem_in = nullptr;
@@ -648,9 +648,11 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
     }
     std::vector<HubInfo> info(nh);
     std::vector<int32_t> items, chunks;
-    int64_t slots = 0;
+    int64_t slots = 0, hub_entries = 0;
     for (int i = 0; i < nh; ++i) {
         int64_t d = offs[3 * i + 1] - offs[3 * i];
+        info[i].ent = hub_entries;
+        hub_entries += d;
         int64_t m = std::min<int64_t>(d, offs[3 * i + 2]);
         info[i].row = hl[i];
         info[i].cap = (int32_t)pow2_at_least((uint64_t)(2 * m));   // by degree: the scratch count below
@@ -713,6 +715,7 @@ static int classify_rows(rs_graph *g, cudaStream_t s) {
         RS_CUDA_TRY(dmalloc(&g->hub_srange, srange.size()));
         RS_CUDA_TRY(cudaMemcpy(g->hub_sitem, sitem.data(), sitem.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
         RS_CUDA_TRY(cudaMemcpy(g->hub_srange, srange.data(), srange.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        RS_CUDA_TRY(dmalloc(&g->hslot, (size_t)hub_entries));
         RS_CUDA_TRY(dmalloc(&g->hkey, slots));
         RS_CUDA_TRY(dmalloc(&g->hcnt, slots));
         RS_CUDA_TRY(dmalloc(&g->hq, 2 * slots));

@@ -46,6 +46,7 @@ struct HubInfo {
     int64_t tab;          // first slot in the hub table arrays
     int32_t first_item;   // first chunk item of this hub
     int32_t n_items;
+    int64_t ent;          // first of its entries in hslot (the hubs' entries, hub by hub)
 };
 struct __align__(16) HubAgg {
     u128 X;               // sum over foreign groups of f LG[f] (own group added later)
@@ -133,6 +134,7 @@ struct rs_graph {
     int32_t *hub_sitem = nullptr;     // per slot-range item: hub index (a hub's table in ranges of
     int32_t *hub_srange = nullptr;    //   kHubSlotRange slots) and the range's number in the hub
     int64_t n_hub_sitems = 0;
+    int32_t *hslot = nullptr;         // per hub entry: its community's table slot (-1: own community)
     int32_t *hkey = nullptr;          // hub hash tables
     uint32_t *hcnt = nullptr;
     unsigned long long *hq = nullptr; // 2 words per slot

@@ -641,7 +641,9 @@ __global__ void __launch_bounds__(NT) hub_p1_finish_kernel(
 // hub rows, P1 step 4: the weight of every foreign column of each slot range, its cube root
 // sigma kept for P2 (a column's weight depends only on the row's aggregates and its count,
 // both final here), and the range's largest weight to w_max (a maximum, so the order of
-// the ranges does not matter)
+// the ranges does not matter).  A positive sigma is stored negated when the column has a
+// single member (no Type-II push to make), so that P2 reads one word instead of two; the
+// sign change is exact, and a zero sigma (no push either) stays +0.
 template <int NT>
 __global__ void __launch_bounds__(NT) hub_p1_colmax_kernel(
     const int64_t *__restrict__ off, const HubInfo *__restrict__ hubs, const int32_t *__restrict__ sitem,
@@ -660,7 +662,8 @@ __global__ void __launch_bounds__(NT) hub_p1_colmax_kernel(
             if (hkey[s] != kEmpty) {
                 const df w = column_weight(a, hcnt[s], LG);
                 cm = df_max(cm, w);
-                hsig[s] = df_cbrt(w);
+                const df sg = df_cbrt(w);
+                hsig[s] = (hcnt[s] > 1 || !(sg.hi > 0.0f)) ? sg : df{-sg.hi, -sg.lo};
             }
         }
         cm = block_max_df<NT>(cm, sh_df);
@@ -1144,13 +1147,14 @@ __global__ void __launch_bounds__(NT) p2_large_kernel(
     }
 }
 
-// hub rows, P2 step 1: Type-II group sums and per-chunk G_x counts
+// hub rows, P2 step 1: Type-II group sums and per-chunk G_x counts; every entry's table slot
+// (found once per group of lanes with the same community) is kept for step 3
 template <int NT>
 __global__ void __launch_bounds__(NT) hub_p2_insert_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const HubInfo *__restrict__ hubs,
     const int32_t *__restrict__ items, const int32_t *__restrict__ chunks, int64_t nitems, int32_t chunk_len,
     const NodeRec *__restrict__ rec, const int32_t *hkey, unsigned long long *hq,
-    int32_t *hitem_out, int32_t *hitem_in, int *err) {
+    int32_t *hitem_out, int32_t *hitem_in, int32_t *__restrict__ hslot, int *err) {
     __shared__ uint32_t sh_u32[NT / 32];
     __shared__ uint64_t stage[NT];
     int tid = threadIdx.x, lane = tid & 31;
@@ -1176,11 +1180,16 @@ __global__ void __launch_bounds__(NT) hub_p2_insert_kernel(
             unsigned fm = __ballot_sync(FULL, foreign);
             if (foreign) {
                 unsigned grp = __match_any_sync(fm, ru.label);
-                if (lane == __ffs(grp) - 1) {
-                    int s = tab_find(t, ru.label);
+                const int leader = __ffs(grp) - 1;
+                int s = -1;
+                if (lane == leader) {
+                    s = tab_find(t, ru.label);
                     if (s < 0) atomicOr(err, 4);
                     else atomic_add_u128(t.q + 2 * s, group_sum_all(st, grp));
                 }
+                hslot[h.ent + e] = __shfl_sync(grp, s, leader);
+            } else if (act) {
+                hslot[h.ent + e] = -1;
             }
             __syncwarp();
             if (rw.dx >= 2 && foreign && ru.dx >= 2) {
@@ -1216,7 +1225,7 @@ template <int NT>
 __global__ void __launch_bounds__(NT) hub_p2_emit_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ col, const HubInfo *__restrict__ hubs,
     const int32_t *__restrict__ items, const int32_t *__restrict__ chunks, int64_t nitems, int32_t chunk_len,
-    const NodeRec *__restrict__ rec, const int32_t *hkey, const uint32_t *hcnt,
+    const NodeRec *__restrict__ rec, const int32_t *__restrict__ hslot,
     const unsigned long long *hq, const df *hsig, const int32_t *hitem_out, const int32_t *hitem_in,
     unsigned long long *acc, const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol,
     df *__restrict__ xS, int *err, Strict SX) {
@@ -1231,7 +1240,6 @@ __global__ void __launch_bounds__(NT) hub_p2_emit_kernel(
         int64_t lo = (int64_t)ch * chunk_len;
         int64_t hi = min(d, lo + chunk_len);
         NodeRec rw = rec[h.row];
-        Tab t{(int32_t *)hkey + h.tab, (uint32_t *)hcnt + h.tab, nullptr, nullptr, (uint32_t)h.cap - 1};
         int32_t bo = 0, bi = 0;
         for (int j = 0; j < ch; ++j) { bo += hitem_out[h.first_item + j]; bi += hitem_in[h.first_item + j]; }
         int64_t xb = xoff[h.row];
@@ -1241,18 +1249,17 @@ __global__ void __launch_bounds__(NT) hub_p2_emit_kernel(
             int32_t u = act ? col[b + e] : -1;
             NodeRec ru{0, -1, 0};
             if (act) ru = rec[u];
-            bool cross = act && ru.label != rw.label;
+            // the slot step 1 found (-1: own community, or a miss step 1 flagged)
+            const int s = act ? hslot[h.ent + e] : -1;
+            bool cross = s >= 0;
             df sig{0.0f, 0.0f};
             if (cross) {
-                int s = tab_find(t, ru.label);
-                if (s < 0) { atomicOr(err, 8); cross = false; }
-                else {
-                    int64_t gs = h.tab + s;
-                    sig = hsig[gs];
-                    if (hcnt[gs] > 1) {
-                        u128 q = ((u128)hq[2 * gs + 1] << 64) | hq[2 * gs];
-                        push_type2(acc, u, sig, strict_rest(SX, off, h.row, u, q - ru.s_fix, b + e));
-                    }
+                int64_t gs = h.tab + s;
+                const df st = hsig[gs];                // negative: a single member, no push
+                sig = st.hi < 0.0f ? df{-st.hi, -st.lo} : st;
+                if (st.hi > 0.0f) {
+                    u128 q = ((u128)hq[2 * gs + 1] << 64) | hq[2 * gs];
+                    push_type2(acc, u, sig, strict_rest(SX, off, h.row, u, q - ru.s_fix, b + e));
                 }
             }
             if (rw.dx >= 2) {
@@ -2239,14 +2246,14 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         hub_p2_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
             g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
             g->hkey, g->hq,
-            g->hitem_out, g->hitem_in, err);
+            g->hitem_out, g->hitem_in, g->hslot, err);
         RS_LAUNCHED(g, g->aux[3], "hub_p2_insert");
         hub_p2_counts_kernel<NT><<<(unsigned)((g->n_hubs + NT - 1) / NT), NT, 0, g->aux[3]>>>(
             g->hubs, g->n_hubs, g->hitem_out, g->hitem_in, g->xout, g->xin);
         RS_LAUNCHED(g, g->aux[3], "hub_p2_counts");
         hub_p2_emit_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
             g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
-            g->hkey, g->hcnt,
+            g->hslot,
             g->hq, g->hsig, g->hitem_out, g->hitem_in, g->acc, g->xoff, g->xcol, g->xS, err, SX);
         RS_LAUNCHED(g, g->aux[3], "hub_p2_emit");
     }
