@@ -300,6 +300,8 @@ def kernel_bytes(name, st):
         # every in-slot (id, value) read once, its out-slot's reverse value written once;
         # in counts, offsets and ranks of every node
         "gx_mirror": lambda: (4 + 8 + 8) * st["out_slots"] + (4 + 8 + 4) * n,
+        # the first id of every 8-slot sector of the G_x slots, read and written once
+        "gx_skip": lambda: (4 + 4) * st["gx_slots"] / 8,
         "finalize": lambda: (8 + 16 + 8) * n,
         "tk_select": lambda: 8 * n,
         # every node record (its dx) read, every G_x row offset written

@@ -779,7 +779,8 @@ static int alloc_workspace(rs_graph *g) {
     RS_CUDA_TRY(dmalloc(&g->cl_col, nnz));
     RS_CUDA_TRY(dmalloc(&g->cl_lab, nnz));
     RS_CUDA_TRY(dmalloc(&g->xoff, n + 1));
-    RS_CUDA_TRY(dmalloc(&g->xcol, nnz));
+    RS_CUDA_TRY(dmalloc(&g->xcol, nnz + 8));
+    RS_CUDA_TRY(dmalloc(&g->xsk, nnz / 8 + 1));
     RS_CUDA_TRY(dmalloc(&g->xS, nnz));
     RS_CUDA_TRY(dmalloc(&g->xout, n));
     RS_CUDA_TRY(dmalloc(&g->xin, n));
@@ -801,7 +802,7 @@ static void free_graph(rs_graph *g) {
     if (!g) return;
     void *ptrs[] = {g->off, g->off_alt, g->col, g->col_alt, g->lab, g->removed, g->dead,
                     g->rows_small, g->rows_mid, g->rows_large, g->rows_sort, g->LG, g->RD, g->rec, g->acc, g->wmax_bits,
-                    g->Lall, g->xoff, g->xcol, g->xS, g->xout, g->xin, g->scan_tmp, g->tk_hist,
+                    g->Lall, g->xoff, g->xcol, g->xsk, g->xS, g->xout, g->xin, g->scan_tmp, g->tk_hist,
                     g->tk_ctrl, g->tk_keys, g->tk_ids, g->d_flag, g->xR, g->xtile, g->rsum, g->cl_col, g->cl_lab,
                     g->winv, g->gid, g->gk, g->gnode, g->p2rows, g->p2cnt, g->sx, g->wq, g->perm};
     pool_free_many(ptrs, sizeof(ptrs) / sizeof(ptrs[0]));

@@ -153,7 +153,8 @@ struct rs_graph {
     int32_t *cl_col = nullptr;                // cross lists: row v's cross neighbours at
     int32_t *cl_lab = nullptr;                //   [off[v], off[v] + dx(v)) (ids, labels)
     int64_t *xoff = nullptr;                  // G_x row offsets (n + 1)
-    int32_t *xcol = nullptr;                  // G_x neighbours (capacity nnz)
+    int32_t *xcol = nullptr;                  // G_x neighbours (capacity nnz + 8: whole 8-slot sectors)
+    int32_t *xsk = nullptr;                   // first id of every 8-slot sector of xcol (nnz / 8 + 1)
     rs::df *xS = nullptr;                     // S(w -> u) = w_w(C(u))^(1/3)
     int32_t *xout = nullptr, *xin = nullptr;  // out / in counts per node
     int32_t *p2rows = nullptr;                // P2 row lists by cross degree (4 n), counted in p2cnt

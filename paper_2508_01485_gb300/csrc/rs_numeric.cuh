@@ -143,25 +143,27 @@ __device__ __forceinline__ void fixed_part(float f, int frac, uint64_t &lo, uint
     hi = h;
 }
 // round-toward-zero of each part of a * 2^frac, summed, for a >= 0 as an unsigned
-// 128-bit integer (0 when the sum is negative).  The usual case (a.hi a positive normal
-// float whose scaled significand ends below bit 64, a.lo small enough for 63 bits) takes
-// a short path with the same result: a.hi's significand shifted into place, and a.lo * 2^frac
-// (exact: a power-of-two scaling) converted to int64 with truncation toward zero, which is
-// the magnitude's truncation with a.lo's sign (and 0 for a subnormal a.lo, below 2^-62 once
-// scaled); ql < 40 keeps that value under 2^63.  For 0 <= frac <= 64 (the scales used),
-// 0 < qh < 64 already makes a.hi a positive normal float, so one range test covers it.
+// 128-bit integer (0 when the sum is negative).  The usual case takes a short path with
+// the same result: a.hi a positive normal float whose scaled significand ends below bit
+// 64 (0 < qh < 64, which for 0 <= frac <= 64, the scales used, already makes a.hi
+// positive, normal and finite), and a.lo at least 2^24 times smaller in exponent
+// (el <= eh - 24, true of every normalised double-float).  Then a.hi's significand is
+// shifted into place, and a.lo * 2^frac (exact: a power-of-two scaling) is converted to
+// int64 with truncation toward zero, which is the magnitude's truncation with a.lo's sign
+// (and 0 for a subnormal a.lo, below 2^-62 once scaled); ql <= qh - 24 < 40 keeps that
+// value under 2^63.  Since |a.lo| < 2^(eh-150) = ulp(a.hi), |a.lo| 2^frac < 2^qh, at most
+// 2^-23 of a.hi's part, so the sum is positive and below 2^88: no clamp is needed there.
 __device__ __forceinline__ u128 df_to_fixed(df a, int frac) {
     const uint32_t bh = __float_as_uint(a.hi), bl = __float_as_uint(a.lo);
     const int eh = (int)(bh >> 23);                // with the sign bit: < 255 means a.hi >= 0, finite
     const int el = (int)((bl >> 23) & 0xFF);
-    const int qh = eh - 150 + frac, ql = el - 150 + frac;
-    if ((uint32_t)(qh - 1) < 63u && ql < 40) {
+    const int qh = eh - 150 + frac;
+    if ((uint32_t)(qh - 1) < 63u && el + 24 <= eh) {
         const uint64_t mh = (uint64_t)((bh & 0x7FFFFFu) | 0x800000u);
         const uint64_t l = mh << qh, h = mh >> (64 - qh);
         const int64_t lp = __float2ll_rz(__fmul_rn(a.lo, pow2f(frac)));
         const uint64_t l2 = l + (uint64_t)lp;
         const uint64_t h2 = h + (lp < 0 ? ~0ull : 0ull) + (l2 < l ? 1ull : 0ull);
-        if ((int64_t)h2 < 0) return 0;
         return ((u128)h2 << 64) | l2;
     }
     uint64_t l1, h1, l2, h2;

@@ -1367,7 +1367,7 @@ __device__ __forceinline__ void mirror_one(int64_t sl, int32_t u, const int64_t 
 __global__ void __launch_bounds__(kThreads) gx_mirror_kernel(
     int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
     const int32_t *__restrict__ xout, const int32_t *__restrict__ xin, const int32_t *__restrict__ cover,
-    df *__restrict__ xR, int *err) {
+    df *__restrict__ xR, int32_t *__restrict__ xsk, int *err) {
     __shared__ int64_t s_lo[kMirNodes];          // first in-slot of each staged node inside the tile
     __shared__ int32_t s_pre[kMirNodes + 1];     // prefix sums of the staged nodes' in-slots in the tile
     __shared__ int32_t s_wsum[kThreads / 32];
@@ -1376,6 +1376,7 @@ __global__ void __launch_bounds__(kThreads) gx_mirror_kernel(
     const int64_t tiles = (S + kMirTile - 1) / kMirTile;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         int64_t s0 = t * kMirTile, s1 = min(S, s0 + kMirTile);
+        for (int64_t q = (s0 >> 3) + tid; q < ((s1 + 7) >> 3); q += blockDim.x) xsk[q] = xcol[8 * q];
         // nodes [ulo, uhi): from the one holding s0 to the one holding s1 (or the last slot)
         int64_t ulo = cover[t], uhi = (int64_t)cover[t + 1] + 1;
         __syncthreads();                             // the previous tile's stage is free
@@ -1509,6 +1510,50 @@ __device__ __forceinline__ int64_t find_in_list(const int32_t *xcol, int64_t lo,
     return (l < len && xcol[lo + l] == key) ? lo + l : -1;
 }
 
+// lists of at most this many ids are binary-searched directly (they span at most 9 sectors)
+constexpr int32_t kSkipMin = 64;
+
+// xsk[t] = xcol[8 t]: the first id of every 8-slot sector of the G_x slot space, a packed
+// index of the out-lists' ids, written once the rows are complete (by the mirror pass, or
+// by this kernel when the mirror pass is off)
+__global__ void gx_skip_kernel(int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol,
+                               int32_t *__restrict__ xsk) {
+    const int64_t T = (xoff[n] + 7) >> 3;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x)
+        xsk[t] = xcol[8 * t];
+}
+
+// position of key in the sorted list xcol[lo, lo + len), or -1.  A list of more than kSkipMin
+// ids is searched in xsk first, over the sectors that start inside it, for the one sector
+// that can hold key (the last whose first id is <= key; before them, the sector holding the
+// list's head, when the list does not start a sector); that sector is then read with two
+// 16-byte loads and its slots inside the list compared with key.  The chain of dependent
+// loads of a long list thus runs over the packed index (8 times denser than the list) and
+// ends with one sector.  xcol is padded to whole sectors, so the last sector is readable.
+__device__ __forceinline__ int64_t find_in_list_sk(const int32_t *xcol, const int32_t *xsk, int64_t lo, int32_t len,
+                                                   int32_t key) {
+    if (len <= kSkipMin) return find_in_list(xcol, lo, len, key);
+    const int64_t end = lo + len;
+    const int64_t t0 = (lo + 7) >> 3;                // first sector starting inside the list
+    const int32_t ns = (int32_t)(((end - 1) >> 3) - t0 + 1);
+    int32_t l = 0, h = ns;                           // first of them whose first id exceeds key
+    while (l < h) {
+        const int32_t mid = (l + h) >> 1;
+        if (__ldg(xsk + t0 + mid) <= key) l = mid + 1; else h = mid;
+    }
+    const int64_t t = t0 + l - 1;
+    if (t < (lo >> 3)) return -1;                    // key is below the first id, which starts a sector
+    const int4 *v = reinterpret_cast<const int4 *>(xcol + 8 * t);
+    const int4 x = __ldg(v), y = __ldg(v + 1);
+    const int32_t e[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+    const int64_t b = 8 * t;
+    int64_t pos = -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if (e[j] == key && b + j >= lo && b + j < end) pos = b + j;
+    return pos;
+}
+
 // Heavy nodes: a wedge walk, one CTA per task.  A task is a heavy node a with a block
 // of kHvBlock of its out-neighbours b.  The CTA stages a's out-list A (sorted by id),
 // kHvIds ids at a time, as a shared-memory hash table of 4-slot buckets (id -> position
@@ -1524,9 +1569,10 @@ __device__ __forceinline__ int64_t find_in_list(const int32_t *xcol, int64_t lo,
 // A third of the heavy wedges close on the 8M-node graph, so finishing the triangles
 // dominates, and its atomics are cut down: hits are queued and finished a warp at a
 // time (one triangle per lane); a's terms are summed in registers over the task, b's
-// over the warp's walk of b (every queued triangle has the same b), and c's in a
-// 128-bit sum per staged position in shared memory, added to the accumulators once per
-// chunk.  The integer sums are exact, so the bits do not depend on how they are split.
+// over the warp's walk of b (every queued triangle has the same b), and c's in two
+// 64-bit words per staged position in shared memory (the term's low 48 bits and the
+// rest, each added without reading the old value back), added to the accumulators once
+// per chunk.  The integer sums are exact, so the bits do not depend on how they are split.
 //
 // The warp whose group holds a heavy node does not walk it: it appends the node's
 // tasks to the task list (slots taken with an atomic counter), and p3_heavy_kernel,
@@ -1546,7 +1592,7 @@ struct P3Heavy {
     int4 key[kHvSlots / 4];                   // the chunk's ids, 4 slots per bucket (-1: empty slot)
     uint16_t slot_pos[kHvSlots];              // their positions in the chunk
     df sca[kHvIds], pac[kHvIds];              // S(c->a), S(a->c) + S(c->a)
-    unsigned long long clo[kHvIds], chi[kHvIds];   // c's terms of the chunk: low, high words
+    unsigned long long clo[kHvIds], chi[kHvIds];   // c's terms of the chunk: bits [0, 48) and [48, 112)
     HvQueue q[kHvWarps];
     int64_t a, bA;
     int32_t dA, eb0, nb, next_b, stop;
@@ -1584,13 +1630,16 @@ __device__ __forceinline__ int32_t hv_find(const P3Heavy &H, int32_t c, uint32_t
     return -1;
 }
 
-__device__ __forceinline__ void shared_add_u128(unsigned long long *lo_w, unsigned long long *hi_w, u128 v) {
-    unsigned long long lo = (unsigned long long)(uint64_t)v, hi = (unsigned long long)(uint64_t)(v >> 64);
-    if (lo) {
-        const unsigned long long old = atomicAdd(lo_w, lo);
-        if (old + lo < old) hi += 1ull;
-    }
-    if (hi) atomicAdd(hi_w, hi);
+// c's term t added to its chunk sums in shared memory: bits [0, 48) of t to lo_w, bits
+// [48, 112) to hi_w, each by an atomic add whose old value is not needed (no carry to
+// propagate).  A position receives at most kHvBlock terms per chunk (one per out-neighbour
+// b of the task), and every term is below 2^101 (at most 2^37 in value: each S(x->y) is
+// the cube root of a weight below 31 * 2^31, so below 2^12, and a term is S * S * (S + S)),
+// so the low word stays below 2^55 and the high one below 2^60; the chunk's sum is
+// lo + hi * 2^48, exactly.
+__device__ __forceinline__ void shared_add_split(unsigned long long *lo_w, unsigned long long *hi_w, u128 t) {
+    atomicAdd(lo_w, (unsigned long long)((uint64_t)t & ((1ull << 48) - 1)));
+    atomicAdd(hi_w, (unsigned long long)(uint64_t)(t >> 48));
 }
 
 // finish the m (<= 32) queued triangles {a, b, c} at queue entries [f, f + m) of the
@@ -1605,7 +1654,7 @@ __device__ __forceinline__ void hv_finish(P3Heavy &H, const HvQueue &Q, int f, i
         const TriTerms t = triangle_term_values_p(Sab, Sba, Sac, H.sca[p], Sbc, Scb, H.pac[p], Pab);
         acc_a += t.a;
         acc_b += t.b;
-        shared_add_u128(&H.clo[p], &H.chi[p], t.c);
+        shared_add_split(&H.clo[p], &H.chi[p], t.c);
     }
 }
 
@@ -1713,9 +1762,9 @@ __device__ __forceinline__ void hv_walk_b(P3Heavy &H, HvQueue &Q, const HvB &B, 
 // its warp; otherwise lane j takes node 32 g + j and stride is unused.
 template <bool kScr>
 __global__ void __launch_bounds__(kThreads, 5) p3_list_kernel(
-    int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
-    Rev R, const int32_t *__restrict__ xout, const NodeRec *__restrict__ rec, unsigned long long *acc,
-    unsigned long long *next_group, int64_t stride, unsigned long long *hvl, int64_t hvcap,
+    int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const int32_t *__restrict__ xsk,
+    const df *__restrict__ xS, Rev R, const int32_t *__restrict__ xout, const NodeRec *__restrict__ rec,
+    unsigned long long *acc, unsigned long long *next_group, int64_t stride, unsigned long long *hvl, int64_t hvcap,
     unsigned long long *hv_count) {
     __shared__ P3Stage stage[kP3Warps];
     __shared__ int32_t s_anode[kScr ? kP3Warps * 32 : 1];
@@ -1810,7 +1859,8 @@ __global__ void __launch_bounds__(kThreads, 5) p3_list_kernel(
                     }
 #pragma unroll
                     for (int q = 0; q < U; ++q)
-                        pos[q] = lo_e[q] >= 0 ? find_in_list(xcol, S.boff[lo_e[q]], S.bdeg[lo_e[q]], S.nb[hi_e[q]]) : -1;
+                        pos[q] = lo_e[q] >= 0 ? find_in_list_sk(xcol, xsk, S.boff[lo_e[q]], S.bdeg[lo_e[q]], S.nb[hi_e[q]])
+                                          : -1;
 #pragma unroll
                     for (int q = 0; q < U; ++q) {
                         bool hit = pos[q] >= 0;
@@ -1955,7 +2005,7 @@ __global__ void __launch_bounds__(kThreads, 3) p3_heavy_kernel(
             for (int32_t i = tid; i < cnt; i += kThreads) {
                 const unsigned long long lo = H.clo[i], hi = H.chi[i];
                 if (lo | hi) {
-                    atomic_add_u128(acc + 2 * (int64_t)xcol[bA + k0 + i], ((u128)hi << 64) | lo);
+                    atomic_add_u128(acc + 2 * (int64_t)xcol[bA + k0 + i], ((u128)hi << 48) + lo);
                     H.clo[i] = 0;
                     H.chi[i] = 0;
                 }
@@ -2310,20 +2360,23 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     // ---- P3: reverse values (mirror mode), then triangles
     if (g->tune.p3_mirror) {
         gx_mirror_kernel<<<grid_for(g->nnz, kMirTile, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xout,
-                                                                       g->xin, g->xtile, g->xR, err);
+                                                                       g->xin, g->xtile, g->xR, g->xsk, err);
         RS_LAUNCHED(g, s, "gx_mirror");
+    } else {
+        gx_skip_kernel<<<grid_for(g->nnz / 8 + 1, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xsk);
+        RS_LAUNCHED(g, s, "gx_skip");
     }
     const Rev R{g->tune.p3_mirror ? g->xR : nullptr, g->xoff, g->xcol, g->xS, g->xin, err};
     unsigned long long *next_group = g->wq + 7;
     unsigned long long *hvl = g->wq + wq_hv_word(n);
     const int64_t hvcap = hv_cap(g->nnz);
     if (g->perm)                                     // a graph numbered by community: scrambled groups
-        p3_list_kernel<true><<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, R, g->xout, g->rec,
-                                                                  g->acc, next_group, p3_stride(n), hvl, hvcap,
-                                                                  g->wq + kWqHvCount);
+        p3_list_kernel<true><<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xsk, g->xS, R, g->xout,
+                                                                  g->rec, g->acc, next_group, p3_stride(n), hvl,
+                                                                  hvcap, g->wq + kWqHvCount);
     else
-        p3_list_kernel<false><<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, R, g->xout, g->rec,
-                                                                   g->acc, next_group, 1, hvl, hvcap,
+        p3_list_kernel<false><<<grid_for(n, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xsk, g->xS, R, g->xout,
+                                                                   g->rec, g->acc, next_group, 1, hvl, hvcap,
                                                                    g->wq + kWqHvCount);
     RS_LAUNCHED(g, s, "p3_list");
     p3_heavy_kernel<<<grid_for(hvcap, 1, 3), NT, sizeof(P3Heavy), s>>>(n, g->xoff, g->xcol, g->xS, R, g->xout,

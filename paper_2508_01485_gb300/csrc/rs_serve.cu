@@ -1022,7 +1022,7 @@ int launch_incremental(rs_server *srv, Slot &sl, const Request &r) {
 
 // device bytes of a full copy of a base graph (CSR twice, cross lists, G_x slots
 // with both values, per-node records and workspaces)
-int64_t full_bytes_estimate(const Base &b) { return 37 * b.nnz + 170 * b.n + (16 << 20); }
+int64_t full_bytes_estimate(const Base &b) { return 38 * b.nnz + 170 * b.n + (16 << 20); }
 
 // full path: restore a copy of the base graph, apply the removals, rescore
 int launch_full(rs_server *srv, Slot &sl, const Request &r) {
