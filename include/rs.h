@@ -258,6 +258,13 @@ rs_status rs_launch_count(const rs_graph *g, int64_t *launches);
  *                columns, then the neighbours' labels, into shared memory
  *                with asynchronous copies (cp.async) before matching; 0:
  *                the loads are pipelined in registers two chunks ahead
+ *   rows_streams how the row kernels of the two passes share the GPU:     {-1, 0, 1, 2}
+ *                0: each row class on a stream of its own, the classes
+ *                with long per-row chains at high priority; 1: the hub
+ *                rows' kernels on one stream and the other classes, in
+ *                turn, on a second; 2: every row kernel in turn on the
+ *                step's stream; -1 (the default): 1 when the graph has
+ *                hub rows, else 0
  * Powers of two are required where a set is given.
  */
 typedef struct {
@@ -271,6 +278,7 @@ typedef struct {
     int32_t ctas_per_sm;
     int32_t p3_mirror;
     int32_t p1_stage;
+    int32_t rows_streams;
 } rs_tuning;
 
 /* rs_default_tuning -- the parameters a new graph starts with. */

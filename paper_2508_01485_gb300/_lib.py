@@ -23,7 +23,7 @@ RS_REORDER = 8
 _lib = None
 
 TUNING_FIELDS = ("small_max", "warp_cap", "cta_cap", "hub_chunk", "p2_cta_dx", "p1_cta_threads",
-                 "p2_cta_threads", "ctas_per_sm", "p3_mirror", "p1_stage")
+                 "p2_cta_threads", "ctas_per_sm", "p3_mirror", "p1_stage", "rows_streams")
 
 
 class Tuning(ctypes.Structure):

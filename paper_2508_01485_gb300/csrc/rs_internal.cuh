@@ -103,6 +103,7 @@ inline rs_tuning default_tuning_value() {
     t.ctas_per_sm = 8;
     t.p3_mirror = 1;
     t.p1_stage = 0;
+    t.rows_streams = -1;
     return t;
 }
 }  // namespace rs

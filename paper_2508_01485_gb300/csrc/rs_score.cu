@@ -2175,15 +2175,15 @@ int rs::prepare_score_kernels() {
 
 // the CTA-per-row kernels at the tuned CTA size
 template <int NT>
-static void launch_p1_large(rs_graph *g, const Batch &B, int *err, size_t smem) {
-    p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, smem, g->aux[2]>>>(
+static void launch_p1_large(rs_graph *g, const Batch &B, int *err, size_t smem, cudaStream_t st) {
+    p1_large_kernel<NT><<<grid_for(g->n_large, 1, 4), NT, smem, st>>>(
         g->off, g->col, g->lab, g->rows_large, g->n_large, B, g->LG, g->rec, g->Lall, err,
         g->rsum, g->cl_col, g->cl_lab, g->wq + 1);
 }
 template <int NT>
-static void launch_p2_large(rs_graph *g, const Batch &B, int *err, size_t smem) {
+static void launch_p2_large(rs_graph *g, const Batch &B, int *err, size_t smem, cudaStream_t st) {
     int32_t *L4 = g->p2rows + p2_list_start(4, g->n_mid, g->n_large);
-    p2_large_kernel<NT><<<grid_for(g->n_large, 1, 2), NT, smem, g->aux[4]>>>(
+    p2_large_kernel<NT><<<grid_for(g->n_large, 1, 2), NT, smem, st>>>(
         g->off, L4, g->p2cnt + 4, B, g->tune.p2_cta_dx + 1, g->LG, g->rec, g->rsum, g->cl_col,
         g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, Strict{g->col, g->sx}, g->wq + 6);
 }
@@ -2220,53 +2220,67 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     }
     prof_mark(g, s, "memset", false);
     size_t p1_smem = 8 * (size_t)g->large_cap, p2_smem = 32 * (size_t)g->large_cap;
-    // ---- P1: every row class on its own stream; the larger classes are launched
-    //      first, on high-priority streams, so their maxima seed w_max early and most
-    //      small rows skip theirs (the small rows fill in at the lowest priority)
-    if (int rc = fork_aux(g, s)) return rc;
+    // streams of the row kernels (rows_streams): every class on its own stream (0); the hub
+    // chain on stream 3 and every other class in turn on stream 0 (1); every kernel in turn
+    // on the step's stream (2).  On the 8M-node hub-skewed graph the hub chain is the longest
+    // path of both passes, and the other classes, spread over five more streams, held it back
+    // (step 65.7 ms against 63.9 with two streams); on graphs without hubs the classes' long
+    // per-row chains overlap best on separate streams (1M-node graph: 0.882 against 1.010 ms)
+    const int rmode = g->tune.rows_streams >= 0 ? g->tune.rows_streams : (g->n_hubs ? 1 : 0);
+    auto AX = [&](int i) -> cudaStream_t {
+        if (rmode == 2) return s;
+        if (rmode == 1) return i == 3 ? g->aux[3] : g->aux[0];
+        return g->aux[i];
+    };
+    // ---- P1: the larger classes are launched first (with per-class streams, on
+    //      high-priority ones), so their maxima seed w_max early and most small rows skip
+    //      theirs (the small rows fill in at the lowest priority)
+    if (rmode != 2)
+        if (int rc = fork_aux(g, s)) return rc;
     if (g->n_hubs) {
-        hub_p1_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
+        hub_p1_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, AX(3)>>>(
             g->off, g->col, g->lab, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items,
             g->tune.hub_chunk, g->hkey, g->hcnt, g->hagg, err);
-        RS_LAUNCHED(g, g->aux[3], "hub_p1_insert");
-        hub_p1_sums_kernel<NT><<<grid_for(g->n_hub_sitems, 1, 8), NT, 0, g->aux[3]>>>(
+        RS_LAUNCHED(g, AX(3), "hub_p1_insert");
+        hub_p1_sums_kernel<NT><<<grid_for(g->n_hub_sitems, 1, 8), NT, 0, AX(3)>>>(
             g->hubs, g->hub_sitem, g->hub_srange, g->n_hub_sitems, g->LG, g->hkey, g->hcnt, g->hagg);
-        RS_LAUNCHED(g, g->aux[3], "hub_p1_sums");
-        hub_p1_finish_kernel<NT><<<(unsigned)((g->n_hubs + NT - 1) / NT), NT, 0, g->aux[3]>>>(
+        RS_LAUNCHED(g, AX(3), "hub_p1_sums");
+        hub_p1_finish_kernel<NT><<<(unsigned)((g->n_hubs + NT - 1) / NT), NT, 0, AX(3)>>>(
             g->off, g->lab, g->hubs, g->n_hubs, B, g->LG, g->hagg, g->rec, g->Lall);
-        RS_LAUNCHED(g, g->aux[3], "hub_p1_finish");
-        hub_p1_colmax_kernel<NT><<<grid_for(g->n_hub_sitems, 1, 8), NT, 0, g->aux[3]>>>(
+        RS_LAUNCHED(g, AX(3), "hub_p1_finish");
+        hub_p1_colmax_kernel<NT><<<grid_for(g->n_hub_sitems, 1, 8), NT, 0, AX(3)>>>(
             g->off, g->hubs, g->hub_sitem, g->hub_srange, g->n_hub_sitems, B, g->LG, g->hkey, g->hcnt, g->hagg,
             g->hsig);
-        RS_LAUNCHED(g, g->aux[3], "hub_p1_colmax");
+        RS_LAUNCHED(g, AX(3), "hub_p1_colmax");
     }
     if (g->n_large) {
         switch (g->tune.p1_cta_threads) {
-        case 128: launch_p1_large<128>(g, B, err, p1_smem); break;
-        case 512: launch_p1_large<512>(g, B, err, p1_smem); break;
-        default: launch_p1_large<256>(g, B, err, p1_smem); break;
+        case 128: launch_p1_large<128>(g, B, err, p1_smem, AX(2)); break;
+        case 512: launch_p1_large<512>(g, B, err, p1_smem, AX(2)); break;
+        default: launch_p1_large<256>(g, B, err, p1_smem, AX(2)); break;
         }
-        RS_LAUNCHED(g, g->aux[2], "p1_large");
+        RS_LAUNCHED(g, AX(2), "p1_large");
     }
     if (g->n_mid) {
-        p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, cps), NT, 0, g->aux[4]>>>(
+        p1_mid_kernel<<<grid_for(g->n_mid * 32, NT, cps), NT, 0, AX(4)>>>(
             g->off, g->col, g->lab, g->rows_mid, g->n_mid, B, g->LG, g->rec, g->Lall, err,
             g->rsum, g->cl_col, g->cl_lab, g->wq + 0);
-        RS_LAUNCHED(g, g->aux[4], "p1_mid");
+        RS_LAUNCHED(g, AX(4), "p1_mid");
     }
     if (g->n_small) {
         if (g->tune.p1_stage)
             p1_small_staged_kernel<<<grid_for(g->n_small, kStageWarps * 32, cps), kStageWarps * 32,
-                                     kStageWarps * (sizeof(SmallTile) + sizeof(SmallStage)), g->aux[0]>>>(
+                                     kStageWarps * (sizeof(SmallTile) + sizeof(SmallStage)), AX(0)>>>(
                 g->off, g->col, g->lab, g->rows_small, g->n_small, B, g->LG, g->rec, g->Lall,
                 g->rsum, g->cl_col, g->cl_lab);
         else
-            p1_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[0]>>>(
+            p1_small_kernel<<<grid_for(g->n_small, NT, cps), NT, 0, AX(0)>>>(
                 g->off, g->col, g->lab, g->rows_small, g->n_small, B, g->LG, g->rec, g->Lall,
                 g->rsum, g->cl_col, g->cl_lab);
-        RS_LAUNCHED(g, g->aux[0], "p1_small");
+        RS_LAUNCHED(g, AX(0), "p1_small");
     }
-    if (int rc = join_aux(g, s, rs_graph::kAux)) return rc;
+    if (rmode != 2)
+        if (int rc = join_aux(g, s, rs_graph::kAux)) return rc;
     // ---- P2 row lists (on stream 5) beside the G_x offsets (on the step's stream)
     const int64_t nm = g->n_mid, nl = g->n_large;
     auto Lst = [&](int c) { return g->p2rows + p2_list_start(c, nm, nl); };
@@ -2287,76 +2301,78 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         strict_pairs_kernel<<<grid_for(n * 32, NT, cps), NT, 0, s>>>(n, g->off, g->col, g->lab, g->rec, g->sx);
         RS_LAUNCHED(g, s, "strict_pairs");
     }
-    // ---- P2: every row class on its own stream; the many-short-rows kernels on the
-    //      low-priority streams 0 and 1, the rows with long chains on the others.  The hub
+    // ---- P2: with per-class streams, the many-short-rows kernels on the low-priority
+    //      streams 0 and 1, the rows with long chains on the others.  The hub
     //      chain (three dependent kernels, the longest of the phase on hub-skewed graphs)
     //      is issued first, so that its blocks are dispatched ahead of the other classes'
-    if (int rc = fork_aux(g, s)) return rc;
+    if (rmode != 2)
+        if (int rc = fork_aux(g, s)) return rc;
     if (g->n_hubs) {
-        hub_p2_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
+        hub_p2_insert_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, AX(3)>>>(
             g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
             g->hkey, g->hq,
             g->hitem_out, g->hitem_in, g->hslot, err);
-        RS_LAUNCHED(g, g->aux[3], "hub_p2_insert");
-        hub_p2_counts_kernel<NT><<<(unsigned)((g->n_hubs + NT - 1) / NT), NT, 0, g->aux[3]>>>(
+        RS_LAUNCHED(g, AX(3), "hub_p2_insert");
+        hub_p2_counts_kernel<NT><<<(unsigned)((g->n_hubs + NT - 1) / NT), NT, 0, AX(3)>>>(
             g->hubs, g->n_hubs, g->hitem_out, g->hitem_in, g->xout, g->xin);
-        RS_LAUNCHED(g, g->aux[3], "hub_p2_counts");
-        hub_p2_emit_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, g->aux[3]>>>(
+        RS_LAUNCHED(g, AX(3), "hub_p2_counts");
+        hub_p2_emit_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, AX(3)>>>(
             g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
             g->hslot,
             g->hq, g->hsig, g->hitem_out, g->hitem_in, g->acc, g->xoff, g->xcol, g->xS, err, SX);
-        RS_LAUNCHED(g, g->aux[3], "hub_p2_emit");
+        RS_LAUNCHED(g, AX(3), "hub_p2_emit");
     }
     if (g->n_small) {
-        p2_small_kernel<32><<<grid_for(g->n_small, NT, cps), NT, 0, g->aux[0]>>>(
+        p2_small_kernel<32><<<grid_for(g->n_small, NT, cps), NT, 0, AX(0)>>>(
             g->off, g->rows_small, g->n_small, nullptr, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
             g->xoff, g->xcol, g->xS, g->xout, g->xin, SX);
-        RS_LAUNCHED(g, g->aux[0], "p2_small");
+        RS_LAUNCHED(g, AX(0), "p2_small");
     }
     if (g->tune.p3_mirror) {                         // the mirror's tile table, beside P2
         if (!g->xR || !g->xtile) return fail(RS_EINVAL, "rs_score: p3_mirror is set but its buffers are missing");
-        mirror_tiles_kernel<<<grid_for(n, NT, cps), NT, 0, g->aux[0]>>>(n, g->xoff, g->xtile);
-        RS_LAUNCHED(g, g->aux[0], "mirror_tiles");
+        mirror_tiles_kernel<<<grid_for(n, NT, cps), NT, 0, AX(0)>>>(n, g->xoff, g->xtile);
+        RS_LAUNCHED(g, AX(0), "mirror_tiles");
     }
     const size_t smem256 = (size_t)kMidWarps * 256 * kMidSlotBytes, smem512 = (size_t)kMidWarps * 512 * kMidSlotBytes;
     if (nm + nl) {
         // the mid and large rows with at most 32 cross neighbours, in the tile kernel
-        p2_small_kernel<kNarrowRows><<<grid_for((nm + nl) * (32 / kNarrowRows), NT, cps), NT, 0, g->aux[1]>>>(
+        p2_small_kernel<kNarrowRows><<<grid_for((nm + nl) * (32 / kNarrowRows), NT, cps), NT, 0, AX(1)>>>(
             g->off, Lst(0), 0, g->p2cnt + 0, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
             g->xcol, g->xS, g->xout, g->xin, SX);
-        RS_LAUNCHED(g, g->aux[1], "p2_narrow");
+        RS_LAUNCHED(g, AX(1), "p2_narrow");
     }
     if (g->n_mid) {
-        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 4), NT, smem256, g->aux[5]>>>(
+        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 4), NT, smem256, AX(5)>>>(
             g->off, Lst(1), g->p2cnt + 1, B, 1 << 30, 256, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
             g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 2);
-        RS_LAUNCHED(g, g->aux[5], "p2_mid");
+        RS_LAUNCHED(g, AX(5), "p2_mid");
         // few rows, each a long single-warp chain: on the lightly loaded stream
-        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, smem512, g->aux[2]>>>(
+        p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, smem512, AX(2)>>>(
             g->off, Lst(5), g->p2cnt + 5, B, 1 << 30, 512, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
             g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 3);
-        RS_LAUNCHED(g, g->aux[2], "p2_mid_wide");
+        RS_LAUNCHED(g, AX(2), "p2_mid_wide");
     }
     if (g->n_large) {
         // large rows whose cross list fits a per-warp table go warp-per-row too
-        p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 4), NT, smem256, g->aux[2]>>>(
+        p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 4), NT, smem256, AX(2)>>>(
             g->off, Lst(3), g->p2cnt + 3, B, g->tune.p2_cta_dx, 256, g->LG, g->rec, g->rsum, g->cl_col,
             g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 4);
-        RS_LAUNCHED(g, g->aux[2], "p2_large_warp");
+        RS_LAUNCHED(g, AX(2), "p2_large_warp");
         // (with hubs, stream 3 carries the hub chain: these rows go beside p2_mid instead)
-        cudaStream_t sw = g->n_hubs ? g->aux[5] : g->aux[3];
+        cudaStream_t sw = g->n_hubs || rmode == 1 ? AX(5) : AX(3);
         p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, smem512, sw>>>(
             g->off, Lst(6), g->p2cnt + 6, B, g->tune.p2_cta_dx, 512, g->LG, g->rec, g->rsum, g->cl_col,
             g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 5);
         RS_LAUNCHED(g, sw, "p2_large_warp_wide");
         switch (g->tune.p2_cta_threads) {
-        case 256: launch_p2_large<256>(g, B, err, p2_smem); break;
-        case 512: launch_p2_large<512>(g, B, err, p2_smem); break;
-        default: launch_p2_large<1024>(g, B, err, p2_smem); break;
+        case 256: launch_p2_large<256>(g, B, err, p2_smem, AX(4)); break;
+        case 512: launch_p2_large<512>(g, B, err, p2_smem, AX(4)); break;
+        default: launch_p2_large<1024>(g, B, err, p2_smem, AX(4)); break;
         }
-        RS_LAUNCHED(g, g->aux[4], "p2_large");
+        RS_LAUNCHED(g, AX(4), "p2_large");
     }
-    if (int rc = join_aux(g, s, rs_graph::kAux)) return rc;
+    if (rmode != 2)
+        if (int rc = join_aux(g, s, rs_graph::kAux)) return rc;
     // ---- P3: reverse values (mirror mode), then triangles
     if (g->tune.p3_mirror) {
         gx_mirror_kernel<<<grid_for(g->nnz, kMirTile, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xout,

@@ -41,6 +41,8 @@ static int check_tuning(const rs_tuning &t) {
         return fail(RS_EINVAL, "rs_tuning: p3_mirror must be 0 or 1");
     if (t.p1_stage != 0 && t.p1_stage != 1)
         return fail(RS_EINVAL, "rs_tuning: p1_stage must be 0 or 1");
+    if (t.rows_streams < -1 || t.rows_streams > 2)
+        return fail(RS_EINVAL, "rs_tuning: rows_streams must be -1, 0, 1 or 2");
     return 0;
 }
 
@@ -154,6 +156,7 @@ extern "C" rs_status rs_autotune(rs_graph *g, double *scores, int32_t topk_k, in
         {&rs_tuning::hub_chunk, {1024, 4096, 16384}},
         {&rs_tuning::p3_mirror, {0, 1}},
         {&rs_tuning::p1_stage, {0, 1}},
+        {&rs_tuning::rows_streams, {0, 1, 2}},
     };
     for (size_t a = 0; !rc && a < axes.size(); ++a) {
         for (int32_t v : axes[a].values) {

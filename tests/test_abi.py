@@ -48,3 +48,14 @@ def test_library_exports_nothing_undeclared(libpath):
         pytest.skip("nm unavailable")
     exported = {line.split()[-1] for line in out.stdout.splitlines() if line.split()[-1].startswith("rs_")}
     assert exported == declared()
+
+
+def test_binding_tuning_struct_matches_the_header():
+    """The Python mirror of rs_tuning lists the header's int32 fields in the header's order."""
+    text = open(os.path.join(ROOT, "include", "rs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\} rs_tuning;", text).group(1)
+    fields = re.findall(r"int32_t\s+(\w+)\s*;", body)
+    assert len(fields) == len([x for x in body.split(";") if x.strip()])
+    from paper_2508_01485_gb300 import _lib
+    assert tuple(fields) == _lib.TUNING_FIELDS

@@ -25,13 +25,13 @@ def rs():
 EXTREMES = [
     # every row above degree 1 is a hub of the global-table path, in tiny chunks
     dict(small_max=1, warp_cap=64, cta_cap=64, hub_chunk=512, p2_cta_dx=32, p1_cta_threads=128,
-         p2_cta_threads=256, ctas_per_sm=1, p3_mirror=1, p1_stage=1),
+         p2_cta_threads=256, ctas_per_sm=1, p3_mirror=1, p1_stage=1, rows_streams=2),
     dict(small_max=16, warp_cap=128, cta_cap=512, hub_chunk=1024, p2_cta_dx=64, p1_cta_threads=512,
-         p2_cta_threads=512, ctas_per_sm=16, p3_mirror=0, p1_stage=1),
+         p2_cta_threads=512, ctas_per_sm=16, p3_mirror=0, p1_stage=1, rows_streams=1),
     dict(small_max=32, warp_cap=512, cta_cap=512, hub_chunk=65536, p2_cta_dx=256, p1_cta_threads=256,
-         p2_cta_threads=1024, ctas_per_sm=32, p3_mirror=1, p1_stage=1),
+         p2_cta_threads=1024, ctas_per_sm=32, p3_mirror=1, p1_stage=1, rows_streams=0),
     dict(small_max=24, warp_cap=256, cta_cap=2048, hub_chunk=2048, p2_cta_dx=100, p1_cta_threads=128,
-         p2_cta_threads=256, ctas_per_sm=3, p3_mirror=0, p1_stage=0),
+         p2_cta_threads=256, ctas_per_sm=3, p3_mirror=0, p1_stage=0, rows_streams=-1),
 ]
 
 
@@ -106,7 +106,7 @@ def test_reverse_values_by_lookup_or_mirror_give_the_same_bits(rs, which):
     dict(warp_cap=512, cta_cap=256), dict(cta_cap=4096), dict(hub_chunk=256), dict(hub_chunk=3000),
     dict(p2_cta_dx=31), dict(p2_cta_dx=257), dict(p1_cta_threads=64), dict(p2_cta_threads=128),
     dict(ctas_per_sm=0), dict(ctas_per_sm=33), dict(p3_mirror=2), dict(p3_mirror=-1),
-    dict(p1_stage=2), dict(p1_stage=-1),
+    dict(p1_stage=2), dict(p1_stage=-1), dict(rows_streams=3), dict(rows_streams=-2),
 ])
 def test_invalid_tuning_is_rejected(rs, bad):
     G = rs.Graph.from_generated(graphgen.sbm_2000())
