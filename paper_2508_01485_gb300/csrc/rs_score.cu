@@ -808,6 +808,16 @@ constexpr int kNarrowRows = 8;                 // rows per tile of the narrow mi
 // lanes); lane l prepares and closes row l.  As no row spans two chunks, a
 // community's count f and Type-II sum come from one warp match on
 // (row, community).
+// one G_x slot p of a row: its id and value, and for the first slot of an 8-slot sector of
+// the slot space also the packed index entry xsk[p / 8] (searches of long out-lists read it;
+// every slot inside a row is written once here, so the entries of sectors starting inside
+// rows are complete when P2 ends)
+__device__ __forceinline__ void gx_put(int32_t *xcol, df *xS, int32_t *xsk, int64_t p, int32_t u, df sig) {
+    xcol[p] = u;
+    xS[p] = sig;
+    if ((p & 7) == 0) xsk[p >> 3] = u;
+}
+
 struct P2Tile {
     int32_t pre[33];            // prefix sums of dx over the tile
     int64_t rb[32], xb[32];     // cross list start (= CSR start), G_x row start
@@ -824,7 +834,7 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ rows, int64_t nrows_host,
     const int32_t *__restrict__ nrows_dev, const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
-    const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
+    const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS, int32_t *__restrict__ xsk,
     int32_t *__restrict__ xout, int32_t *__restrict__ xin, Strict SX) {
     __shared__ P2Tile tiles[kThreads / 32];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -918,12 +928,12 @@ __global__ void __launch_bounds__(kThreads) p2_small_kernel(
             __syncwarp();
             if (o) {
                 int64_t p = T.xb[r] + bo + __popc(go & lanemask_lt());
-                xcol[p] = u; xS[p] = sig;
+                gx_put(xcol, xS, xsk, p, u, sig);
                 if (lane == __ffs(go) - 1) T.no[r] = bo + __popc(go);
             }
             if (in) {
                 int64_t p = T.xb[r] + T.dx[r] - 1 - (bi + __popc(gi & lanemask_lt()));
-                xcol[p] = u; xS[p] = sig;
+                gx_put(xcol, xS, xsk, p, u, sig);
                 if (lane == __ffs(gi) - 1) T.ni[r] = bi + __popc(gi);
             }
             __syncwarp();
@@ -942,7 +952,7 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_dev, Batch B, int32_t dx_max, int32_t wslots,
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
-    const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
+    const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS, int32_t *__restrict__ xsk,
     int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err, Strict SX, unsigned long long *wq) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t stage[kThreads];
@@ -1014,8 +1024,8 @@ __global__ void __launch_bounds__(kThreads) p2_mid_kernel(
                     bool o = inx && rank_after(ru.dx, u, dx, w);
                     bool in = inx && !o;
                     unsigned mo = __ballot_sync(FULL, o), mi = __ballot_sync(FULL, in);
-                    if (o) { int64_t p = xb + bo + __popc(mo & lanemask_lt()); xcol[p] = u; xS[p] = sig; }
-                    if (in) { int64_t p = xb + dx - 1 - (bi + __popc(mi & lanemask_lt())); xcol[p] = u; xS[p] = sig; }
+                    if (o) gx_put(xcol, xS, xsk, xb + bo + __popc(mo & lanemask_lt()), u, sig);
+                    if (in) gx_put(xcol, xS, xsk, xb + dx - 1 - (bi + __popc(mi & lanemask_lt())), u, sig);
                     bo += __popc(mo); bi += __popc(mi);
                 }
             }
@@ -1040,7 +1050,7 @@ __device__ __forceinline__ Tab p2_table(unsigned char *base, uint32_t cap) {
 template <int NT>
 __device__ __forceinline__ void gx_round(bool out, bool in, int64_t xb, int32_t dxw, int32_t u, df sig,
                                          int32_t &base_out, int32_t &base_in, int32_t *xcol, df *xS,
-                                         int32_t *sh_cnt /* 2 * NT/32 */) {
+                                         int32_t *xsk, int32_t *sh_cnt /* 2 * NT/32 */) {
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned mo = __ballot_sync(FULL, out), mi = __ballot_sync(FULL, in);
     if (lane == 0) { sh_cnt[wid] = __popc(mo); sh_cnt[NT / 32 + wid] = __popc(mi); }
@@ -1050,14 +1060,8 @@ __device__ __forceinline__ void gx_round(bool out, bool in, int64_t xb, int32_t 
         if (j < wid) { po += sh_cnt[j]; pi += sh_cnt[NT / 32 + j]; }
         to += sh_cnt[j]; ti += sh_cnt[NT / 32 + j];
     }
-    if (out) {
-        int64_t p = xb + po + __popc(mo & lanemask_lt());
-        xcol[p] = u; xS[p] = sig;
-    }
-    if (in) {
-        int64_t p = xb + dxw - 1 - (pi + __popc(mi & lanemask_lt()));
-        xcol[p] = u; xS[p] = sig;
-    }
+    if (out) gx_put(xcol, xS, xsk, xb + po + __popc(mo & lanemask_lt()), u, sig);
+    if (in) gx_put(xcol, xS, xsk, xb + dxw - 1 - (pi + __popc(mi & lanemask_lt())), u, sig);
     base_out += to; base_in += ti;
     __syncthreads();
 }
@@ -1067,7 +1071,7 @@ __global__ void __launch_bounds__(NT) p2_large_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_dev, Batch B, int32_t dx_min,
     const uint64_t *__restrict__ LG, const NodeRec *__restrict__ rec, const RowSum *__restrict__ rsum,
     const int32_t *__restrict__ cl_col, const int32_t *__restrict__ cl_lab, unsigned long long *acc,
-    const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS,
+    const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol, df *__restrict__ xS, int32_t *__restrict__ xsk,
     int32_t *__restrict__ xout, int32_t *__restrict__ xin, int *err, Strict SX, unsigned long long *wq) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int32_t sh_cnt[2 * NT / 32];
@@ -1139,7 +1143,7 @@ __global__ void __launch_bounds__(NT) p2_large_kernel(
             if (dx >= 2) {
                 bool inx = ok && ru.dx >= 2;
                 bool o = inx && rank_after(ru.dx, u, dx, w);
-                gx_round<NT>(o, inx && !o, xb, dx, u, sig, bo, bi, xcol, xS, sh_cnt);
+                gx_round<NT>(o, inx && !o, xb, dx, u, sig, bo, bi, xcol, xS, xsk, sh_cnt);
             }
         }
         if (tid == 0) { xout[w] = bo; xin[w] = bi; }
@@ -1228,7 +1232,7 @@ __global__ void __launch_bounds__(NT) hub_p2_emit_kernel(
     const NodeRec *__restrict__ rec, const int32_t *__restrict__ hslot,
     const unsigned long long *hq, const df *hsig, const int32_t *hitem_out, const int32_t *hitem_in,
     unsigned long long *acc, const int64_t *__restrict__ xoff, int32_t *__restrict__ xcol,
-    df *__restrict__ xS, int *err, Strict SX) {
+    df *__restrict__ xS, int32_t *__restrict__ xsk, int *err, Strict SX) {
     __shared__ int32_t sh_cnt[2 * NT / 32];
     int tid = threadIdx.x;
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -1265,7 +1269,7 @@ __global__ void __launch_bounds__(NT) hub_p2_emit_kernel(
             if (rw.dx >= 2) {
                 bool inx = cross && ru.dx >= 2;
                 bool o = inx && rank_after(ru.dx, u, rw.dx, h.row);
-                gx_round<NT>(o, inx && !o, xb, rw.dx, u, sig, bo, bi, xcol, xS, sh_cnt);
+                gx_round<NT>(o, inx && !o, xb, rw.dx, u, sig, bo, bi, xcol, xS, xsk, sh_cnt);
             }
         }
     }
@@ -1313,6 +1317,51 @@ struct Rev {
     }
 };
 
+// position of key in the sorted list xcol[lo, lo + len), or -1
+__device__ __forceinline__ int64_t find_in_list(const int32_t *xcol, int64_t lo, int32_t len, int32_t key) {
+    int32_t l = 0, h = len;
+    while (l < h) {
+        int32_t mid = (l + h) >> 1;
+        if (xcol[lo + mid] < key) l = mid + 1; else h = mid;
+    }
+    return (l < len && xcol[lo + l] == key) ? lo + l : -1;
+}
+
+// lists of at most this many ids are binary-searched directly (they span at most 9 sectors)
+constexpr int32_t kSkipMin = 64;
+
+// position of key in the sorted list xcol[lo, lo + len), or -1.  A list of more than kSkipMin
+// ids is searched in xsk (xsk[t] = xcol[8 t], the first id of every 8-slot sector of the
+// slot space, written by P2 with the slots) first, over the sectors that start inside it, for the one sector
+// that can hold key (the last whose first id is <= key; before them, the sector holding the
+// list's head, when the list does not start a sector); that sector is then read with two
+// 16-byte loads and its slots inside the list compared with key.  The chain of dependent
+// loads of a long list thus runs over the packed index (8 times denser than the list) and
+// ends with one sector.  xcol is padded to whole sectors, so the last sector is readable.
+__device__ __forceinline__ int64_t find_in_list_sk(const int32_t *xcol, const int32_t *xsk, int64_t lo, int32_t len,
+                                                   int32_t key) {
+    if (len <= kSkipMin) return find_in_list(xcol, lo, len, key);
+    const int64_t end = lo + len;
+    const int64_t t0 = (lo + 7) >> 3;                // first sector starting inside the list
+    const int32_t ns = (int32_t)(((end - 1) >> 3) - t0 + 1);
+    int32_t l = 0, h = ns;                           // first of them whose first id exceeds key
+    while (l < h) {
+        const int32_t mid = (l + h) >> 1;
+        if (__ldg(xsk + t0 + mid) <= key) l = mid + 1; else h = mid;
+    }
+    const int64_t t = t0 + l - 1;
+    if (t < (lo >> 3)) return -1;                    // key is below the first id, which starts a sector
+    const int4 *v = reinterpret_cast<const int4 *>(xcol + 8 * t);
+    const int4 x = __ldg(v), y = __ldg(v + 1);
+    const int32_t e[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+    const int64_t b = 8 * t;
+    int64_t pos = -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if (e[j] == key && b + j >= lo && b + j < end) pos = b + j;
+    return pos;
+}
+
 // P3m (mirror, when p3_mirror is set): every G_x out-slot (w -> u) receives the reverse value
 // S(u -> w), which row u wrote at its in-slot for w.  Node u's slots are
 // [xoff[u], xoff[u] + dx(u)), its in-slots the last xin(u) of them.  The slot
@@ -1350,24 +1399,20 @@ __device__ __forceinline__ int64_t last_leq(const int64_t *xoff, int64_t lo, int
     return lo;
 }
 
-// copy S(u -> w) from u's in-slot sl to w's out-slot for u
+// copy S(u -> w) from u's in-slot sl to w's out-slot for u (found in w's out-list, through
+// the packed index when the list is long)
 __device__ __forceinline__ void mirror_one(int64_t sl, int32_t u, const int64_t *xoff, const int32_t *xcol,
-                                           const df *xS, const int32_t *xout, df *xR, int *err) {
-    int32_t w = xcol[sl];
-    int64_t wb = xoff[w];
-    int32_t len = xout[w], l = 0, h = len;
-    while (l < h) {
-        int32_t mid = (l + h) >> 1;
-        if (xcol[wb + mid] < u) l = mid + 1; else h = mid;
-    }
-    if (l < len && xcol[wb + l] == u) xR[wb + l] = xS[sl];
+                                           const int32_t *xsk, const df *xS, const int32_t *xout, df *xR, int *err) {
+    const int32_t w = xcol[sl];
+    const int64_t pos = find_in_list_sk(xcol, xsk, xoff[w], xout[w], u);
+    if (pos >= 0) xR[pos] = xS[sl];
     else atomicOr(err, 16);
 }
 
 __global__ void __launch_bounds__(kThreads) gx_mirror_kernel(
     int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol, const df *__restrict__ xS,
     const int32_t *__restrict__ xout, const int32_t *__restrict__ xin, const int32_t *__restrict__ cover,
-    df *__restrict__ xR, int32_t *__restrict__ xsk, int *err) {
+    df *__restrict__ xR, const int32_t *__restrict__ xsk, int *err) {
     __shared__ int64_t s_lo[kMirNodes];          // first in-slot of each staged node inside the tile
     __shared__ int32_t s_pre[kMirNodes + 1];     // prefix sums of the staged nodes' in-slots in the tile
     __shared__ int32_t s_wsum[kThreads / 32];
@@ -1376,7 +1421,6 @@ __global__ void __launch_bounds__(kThreads) gx_mirror_kernel(
     const int64_t tiles = (S + kMirTile - 1) / kMirTile;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         int64_t s0 = t * kMirTile, s1 = min(S, s0 + kMirTile);
-        for (int64_t q = (s0 >> 3) + tid; q < ((s1 + 7) >> 3); q += blockDim.x) xsk[q] = xcol[8 * q];
         // nodes [ulo, uhi): from the one holding s0 to the one holding s1 (or the last slot)
         int64_t ulo = cover[t], uhi = (int64_t)cover[t + 1] + 1;
         __syncthreads();                             // the previous tile's stage is free
@@ -1384,7 +1428,7 @@ __global__ void __launch_bounds__(kThreads) gx_mirror_kernel(
         if (nn > kMirNodes) {
             for (int64_t sl = s0 + tid; sl < s1; sl += blockDim.x) {
                 int64_t u = last_leq(xoff, ulo, uhi, sl);
-                if (sl >= xoff[u + 1] - xin[u]) mirror_one(sl, (int32_t)u, xoff, xcol, xS, xout, xR, err);
+                if (sl >= xoff[u + 1] - xin[u]) mirror_one(sl, (int32_t)u, xoff, xcol, xsk, xS, xout, xR, err);
             }
             continue;
         }
@@ -1432,7 +1476,7 @@ __global__ void __launch_bounds__(kThreads) gx_mirror_kernel(
                 int32_t mid = (lo + hi) >> 1;
                 if (s_pre[mid] <= q) lo = mid; else hi = mid;
             }
-            mirror_one(s_lo[lo] + (q - s_pre[lo]), (int32_t)(ulo + lo), xoff, xcol, xS, xout, xR, err);
+            mirror_one(s_lo[lo] + (q - s_pre[lo]), (int32_t)(ulo + lo), xoff, xcol, xsk, xS, xout, xR, err);
         }
     }
 }
@@ -1498,60 +1542,6 @@ __device__ __forceinline__ void p3_flush(const P3Stage &S, const int32_t *anode,
 
 __device__ __forceinline__ bool rank_less(int32_t dx1, int32_t id1, int32_t dx2, int32_t id2) {
     return dx1 < dx2 || (dx1 == dx2 && id1 < id2);
-}
-
-// position of key in the sorted list xcol[lo, lo + len), or -1
-__device__ __forceinline__ int64_t find_in_list(const int32_t *xcol, int64_t lo, int32_t len, int32_t key) {
-    int32_t l = 0, h = len;
-    while (l < h) {
-        int32_t mid = (l + h) >> 1;
-        if (xcol[lo + mid] < key) l = mid + 1; else h = mid;
-    }
-    return (l < len && xcol[lo + l] == key) ? lo + l : -1;
-}
-
-// lists of at most this many ids are binary-searched directly (they span at most 9 sectors)
-constexpr int32_t kSkipMin = 64;
-
-// xsk[t] = xcol[8 t]: the first id of every 8-slot sector of the G_x slot space, a packed
-// index of the out-lists' ids, written once the rows are complete (by the mirror pass, or
-// by this kernel when the mirror pass is off)
-__global__ void gx_skip_kernel(int64_t n, const int64_t *__restrict__ xoff, const int32_t *__restrict__ xcol,
-                               int32_t *__restrict__ xsk) {
-    const int64_t T = (xoff[n] + 7) >> 3;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x)
-        xsk[t] = xcol[8 * t];
-}
-
-// position of key in the sorted list xcol[lo, lo + len), or -1.  A list of more than kSkipMin
-// ids is searched in xsk first, over the sectors that start inside it, for the one sector
-// that can hold key (the last whose first id is <= key; before them, the sector holding the
-// list's head, when the list does not start a sector); that sector is then read with two
-// 16-byte loads and its slots inside the list compared with key.  The chain of dependent
-// loads of a long list thus runs over the packed index (8 times denser than the list) and
-// ends with one sector.  xcol is padded to whole sectors, so the last sector is readable.
-__device__ __forceinline__ int64_t find_in_list_sk(const int32_t *xcol, const int32_t *xsk, int64_t lo, int32_t len,
-                                                   int32_t key) {
-    if (len <= kSkipMin) return find_in_list(xcol, lo, len, key);
-    const int64_t end = lo + len;
-    const int64_t t0 = (lo + 7) >> 3;                // first sector starting inside the list
-    const int32_t ns = (int32_t)(((end - 1) >> 3) - t0 + 1);
-    int32_t l = 0, h = ns;                           // first of them whose first id exceeds key
-    while (l < h) {
-        const int32_t mid = (l + h) >> 1;
-        if (__ldg(xsk + t0 + mid) <= key) l = mid + 1; else h = mid;
-    }
-    const int64_t t = t0 + l - 1;
-    if (t < (lo >> 3)) return -1;                    // key is below the first id, which starts a sector
-    const int4 *v = reinterpret_cast<const int4 *>(xcol + 8 * t);
-    const int4 x = __ldg(v), y = __ldg(v + 1);
-    const int32_t e[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-    const int64_t b = 8 * t;
-    int64_t pos = -1;
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-        if (e[j] == key && b + j >= lo && b + j < end) pos = b + j;
-    return pos;
 }
 
 // Heavy nodes: a wedge walk, one CTA per task.  A task is a heavy node a with a block
@@ -2185,7 +2175,7 @@ static void launch_p2_large(rs_graph *g, const Batch &B, int *err, size_t smem, 
     int32_t *L4 = g->p2rows + p2_list_start(4, g->n_mid, g->n_large);
     p2_large_kernel<NT><<<grid_for(g->n_large, 1, 2), NT, smem, st>>>(
         g->off, L4, g->p2cnt + 4, B, g->tune.p2_cta_dx + 1, g->LG, g->rec, g->rsum, g->cl_col,
-        g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, Strict{g->col, g->sx}, g->wq + 6);
+        g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xsk, g->xout, g->xin, err, Strict{g->col, g->sx}, g->wq + 6);
 }
 
 // a stride near n / golden ratio, coprime to n (a bijection of [0, n) by multiplication)
@@ -2319,13 +2309,13 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         hub_p2_emit_kernel<NT><<<grid_for(g->n_hub_items, 1, 8), NT, 0, AX(3)>>>(
             g->off, g->col, g->hubs, g->hub_items, g->hub_item_chunk, g->n_hub_items, g->tune.hub_chunk, g->rec,
             g->hslot,
-            g->hq, g->hsig, g->hitem_out, g->hitem_in, g->acc, g->xoff, g->xcol, g->xS, err, SX);
+            g->hq, g->hsig, g->hitem_out, g->hitem_in, g->acc, g->xoff, g->xcol, g->xS, g->xsk, err, SX);
         RS_LAUNCHED(g, AX(3), "hub_p2_emit");
     }
     if (g->n_small) {
         p2_small_kernel<32><<<grid_for(g->n_small, NT, cps), NT, 0, AX(0)>>>(
             g->off, g->rows_small, g->n_small, nullptr, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
-            g->xoff, g->xcol, g->xS, g->xout, g->xin, SX);
+            g->xoff, g->xcol, g->xS, g->xsk, g->xout, g->xin, SX);
         RS_LAUNCHED(g, AX(0), "p2_small");
     }
     if (g->tune.p3_mirror) {                         // the mirror's tile table, beside P2
@@ -2338,31 +2328,31 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         // the mid and large rows with at most 32 cross neighbours, in the tile kernel
         p2_small_kernel<kNarrowRows><<<grid_for((nm + nl) * (32 / kNarrowRows), NT, cps), NT, 0, AX(1)>>>(
             g->off, Lst(0), 0, g->p2cnt + 0, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc, g->xoff,
-            g->xcol, g->xS, g->xout, g->xin, SX);
+            g->xcol, g->xS, g->xsk, g->xout, g->xin, SX);
         RS_LAUNCHED(g, AX(1), "p2_narrow");
     }
     if (g->n_mid) {
         p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 4), NT, smem256, AX(5)>>>(
             g->off, Lst(1), g->p2cnt + 1, B, 1 << 30, 256, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
-            g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 2);
+            g->xoff, g->xcol, g->xS, g->xsk, g->xout, g->xin, err, SX, g->wq + 2);
         RS_LAUNCHED(g, AX(5), "p2_mid");
         // few rows, each a long single-warp chain: on the lightly loaded stream
         p2_mid_kernel<<<grid_for(g->n_mid * 32, NT, 2), NT, smem512, AX(2)>>>(
             g->off, Lst(5), g->p2cnt + 5, B, 1 << 30, 512, g->LG, g->rec, g->rsum, g->cl_col, g->cl_lab, g->acc,
-            g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 3);
+            g->xoff, g->xcol, g->xS, g->xsk, g->xout, g->xin, err, SX, g->wq + 3);
         RS_LAUNCHED(g, AX(2), "p2_mid_wide");
     }
     if (g->n_large) {
         // large rows whose cross list fits a per-warp table go warp-per-row too
         p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 4), NT, smem256, AX(2)>>>(
             g->off, Lst(3), g->p2cnt + 3, B, g->tune.p2_cta_dx, 256, g->LG, g->rec, g->rsum, g->cl_col,
-            g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 4);
+            g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xsk, g->xout, g->xin, err, SX, g->wq + 4);
         RS_LAUNCHED(g, AX(2), "p2_large_warp");
         // (with hubs, stream 3 carries the hub chain: these rows go beside p2_mid instead)
         cudaStream_t sw = g->n_hubs || rmode == 1 ? AX(5) : AX(3);
         p2_mid_kernel<<<grid_for(g->n_large * 32, NT, 2), NT, smem512, sw>>>(
             g->off, Lst(6), g->p2cnt + 6, B, g->tune.p2_cta_dx, 512, g->LG, g->rec, g->rsum, g->cl_col,
-            g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xout, g->xin, err, SX, g->wq + 5);
+            g->cl_lab, g->acc, g->xoff, g->xcol, g->xS, g->xsk, g->xout, g->xin, err, SX, g->wq + 5);
         RS_LAUNCHED(g, sw, "p2_large_warp_wide");
         switch (g->tune.p2_cta_threads) {
         case 256: launch_p2_large<256>(g, B, err, p2_smem, AX(4)); break;
@@ -2378,9 +2368,6 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
         gx_mirror_kernel<<<grid_for(g->nnz, kMirTile, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xS, g->xout,
                                                                        g->xin, g->xtile, g->xR, g->xsk, err);
         RS_LAUNCHED(g, s, "gx_mirror");
-    } else {
-        gx_skip_kernel<<<grid_for(g->nnz / 8 + 1, NT, cps), NT, 0, s>>>(n, g->xoff, g->xcol, g->xsk);
-        RS_LAUNCHED(g, s, "gx_skip");
     }
     const Rev R{g->tune.p3_mirror ? g->xR : nullptr, g->xoff, g->xcol, g->xS, g->xin, err};
     unsigned long long *next_group = g->wq + 7;
