@@ -1330,14 +1330,15 @@ __device__ __forceinline__ int64_t find_in_list(const int32_t *xcol, int64_t lo,
 // lists of at most this many ids are binary-searched directly (they span at most 9 sectors)
 constexpr int32_t kSkipMin = 64;
 
-// position of key in the sorted list xcol[lo, lo + len), or -1.  A list of more than kSkipMin
-// ids is searched in xsk (xsk[t] = xcol[8 t], the first id of every 8-slot sector of the
-// slot space, written by P2 with the slots) first, over the sectors that start inside it, for the one sector
-// that can hold key (the last whose first id is <= key; before them, the sector holding the
-// list's head, when the list does not start a sector); that sector is then read with two
-// 16-byte loads and its slots inside the list compared with key.  The chain of dependent
-// loads of a long list thus runs over the packed index (8 times denser than the list) and
-// ends with one sector.  xcol is padded to whole sectors, so the last sector is readable.
+// position of key in the sorted list xcol[lo, lo + len), or -1.  A list of more than
+// kSkipMin ids is searched first in xsk (xsk[t] = xcol[8 t], the first id of every 8-slot
+// sector of the slot space, written by P2 with the slots), over the sectors that start
+// inside the list, for the one sector that can hold key (the last whose first id is <= key;
+// before them, the sector holding the list's head, when the list does not start a sector);
+// that sector is then read with two 16-byte loads and its slots inside the list compared
+// with key.  The chain of dependent loads of a long list thus runs over the packed index (8
+// times denser than the list) and ends with one sector.  xcol is padded to whole sectors,
+// so the last sector is readable.
 __device__ __forceinline__ int64_t find_in_list_sk(const int32_t *xcol, const int32_t *xsk, int64_t lo, int32_t len,
                                                    int32_t key) {
     if (len <= kSkipMin) return find_in_list(xcol, lo, len, key);
@@ -1371,8 +1372,9 @@ __device__ __forceinline__ int64_t find_in_list_sk(const int32_t *xcol, const in
 // holding the next tile's first slot (a table filled during P2, so no tile
 // searches the offsets).  A tile stages their offsets in shared memory, counts
 // their in-slots inside the tile and spreads only those over the threads; a
-// slot's out-slot twin is found by binary search in w's out-list, which is
-// short (w has the lower rank).  A tile spanning more than kMirNodes nodes
+// slot's out-slot twin is found in w's out-list (w has the lower rank), by
+// find_in_list_sk: a binary search, or for a list of more than kSkipMin ids one
+// through the packed sector index.  A tile spanning more than kMirNodes nodes
 // (long runs of nodes outside G_x) searches the offsets in global memory.
 constexpr int kMirNodes = 1024;
 
@@ -1498,10 +1500,11 @@ __device__ __forceinline__ void triangle_terms(int32_t a, int32_t b, int32_t c, 
 // entry's G_x offset, out-degree and rank) in shared memory, window by window
 // of at most kWinCap entries.  All candidate pairs of a window form one flat
 // index space that the lanes share evenly (two per lane per trip): entry e
-// owns the pairs (e, f > e) of its node.  The closing edge is looked up by
-// binary search in the lower-ranked node's out-list in global memory (short:
-// the out-degree of a low-ranked node).  Found triangles are queued in shared
-// memory and finished a warp at a time, one per lane: the three forward values
+// owns the pairs (e, f > e) of its node.  The closing edge is looked up in the
+// lower-ranked node's out-list in global memory by find_in_list_sk (a binary
+// search, or for a long list one through the packed sector index).  Found
+// triangles are queued in shared memory and finished a warp at a time, one per
+// lane: the three forward values
 // sit at the out-slots, the three reverse ones in xR (the mirror pass) or, with
 // p3_mirror = 0, in the in-lists of the two higher-ranked nodes, and the terms
 // of the three apexes are added.  Nodes with more than kWinCap out-neighbours
