@@ -264,7 +264,7 @@ rs_status rs_launch_count(const rs_graph *g, int64_t *launches);
  *                rows' kernels on one stream and the other classes, in
  *                turn, on a second; 2: every row kernel in turn on the
  *                step's stream; -1 (the default): 1 when the graph has
- *                hub rows, else 0
+ *                hub rows and at least 32,000,000 CSR entries, else 0
  * Powers of two are required where a set is given.
  */
 typedef struct {

@@ -2219,11 +2219,16 @@ int rs::score_graph(rs_graph *g, double *scores, cudaStream_t s) {
     size_t p1_smem = 8 * (size_t)g->large_cap, p2_smem = 32 * (size_t)g->large_cap;
     // streams of the row kernels (rows_streams): every class on its own stream (0); the hub
     // chain on stream 3 and every other class in turn on stream 0 (1); every kernel in turn
-    // on the step's stream (2).  On the 8M-node hub-skewed graph the hub chain is the longest
-    // path of both passes, and the other classes, spread over five more streams, held it back
-    // (step 65.7 ms against 63.9 with two streams); on graphs without hubs the classes' long
-    // per-row chains overlap best on separate streams (1M-node graph: 0.882 against 1.010 ms)
-    const int rmode = g->tune.rows_streams >= 0 ? g->tune.rows_streams : (g->n_hubs ? 1 : 0);
+    // on the step's stream (2).  On large graphs with hub rows each class fills the GPU alone,
+    // and the classes spread over six streams held the hub chain back (8M-node hub-skewed
+    // graph: step 65.7 ms against 63.9 with two streams; a batch of 1,024 graphs: 46.5 against
+    // 42.1 ms); on smaller graphs the classes' long per-row chains overlap best on separate
+    // streams (1M-node graph without hubs: 0.901 against 1.039 ms; a 1.2M-node graph with 489
+    // hubs: 1.095 against 1.189 ms).  The automatic choice (-1) takes two streams for graphs
+    // with hub rows and at least kRowsTwoStreamNnz CSR entries.
+    constexpr int64_t kRowsTwoStreamNnz = 32000000;
+    const int rmode = g->tune.rows_streams >= 0 ? g->tune.rows_streams
+                                                : (g->n_hubs && g->nnz >= kRowsTwoStreamNnz ? 1 : 0);
     auto AX = [&](int i) -> cudaStream_t {
         if (rmode == 2) return s;
         if (rmode == 1) return i == 3 ? g->aux[3] : g->aux[0];
